@@ -1,0 +1,328 @@
+"""Benchmark: shifted solutions/sec to a 1e-8 FP64 residual (mixed + batched
+vs plain FP64) on the Wilson-Dirac-style 8^4 lattice (49,152 unknowns,
+6 kappa shifts, GMRES-DR(40,20)), plus the roofline of the dominant kernel.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one complete multi-shift solve (every shift of every right-hand
+side to a true FP64 relative residual <= 1e-8, checked inside the library)
+with the operator and right-hand sides resident in HBM.  L2 is flushed
+(a 512 MB write) before every timed step.  With N > 1 (torchrun) every rank
+solves its own replica of the workload (the solver does not shard); the
+value is the aggregate over ranks.  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+CONFIG_ID = 2
+METRIC = "shifted solutions/sec to 1e-8 FP64 residual, mixed+batched vs plain FP64; matvec HBM GB/s"
+UNIT = "solutions/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=CONFIG_ID)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(cid):
+    p = W.config(cid)
+    return p, {
+        "workload": f"{p.name} Wilson-Dirac-style, n={p.n}, {len(p.sigma)} kappa shifts, "
+                    f"{p.B.shape[1]} rhs, GMRES-DR({p.m},{p.k}), m_proj={p.m_proj}",
+        "config_id": cid,
+        "lattice": "x".join(map(str, p.op[1])) if p.op[0] == "wilson" else None,
+        "n": p.n, "ns": len(p.sigma), "nrhs": int(p.B.shape[1]), "m": p.m, "k": p.k, "m_proj": p.m_proj,
+        "tol": 1e-8, "prec": "c64 inner + FP64 refinement", "links": p.extra.get("links", "c64"),
+        "l2": "flushed before every timed step (512 MB write)",
+    }
+
+
+# ------------------------------------------------------------- clock sampling
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- reference arm
+
+def oracle_solve(p):
+    """The oracle (complex128, numpy/scipy) solving every shift of every rhs."""
+    from oracle import CSROperator, WilsonOperator, solve_all_rhs
+    if p.op[0] == "wilson":
+        A = WilsonOperator(p.op[1], p.op[3], p.op[2])
+    else:
+        A = CSROperator(*p.op[1:])
+    t = time.perf_counter()
+    out = solve_all_rhs(A.matvec, p.B, p.sigma, p.m, p.k, p.m_proj, p.tol, p.extra_tol, max_mvps=20000)
+    return time.perf_counter() - t, out
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def cpu_baseline(p):
+    dt, out = oracle_solve(p)
+    sols = len(p.sigma) * p.B.shape[1]
+    return {"value": sols / dt, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"one complete oracle solve of the workload ({sols} shifted solutions, "
+                      f"{out['mvps_rhs1']} mvps for rhs 1) in {dt:.2f} s, numpy/BLAS threads = cores"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    p, cfg = workload(args.config)
+    times = []
+    for _ in range(args.warmup):
+        oracle_solve(p)
+    for _ in range(args.steps):
+        dt, _ = oracle_solve(p)
+        times.append(dt)
+    sols = len(p.sigma) * p.B.shape[1]
+    value = sols * len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": "each step one complete oracle solve of the workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_0707_0502_gb300 as g
+
+    p, cfg = workload(args.config)
+    ns, nrhs = len(p.sigma), p.B.shape[1]
+    sols = ns * nrhs
+    stream = torch.cuda.Stream()
+    ctx = g.gdr_create(local, stream)
+    store = g.GDR_LINK_BF16 if p.extra.get("links") == "bf16" else g.GDR_LINK_C64
+    with torch.cuda.stream(stream):
+        op = g.make_operator(ctx, p, store=store)
+        B = torch.as_tensor(np.ascontiguousarray(p.B.T), device="cuda")
+        X = torch.zeros((nrhs, ns, p.n), dtype=torch.complex128, device="cuda")
+        flush = torch.empty(512 * 2**20, dtype=torch.uint8, device="cuda")
+    stream.synchronize()
+    mixed = g.gdr_params_default(m=p.m, k=p.k, m_proj=p.m_proj, tol=p.tol, extra_tol=p.extra_tol,
+                                 prec=g.GDR_PREC_MIXED)
+    plain = g.gdr_params_default(m=p.m, k=p.k, m_proj=p.m_proj, tol=p.tol, extra_tol=p.extra_tol,
+                                 prec=g.GDR_PREC_FP64, flags=g.GDR_FLAG_SEQUENTIAL | g.GDR_FLAG_NO_GRAPH)
+
+    def timed(params, steps, warm, Bx=B, Xx=X):
+        reps = []
+        for _ in range(warm):
+            st, rep, _ = g.gdr_solve_multishift(ctx, op, p.sigma, Bx, Xx, params)
+            assert st == g.GDR_OK, (st, rep)
+        ms = []
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, rep, _ = g.gdr_solve_multishift(ctx, op, p.sigma, Bx, Xx, params)
+            e1.record(stream)
+            e1.synchronize()
+            assert st == g.GDR_OK and rep["max_relres"] <= p.tol, (st, rep)
+            ms.append(e0.elapsed_time(e1))
+            reps.append(rep)
+        return ms, reps
+
+    # ---- timed region: mixed + batched path
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    ms, reps = timed(mixed, args.steps, args.warmup)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_s = sum(ms) / 1e3
+    t_max = total_s
+    if world > 1:
+        t = torch.tensor([total_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        dist.barrier()
+    value = world * sols * args.steps / t_max
+    rep = reps[-1]
+    launches = rep["kernel_launches"]
+
+    # ---- plain FP64 GPU path (same algorithm, complex128, rhs sequential, no graphs)
+    ms64, reps64 = timed(plain, max(1, min(args.steps, 3)), 1)
+    fp64_value = sols * len(ms64) / (sum(ms64) / 1e3)
+
+    # ---- end to end through the C ABI with host buffers (copies inside)
+    Bh = torch.as_tensor(np.ascontiguousarray(p.B.T)).pin_memory()
+    Xh = torch.zeros((nrhs, ns, p.n), dtype=torch.complex128).pin_memory()
+    host_params = g.gdr_params_default(m=p.m, k=p.k, m_proj=p.m_proj, tol=p.tol, extra_tol=p.extra_tol,
+                                       prec=g.GDR_PREC_MIXED, flags=g.GDR_FLAG_HOST_PTRS)
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        st, r2, _ = g.gdr_solve_multishift(ctx, op, p.sigma, Bh.numpy(), Xh.numpy(), host_params)
+        t1 = time.perf_counter()
+        assert st == g.GDR_OK
+        if i >= args.warmup:
+            e2e_ms.append((t1 - t0) * 1e3)
+    e2e_value = world * sols * len(e2e_ms) / (sum(e2e_ms) / 1e3)
+
+    # ---- dominant kernel roofline (per-kernel CUDA events on the library stream)
+    roof = kernel_roofline(g, ctx, op, p, mixed, stream)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic", "config": cfg,
+        "clocks": clk, "gpu_launches": launches * args.steps,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(p.B.nbytes),
+                "d2h_bytes_per_step": int(nrhs * ns * p.n * 16)},
+        "fp64_plain": {"value": fp64_value, "unit": UNIT, "ms_per_step": sum(ms64) / len(ms64),
+                       "speedup_mixed_over_fp64": value / world / fp64_value,
+                       "mvps_rhs1": reps64[-1]["mvps_rhs1"]},
+        "solve": {k: rep[k] for k in ("mvps_rhs1", "cycles_rhs1", "mvps_extra", "mvps_proj", "mvps_refine",
+                                      "refine_passes", "pairs_cleaned", "max_relres")},
+        "roofline": roof,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    g.gdr_op_destroy(op)
+    g.gdr_destroy(ctx)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def kernel_roofline(g, ctx, op, p, params, stream):
+    """Average duration of the Wilson matvec kernel (complex64 vectors,
+    complex64 links, one right-hand side) at the workload's lattice, CUDA
+    events on the library stream, against the measured copy bandwidth."""
+    import torch
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    n = p.n
+    sites = n // 12
+    with torch.cuda.stream(stream):
+        x = torch.randn(n, dtype=torch.complex64, device="cuda")
+        y = torch.empty_like(x)
+    reps = 200
+    sig = np.zeros(1, dtype=complex)
+    for _ in range(10):
+        g.gdr_op_apply(ctx, op, g.GDR_PREC_MIXED, sig, x, y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        g.gdr_op_apply(ctx, op, g.GDR_PREC_MIXED, sig, x, y)
+    e1.record(stream)
+    e1.synchronize()
+    dt = e0.elapsed_time(e1) / reps / 1e3
+    bytes_per_site = 4 * 18 * 4 + 2 * 24 * 4     # links (4 per site, 18 fp32) + x read + y write
+    achieved = bytes_per_site * sites / dt / 1e9
+    return {"kernel": "wilson_kernel<float,c64>", "bound": "hbm", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+            "bytes_per_launch": bytes_per_site * sites, "us_per_launch": dt * 1e6,
+            "note": "peak = MEASURED_PEAKS.json hbm_gbs (of measured)"}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * gdr.h -- C ABI of a GB300 (sm_103a) implementation of deflated multi-shift
+ * GMRES: GMRES-DR(m,k)-Sh for the first right-hand side and GMRES(m_p)-Proj(k)-Sh
+ * with the extra right-hand side v_{k+1} and the correction phase for the
+ * others, after Darnell, Morgan and Wilcox, "Deflated GMRES for Systems with
+ * Multiple Shifts and Multiple Right-Hand Sides".
+ *
+ * Problem (Sec. 1, eq. (1)):  (A - sigma_i I) x_i^j = b^j,  i = 1..ns, j = 1..nrhs,
+ * sigma_1 (sigma[0] here) is the base shift, no preconditioning.
+ *
+ * Conventions for every entry point
+ *  - Complex numbers are interleaved (re, im) doubles: a "c128 array of length L"
+ *    is 2*L doubles.  Matrices are column-major.
+ *  - Pointers are DEVICE pointers on the context's device unless the entry point
+ *    says "host".  The caller owns every buffer it passes; the library owns its
+ *    workspace (allocated on first use, grown on demand, freed by gdr_destroy).
+ *  - Work is queued on the context's stream.  Solves synchronise that stream
+ *    before returning (they read convergence words between cycles); the
+ *    step-level entry points do not.
+ *  - Every entry point returns a gdr_status; on error gdr_last_error() holds a
+ *    one-line message.  No C++ exception crosses the ABI.  The library never
+ *    falls back to host computation: without a usable CUDA device gdr_create
+ *    fails with GDR_ECUDA.
+ *  - Vectors of a Wilson operator use the site-major layout
+ *    index = site*12 + spin*3 + color, site = ((t*Lz + z)*Ly + y)*Lx + x.
+ */
+#ifndef GDR_H
+#define GDR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GDR_OK = 0,
+  GDR_EINVAL = 1,      /* bad argument (sizes, null pointers, m > GDR_MAX_M, k >= m, ...) */
+  GDR_ENOMEM = 2,      /* device allocation failed */
+  GDR_ECUDA = 3,       /* a CUDA call failed; the context is unusable */
+  GDR_ENOCONV = 4,     /* max_mvps / max_cycles reached before tol; X holds the last iterate */
+  GDR_EBREAKDOWN = 5,  /* a singular reduced system (shift at an eigenvalue of the recurrence) */
+  GDR_ENAN = 6,        /* NaN/Inf appeared in the recurrence */
+  GDR_ETIMEOUT = 7,    /* a bounded device wait ran out */
+  GDR_ENOTIMPL = 8
+} gdr_status;
+
+/* Arithmetic of the bulk vectors.  FP64: complex128 everywhere.  MIXED: matvec,
+ * Gram-Schmidt and basis updates in complex64 (FP32 accumulation), small dense
+ * steps, solutions and true residuals in FP64, with iterative refinement. */
+typedef enum { GDR_PREC_FP64 = 0, GDR_PREC_MIXED = 1 } gdr_prec;
+
+/* Storage of Wilson gauge links used by the complex64 matvec (the FP64
+ * residuals always use the complex128 links given at creation). */
+typedef enum { GDR_LINK_C128 = 0, GDR_LINK_C64 = 1, GDR_LINK_BF16 = 2 } gdr_link_fmt;
+
+#define GDR_MAX_M 96            /* largest basis size m (and m_proj) */
+
+/* gdr_params.flags */
+#define GDR_FLAG_HOST_PTRS    1u  /* B and X of a solve are HOST pointers; copies are made inside */
+#define GDR_FLAG_NO_GRAPH     2u  /* launch every kernel directly instead of replaying CUDA graphs */
+#define GDR_FLAG_SEQUENTIAL   4u  /* right-hand sides 2.. one at a time (no column batching) */
+#define GDR_FLAG_NO_PROJ      8u  /* later right-hand sides by plain GMRES(m_p)-Sh (no deflation) */
+#define GDR_FLAG_NO_REFINE   16u  /* no refinement / cleanup after the stages (residuals still reported) */
+
+typedef struct gdr_ctx gdr_ctx;
+typedef struct gdr_op gdr_op;
+typedef struct gdr_defl gdr_defl;
+
+typedef struct {
+  int m;              /* GMRES-DR basis size (first right-hand side) */
+  int k;              /* harmonic Ritz vectors kept across restarts, 0 < k < m */
+  int m_proj;         /* GMRES cycle length in the Proj phase (0: m - k) */
+  double tol;         /* relative residual target ||b - (A - sigma_i I) x|| / ||b|| */
+  double extra_tol;   /* relative tolerance for the extra right-hand side v_{k+1} */
+  double inner_tol;   /* MIXED: relative reduction asked of each complex64 pass */
+  long max_mvps;      /* cap on Arnoldi matvecs per solve stage (per column) */
+  int max_cycles;     /* 0: unlimited; else stop RHS 1 after this many cycles */
+  int refine_max;     /* MIXED: refinement passes before the FP64 cleanup */
+  gdr_prec prec;
+  unsigned flags;
+} gdr_params;
+
+typedef struct {
+  long mvps_rhs1;       /* Arnoldi matvecs, first right-hand side (m + (cycles-1)(m-k)) */
+  long cycles_rhs1;
+  long mvps_extra;      /* matvecs spent on the extra right-hand side v_{k+1} */
+  long mvps_proj;       /* matvecs of the Proj phase, summed over right-hand sides 2.. */
+  long mvps_refine;     /* matvecs of refinement / cleanup solves, summed over columns */
+  long resid_cols;      /* FP64 true-residual matvec columns */
+  int refine_passes;
+  int pairs_cleaned;    /* (shift, rhs) pairs finished by the FP64 cleanup */
+  double max_relres;    /* max over (shift, rhs) of the final FP64 true relative residual */
+  double t_total_ms;    /* wall time of the solve */
+  long kernel_launches; /* kernels of this library launched by the solve (graph nodes counted) */
+} gdr_report;
+
+/* ---------------------------------------------------------------- context */
+
+void gdr_params_default(gdr_params *p);
+
+/* Create a context on `device`; `cuda_stream` is a cudaStream_t (NULL: the
+ * legacy default stream).  Fails with GDR_ECUDA when no device is usable. */
+gdr_status gdr_create(gdr_ctx **ctx, int device, void *cuda_stream);
+void gdr_destroy(gdr_ctx *ctx);
+const char *gdr_last_error(const gdr_ctx *ctx);
+const char *gdr_status_string(gdr_status s);
+
+/* --------------------------------------------------------------- operators
+ * A is n x n.  The operator keeps its own device copies (and complex64 /
+ * bfloat16 copies for the MIXED path), so the caller's arrays may be freed
+ * after creation returns (the stream is synchronised). */
+
+/* CSR (Examples 1-6, Sec. 3-4): int32 rowptr[n+1], int32 col[nnz], c128 vals[nnz]. */
+gdr_status gdr_op_csr(gdr_ctx *ctx, long n, long nnz, const int *rowptr, const int *col,
+                      const double *vals, gdr_op **out);
+
+/* Wilson-Dirac-style matrix (Example 7, Sec. 4): A = diag_a I - H with
+ * (H psi)(x) = sum_mu [(1 - gamma_mu) U_mu(x) psi(x+mu) + (1 + gamma_mu) U_mu(x-mu)^H psi(x-mu)],
+ * periodic, chiral gamma basis (gamma_k = [[0,-i s_k],[i s_k,0]], gamma_t = [[0,I],[I,0]]).
+ * dims = {Lx, Ly, Lz, Lt} (each >= 2); links: c128 [4][V][3][3], U_mu(x)_{ab}
+ * row-major, mu = x,y,z,t.  `store` picks the link storage of the complex64 matvec. */
+gdr_status gdr_op_wilson(gdr_ctx *ctx, const int dims[4], double diag_a, const double *links,
+                         gdr_link_fmt store, gdr_op **out);
+void gdr_op_destroy(gdr_op *op);
+long gdr_op_n(const gdr_op *op);
+
+/* Matvec (step a1 / a2): Y[:,c] = (A - sigma_c I) X[:,c], c < ncol, in the
+ * precision `prec` (FP64: X, Y are c128; MIXED: X, Y are complex64, interleaved
+ * floats).  sigma: host c128[ncol].  Leading dimension n.  Asynchronous. */
+gdr_status gdr_op_apply(gdr_ctx *ctx, const gdr_op *A, gdr_prec prec, int ncol, const double *sigma,
+                        const void *X, void *Y);
+
+/* ------------------------------------------------------------------ solves */
+
+/* All shifts of all right-hand sides (Sec. 3 and Sec. 4, Example 5 order):
+ * RHS 1 by GMRES-DR(m,k)-Sh, then (nrhs > 1) the extra right-hand side v_{k+1}
+ * and RHS 2..nrhs by GMRES(m_p)-Proj(k)-Sh (column-batched unless
+ * GDR_FLAG_SEQUENTIAL), then the correction x_i^j += (v_{k+1}^H r_i^j) s_i.
+ * MIXED adds FP64 true residuals and refinement / FP64 cleanup per pair.
+ * sigma: host c128[ns], sigma[0] the base shift.  B: c128 n x nrhs.
+ * X: c128 n x ns x nrhs (X[:, i, j] solves shift i, rhs j), written.
+ * defl_out (optional): receives the kept pair A V_k = V_{k+1} Hbar_k (eq. recur1).
+ * report (optional, host).  Returns GDR_ENOCONV when a pair missed tol. */
+gdr_status gdr_solve_multishift(gdr_ctx *ctx, const gdr_op *A, int ns, const double *sigma, int nrhs,
+                                const double *B, double *X, const gdr_params *params,
+                                gdr_defl **defl_out, gdr_report *report);
+
+/* GMRES(m_p)-Proj(k)-Sh with a kept deflation space (Sec. 4), without the
+ * correction phase: X[:, i, j] with residuals beta_i r + g_i v_{k+1}.
+ * Same argument conventions as gdr_solve_multishift. */
+gdr_status gdr_solve_proj(gdr_ctx *ctx, const gdr_op *A, const gdr_defl *defl, int ns, const double *sigma,
+                          int nrhs, const double *B, double *X, const gdr_params *params, gdr_report *report);
+
+/* Copy the kept pair out: V (device c128 n x (k+1)) and Hbar (HOST c128
+ * (k+1) x k, column-major).  Either may be NULL.  *k_out receives k. */
+gdr_status gdr_defl_export(gdr_ctx *ctx, const gdr_defl *defl, double *V, double *Hbar, int *k_out);
+void gdr_defl_destroy(gdr_defl *defl);
+
+/* --------------------------------------------------------- step-level calls
+ * Single steps of the cycle, exposed for parity checks and benchmarks.  All
+ * asynchronous on the context stream; FP64 unless `prec` says otherwise. */
+
+/* Arnoldi step with classical Gram-Schmidt twice (eq. recurAr): with V holding
+ * v_0..v_j (n x (j+2) buffer, leading dimension n, vectors in `prec`), compute
+ * w = A v_j, h = V_{j+1}^H w twice, v_{j+1} = w / ||w|| into V[:, j+1] and the
+ * FP64 column h (c128[j+2]: h_0..h_j, h_{j+1,j}) into `hcol`. */
+gdr_status gdr_arnoldi_step(gdr_ctx *ctx, const gdr_op *A, gdr_prec prec, void *V, int j, double *hcol);
+
+/* GMRES-Sh reduced solve (Sec. 2.1, eqs. gsh1-gsh3; GMRES-DR-Sh steps 3-5), FP64:
+ * Hbar: c128 (m+1) x m, c: c128[m+1], sigma: host c128[ns], beta: c128[ns] in.
+ * Out: D c128 m x ns, s c128[m+1], beta_new c128[ns], norms double[ns]
+ * (norms[0] = ||s||, norms[i] = |beta_new_i| ||s||). */
+gdr_status gdr_dense_gmres_sh(gdr_ctx *ctx, int m, int ns, const double *Hbar, const double *c,
+                              const double *sigma, const double *beta, double *D, double *s,
+                              double *beta_new, double *norms);
+
+/* GMRES-DR restart (Sec. 2.2): harmonic Ritz pairs of Hhat = Hbar - sigma1 Ibar,
+ * k of smallest |theta| (ties: larger Im, then larger Re), P_{k+1} = [orth([G;0]), p],
+ * p from s; Hk = P^H Hbar P_k ((k+1) x k), ck = P^H s (k+1).
+ * In: Hbar c128 (m+1) x m, s c128[m+1], sigma1 host c128.  Out: theta c128[m]
+ * (all harmonic Ritz values, unordered), P c128 (m+1) x (k+1), Hk, ck. */
+gdr_status gdr_dense_restart(gdr_ctx *ctx, int m, int k, const double *sigma1, const double *Hbar,
+                             const double *s, double *theta, double *P, double *Hk, double *ck);
+
+/* Basis update (restart, eq. recur1, fused with the multi-shift update):
+ * V (n x nv, `prec`) times coefficients C (c128 nv x (nout + nx)):
+ * V[:, 0:nout] <- V C[:, 0:nout]  (in place, nout <= nv) and
+ * X[:, i] += V C[:, nout + i] for i < nx (X c128 n x nx). */
+gdr_status gdr_basis_update(gdr_ctx *ctx, gdr_prec prec, long n, int nv, void *V, const double *C, int nout,
+                            int nx, double *X);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GDR_H */

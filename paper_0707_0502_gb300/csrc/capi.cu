@@ -1,0 +1,473 @@
+// extern "C" entry points of include/gdr.h: argument checks, buffer staging
+// and error translation around the solver drivers.  No C++ exception crosses
+// this boundary.
+#include <chrono>
+#include <cstring>
+#include <type_traits>
+
+#include "kernels.cuh"
+#include "solver.cuh"
+
+namespace {
+
+thread_local std::string g_err;  // message of the last failure without a context
+
+template <typename F>
+gdr_status guarded(gdr_ctx* ctx, F&& f) {
+  try {
+    f();
+    return GDR_OK;
+  } catch (const gdr_error& e) {
+    if (ctx) ctx->err = e.what();
+    g_err = e.what();
+    return e.st;
+  } catch (const std::exception& e) {
+    if (ctx) ctx->err = e.what();
+    g_err = e.what();
+    return GDR_ECUDA;
+  }
+}
+
+void check_params(const gdr_params& p) {
+  GDR_REQUIRE(p.m >= 2 && p.m <= GDR_MAX_M, "m must be in [2, GDR_MAX_M]");
+  GDR_REQUIRE(p.k >= 0 && p.k < p.m, "k must satisfy 0 <= k < m");
+  GDR_REQUIRE(p.m_proj >= 0 && p.m_proj <= GDR_MAX_M, "m_proj must be in [0, GDR_MAX_M]");
+  GDR_REQUIRE(p.tol > 0 && p.extra_tol > 0 && p.inner_tol > 0, "tolerances must be positive");
+  GDR_REQUIRE(p.max_mvps > 0, "max_mvps must be positive");
+  GDR_REQUIRE(p.prec == GDR_PREC_FP64 || p.prec == GDR_PREC_MIXED, "unknown precision");
+}
+
+std::vector<c128> host_c128(const double* p, int count) {
+  std::vector<c128> v(count);
+  for (int i = 0; i < count; ++i) v[i] = {p[2 * i], p[2 * i + 1]};
+  return v;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gdr_params_default(gdr_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->m = 40;
+  p->k = 20;
+  p->m_proj = 0;
+  p->tol = 1e-8;
+  p->extra_tol = 1e-5;
+  p->inner_tol = 1e-5;
+  p->max_mvps = 100000;
+  p->max_cycles = 0;
+  p->refine_max = 3;
+  p->prec = GDR_PREC_FP64;
+  p->flags = 0;
+}
+
+const char* gdr_status_string(gdr_status s) {
+  switch (s) {
+    case GDR_OK: return "GDR_OK";
+    case GDR_EINVAL: return "GDR_EINVAL";
+    case GDR_ENOMEM: return "GDR_ENOMEM";
+    case GDR_ECUDA: return "GDR_ECUDA";
+    case GDR_ENOCONV: return "GDR_ENOCONV";
+    case GDR_EBREAKDOWN: return "GDR_EBREAKDOWN";
+    case GDR_ENAN: return "GDR_ENAN";
+    case GDR_ETIMEOUT: return "GDR_ETIMEOUT";
+    case GDR_ENOTIMPL: return "GDR_ENOTIMPL";
+  }
+  return "GDR_?";
+}
+
+gdr_status gdr_create(gdr_ctx** out, int device, void* cuda_stream) {
+  if (!out) return GDR_EINVAL;
+  *out = nullptr;
+  gdr_ctx* ctx = new gdr_ctx();
+  gdr_status st = guarded(nullptr, [&] {
+    int count = 0;
+    GDR_CUDA(cudaGetDeviceCount(&count));
+    GDR_REQUIRE(device >= 0 && device < count, "no such CUDA device");
+    GDR_CUDA(cudaSetDevice(device));
+    cudaDeviceProp prop;
+    GDR_CUDA(cudaGetDeviceProperties(&prop, device));
+    ctx->device = device;
+    ctx->num_sms = prop.multiProcessorCount;
+    ctx->max_smem_optin = prop.sharedMemPerBlockOptin;
+    if (cuda_stream) {
+      ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+      // a blocking stream orders with the legacy default stream and can be captured
+      GDR_CUDA(cudaStreamCreate(&ctx->stream));
+      ctx->own_stream = true;
+    }
+    dense_init(ctx);
+    krylov_init(ctx);
+  });
+  if (st != GDR_OK) {
+    delete ctx;
+    return st;
+  }
+  *out = ctx;
+  return GDR_OK;
+}
+
+void gdr_destroy(gdr_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto& kv : ctx->ws)
+    if (kv.second.p) cudaFree(kv.second.p);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char* gdr_last_error(const gdr_ctx* ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+gdr_status gdr_op_csr(gdr_ctx* ctx, long n, long nnz, const int* rowptr, const int* col, const double* vals,
+                      gdr_op** out) {
+  if (!ctx || !out) return GDR_EINVAL;
+  *out = nullptr;
+  gdr_op* op = new gdr_op();
+  gdr_status st = guarded(ctx, [&] {
+    GDR_REQUIRE(n > 0 && nnz >= 0, "bad CSR sizes");
+    GDR_REQUIRE(rowptr && (nnz == 0 || (col && vals)), "null CSR array");
+    GDR_CUDA(cudaSetDevice(ctx->device));
+    op->ctx = ctx;
+    op->kind = OP_CSR;
+    op->n = n;
+    op->nnz = nnz;
+    op_build_csr(ctx, op, rowptr, col, vals);
+  });
+  if (st != GDR_OK) {
+    gdr_op_destroy(op);
+    return st;
+  }
+  *out = op;
+  return GDR_OK;
+}
+
+gdr_status gdr_op_wilson(gdr_ctx* ctx, const int dims[4], double diag_a, const double* links, gdr_link_fmt store,
+                         gdr_op** out) {
+  if (!ctx || !out || !dims) return GDR_EINVAL;
+  *out = nullptr;
+  gdr_op* op = new gdr_op();
+  gdr_status st = guarded(ctx, [&] {
+    for (int i = 0; i < 4; ++i) GDR_REQUIRE(dims[i] >= 2, "each lattice extent must be >= 2");
+    GDR_REQUIRE(links != nullptr, "null links");
+    GDR_REQUIRE(store == GDR_LINK_C128 || store == GDR_LINK_C64 || store == GDR_LINK_BF16, "bad link format");
+    GDR_CUDA(cudaSetDevice(ctx->device));
+    op->ctx = ctx;
+    op->kind = OP_WILSON;
+    for (int i = 0; i < 4; ++i) op->dims[i] = dims[i];
+    op->V = (long)dims[0] * dims[1] * dims[2] * dims[3];
+    op->n = 12 * op->V;
+    op->diag_a = diag_a;
+    op->store = store;
+    op_build_wilson(ctx, op, links);
+  });
+  if (st != GDR_OK) {
+    gdr_op_destroy(op);
+    return st;
+  }
+  *out = op;
+  return GDR_OK;
+}
+
+void gdr_op_destroy(gdr_op* op) {
+  if (!op) return;
+  cudaFree(op->rowptr);
+  cudaFree(op->col);
+  cudaFree(op->vals128);
+  cudaFree(op->vals64);
+  cudaFree(op->links128);
+  cudaFree(op->links64);
+  cudaFree(op->links16);
+  delete op;
+}
+
+long gdr_op_n(const gdr_op* op) { return op ? op->n : 0; }
+
+gdr_status gdr_op_apply(gdr_ctx* ctx, const gdr_op* A, gdr_prec prec, int ncol, const double* sigma, const void* X,
+                        void* Y) {
+  if (!ctx || !A) return GDR_EINVAL;
+  return guarded(ctx, [&] {
+    GDR_REQUIRE(ncol >= 0 && (ncol == 0 || (sigma && X && Y)), "bad gdr_op_apply arguments");
+    if (ncol == 0) return;
+    c128* sd = ctx->get<c128>("apply.sigma", (size_t)ncol);
+    GDR_CUDA(cudaMemcpyAsync(sd, sigma, sizeof(c128) * ncol, cudaMemcpyHostToDevice, ctx->stream));
+    if (prec == GDR_PREC_FP64)
+      op_apply<double>(ctx, A, ncol, sd, (const c128*)X, A->n, (c128*)Y, A->n, nullptr, 0);
+    else
+      op_apply<float>(ctx, A, ncol, sd, (const c64*)X, A->n, (c64*)Y, A->n, nullptr, 0);
+  });
+}
+
+gdr_status gdr_solve_multishift(gdr_ctx* ctx, const gdr_op* A, int ns, const double* sigma, int nrhs, const double* B,
+                                double* X, const gdr_params* params, gdr_defl** defl_out, gdr_report* report) {
+  if (!ctx || !A) return GDR_EINVAL;
+  if (defl_out) *defl_out = nullptr;
+  gdr_report rep{};
+  gdr_status result = GDR_OK;
+  gdr_status st = guarded(ctx, [&] {
+    GDR_REQUIRE(params && sigma && B && X, "null argument");
+    GDR_REQUIRE(ns >= 1 && nrhs >= 1, "ns and nrhs must be >= 1");
+    const gdr_params& p = *params;
+    check_params(p);
+    GDR_CUDA(cudaSetDevice(ctx->device));
+    const auto t0 = std::chrono::steady_clock::now();
+    const long launches0 = ctx->launches;
+    const long n = A->n, ld = pad_ld(n);
+    std::vector<c128> sig = host_c128(sigma, ns);
+    c128* Bi = ctx->get<c128>("api.B", (size_t)ld * nrhs);
+    c128* Xi = ctx->get<c128>("api.X", (size_t)ld * ns * nrhs);
+    const cudaMemcpyKind kin = (p.flags & GDR_FLAG_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const cudaMemcpyKind kout = (p.flags & GDR_FLAG_HOST_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    GDR_CUDA(cudaMemcpy2DAsync(Bi, ld * sizeof(c128), B, n * sizeof(c128), n * sizeof(c128), nrhs, kin,
+                               ctx->stream));
+    if (p.prec == GDR_PREC_MIXED)
+      result = solve_pipeline<float>(ctx, A, sig, nrhs, Bi, ld, Xi, ld, p, defl_out, rep);
+    else
+      result = solve_pipeline<double>(ctx, A, sig, nrhs, Bi, ld, Xi, ld, p, defl_out, rep);
+    GDR_CUDA(cudaMemcpy2DAsync(X, n * sizeof(c128), Xi, ld * sizeof(c128), n * sizeof(c128), (size_t)ns * nrhs, kout,
+                               ctx->stream));
+    GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+    rep.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    rep.kernel_launches = ctx->launches - launches0;
+  });
+  if (report) *report = rep;
+  return st != GDR_OK ? st : result;
+}
+
+gdr_status gdr_solve_proj(gdr_ctx* ctx, const gdr_op* A, const gdr_defl* defl, int ns, const double* sigma, int nrhs,
+                          const double* B, double* X, const gdr_params* params, gdr_report* report) {
+  if (!ctx || !A || !defl) return GDR_EINVAL;
+  gdr_report rep{};
+  gdr_status result = GDR_OK;
+  gdr_status st = guarded(ctx, [&] {
+    GDR_REQUIRE(params && sigma && B && X, "null argument");
+    GDR_REQUIRE(ns >= 1 && nrhs >= 1, "ns and nrhs must be >= 1");
+    GDR_REQUIRE(defl->n == A->n, "deflation space size differs from the operator");
+    const gdr_params& p = *params;
+    check_params(p);
+    GDR_CUDA(cudaSetDevice(ctx->device));
+    const auto t0 = std::chrono::steady_clock::now();
+    const long launches0 = ctx->launches;
+    const long n = A->n, ld = pad_ld(n);
+    const int mp = p.m_proj > 0 ? p.m_proj : p.m - p.k;
+    std::vector<c128> sig = host_c128(sigma, ns);
+    c128* Bi = ctx->get<c128>("api.B", (size_t)ld * nrhs);
+    c128* Xi = ctx->get<c128>("api.X", (size_t)ld * ns * nrhs);
+    const cudaMemcpyKind kin = (p.flags & GDR_FLAG_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const cudaMemcpyKind kout = (p.flags & GDR_FLAG_HOST_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    GDR_CUDA(cudaMemcpy2DAsync(Bi, ld * sizeof(c128), B, n * sizeof(c128), n * sizeof(c128), nrhs, kin,
+                               ctx->stream));
+    GDR_CUDA(cudaMemsetAsync(Xi, 0, sizeof(c128) * ld * ns * nrhs, ctx->stream));
+    auto run = [&](auto tag) {
+      using R = decltype(tag);
+      cx<R>* rin = ctx->get<cx<R>>("api.rin", (size_t)ld * nrhs);
+      cx<R>* vd = ctx->get<cx<R>>("api.vd", (size_t)ld * (defl->k + 1));
+      if (std::is_same<R, double>::value) {
+        copy128(ctx, n, nrhs, Bi, ld, reinterpret_cast<c128*>(rin), ld);
+        copy128(ctx, n, defl->k + 1, defl->V128, defl->ldv, reinterpret_cast<c128*>(vd), ld);
+      } else {
+        cvt_128_to_64(ctx, n, nrhs, Bi, ld, reinterpret_cast<c64*>(rin), ld);
+        cvt_128_to_64(ctx, n, defl->k + 1, defl->V128, defl->ldv, reinterpret_cast<c64*>(vd), ld);
+      }
+      ProjJob<R> job;
+      job.ncol = nrhs;
+      job.ns = ns;
+      job.m_p = mp;
+      job.k = defl->k;
+      job.project = !(p.flags & GDR_FLAG_NO_PROJ);
+      job.Vd = vd;
+      job.ldvd = ld;
+      job.Hk = defl->Hk;
+      job.rhs = rin;
+      job.ldrhs = ld;
+      job.sigma.resize((size_t)nrhs * ns);
+      for (int c = 0; c < nrhs; ++c)
+        for (int i = 0; i < ns; ++i) job.sigma[(size_t)c * ns + i] = sig[i];
+      job.tol.assign(nrhs, p.tol);
+      job.X = Xi;
+      job.ldx = ld;
+      job.xcs = (long)ns * ld;
+      job.max_mvps = p.max_mvps;
+      ProjResult pr = proj_batch<R>(ctx, A, job, !(p.flags & GDR_FLAG_NO_GRAPH));
+      for (long v : pr.mvps) rep.mvps_proj += v;
+      result = pr.status;
+    };
+    if (p.prec == GDR_PREC_MIXED)
+      run(float{});
+    else
+      run(double{});
+    GDR_CUDA(cudaMemcpy2DAsync(X, n * sizeof(c128), Xi, ld * sizeof(c128), n * sizeof(c128), (size_t)ns * nrhs, kout,
+                               ctx->stream));
+    GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+    rep.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    rep.kernel_launches = ctx->launches - launches0;
+  });
+  if (report) *report = rep;
+  return st != GDR_OK ? st : result;
+}
+
+gdr_status gdr_defl_export(gdr_ctx* ctx, const gdr_defl* defl, double* V, double* Hbar, int* k_out) {
+  if (!ctx || !defl) return GDR_EINVAL;
+  return guarded(ctx, [&] {
+    if (k_out) *k_out = defl->k;
+    if (V)
+      GDR_CUDA(cudaMemcpy2DAsync(V, defl->n * sizeof(c128), defl->V128, defl->ldv * sizeof(c128),
+                                 defl->n * sizeof(c128), defl->k + 1, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (Hbar) std::memcpy(Hbar, defl->Hk_host.data(), sizeof(c128) * defl->Hk_host.size());
+    GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+void gdr_defl_destroy(gdr_defl* defl) {
+  if (!defl) return;
+  cudaFree(defl->V);
+  cudaFree(defl->V128);
+  cudaFree(defl->Hk);
+  delete defl;
+}
+
+// ------------------------------------------------------------ step level
+
+gdr_status gdr_arnoldi_step(gdr_ctx* ctx, const gdr_op* A, gdr_prec prec, void* V, int j, double* hcol) {
+  if (!ctx || !A || !V || !hcol) return GDR_EINVAL;
+  return guarded(ctx, [&] {
+    GDR_REQUIRE(j >= 0 && j + 1 <= GDR_MAX_M, "j out of range");
+    const long n = A->n;
+    GDR_REQUIRE(prec == GDR_PREC_FP64 || n % 2 == 0, "complex64 step-level calls need an even n");
+    auto run = [&](auto tag) {
+      using R = decltype(tag);
+      Batch<R> b;
+      b.ncol = 1;
+      b.n = n;
+      b.m = j + 1;
+      b.ns = 1;
+      b.V = static_cast<cx<R>*>(V);
+      b.ldv = n;
+      b.vcs = 0;
+      b.W = ctx->get<cx<R>>("step.W", (size_t)pad_ld(n));
+      b.wcs = 0;
+      b.H = ctx->get<c128>("step.H", (size_t)(j + 2) * (j + 1));
+      b.cvec = nullptr;
+      b.h1 = ctx->get<c128>("step.h1", (size_t)(j + 3));
+      b.h2 = ctx->get<c128>("step.h2", (size_t)(j + 3));
+      const long units = (n * (long)sizeof(cx<R>) + 15) / 16;
+      b.nblk = (int)std::max<long>(1, std::min<long>((units + 255) / 256, 2L * ctx->num_sms));
+      b.pstride = (long)b.nblk * (j + 3);
+      b.part = ctx->get<c128>("step.part", (size_t)b.pstride + 64);
+      b.cnt = ctx->get<unsigned>("step.cnt", 4);
+      b.st = ctx->get<ColState>("step.st", 1);
+      b.sigma = nullptr;
+      ColState s = {};
+      s.run = 1;
+      s.active = 1;
+      s.m_eff = j + 1;
+      GDR_CUDA(cudaMemsetAsync(b.cnt, 0, 4 * sizeof(unsigned), ctx->stream));
+      GDR_CUDA(cudaMemcpyAsync(b.st, &s, sizeof(s), cudaMemcpyHostToDevice, ctx->stream));
+      GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+      arnoldi_step<R>(ctx, A, b, j);
+      GDR_CUDA(cudaMemcpyAsync(hcol, b.H + (long)j * (j + 2), sizeof(c128) * (j + 2), cudaMemcpyDeviceToDevice,
+                               ctx->stream));
+    };
+    if (prec == GDR_PREC_FP64)
+      run(double{});
+    else
+      run(float{});
+  });
+}
+
+gdr_status gdr_dense_gmres_sh(gdr_ctx* ctx, int m, int ns, const double* Hbar, const double* c, const double* sigma,
+                              const double* beta, double* D, double* s, double* beta_new, double* norms) {
+  if (!ctx) return GDR_EINVAL;
+  return guarded(ctx, [&] {
+    GDR_REQUIRE(m >= 1 && m <= GDR_MAX_M && ns >= 1, "bad sizes");
+    GDR_REQUIRE(Hbar && c && sigma && beta && D && s && beta_new && norms, "null argument");
+    DenseCycle d{};
+    d.ncol = 1; d.m = m; d.k = 0; d.ns = ns;
+    c128* H = ctx->get<c128>("dstep.H", (size_t)(m + 1) * m);
+    c128* cv = ctx->get<c128>("dstep.c", (size_t)(m + 1));
+    c128* sg = ctx->get<c128>("dstep.sigma", (size_t)ns);
+    GDR_CUDA(cudaMemcpyAsync(H, Hbar, sizeof(c128) * (m + 1) * m, cudaMemcpyDeviceToDevice, ctx->stream));
+    GDR_CUDA(cudaMemcpyAsync(cv, c, sizeof(c128) * (m + 1), cudaMemcpyDeviceToDevice, ctx->stream));
+    GDR_CUDA(cudaMemcpyAsync(sg, sigma, sizeof(c128) * ns, cudaMemcpyHostToDevice, ctx->stream));
+    d.H = H; d.cvec = cv; d.sigma = sg;
+    d.beta = reinterpret_cast<c128*>(beta_new);
+    GDR_CUDA(cudaMemcpyAsync(d.beta, beta, sizeof(c128) * ns, cudaMemcpyDeviceToDevice, ctx->stream));
+    d.norms = norms;
+    d.sact = ctx->get<int>("dstep.sact", (size_t)ns);
+    std::vector<int> ones(ns, 1);
+    GDR_CUDA(cudaMemcpyAsync(d.sact, ones.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, ctx->stream));
+    d.ldc = m + 1;
+    d.ccs = (long)(m + 1) * (ns + 1);
+    d.Cf = ctx->get<c128>("dstep.Cf", (size_t)d.ccs);
+    d.s = reinterpret_cast<c128*>(s);
+    d.st = ctx->get<ColState>("dstep.st", 1);
+    ColState st = {};
+    st.active = 1;
+    st.m_eff = m;
+    GDR_CUDA(cudaMemcpyAsync(d.st, &st, sizeof(st), cudaMemcpyHostToDevice, ctx->stream));
+    GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+    dense_cycle(ctx, d);
+    GDR_CUDA(cudaMemcpy2DAsync(D, m * sizeof(c128), d.Cf, (m + 1) * sizeof(c128), m * sizeof(c128), ns,
+                               cudaMemcpyDeviceToDevice, ctx->stream));
+    ColState out;
+    GDR_CUDA(cudaMemcpyAsync(&out, d.st, sizeof(out), cudaMemcpyDeviceToHost, ctx->stream));
+    GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (out.err) throw gdr_error((gdr_status)out.err, "singular reduced system");
+  });
+}
+
+gdr_status gdr_dense_restart(gdr_ctx* ctx, int m, int k, const double* sigma1, const double* Hbar, const double* s,
+                             double* theta, double* P, double* Hk, double* ck) {
+  if (!ctx) return GDR_EINVAL;
+  return guarded(ctx, [&] {
+    GDR_REQUIRE(m >= 2 && m <= GDR_MAX_M && k >= 1 && k < m, "bad sizes");
+    GDR_REQUIRE(sigma1 && Hbar && s && theta && P && Hk && ck, "null argument");
+    DenseCycle d{};
+    d.ncol = 1; d.m = m; d.k = k; d.ns = 1;
+    c128* sg = ctx->get<c128>("rstep.sigma", 1);
+    GDR_CUDA(cudaMemcpyAsync(sg, sigma1, sizeof(c128), cudaMemcpyHostToDevice, ctx->stream));
+    d.H = reinterpret_cast<const c128*>(Hbar);
+    d.sigma = sg;
+    d.s = const_cast<c128*>(reinterpret_cast<const c128*>(s));
+    d.ldc = m + 1;
+    d.ccs = (long)(m + 1) * (k + 1);
+    d.Cf = reinterpret_cast<c128*>(P);
+    d.Pk = ctx->get<c128>("rstep.Pk", (size_t)(m + 1) * k);
+    d.Hk = reinterpret_cast<c128*>(Hk);
+    d.ck = reinterpret_cast<c128*>(ck);
+    d.theta = reinterpret_cast<c128*>(theta);
+    d.scratch_per_col = (long)2 * ((long)m * m + 2L * m * k + 64);
+    d.scratch = ctx->get<double>("rstep.scratch", (size_t)d.scratch_per_col);
+    d.st = ctx->get<ColState>("rstep.st", 1);
+    ColState st = {};
+    st.active = 1;
+    st.m_eff = m;
+    GDR_CUDA(cudaMemcpyAsync(d.st, &st, sizeof(st), cudaMemcpyHostToDevice, ctx->stream));
+    dense_restart(ctx, d);
+    ColState out;
+    GDR_CUDA(cudaMemcpyAsync(&out, d.st, sizeof(out), cudaMemcpyDeviceToHost, ctx->stream));
+    GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (out.err) throw gdr_error((gdr_status)out.err, "harmonic Ritz restart failed");
+  });
+}
+
+gdr_status gdr_basis_update(gdr_ctx* ctx, gdr_prec prec, long n, int nv, void* V, const double* C, int nout, int nx,
+                            double* X) {
+  if (!ctx) return GDR_EINVAL;
+  return guarded(ctx, [&] {
+    GDR_REQUIRE(n > 0 && nv >= 1 && nout >= 0 && nout <= nv && nx >= 0, "bad sizes");
+    GDR_REQUIRE(V && C && (nx == 0 || X), "null argument");
+    if (prec == GDR_PREC_FP64)
+      combine<double>(ctx, n, 1, static_cast<c128*>(V), n, 0, nv, reinterpret_cast<const c128*>(C), nv, 0, nout, nx,
+                      0, reinterpret_cast<c128*>(X), n, 0, nullptr, 0, nullptr);
+    else
+      combine<float>(ctx, n, 1, static_cast<c64*>(V), n, 0, nv, reinterpret_cast<const c128*>(C), nv, 0, nout, nx, 0,
+                     reinterpret_cast<c128*>(X), n, 0, nullptr, 0, nullptr);
+  });
+}
+
+}  // extern "C"

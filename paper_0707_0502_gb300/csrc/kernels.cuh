@@ -1,0 +1,135 @@
+// Launchers shared between the kernel files and the solver driver.
+#pragma once
+#include "common.cuh"
+
+// Per-column device state of a (possibly column-batched) Arnoldi cycle.
+struct ColState {
+  int run;          // 1 while this cycle's vector kernels should work on the column
+  int active;       // column still iterating; 0 makes every kernel skip it
+  int broke;        // lucky breakdown in this cycle
+  int m_eff;        // Arnoldi length of this cycle (m unless breakdown)
+  int nan;          // NaN/Inf seen
+  int err;          // gdr_status from a reduced solve (0 = ok)
+  int conv;         // every shift of the column converged after this cycle
+  int j;            // current Arnoldi column (diagnostic)
+  double inv_norm;  // 1 / h_{j+1,j}, read by the scale kernel
+  double bnorm;     // ||b|| of the column (relative tolerance)
+  double tol;       // relative tolerance of the column
+  double rnorm;     // base residual norm after this cycle (||s||)
+  double wnorm0;    // ||A v_j|| of the last step (breakdown test)
+  double pad2;
+};
+
+// Layout of one batched Arnoldi problem set (all device pointers).
+template <typename R>
+struct Batch {
+  int ncol = 1;          // columns (independent Krylov spaces)
+  long n = 0;
+  int m = 0;             // basis size
+  int ns = 1;            // shifts per column
+  cx<R>* V = nullptr;    // basis, column c at V + c*vcs, vectors at stride ldv
+  long ldv = 0, vcs = 0;
+  cx<R>* W = nullptr;    // work vector per column (stride wcs)
+  long wcs = 0;
+  c128* H = nullptr;     // (m+1) x m per column, stride (m+1)*m
+  c128* cvec = nullptr;  // m+1 per column
+  c128* h1 = nullptr;    // (m+2) per column: GS dots (+ ||w||^2 in slot m+1)
+  c128* h2 = nullptr;
+  c128* part = nullptr;  // block partials, per column pstride
+  long pstride = 0;
+  unsigned* cnt = nullptr;  // last-block counters, per column (4 slots)
+  ColState* st = nullptr;
+  c128* sigma = nullptr;    // ns per column
+  int nblk = 0;             // grid size of the reduction kernels
+};
+
+// krylov.cu --------------------------------------------------------------
+// h_out[c][0..nv-1] = V_c[:, 0:nv]^H w_c  (+ ||w_c||^2 in h_out[c][nv] if wnorm)
+template <typename R>
+void gs_dot(gdr_ctx* ctx, const Batch<R>& b, int nv, const cx<R>* w, long wcs, c128* h_out, bool wnorm);
+// w_c -= V_c[:, 0:nv] h_c ; if final: Arnoldi step j = nv-1 is completed (Hbar column, norm, breakdown)
+template <typename R>
+void gs_update(gdr_ctx* ctx, const Batch<R>& b, int nv, cx<R>* w, long wcs, const c128* h, bool final_step);
+// V_c[:, j] = w_c * inv_norm_c   (skips broken / inactive columns)
+template <typename R>
+void scale_into(gdr_ctx* ctx, const Batch<R>& b, int j, const cx<R>* w, long wcs);
+// one full CGS2 Arnoldi step on every column: w = A v_j, two GS passes, v_{j+1}
+template <typename R>
+void arnoldi_step(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b, int j);
+// start a cycle from r_c: V_c[:,0] = r_c/||r_c||, cvec_c = ||r_c|| e_1, H_c = 0, state reset
+template <typename R>
+void start_cycle(gdr_ctx* ctx, const Batch<R>& b, const cx<R>* r, long rcs);
+// out[c] = ||x_c||^2 (FP64 accumulation), x c128 or cx<R>, `cols` columns of length n at stride xcs
+template <typename T>
+void norms2(gdr_ctx* ctx, long n, int cols, const T* x, long xcs, double* out, c128* part, int nblk, unsigned* cnt);
+// dots[c] = u_c^H x_c (FP64)   (ucs = 0 shares u)
+void dots128(gdr_ctx* ctx, long n, int cols, const c128* u, long ucs, const c128* x, long xcs, c128* out,
+             c128* part, int nblk, unsigned* cnt);
+
+// Basis combination (restart + multi-shift update, Proj updates):
+//   V_c[:, 0:nout] <- V_c[:, 0:nv] C_c[:, 0:nout]            (in place)
+//   X_c[:, i]      += V_c[:, 0:nv] C_c[:, nout+i], i < nx    (X is FP64)
+//   rmode 1: Rv_c = V_c C_c[:, nout+nx];  rmode 2: Rv_c += V_c C_c[:, nout+nx]
+// C_c is c128 nv x (nout+nx+(rmode?1:0)), column-major with leading dim ldc, column stride ccs.
+// vcs = 0 shares one basis between all columns.
+template <typename R>
+void combine(gdr_ctx* ctx, long n, int ncol, cx<R>* V, long ldv, long vcs, int nv, const c128* C, int ldc, long ccs,
+             int nout, int nx, int rmode, c128* X, long ldx, long xcs, cx<R>* Rv, long rcs, const ColState* st);
+
+void krylov_init(gdr_ctx* ctx);
+
+// conversions / small vector ops (FP64 <-> complex64)
+void cvt_128_to_64(gdr_ctx* ctx, long n, int cols, const c128* in, long ics, c64* out, long ocs);
+void cvt_64_to_128(gdr_ctx* ctx, long n, int cols, const c64* in, long ics, c128* out, long ocs);
+void copy128(gdr_ctx* ctx, long n, int cols, const c128* in, long ics, c128* out, long ocs);
+// X[:, c] += a_c * S[:, c]   (a: device c128 per column; ssc = 0 shares S)
+void axpy_cols(gdr_ctx* ctx, long n, int cols, const c128* a, const c128* S, long ssc, c128* X, long xcs);
+// X[:, c] *= a_c
+void scal_cols(gdr_ctx* ctx, long n, int cols, const c128* a, c128* X, long xcs);
+
+// ops.cu -----------------------------------------------------------------
+void op_apply_skip(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, const c128* X, long ldx, c128* Y,
+                   long ldy, const c128* B, long ldb, const int* run, int run_stride);
+void op_apply_skip(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, const c64* X, long ldx, c64* Y,
+                   long ldy, const c64* B, long ldb, const int* run, int run_stride);
+void op_build_csr(gdr_ctx* ctx, gdr_op* op, const int* rowptr, const int* col, const double* vals);
+void op_build_wilson(gdr_ctx* ctx, gdr_op* op, const double* links);
+
+// dense.cu ---------------------------------------------------------------
+// Reduced solves of one cycle.  Per column c (grid.y) with m_eff from the state:
+//  base: d_1 = argmin ||c - (Hbar - sigma_1 Ibar) d||, s = c - (...) d_1
+//  shifts i >= 1 (active): [(Hbar - sigma_i Ibar) | s] [d_i ; beta_new] = beta_i c  via QR
+//  restart (k > 0): harmonic Ritz of Hbar - sigma_1 Ibar, P_{k+1}, Hbar_k, c_k
+// Coefficients for `combine` go to Cf (ldc = m+1, per column ccs): columns
+//  [0, k+1) = P_{k+1} (when k > 0), [k+1, k+1+ns) = [d_i ; 0],
+//  and when want_r: column k+1+ns = s (the new residual r = V_{m+1} s).
+struct DenseCycle {
+  int ncol, m, k, ns;
+  const c128* H; const c128* cvec; const c128* sigma;
+  c128* beta; double* norms; int* sact;     // per column: ns each
+  c128* Cf; int ldc; long ccs;              // coefficient matrices
+  c128* s;                                  // (m+1) per column
+  c128* Pk; c128* Hk; c128* ck;             // restart products (k>0)
+  c128* theta;                              // m per column (harmonic Ritz values)
+  double* scratch;                          // per column dense scratch
+  long scratch_per_col;
+  ColState* st;
+  bool want_r;
+};
+void dense_cycle(gdr_ctx* ctx, const DenseCycle& d);
+// cycle bookkeeping after the reduced solves: convergence test, beta/active update,
+// the next cycle's Hbar/c (from Hk/ck when k > 0)
+void cycle_finish(gdr_ctx* ctx, const DenseCycle& d, c128* H, c128* cvec);
+
+// Minres projection over V_k for every column (Sec. 2.3; Proj-Sh steps 3-4):
+// c = V_{k+1}^H r given in cproj (stride k+2 per column), base LS on Hbar_k - sigma_1 Ibar,
+// shifts: (H_k - sigma_i I) d_i = beta_i (H_k - sigma_1 I) d_1; gamma_i accumulated.
+// Writes Cf (ldc = k+1): columns [0, ns) = [d_i ; 0], column ns = -(Hbar_k - sigma_1 Ibar) d_1.
+void dense_projection(gdr_ctx* ctx, int ncol, int k, int ns, const c128* Hk, const c128* cproj, const c128* sigma,
+                      const c128* beta, const int* sact, c128* gamma, c128* Cf, long ccs, double* scratch,
+                      long scratch_per_col, ColState* st);
+
+size_t dense_smem_bytes(int m, int k);
+// harmonic Ritz restart products alone, for the s already in d.s
+void dense_restart(gdr_ctx* ctx, const DenseCycle& d);
+void dense_init(gdr_ctx* ctx);

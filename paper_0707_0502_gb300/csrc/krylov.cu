@@ -1,0 +1,519 @@
+// Krylov-basis kernels: classical Gram-Schmidt twice (CGS2) for the Arnoldi
+// recurrence A V_m = V_{m+1} Hbar_m (eq. recurAr / recur0), the fused basis
+// combination used by the GMRES-DR restart (eq. recur1) and the multi-shift
+// solution updates x_i += V_m d_i (GMRES-DR-Sh step 5), and small vector ops.
+//
+// Every kernel works on a batch of independent columns (grid.y = column); a
+// column whose state says `run == 0` is skipped.  Reductions are
+// deterministic: each block writes FP64 partials, the last block to finish
+// (atomic ticket) sums them in block order.
+#include <type_traits>
+
+#include "kernels.cuh"
+
+namespace {
+
+constexpr int NT = 256;  // threads of the reduction kernels
+constexpr int JB = 8;    // basis vectors per register chunk
+constexpr unsigned FULL = 0xffffffffu;
+
+// 16-byte units: 2 complex64 or 1 complex128
+template <typename R> struct U { static constexpr int K = 16 / (2 * sizeof(R)); };
+
+template <typename R> DEV void ldu(const cx<R>* p, long u, long n, cx<R> (&o)[U<R>::K]);
+template <> DEV void ldu<float>(const c64* p, long u, long n, c64 (&o)[2]) {
+  if (2 * u + 1 < n) {
+    float4 v = *(reinterpret_cast<const float4*>(p) + u);
+    o[0] = {v.x, v.y};
+    o[1] = {v.z, v.w};
+  } else {
+    o[0] = p[2 * u];
+    o[1] = {0.f, 0.f};
+  }
+}
+template <> DEV void ldu<double>(const c128* p, long u, long, c128 (&o)[1]) {
+  double2 v = *(reinterpret_cast<const double2*>(p) + u);
+  o[0] = {v.x, v.y};
+}
+template <typename R> DEV void stu(cx<R>* p, long u, long n, const cx<R> (&o)[U<R>::K]);
+template <> DEV void stu<float>(c64* p, long u, long n, const c64 (&o)[2]) {
+  if (2 * u + 1 < n) {
+    *(reinterpret_cast<float4*>(p) + u) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+  } else {
+    p[2 * u] = o[0];
+  }
+}
+template <> DEV void stu<double>(c128* p, long u, long, const c128 (&o)[1]) {
+  *(reinterpret_cast<double2*>(p) + u) = make_double2(o[0].x, o[0].y);
+}
+template <typename R> HD long nunits(long n) { return (n + U<R>::K - 1) / U<R>::K; }
+
+DEV c128 ldcg128(const c128* p) {
+  double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return {v.x, v.y};
+}
+
+// Reduce NV complex values over the block; threads < nvalid write out[t].
+template <typename R, int NV>
+DEV void block_reduce(cx<R> (&acc)[NV], c128* out, int nvalid) {
+  __shared__ c128 sred[NT / 32][NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      acc[i].x += __shfl_down_sync(FULL, acc[i].x, off);
+      acc[i].y += __shfl_down_sync(FULL, acc[i].y, off);
+    }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sred[warp][i] = up(acc[i]);
+  }
+  __syncthreads();
+  if (threadIdx.x < nvalid) {
+    c128 s = {0, 0};
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) s += sred[w][threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// true in exactly one block per column: the last one to finish
+DEV bool last_block(unsigned* cnt) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(cnt, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// ------------------------------------------------------------ Gram-Schmidt
+
+template <typename R>
+__global__ void __launch_bounds__(NT) gs_dot_kernel(Batch<R> b, int nv, const cx<R>* __restrict__ W, long wcs,
+                                                    c128* __restrict__ hout, int hstride, int wnorm) {
+  const int c = blockIdx.y;
+  if (!b.st[c].run) return;
+  constexpr int K = U<R>::K;
+  const cx<R>* __restrict__ V = b.V + c * b.vcs;
+  const cx<R>* __restrict__ w = W + c * wcs;
+  const long n = b.n, nu = nunits<R>(n);
+  c128* part = b.part + c * b.pstride;
+  const long gt = blockIdx.x * (long)NT + threadIdx.x, gs = (long)gridDim.x * NT;
+  for (int i0 = 0; i0 < nv; i0 += JB) {
+    cx<R> acc[JB];
+#pragma unroll
+    for (int q = 0; q < JB; ++q) acc[q] = {0, 0};
+    for (long u = gt; u < nu; u += gs) {
+      cx<R> wv[K];
+      ldu<R>(w, u, n, wv);
+#pragma unroll
+      for (int q = 0; q < JB; ++q) {
+        if (i0 + q < nv) {
+          cx<R> vv[K];
+          ldu<R>(V + (long)(i0 + q) * b.ldv, u, n, vv);
+#pragma unroll
+          for (int kk = 0; kk < K; ++kk) acc[q] += cmulc(vv[kk], wv[kk]);
+        }
+      }
+    }
+    block_reduce<R, JB>(acc, part + (long)blockIdx.x * hstride + i0, min(JB, nv - i0));
+  }
+  if (wnorm) {
+    cx<R> a[1] = {{0, 0}};
+    for (long u = gt; u < nu; u += gs) {
+      cx<R> wv[K];
+      ldu<R>(w, u, n, wv);
+#pragma unroll
+      for (int kk = 0; kk < K; ++kk) a[0].x += norm2(wv[kk]);
+    }
+    block_reduce<R, 1>(a, part + (long)blockIdx.x * hstride + nv, 1);
+  }
+  if (!last_block(b.cnt + 4 * c)) return;
+  const int tot = nv + (wnorm ? 1 : 0);
+  for (int i = threadIdx.x; i < tot; i += NT) {
+    c128 s = {0, 0};
+    for (int bk = 0; bk < (int)gridDim.x; ++bk) s += ldcg128(part + (long)bk * hstride + i);
+    hout[(long)c * hstride + i] = s;
+  }
+  if (threadIdx.x == 0) b.cnt[4 * c] = 0;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(NT) gs_update_kernel(Batch<R> b, int nv, cx<R>* __restrict__ W, long wcs,
+                                                       const c128* __restrict__ h, int hstride, int final_step) {
+  const int c = blockIdx.y;
+  if (!b.st[c].run) return;
+  constexpr int K = U<R>::K;
+  __shared__ cx<R> hs[GDR_MAX_M + 2];
+  for (int i = threadIdx.x; i < nv; i += NT) hs[i] = cvt<R>(h[(long)c * hstride + i]);
+  __syncthreads();
+  const cx<R>* __restrict__ V = b.V + c * b.vcs;
+  cx<R>* __restrict__ w = W + c * wcs;
+  const long n = b.n, nu = nunits<R>(n);
+  const long gt = blockIdx.x * (long)NT + threadIdx.x, gs = (long)gridDim.x * NT;
+  cx<R> nrm[1] = {{0, 0}};
+  for (long u = gt; u < nu; u += gs) {
+    cx<R> acc[K];
+    ldu<R>(w, u, n, acc);
+    for (int i = 0; i < nv; ++i) {
+      cx<R> vv[K];
+      ldu<R>(V + (long)i * b.ldv, u, n, vv);
+      const cx<R> hi = hs[i];
+#pragma unroll
+      for (int kk = 0; kk < K; ++kk) acc[kk] -= vv[kk] * hi;
+    }
+    stu<R>(w, u, n, acc);
+#pragma unroll
+    for (int kk = 0; kk < K; ++kk) nrm[0].x += norm2(acc[kk]);
+  }
+  if (!final_step) return;
+  c128* part = b.part + c * b.pstride;
+  block_reduce<R, 1>(nrm, part + (long)blockIdx.x * hstride, 1);
+  if (!last_block(b.cnt + 4 * c)) return;
+  __shared__ double wn_s;
+  if (threadIdx.x < 32) {
+    double s = 0;
+    for (int bk = threadIdx.x; bk < (int)gridDim.x; bk += 32) s += ldcg128(part + (long)bk * hstride).x;
+    // fixed-order warp sum
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(FULL, s, off);
+    if (threadIdx.x == 0) wn_s = sqrt(s);
+  }
+  __syncthreads();
+  const double wn = wn_s;
+  const int j = nv - 1;
+  const int m = b.m;
+  c128* Hc = b.H + (long)c * (m + 1) * m + (long)j * (m + 1);
+  for (int i = threadIdx.x; i < nv; i += NT) Hc[i] = b.h1[(long)c * hstride + i] + b.h2[(long)c * hstride + i];
+  if (threadIdx.x == 0) {
+    Hc[nv] = {wn, 0.0};
+    ColState& st = b.st[c];
+    const double w0 = sqrt(b.h1[(long)c * hstride + nv].x);
+    st.j = j;
+    st.wnorm0 = w0;
+    if (!isfinite(wn) || !isfinite(w0)) {
+      st.nan = 1;
+      st.broke = 1;
+      st.run = 0;
+      st.m_eff = j + 1;
+    } else if (wn <= 1e-12 * w0) {
+      st.broke = 1;
+      st.run = 0;
+      st.m_eff = j + 1;
+    } else {
+      st.inv_norm = 1.0 / wn;
+    }
+    b.cnt[4 * c] = 0;
+  }
+}
+
+template <typename R>
+__global__ void scale_kernel(Batch<R> b, int j, const cx<R>* __restrict__ W, long wcs) {
+  const int c = blockIdx.y;
+  if (!b.st[c].run) return;
+  constexpr int K = U<R>::K;
+  const long n = b.n, nu = nunits<R>(n);
+  const R s = (R)b.st[c].inv_norm;
+  const cx<R>* w = W + c * wcs;
+  cx<R>* v = b.V + c * b.vcs + (long)j * b.ldv;
+  for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < nu; u += (long)gridDim.x * blockDim.x) {
+    cx<R> a[K];
+    ldu<R>(w, u, n, a);
+#pragma unroll
+    for (int kk = 0; kk < K; ++kk) a[kk] = s * a[kk];
+    stu<R>(v, u, n, a);
+  }
+}
+
+// ||x_c||^2 with FP64 block partials; result written by the last block
+template <typename T> struct Real;
+template <> struct Real<c64> { using R = float; };
+template <> struct Real<c128> { using R = double; };
+
+template <typename T>
+__global__ void __launch_bounds__(NT) norms2_kernel(long n, const T* __restrict__ x, long xcs, double* out,
+                                                    c128* part, unsigned* cnt) {
+  using R = typename Real<T>::R;
+  const int c = blockIdx.y;
+  const T* xc = x + c * xcs;
+  cx<R> a[1] = {{0, 0}};
+  // FP64 per-thread accumulation for accuracy of ||b||
+  double s = 0;
+  for (long i = blockIdx.x * (long)NT + threadIdx.x; i < n; i += (long)gridDim.x * NT) {
+    const T v = xc[i];
+    s += (double)v.x * v.x + (double)v.y * v.y;
+  }
+  c128 d[1] = {{s, 0}};
+  block_reduce<double, 1>(d, part + (long)c * gridDim.x + blockIdx.x, 1);
+  (void)a;
+  if (!last_block(cnt + 4 * c)) return;
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int bk = 0; bk < (int)gridDim.x; ++bk) t += ldcg128(part + (long)c * gridDim.x + bk).x;
+    out[c] = t;
+    cnt[4 * c] = 0;
+  }
+}
+
+__global__ void __launch_bounds__(NT) dots128_kernel(long n, const c128* __restrict__ u, long ucs,
+                                                     const c128* __restrict__ x, long xcs, c128* out, c128* part,
+                                                     unsigned* cnt) {
+  const int c = blockIdx.y;
+  const c128* uc = u + c * ucs;
+  const c128* xc = x + c * xcs;
+  c128 a[1] = {{0, 0}};
+  for (long i = blockIdx.x * (long)NT + threadIdx.x; i < n; i += (long)gridDim.x * NT) a[0] += cmulc(uc[i], xc[i]);
+  block_reduce<double, 1>(a, part + (long)c * gridDim.x + blockIdx.x, 1);
+  if (!last_block(cnt + 4 * c)) return;
+  if (threadIdx.x == 0) {
+    c128 t = {0, 0};
+    for (int bk = 0; bk < (int)gridDim.x; ++bk) t += ldcg128(part + (long)c * gridDim.x + bk);
+    out[c] = t;
+    cnt[4 * c] = 0;
+  }
+}
+
+// start of a cycle: V[:,0] = r / ||r||  (||r||^2 in rn2[c])
+template <typename R>
+__global__ void start_scale_kernel(Batch<R> b, const cx<R>* __restrict__ r, long rcs, const double* rn2) {
+  const int c = blockIdx.y;
+  if (!b.st[c].active) return;
+  const double rn = sqrt(rn2[c]);
+  if (!(rn > 0)) return;
+  const R s = (R)(1.0 / rn);
+  const cx<R>* rc = r + c * rcs;
+  cx<R>* v = b.V + c * b.vcs;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < b.n; i += (long)gridDim.x * blockDim.x)
+    v[i] = s * rc[i];
+}
+
+template <typename R>
+__global__ void start_state_kernel(Batch<R> b, const double* rn2) {
+  const int c = blockIdx.x;
+  const int m = b.m;
+  c128* H = b.H + (long)c * (m + 1) * m;
+  for (long i = threadIdx.x; i < (long)(m + 1) * m; i += blockDim.x) H[i] = {0, 0};
+  c128* cv = b.cvec + (long)c * (m + 1);
+  const double rn = sqrt(rn2[c]);
+  for (int i = threadIdx.x; i <= m; i += blockDim.x) cv[i] = {i == 0 ? rn : 0.0, 0.0};
+  if (threadIdx.x == 0) {
+    ColState& st = b.st[c];
+    st.broke = 0;
+    st.m_eff = m;
+    st.rnorm = rn;
+    if (!isfinite(rn)) st.nan = 1;
+    // a zero residual needs no cycle
+    st.run = (st.active && rn > 0 && isfinite(rn)) ? 1 : 0;
+  }
+}
+
+// ------------------------------------------------------ basis combination
+
+constexpr int CT = 256;  // threads
+constexpr int CR = 64;   // rows per tile
+
+template <typename R>
+__global__ void __launch_bounds__(CT) combine_kernel(long n, cx<R>* V, long ldv, long vcs, int nv,
+                                                     const c128* __restrict__ C, int ldc, long ccs, int nout, int nx,
+                                                     int rmode, c128* X, long ldx, long xcs, cx<R>* Rv, long rcs,
+                                                     const ColState* st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int c = blockIdx.y;
+  if (st && !st[c].active) return;
+  const int ntot = nout + nx + (rmode ? 1 : 0);
+  cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);             // CR x nv  (row-fast)
+  cx<R>* cf = tile + (long)CR * nv;                              // nv x ntot
+  cx<R>* Vc = V + c * vcs;
+  const c128* Cc = C + c * ccs;
+  const long r0 = blockIdx.x * (long)CR;
+  const int rows = (int)min((long)CR, n - r0);
+  for (int t = threadIdx.x; t < nv * ntot; t += CT) {
+    const int i = t % nv, o = t / nv;
+    cf[t] = cvt<R>(Cc[(long)o * ldc + i]);
+  }
+  for (int t = threadIdx.x; t < CR * nv; t += CT) {
+    const int rr = t % CR, i = t / CR;
+    tile[t] = (rr < rows) ? Vc[(long)i * ldv + r0 + rr] : cx<R>{0, 0};
+  }
+  __syncthreads();
+  const int rr = threadIdx.x % CR;
+  if (rr >= rows) return;
+  const long row = r0 + rr;
+  for (int o = threadIdx.x / CR; o < ntot; o += CT / CR) {
+    cx<R> acc = {0, 0};
+    const cx<R>* co = cf + (long)o * nv;
+    for (int i = 0; i < nv; ++i) acc += tile[(long)i * CR + rr] * co[i];
+    if (o < nout) {
+      Vc[(long)o * ldv + row] = acc;
+    } else if (o < nout + nx) {
+      c128* xp = X + c * xcs + (long)(o - nout) * ldx + row;
+      *xp = *xp + up(acc);
+    } else {
+      cx<R>* rp = Rv + c * rcs + row;
+      if (rmode == 1) *rp = acc;
+      else *rp = *rp + acc;
+    }
+  }
+}
+
+// -------------------------------------------------------- small vector ops
+
+__global__ void cvt_128_64_kernel(long n, const c128* in, long ics, c64* out, long ocs) {
+  const int c = blockIdx.y;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    out[c * ocs + i] = to64(in[c * ics + i]);
+}
+__global__ void cvt_64_128_kernel(long n, const c64* in, long ics, c128* out, long ocs) {
+  const int c = blockIdx.y;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    out[c * ocs + i] = to128(in[c * ics + i]);
+}
+__global__ void copy128_kernel(long n, const c128* in, long ics, c128* out, long ocs) {
+  const int c = blockIdx.y;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    out[c * ocs + i] = in[c * ics + i];
+}
+__global__ void axpy_cols_kernel(long n, const c128* a, const c128* S, long ssc, c128* X, long xcs) {
+  const int c = blockIdx.y;
+  const c128 ac = a[c];
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    X[c * xcs + i] += ac * S[c * ssc + i];
+}
+__global__ void scal_cols_kernel(long n, const c128* a, c128* X, long xcs) {
+  const int c = blockIdx.y;
+  const c128 ac = a[c];
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    X[c * xcs + i] = ac * X[c * xcs + i];
+}
+
+unsigned grid_for(gdr_ctx* ctx, long work, int threads) {
+  long g = (work + threads - 1) / threads;
+  long cap = (long)ctx->num_sms * 8;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- launchers
+
+template <typename R>
+void gs_dot(gdr_ctx* ctx, const Batch<R>& b, int nv, const cx<R>* w, long wcs, c128* h_out, bool wnorm) {
+  dim3 grid((unsigned)b.nblk, (unsigned)b.ncol);
+  gs_dot_kernel<R><<<grid, NT, 0, ctx->stream>>>(b, nv, w, wcs, h_out, b.m + 2, wnorm ? 1 : 0);
+  GDR_LAUNCHED(ctx);
+}
+template <typename R>
+void gs_update(gdr_ctx* ctx, const Batch<R>& b, int nv, cx<R>* w, long wcs, const c128* h, bool final_step) {
+  dim3 grid((unsigned)b.nblk, (unsigned)b.ncol);
+  gs_update_kernel<R><<<grid, NT, 0, ctx->stream>>>(b, nv, w, wcs, h, b.m + 2, final_step ? 1 : 0);
+  GDR_LAUNCHED(ctx);
+}
+template <typename R>
+void scale_into(gdr_ctx* ctx, const Batch<R>& b, int j, const cx<R>* w, long wcs) {
+  dim3 grid(grid_for(ctx, nunits<R>(b.n), 256), (unsigned)b.ncol);
+  scale_kernel<R><<<grid, 256, 0, ctx->stream>>>(b, j, w, wcs);
+  GDR_LAUNCHED(ctx);
+}
+
+template <typename R>
+void arnoldi_step(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b, int j) {
+  op_apply_skip(ctx, A, b.ncol, nullptr, b.V + (long)j * b.ldv, b.vcs, b.W, b.wcs, nullptr, 0, &b.st[0].run,
+                (int)(sizeof(ColState) / sizeof(int)));
+  gs_dot<R>(ctx, b, j + 1, b.W, b.wcs, b.h1, true);
+  gs_update<R>(ctx, b, j + 1, b.W, b.wcs, b.h1, false);
+  gs_dot<R>(ctx, b, j + 1, b.W, b.wcs, b.h2, false);
+  gs_update<R>(ctx, b, j + 1, b.W, b.wcs, b.h2, true);
+  scale_into<R>(ctx, b, j + 1, b.W, b.wcs);
+}
+
+template <typename R>
+void start_cycle(gdr_ctx* ctx, const Batch<R>& b, const cx<R>* r, long rcs) {
+  double* rn2 = ctx->get<double>("start_rn2", b.ncol);
+  norms2<cx<R>>(ctx, b.n, b.ncol, r, rcs, rn2, b.part, b.nblk, b.cnt);
+  dim3 grid(grid_for(ctx, b.n, 256), (unsigned)b.ncol);
+  start_scale_kernel<R><<<grid, 256, 0, ctx->stream>>>(b, r, rcs, rn2);
+  GDR_LAUNCHED(ctx);
+  start_state_kernel<R><<<b.ncol, 256, 0, ctx->stream>>>(b, rn2);
+  GDR_LAUNCHED(ctx);
+}
+
+template <typename T>
+void norms2(gdr_ctx* ctx, long n, int cols, const T* x, long xcs, double* out, c128* part, int nblk, unsigned* cnt) {
+  dim3 grid((unsigned)nblk, (unsigned)cols);
+  norms2_kernel<T><<<grid, NT, 0, ctx->stream>>>(n, x, xcs, out, part, cnt);
+  GDR_LAUNCHED(ctx);
+}
+void dots128(gdr_ctx* ctx, long n, int cols, const c128* u, long ucs, const c128* x, long xcs, c128* out, c128* part,
+             int nblk, unsigned* cnt) {
+  dim3 grid((unsigned)nblk, (unsigned)cols);
+  dots128_kernel<<<grid, NT, 0, ctx->stream>>>(n, u, ucs, x, xcs, out, part, cnt);
+  GDR_LAUNCHED(ctx);
+}
+
+template <typename R>
+void combine(gdr_ctx* ctx, long n, int ncol, cx<R>* V, long ldv, long vcs, int nv, const c128* C, int ldc, long ccs,
+             int nout, int nx, int rmode, c128* X, long ldx, long xcs, cx<R>* Rv, long rcs, const ColState* st) {
+  const int ntot = nout + nx + (rmode ? 1 : 0);
+  if (ntot == 0 || ncol == 0) return;
+  const size_t smem = sizeof(cx<R>) * ((size_t)CR * nv + (size_t)nv * ntot);
+  GDR_REQUIRE(smem <= ctx->combine_smem_limit, "combine: too many basis vectors / outputs for shared memory");
+  dim3 grid((unsigned)((n + CR - 1) / CR), (unsigned)ncol);
+  combine_kernel<R><<<grid, CT, smem, ctx->stream>>>(n, V, ldv, vcs, nv, C, ldc, ccs, nout, nx, rmode, X, ldx, xcs,
+                                                     Rv, rcs, st);
+  GDR_LAUNCHED(ctx);
+}
+
+void krylov_init(gdr_ctx* ctx) {
+  ctx->combine_smem_limit =
+      std::min(set_max_dyn_smem(ctx, combine_kernel<float>), set_max_dyn_smem(ctx, combine_kernel<double>));
+}
+
+void cvt_128_to_64(gdr_ctx* ctx, long n, int cols, const c128* in, long ics, c64* out, long ocs) {
+  dim3 grid(grid_for(ctx, n, 256), (unsigned)cols);
+  cvt_128_64_kernel<<<grid, 256, 0, ctx->stream>>>(n, in, ics, out, ocs);
+  GDR_LAUNCHED(ctx);
+}
+void cvt_64_to_128(gdr_ctx* ctx, long n, int cols, const c64* in, long ics, c128* out, long ocs) {
+  dim3 grid(grid_for(ctx, n, 256), (unsigned)cols);
+  cvt_64_128_kernel<<<grid, 256, 0, ctx->stream>>>(n, in, ics, out, ocs);
+  GDR_LAUNCHED(ctx);
+}
+void copy128(gdr_ctx* ctx, long n, int cols, const c128* in, long ics, c128* out, long ocs) {
+  dim3 grid(grid_for(ctx, n, 256), (unsigned)cols);
+  copy128_kernel<<<grid, 256, 0, ctx->stream>>>(n, in, ics, out, ocs);
+  GDR_LAUNCHED(ctx);
+}
+void axpy_cols(gdr_ctx* ctx, long n, int cols, const c128* a, const c128* S, long ssc, c128* X, long xcs) {
+  dim3 grid(grid_for(ctx, n, 256), (unsigned)cols);
+  axpy_cols_kernel<<<grid, 256, 0, ctx->stream>>>(n, a, S, ssc, X, xcs);
+  GDR_LAUNCHED(ctx);
+}
+void scal_cols(gdr_ctx* ctx, long n, int cols, const c128* a, c128* X, long xcs) {
+  dim3 grid(grid_for(ctx, n, 256), (unsigned)cols);
+  scal_cols_kernel<<<grid, 256, 0, ctx->stream>>>(n, a, X, xcs);
+  GDR_LAUNCHED(ctx);
+}
+
+template void gs_dot<float>(gdr_ctx*, const Batch<float>&, int, const c64*, long, c128*, bool);
+template void gs_dot<double>(gdr_ctx*, const Batch<double>&, int, const c128*, long, c128*, bool);
+template void gs_update<float>(gdr_ctx*, const Batch<float>&, int, c64*, long, const c128*, bool);
+template void gs_update<double>(gdr_ctx*, const Batch<double>&, int, c128*, long, const c128*, bool);
+template void scale_into<float>(gdr_ctx*, const Batch<float>&, int, const c64*, long);
+template void scale_into<double>(gdr_ctx*, const Batch<double>&, int, const c128*, long);
+template void arnoldi_step<float>(gdr_ctx*, const gdr_op*, const Batch<float>&, int);
+template void arnoldi_step<double>(gdr_ctx*, const gdr_op*, const Batch<double>&, int);
+template void start_cycle<float>(gdr_ctx*, const Batch<float>&, const c64*, long);
+template void start_cycle<double>(gdr_ctx*, const Batch<double>&, const c128*, long);
+template void norms2<c64>(gdr_ctx*, long, int, const c64*, long, double*, c128*, int, unsigned*);
+template void norms2<c128>(gdr_ctx*, long, int, const c128*, long, double*, c128*, int, unsigned*);
+template void combine<float>(gdr_ctx*, long, int, c64*, long, long, int, const c128*, int, long, int, int, int, c128*,
+                             long, long, c64*, long, const ColState*);
+template void combine<double>(gdr_ctx*, long, int, c128*, long, long, int, const c128*, int, long, int, int, int,
+                              c128*, long, long, c128*, long, const ColState*);

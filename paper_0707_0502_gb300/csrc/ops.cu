@@ -1,0 +1,304 @@
+// Operator kernels: y = (A - sigma_c I) x_c for ncol columns, optionally as the
+// residual y = b - (A - sigma_c I) x_c.
+//
+//  * CSR matvec (the matrices of Examples 1-6, Sec. 3-4; convection-diffusion).
+//  * Wilson-Dirac-style stencil A = a I - H (Example 7, Sec. 4):
+//      (H psi)(x) = sum_mu (1 - gamma_mu) U_mu(x) psi(x+mu) + (1 + gamma_mu) U_mu(x-mu)^H psi(x-mu)
+//    evaluated with the spin projection of the chiral basis: writing
+//    gamma_mu = [[0, B_mu], [B_mu^H, 0]] with B_mu unitary 2x2,
+//      (1 -+ gamma_mu) psi = [h ; -+ B_mu^H h],   h = u -+ B_mu d,   psi = [u ; d],
+//    so each hop multiplies one link into a 2-spin half spinor only.
+//
+// Vectors are site-major (site*12 + spin*3 + colour).  Links are stored
+// structure-of-arrays [mu][e][V] (e = a*3 + b) so that a warp's loads of one
+// link element are contiguous.
+#include "common.cuh"
+
+namespace {
+
+// ------------------------------------------------------------- CSR kernel
+
+template <typename R, typename VT>
+__global__ void csr_kernel(long n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                           const VT* __restrict__ vals, const c128* __restrict__ sigma,
+                           const cx<R>* __restrict__ X, long ldx, cx<R>* __restrict__ Y, long ldy,
+                           const cx<R>* __restrict__ B, long ldb, const int* __restrict__ run, int run_stride) {
+  const long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (r >= n) return;
+  if (run && !run[(long)c * run_stride]) return;
+  const cx<R>* x = X + c * ldx;
+  cx<R> acc = {0, 0};
+  const int p0 = rowptr[r], p1 = rowptr[r + 1];
+  for (int p = p0; p < p1; ++p) {
+    VT v = vals[p];
+    cx<R> a = {(R)v.x, (R)v.y};
+    acc += a * x[col[p]];
+  }
+  if (sigma) acc -= cvt<R>(sigma[c]) * x[r];
+  if (B) acc = B[c * ldb + r] - acc;
+  Y[c * ldy + r] = acc;
+}
+
+// ---------------------------------------------------------- Wilson kernel
+
+template <typename R, typename LT> struct LinkLd;
+template <> struct LinkLd<double, c128> {
+  static DEV c128 ld(const c128* L, long i) {
+    double2 v = __ldg(reinterpret_cast<const double2*>(L) + i);
+    return {v.x, v.y};
+  }
+};
+template <> struct LinkLd<float, c64> {
+  static DEV c64 ld(const c64* L, long i) {
+    float2 v = __ldg(reinterpret_cast<const float2*>(L) + i);
+    return {v.x, v.y};
+  }
+};
+template <> struct LinkLd<float, __nv_bfloat162> {
+  static DEV c64 ld(const __nv_bfloat162* L, long i) {
+    float2 v = __bfloat1622float2(L[i]);
+    return {v.x, v.y};
+  }
+};
+
+// B_mu d (chiral basis; B_x = -i s1, B_y = -i s2, B_z = -i s3, B_t = I)
+template <int MU, typename R>
+DEV void b_mul(cx<R> d0, cx<R> d1, cx<R>& o0, cx<R>& o1) {
+  if (MU == 0) { o0 = -mul_i(d1); o1 = -mul_i(d0); }
+  if (MU == 1) { o0 = -d1; o1 = d0; }
+  if (MU == 2) { o0 = -mul_i(d0); o1 = mul_i(d1); }
+  if (MU == 3) { o0 = d0; o1 = d1; }
+}
+// B_mu^H g
+template <int MU, typename R>
+DEV void bh_mul(cx<R> g0, cx<R> g1, cx<R>& o0, cx<R>& o1) {
+  if (MU == 0) { o0 = mul_i(g1); o1 = mul_i(g0); }
+  if (MU == 1) { o0 = g1; o1 = -g0; }
+  if (MU == 2) { o0 = mul_i(g0); o1 = -mul_i(g1); }
+  if (MU == 3) { o0 = g0; o1 = g1; }
+}
+
+template <typename R> struct Spinor { cx<R> s[12]; };
+
+template <typename R> DEV void load_spinor(const cx<R>* __restrict__ x, long site, Spinor<R>& p);
+template <> DEV void load_spinor<float>(const c64* __restrict__ x, long site, Spinor<float>& p) {
+  const float4* q = reinterpret_cast<const float4*>(x + site * 12);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    float4 v = __ldg(q + i);
+    p.s[2 * i] = {v.x, v.y};
+    p.s[2 * i + 1] = {v.z, v.w};
+  }
+}
+template <> DEV void load_spinor<double>(const c128* __restrict__ x, long site, Spinor<double>& p) {
+  const double2* q = reinterpret_cast<const double2*>(x + site * 12);
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    double2 v = __ldg(q + i);
+    p.s[i] = {v.x, v.y};
+  }
+}
+
+// one hop in direction MU; FWD: (1 - gamma) U(x) psi(x+mu), else (1 + gamma) U(x-mu)^H psi(x-mu)
+template <int MU, bool FWD, typename R, typename LT>
+DEV void hop(const LT* __restrict__ links, long V, long lsite, const Spinor<R>& p, Spinor<R>& acc) {
+  // half spinor h_s = u_s -+ (B d)_s, s = 0, 1, per colour
+  cx<R> h[2][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    cx<R> b0, b1;
+    b_mul<MU, R>(p.s[6 + a], p.s[9 + a], b0, b1);
+    if (FWD) { h[0][a] = p.s[a] - b0; h[1][a] = p.s[3 + a] - b1; }
+    else     { h[0][a] = p.s[a] + b0; h[1][a] = p.s[3 + a] + b1; }
+  }
+  // g = U h  (forward)  or  U^H h  (backward)
+  cx<R> g[2][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) { g[0][a] = {0, 0}; g[1][a] = {0, 0}; }
+  const LT* L = links + (long)MU * 9 * V + lsite;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      cx<R> u = LinkLd<R, LT>::ld(L, (long)(a * 3 + b) * V);
+      if (FWD) {  // g_a += U_ab h_b
+        g[0][a] += u * h[0][b];
+        g[1][a] += u * h[1][b];
+      } else {    // g_b += conj(U_ab) h_a
+        g[0][b] += cmulc(u, h[0][a]);
+        g[1][b] += cmulc(u, h[1][a]);
+      }
+    }
+  }
+  // reconstruct: upper += g, lower += -+ B^H g
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    cx<R> l0, l1;
+    bh_mul<MU, R>(g[0][a], g[1][a], l0, l1);
+    acc.s[a] += g[0][a];
+    acc.s[3 + a] += g[1][a];
+    if (FWD) { acc.s[6 + a] -= l0; acc.s[9 + a] -= l1; }
+    else     { acc.s[6 + a] += l0; acc.s[9 + a] += l1; }
+  }
+}
+
+template <int MU, typename R, typename LT>
+DEV void hop_mu(const LT* __restrict__ links, const cx<R>* __restrict__ x, long V, long site, int coord, int L,
+                long stride, Spinor<R>& acc) {
+  const long fwd = (coord == L - 1) ? site - (long)(L - 1) * stride : site + stride;
+  const long bwd = (coord == 0) ? site + (long)(L - 1) * stride : site - stride;
+  Spinor<R> p;
+  load_spinor<R>(x, fwd, p);
+  hop<MU, true, R, LT>(links, V, site, p, acc);
+  load_spinor<R>(x, bwd, p);
+  hop<MU, false, R, LT>(links, V, bwd, p, acc);
+}
+
+template <typename R, typename LT>
+__global__ void __launch_bounds__(128) wilson_kernel(const LT* __restrict__ links, int Lx, int Ly, int Lz, int Lt,
+                                                    double diag_a, const c128* __restrict__ sigma,
+                                                    const cx<R>* __restrict__ X, long ldx, cx<R>* __restrict__ Y,
+                                                    long ldy, const cx<R>* __restrict__ B, long ldb,
+                                                    const int* __restrict__ run, int run_stride) {
+  const long V = (long)Lx * Ly * Lz * Lt;
+  const long site = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (site >= V) return;
+  if (run && !run[(long)c * run_stride]) return;
+  const cx<R>* x = X + c * ldx;
+  long q = site;
+  const int ix = (int)(q % Lx); q /= Lx;
+  const int iy = (int)(q % Ly); q /= Ly;
+  const int iz = (int)(q % Lz);
+  const int it = (int)(q / Lz);
+  Spinor<R> acc;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) acc.s[i] = {0, 0};
+  hop_mu<0, R, LT>(links, x, V, site, ix, Lx, 1, acc);
+  hop_mu<1, R, LT>(links, x, V, site, iy, Ly, (long)Lx, acc);
+  hop_mu<2, R, LT>(links, x, V, site, iz, Lz, (long)Lx * Ly, acc);
+  hop_mu<3, R, LT>(links, x, V, site, it, Lt, (long)Lx * Ly * Lz, acc);
+  // y = (a - sigma_c) x - H x   [ or b - that ]
+  Spinor<R> p;
+  load_spinor<R>(x, site, p);
+  const c128 sg = sigma ? sigma[c] : c128{0.0, 0.0};
+  const cx<R> dg = {(R)(diag_a - sg.x), (R)(-sg.y)};
+  cx<R>* y = Y + c * ldy + site * 12;
+  const cx<R>* b = B ? B + c * ldb + site * 12 : nullptr;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    cx<R> v = dg * p.s[i] - acc.s[i];
+    if (b) v = b[i] - v;
+    y[i] = v;
+  }
+}
+
+}  // namespace
+
+template <typename R>
+static void op_apply_impl(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, const cx<R>* X, long ldx,
+                          cx<R>* Y, long ldy, const cx<R>* B, long ldb, const int* run, int run_stride) {
+  if (ncol <= 0) return;
+  if (A->kind == OP_CSR) {
+    dim3 grid((unsigned)((A->n + 255) / 256), (unsigned)ncol);
+    if (std::is_same<R, double>::value) {
+      csr_kernel<double, c128><<<grid, 256, 0, ctx->stream>>>(
+          A->n, A->rowptr, A->col, A->vals128, sigma, (const c128*)X, ldx, (c128*)Y, ldy, (const c128*)B, ldb, run,
+          run_stride);
+    } else {
+      csr_kernel<float, c64><<<grid, 256, 0, ctx->stream>>>(A->n, A->rowptr, A->col, A->vals64, sigma,
+                                                             (const c64*)X, ldx, (c64*)Y, ldy, (const c64*)B, ldb,
+                                                             run, run_stride);
+    }
+    GDR_LAUNCHED(ctx);
+  } else {
+    dim3 grid((unsigned)((A->V + 127) / 128), (unsigned)ncol);
+    const int* d = A->dims;
+    if (std::is_same<R, double>::value) {
+      wilson_kernel<double, c128><<<grid, 128, 0, ctx->stream>>>(A->links128, d[0], d[1], d[2], d[3], A->diag_a,
+                                                                 sigma, (const c128*)X, ldx, (c128*)Y, ldy,
+                                                                 (const c128*)B, ldb, run, run_stride);
+    } else if (A->store == GDR_LINK_BF16) {
+      wilson_kernel<float, __nv_bfloat162><<<grid, 128, 0, ctx->stream>>>(
+          A->links16, d[0], d[1], d[2], d[3], A->diag_a, sigma, (const c64*)X, ldx, (c64*)Y, ldy, (const c64*)B, ldb,
+          run, run_stride);
+    } else {
+      wilson_kernel<float, c64><<<grid, 128, 0, ctx->stream>>>(A->links64, d[0], d[1], d[2], d[3], A->diag_a, sigma,
+                                                               (const c64*)X, ldx, (c64*)Y, ldy, (const c64*)B, ldb,
+                                                               run, run_stride);
+    }
+    GDR_LAUNCHED(ctx);
+  }
+}
+
+void op_apply_skip(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, const c128* X, long ldx, c128* Y,
+                   long ldy, const c128* B, long ldb, const int* run, int run_stride) {
+  op_apply_impl<double>(ctx, A, ncol, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride);
+}
+void op_apply_skip(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, const c64* X, long ldx, c64* Y,
+                   long ldy, const c64* B, long ldb, const int* run, int run_stride) {
+  op_apply_impl<float>(ctx, A, ncol, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride);
+}
+
+template <typename R>
+void op_apply(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, const cx<R>* X, long ldx, cx<R>* Y,
+              long ldy, const cx<R>* B, long ldb) {
+  op_apply_skip(ctx, A, ncol, sigma, X, ldx, Y, ldy, B, ldb, nullptr, 0);
+}
+template void op_apply<double>(gdr_ctx*, const gdr_op*, int, const c128*, const c128*, long, c128*, long, const c128*,
+                               long);
+template void op_apply<float>(gdr_ctx*, const gdr_op*, int, const c128*, const c64*, long, c64*, long, const c64*,
+                              long);
+
+// ------------------------------------------------------ operator creation
+
+namespace {
+__global__ void links_soa_kernel(const c128* __restrict__ in, long V, c128* o128, c64* o64, __nv_bfloat162* o16) {
+  // in: [mu][V][9] (AoS, API layout) -> out [mu][e][V]
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= 4 * V * 9) return;
+  const long mu = t / (V * 9);
+  const long rem = t % (V * 9);
+  const long site = rem / 9;
+  const int e = (int)(rem % 9);
+  const c128 u = in[t];
+  const long o = (mu * 9 + e) * V + site;
+  o128[o] = u;
+  if (o64) o64[o] = to64(u);
+  if (o16) o16[o] = __floats2bfloat162_rn((float)u.x, (float)u.y);
+}
+__global__ void vals_to64_kernel(const c128* __restrict__ in, long n, c64* out) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t < n) out[t] = to64(in[t]);
+}
+}  // namespace
+
+void op_build_csr(gdr_ctx* ctx, gdr_op* op, const int* rowptr, const int* col, const double* vals) {
+  GDR_CUDA(cudaMalloc(&op->rowptr, (op->n + 1) * sizeof(int)));
+  GDR_CUDA(cudaMalloc(&op->col, std::max<long>(op->nnz, 1) * sizeof(int)));
+  GDR_CUDA(cudaMalloc(&op->vals128, std::max<long>(op->nnz, 1) * sizeof(c128)));
+  GDR_CUDA(cudaMalloc(&op->vals64, std::max<long>(op->nnz, 1) * sizeof(c64)));
+  GDR_CUDA(cudaMemcpyAsync(op->rowptr, rowptr, (op->n + 1) * sizeof(int), cudaMemcpyDeviceToDevice, ctx->stream));
+  if (op->nnz > 0) {
+    GDR_CUDA(cudaMemcpyAsync(op->col, col, op->nnz * sizeof(int), cudaMemcpyDeviceToDevice, ctx->stream));
+    GDR_CUDA(cudaMemcpyAsync(op->vals128, vals, op->nnz * sizeof(c128), cudaMemcpyDeviceToDevice, ctx->stream));
+    vals_to64_kernel<<<(unsigned)((op->nnz + 255) / 256), 256, 0, ctx->stream>>>(op->vals128, op->nnz, op->vals64);
+    GDR_LAUNCHED(ctx);
+  }
+  GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+
+void op_build_wilson(gdr_ctx* ctx, gdr_op* op, const double* links) {
+  const long nl = 4 * op->V * 9;
+  GDR_CUDA(cudaMalloc(&op->links128, nl * sizeof(c128)));
+  if (op->store == GDR_LINK_BF16) {
+    GDR_CUDA(cudaMalloc(&op->links16, nl * sizeof(__nv_bfloat162)));
+  } else {
+    GDR_CUDA(cudaMalloc(&op->links64, nl * sizeof(c64)));
+  }
+  links_soa_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, ctx->stream>>>((const c128*)links, op->V, op->links128,
+                                                                          op->links64, op->links16);
+  GDR_LAUNCHED(ctx);
+  GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+}

@@ -1,0 +1,679 @@
+// Solver drivers (host code + small kernels).
+//
+//  dr_sh      GMRES-DR(m,k)-Sh for one right-hand side (Sec. 3, algorithm
+//             "GMRES-DR-Sh"): each cycle extends the recurrence, solves the
+//             reduced problems of every shift, restarts with k harmonic Ritz
+//             vectors and updates all solutions in one pass over the basis.
+//  proj_batch GMRES(m_p)-Proj(k)-Sh (Sec. 4) on a batch of columns in lockstep:
+//             Minres projection over the kept V_k, then one GMRES(m_p)-Sh
+//             cycle per column; every column has its own Krylov basis but the
+//             matvec is one multi-column launch.
+//  solve      Sec. 4 pipeline (Example 5 order) + correction phase, FP64 true
+//             residuals, and (MIXED) iterative refinement of every (shift, rhs)
+//             pair by batched single-shift Proj solves, with an FP64 cleanup.
+//
+// One cycle is a fixed sequence of kernels on the context stream; it is
+// captured once into a CUDA graph and replayed.  The host reads one small
+// status block per cycle.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <functional>
+#include <type_traits>
+
+#include "kernels.cuh"
+#include "solver.cuh"
+
+namespace {
+
+__global__ void init_cols_kernel(ColState* st, int ncol, const double* bn2, const double* tolv, const int* mask,
+                                 int ns, int* sact, c128* beta, c128* gamma, double* norms) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncol) return;
+  const double bn = sqrt(bn2[c]);
+  ColState s = {};
+  s.run = 0;
+  s.active = (mask ? mask[c] : 1) && bn > 0 && isfinite(bn);
+  s.bnorm = bn;
+  s.tol = tolv[c];
+  s.rnorm = bn;
+  s.conv = s.active ? 0 : 1;
+  st[c] = s;
+  for (int i = 0; i < ns; ++i) {
+    sact[(long)c * ns + i] = 1;
+    beta[(long)c * ns + i] = {1, 0};
+    if (gamma) gamma[(long)c * ns + i] = {0, 0};
+    norms[(long)c * ns + i] = bn;
+  }
+}
+
+__global__ void set_run_kernel(ColState* st, int ncol) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < ncol) st[c].run = st[c].active;
+}
+
+// normalise V[:, j] of every column with ||.||^2 in nrm2[c]
+template <typename R>
+__global__ void normalize_kernel(cx<R>* V, long ldv, long vcs, int j, long n, const double* nrm2, const ColState* st) {
+  const int c = blockIdx.y;
+  if (st && !st[c].active) return;
+  const double nn = nrm2[c];
+  if (!(nn > 0)) return;
+  const R s = (R)(1.0 / sqrt(nn));
+  cx<R>* v = V + c * vcs + (long)j * ldv;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) v[i] = s * v[i];
+}
+
+// s_i <- s_i / (1 - gamma_i) for i >= 1 (extra right-hand side correction)
+__global__ void extra_scale_kernel(long n, int ns, const c128* gam, c128* S, long lds) {
+  const int i = blockIdx.y + 1;
+  const c128 g = gam[i];
+  const c128 one_minus = {1.0 - g.x, -g.y};
+  const double d = one_minus.x * one_minus.x + one_minus.y * one_minus.y;
+  const c128 f = {one_minus.x / d, -one_minus.y / d};
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < n; r += (long)gridDim.x * blockDim.x)
+    S[(long)i * lds + r] = f * S[(long)i * lds + r];
+}
+
+// X[:, j*ns + i] += gam[j*ns + i] * S[:, i] for i >= 1, every rhs j of the batch
+__global__ void correct_kernel(long n, int ns, const c128* gam, const c128* S, long lds, c128* X, long ldx) {
+  const int p = blockIdx.y;  // pair index j*ns + i
+  const int i = p % ns;
+  if (i == 0) return;
+  const c128 g = gam[p];
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < n; r += (long)gridDim.x * blockDim.x)
+    X[(long)p * ldx + r] += g * S[(long)i * lds + r];
+}
+
+unsigned grid1(gdr_ctx* ctx, long n) {
+  long g = (n + 255) / 256;
+  long cap = (long)ctx->num_sms * 8;
+  return (unsigned)std::max(1L, std::min(g, cap));
+}
+
+struct Graph {
+  cudaGraphExec_t exec = nullptr;
+  long nodes = 0;
+  ~Graph() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
+void run_cycle(gdr_ctx* ctx, bool use_graph, Graph& g, const std::function<void()>& enqueue) {
+  if (!use_graph) {
+    enqueue();
+    return;
+  }
+  if (!g.exec) {
+    const long before = ctx->launches;
+    GDR_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    try {
+      enqueue();
+    } catch (...) {
+      cudaGraph_t gg;
+      cudaStreamEndCapture(ctx->stream, &gg);
+      if (gg) cudaGraphDestroy(gg);
+      throw;
+    }
+    cudaGraph_t gg;
+    GDR_CUDA(cudaStreamEndCapture(ctx->stream, &gg));
+    GDR_CUDA(cudaGraphInstantiate(&g.exec, gg, 0));
+    GDR_CUDA(cudaGraphDestroy(gg));
+    g.nodes = ctx->launches - before;
+    ctx->launches = before;
+  }
+  GDR_CUDA(cudaGraphLaunch(g.exec, ctx->stream));
+  ctx->launches += g.nodes;
+}
+
+template <typename R>
+int nblk_for(gdr_ctx* ctx, long n) {
+  const long units = (n * (long)sizeof(cx<R>) + 15) / 16;
+  long g = (units + 255) / 256;
+  g = std::min<long>(g, 2L * ctx->num_sms);
+  return (int)std::max<long>(g, 1);
+}
+
+// Allocate a batch of `ncol` Krylov spaces of size m (workspace names prefixed by tag).
+template <typename R>
+Batch<R> make_batch(gdr_ctx* ctx, const std::string& tag, long n, int ncol, int m, int ns, int hmin = 0) {
+  Batch<R> b;
+  b.ncol = ncol;
+  b.n = n;
+  b.m = m;
+  b.ns = ns;
+  b.ldv = pad_ld(n);
+  b.vcs = b.ldv * (m + 1);
+  b.V = ctx->get<cx<R>>(tag + ".V", (size_t)b.vcs * ncol);
+  b.wcs = b.ldv;
+  b.W = ctx->get<cx<R>>(tag + ".W", (size_t)b.wcs * ncol);
+  b.H = ctx->get<c128>(tag + ".H", (size_t)(m + 1) * m * ncol);
+  b.cvec = ctx->get<c128>(tag + ".c", (size_t)(m + 1) * ncol);
+  b.h1 = ctx->get<c128>(tag + ".h1", (size_t)(m + 2) * ncol);
+  b.h2 = ctx->get<c128>(tag + ".h2", (size_t)(m + 2) * ncol);
+  b.nblk = nblk_for<R>(ctx, n);
+  b.pstride = (long)b.nblk * std::max(m + 2, hmin);
+  b.part = ctx->get<c128>(tag + ".part", (size_t)b.pstride * ncol + 64);
+  b.cnt = ctx->get<unsigned>(tag + ".cnt", (size_t)4 * ncol);
+  GDR_CUDA(cudaMemsetAsync(b.cnt, 0, sizeof(unsigned) * 4 * ncol, ctx->stream));
+  b.st = ctx->get<ColState>(tag + ".st", (size_t)ncol);
+  b.sigma = ctx->get<c128>(tag + ".sigma", (size_t)ns * ncol);
+  ctx->get<double>("start_rn2", (size_t)ncol + 4);  // used inside captured cycles: allocate now
+  return b;
+}
+
+struct Shifted {  // per-column shift bookkeeping
+  int* sact;
+  c128* beta;
+  c128* gamma;
+  double* norms;
+};
+
+Shifted make_shifted(gdr_ctx* ctx, const std::string& tag, int ncol, int ns) {
+  Shifted s;
+  s.sact = ctx->get<int>(tag + ".sact", (size_t)ncol * ns);
+  s.beta = ctx->get<c128>(tag + ".beta", (size_t)ncol * ns);
+  s.gamma = ctx->get<c128>(tag + ".gamma", (size_t)ncol * ns);
+  s.norms = ctx->get<double>(tag + ".norms", (size_t)ncol * ns);
+  return s;
+}
+
+template <typename R>
+void reorth_column(gdr_ctx* ctx, const Batch<R>& b, int j, double* nrm2) {
+  // classical Gram-Schmidt twice of v_j against v_0..v_{j-1}, then normalise
+  cx<R>* vj = b.V + (long)j * b.ldv;
+  gs_dot<R>(ctx, b, j, vj, b.vcs, b.h1, false);
+  gs_update<R>(ctx, b, j, vj, b.vcs, b.h1, false);
+  gs_dot<R>(ctx, b, j, vj, b.vcs, b.h1, false);
+  gs_update<R>(ctx, b, j, vj, b.vcs, b.h1, false);
+  norms2<cx<R>>(ctx, b.n, b.ncol, vj, b.vcs, nrm2, b.part, b.nblk, b.cnt);
+  dim3 g(grid1(ctx, b.n), (unsigned)b.ncol);
+  normalize_kernel<R><<<g, 256, 0, ctx->stream>>>(b.V, b.ldv, b.vcs, j, b.n, nrm2, b.st);
+  GDR_LAUNCHED(ctx);
+}
+
+std::vector<ColState> read_states(gdr_ctx* ctx, const ColState* st, int ncol) {
+  ColState* h = static_cast<ColState*>(ctx->host_status(sizeof(ColState) * ncol));
+  GDR_CUDA(cudaMemcpyAsync(h, st, sizeof(ColState) * ncol, cudaMemcpyDeviceToHost, ctx->stream));
+  GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+  return std::vector<ColState>(h, h + ncol);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- GMRES-DR-Sh
+
+template <typename R>
+DrResult dr_sh(gdr_ctx* ctx, const gdr_op* A, const cx<R>* b_in, const std::vector<c128>& sigma, int m, int k,
+               double tol, long max_mvps, int max_cycles, c128* X, long ldx, bool use_graph) {
+  const long n = A->n;
+  const int ns = (int)sigma.size();
+  Batch<R> b = make_batch<R>(ctx, "dr", n, 1, m, ns);
+  Shifted sh = make_shifted(ctx, "dr", 1, ns);
+  GDR_CUDA(cudaMemcpyAsync(b.sigma, sigma.data(), sizeof(c128) * ns, cudaMemcpyHostToDevice, ctx->stream));
+  const int ldc = m + 1;
+  const int ncf = k + 1 + ns + 1;
+  DenseCycle d{};
+  d.ncol = 1; d.m = m; d.k = k; d.ns = ns;
+  d.H = b.H; d.cvec = b.cvec; d.sigma = b.sigma;
+  d.beta = sh.beta; d.norms = sh.norms; d.sact = sh.sact;
+  d.Cf = ctx->get<c128>("dr.Cf", (size_t)ldc * ncf); d.ldc = ldc; d.ccs = (long)ldc * ncf;
+  d.s = ctx->get<c128>("dr.s", (size_t)(m + 1));
+  d.Pk = ctx->get<c128>("dr.Pk", (size_t)(m + 1) * std::max(k, 1));
+  d.Hk = ctx->get<c128>("dr.Hk", (size_t)(k + 1) * std::max(k, 1));
+  d.ck = ctx->get<c128>("dr.ck", (size_t)(k + 1));
+  d.theta = ctx->get<c128>("dr.theta", (size_t)m);
+  d.scratch_per_col = (long)2 * ((long)m * m + 2L * m * std::max(k, 1) + 64);
+  d.scratch = ctx->get<double>("dr.scratch", (size_t)d.scratch_per_col);
+  d.st = b.st;
+  d.want_r = (k == 0);  // GMRES(m): restart from the residual vector r = V_{m+1} s
+  cx<R>* rres = ctx->get<cx<R>>("dr.r", (size_t)b.ldv);
+  double* bn2 = ctx->get<double>("dr.bn2", 4);
+  double* tolv = ctx->get<double>("dr.tol", 4);
+  double* rn2 = ctx->get<double>("start_rn2", 4);
+  (void)rn2;
+  GDR_CUDA(cudaMemcpyAsync(tolv, &tol, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  norms2<cx<R>>(ctx, n, 1, b_in, 0, bn2, b.part, b.nblk, b.cnt);
+  init_cols_kernel<<<1, 32, 0, ctx->stream>>>(b.st, 1, bn2, tolv, nullptr, ns, sh.sact, sh.beta, sh.gamma, sh.norms);
+  GDR_LAUNCHED(ctx);
+  start_cycle<R>(ctx, b, b_in, 0);
+
+  Graph g_first, g_next;
+  DrResult res;
+  res.k_eff = k;
+  int j0 = 0;
+  for (;;) {
+    const int jstart = j0;
+    auto enqueue = [&]() {
+      set_run_kernel<<<1, 32, 0, ctx->stream>>>(b.st, 1);
+      GDR_LAUNCHED(ctx);
+      for (int j = jstart; j < m; ++j) arnoldi_step<R>(ctx, A, b, j);
+      dense_cycle(ctx, d);
+      // restart (V_{k+1} <- V_{m+1} P_{k+1}) fused with x_i += V_m d_i
+      combine<R>(ctx, n, 1, b.V, b.ldv, b.vcs, m + 1, d.Cf, ldc, d.ccs, k > 0 ? k + 1 : 0, ns, k > 0 ? 0 : 1, X, ldx,
+                 (long)ns * ldx, rres, 0, b.st);
+      if (k > 0) reorth_column<R>(ctx, b, k, bn2 + 1);
+      cycle_finish(ctx, d, b.H, b.cvec);
+    };
+    run_cycle(ctx, use_graph, jstart == 0 ? g_first : g_next, enqueue);
+    const ColState st = read_states(ctx, b.st, 1)[0];
+    res.cycles++;
+    res.mvps += st.broke ? (st.m_eff - jstart) : (m - jstart);
+    if (st.nan) { res.status = GDR_ENAN; break; }
+    if (st.err) { res.status = (gdr_status)st.err; break; }
+    if (st.conv) { res.status = GDR_OK; res.broke = st.broke; break; }
+    if (res.mvps >= max_mvps || (max_cycles > 0 && res.cycles >= max_cycles)) { res.status = GDR_ENOCONV; break; }
+    j0 = k;
+    if (k == 0) start_cycle<R>(ctx, b, rres, 0);
+  }
+  res.V = b.V;
+  res.ldv = b.ldv;
+  res.Hk = d.Hk;
+  res.valid_defl = (k > 0) && !res.broke && res.status != GDR_ENAN && res.status != GDR_EBREAKDOWN;
+  std::vector<double> nr(ns);
+  GDR_CUDA(cudaMemcpyAsync(nr.data(), sh.norms, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->stream));
+  GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+  res.norms = nr;
+  return res;
+}
+
+// ------------------------------------------------- GMRES(m_p)-Proj(k)-Sh
+
+template <typename R>
+ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool use_graph) {
+  const long n = A->n;
+  const int ncol = job.ncol, ns = job.ns, mp = job.m_p, k = job.k;
+  Batch<R> b = make_batch<R>(ctx, "pj", n, ncol, mp, ns, k + 2);
+  Shifted sh = make_shifted(ctx, "pj", ncol, ns);
+  GDR_CUDA(cudaMemcpyAsync(b.sigma, job.sigma.data(), sizeof(c128) * ns * ncol, cudaMemcpyHostToDevice,
+                           ctx->stream));
+  // residual vectors r_c (the batch's own copy of the right-hand sides)
+  const long ldr = pad_ld(n);
+  cx<R>* r = ctx->get<cx<R>>("pj.r", (size_t)ldr * ncol);
+  GDR_CUDA(cudaMemcpy2DAsync(r, ldr * sizeof(cx<R>), job.rhs, job.ldrhs * sizeof(cx<R>), n * sizeof(cx<R>), ncol,
+                             cudaMemcpyDeviceToDevice, ctx->stream));
+  double* bn2 = ctx->get<double>("pj.bn2", (size_t)ncol + 4);
+  double* tolv = ctx->get<double>("pj.tol", (size_t)ncol);
+  int* mask = ctx->get<int>("pj.mask", (size_t)ncol);
+  double* nrm2 = ctx->get<double>("pj.nrm2", (size_t)ncol);
+  GDR_CUDA(cudaMemcpyAsync(tolv, job.tol.data(), sizeof(double) * ncol, cudaMemcpyHostToDevice, ctx->stream));
+  std::vector<int> mk(ncol, 1);
+  if (!job.mask.empty()) mk = job.mask;
+  GDR_CUDA(cudaMemcpyAsync(mask, mk.data(), sizeof(int) * ncol, cudaMemcpyHostToDevice, ctx->stream));
+  norms2<cx<R>>(ctx, n, ncol, r, ldr, bn2, b.part, b.nblk, b.cnt);
+  init_cols_kernel<<<(ncol + 31) / 32, 32, 0, ctx->stream>>>(b.st, ncol, bn2, tolv, mask, ns, sh.sact, sh.beta,
+                                                              sh.gamma, sh.norms);
+  GDR_LAUNCHED(ctx);
+  // projection: shared deflation basis (vcs = 0)
+  Batch<R> bd = b;
+  bd.V = const_cast<cx<R>*>(job.Vd);
+  bd.ldv = job.ldvd;
+  bd.vcs = 0;
+  bd.m = k;
+  c128* cproj = ctx->get<c128>("pj.cproj", (size_t)(k + 2) * ncol);
+  c128* Cp = ctx->get<c128>("pj.Cp", (size_t)(k + 1) * (ns + 1) * ncol);
+  // GMRES-Sh dense step
+  const int ldc = mp + 1;
+  DenseCycle d{};
+  d.ncol = ncol; d.m = mp; d.k = 0; d.ns = ns;
+  d.H = b.H; d.cvec = b.cvec; d.sigma = b.sigma;
+  d.beta = sh.beta; d.norms = sh.norms; d.sact = sh.sact;
+  d.Cf = ctx->get<c128>("pj.Cf", (size_t)ldc * (ns + 1) * ncol); d.ldc = ldc; d.ccs = (long)ldc * (ns + 1);
+  d.s = ctx->get<c128>("pj.s", (size_t)(mp + 1) * ncol);
+  d.Pk = d.Hk = d.ck = nullptr;
+  d.theta = nullptr;
+  d.scratch = nullptr;
+  d.scratch_per_col = 0;
+  d.st = b.st;
+  d.want_r = true;
+
+  Graph gr;
+  ProjResult res;
+  res.mvps.assign(ncol, 0);
+  res.converged.assign(ncol, 0);
+  std::vector<int> done(ncol, 0);
+  auto enqueue = [&]() {
+    set_run_kernel<<<(ncol + 31) / 32, 32, 0, ctx->stream>>>(b.st, ncol);
+    GDR_LAUNCHED(ctx);
+    if (k > 0 && job.project) {
+      // steps 3-4: Minres projection over V_k; c = V_{k+1}^H r
+      gs_dot<R>(ctx, bd, k + 1, r, ldr, cproj, false);
+      dense_projection(ctx, ncol, k, ns, job.Hk, cproj, b.sigma, sh.beta, sh.sact, sh.gamma, Cp, (long)(k + 1) * (ns + 1),
+                       nullptr, 0, b.st);
+      // x_i += V_k d_i, r -= V_{k+1} (Hbar_k - sigma_1 Ibar) d_1
+      combine<R>(ctx, n, ncol, bd.V, bd.ldv, 0, k + 1, Cp, k + 1, (long)(k + 1) * (ns + 1), 0, ns, 2, job.X, job.ldx,
+                 job.xcs, r, ldr, b.st);
+    }
+    // step 5: one GMRES(m_p)-Sh cycle on r
+    start_cycle<R>(ctx, b, r, ldr);
+    for (int j = 0; j < mp; ++j) arnoldi_step<R>(ctx, A, b, j);
+    dense_cycle(ctx, d);
+    combine<R>(ctx, n, ncol, b.V, b.ldv, b.vcs, mp + 1, d.Cf, ldc, d.ccs, 0, ns, 1, job.X, job.ldx, job.xcs, r, ldr,
+               b.st);
+    cycle_finish(ctx, d, b.H, b.cvec);
+  };
+  for (;;) {
+    run_cycle(ctx, use_graph, gr, enqueue);
+    std::vector<ColState> st = read_states(ctx, b.st, ncol);
+    res.cycles++;
+    bool any_active = false;
+    bool cap = false;
+    for (int c = 0; c < ncol; ++c) {
+      if (done[c] || !mk[c]) continue;
+      res.mvps[c] += st[c].broke ? st[c].m_eff : mp;
+      if (st[c].nan) res.status = GDR_ENAN;
+      else if (st[c].err && res.status == GDR_OK) res.status = (gdr_status)st[c].err;
+      if (st[c].conv) res.converged[c] = 1;
+      if (st[c].active) any_active = true;
+      else done[c] = 1;
+      if (res.mvps[c] >= job.max_mvps) cap = true;
+    }
+    if (!any_active) break;
+    if (cap) {
+      if (res.status == GDR_OK) res.status = GDR_ENOCONV;
+      break;
+    }
+  }
+  res.gamma.resize((size_t)ncol * ns);
+  GDR_CUDA(cudaMemcpyAsync(res.gamma.data(), sh.gamma, sizeof(c128) * ncol * ns, cudaMemcpyDeviceToHost, ctx->stream));
+  GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+  return res;
+}
+
+// --------------------------------------------------------- FP64 residuals
+
+// R[:, j*ns + i] = B[:, j] - (A - sigma_i I) X[:, j*ns + i]; relres[p] = ||R_p|| / ||b_j||
+void true_residuals(gdr_ctx* ctx, const gdr_op* A, int ns, const c128* sigma_dev, int nrhs, const c128* B, long ldb,
+                    const c128* X, long ldx, c128* R, long ldr, std::vector<double>& relres,
+                    const std::vector<double>& bnorm) {
+  const long n = A->n;
+  for (int j = 0; j < nrhs; ++j)
+    op_apply<double>(ctx, A, ns, sigma_dev, X + (long)j * ns * ldx, ldx, R + (long)j * ns * ldr, ldr, B + j * ldb, 0);
+  const int np = ns * nrhs;
+  const int nblk = (int)std::min<long>((n + 255) / 256, 2L * ctx->num_sms);
+  c128* part = ctx->get<c128>("res.part", (size_t)nblk * np + 64);
+  unsigned* cnt = ctx->get<unsigned>("res.cnt", (size_t)4 * np);
+  double* out = ctx->get<double>("res.out", (size_t)np);
+  GDR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * 4 * np, ctx->stream));
+  norms2<c128>(ctx, n, np, R, ldr, out, part, nblk, cnt);
+  std::vector<double> h(np);
+  GDR_CUDA(cudaMemcpyAsync(h.data(), out, sizeof(double) * np, cudaMemcpyDeviceToHost, ctx->stream));
+  GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+  relres.resize(np);
+  for (int p = 0; p < np; ++p) relres[p] = std::sqrt(h[p]) / (bnorm[p / ns] > 0 ? bnorm[p / ns] : 1.0);
+}
+
+// ------------------------------------------------------------ the pipeline
+
+template <typename R>
+static void to_inner(gdr_ctx* ctx, long n, int cols, const c128* in, long ldi, cx<R>* out, long ldo) {
+  if (std::is_same<R, double>::value)
+    copy128(ctx, n, cols, in, ldi, reinterpret_cast<c128*>(out), ldo);
+  else
+    cvt_128_to_64(ctx, n, cols, in, ldi, reinterpret_cast<c64*>(out), ldo);
+}
+
+template <typename R>
+gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>& sigma, int nrhs, const c128* B,
+                          long ldb, c128* X, long ldx, const gdr_params& p, gdr_defl** defl_out, gdr_report& rep) {
+  const long n = A->n;
+  const int ns = (int)sigma.size();
+  const bool mixed = std::is_same<R, float>::value;
+  const bool use_graph = !(p.flags & GDR_FLAG_NO_GRAPH);
+  const int m = p.m, k = p.k, mp = p.m_proj > 0 ? p.m_proj : p.m - p.k;
+  const long ld = pad_ld(n);
+  gdr_status status = GDR_OK;
+  auto worst = [&](gdr_status s) {
+    if (s != GDR_OK && (status == GDR_OK || status == GDR_ENOCONV)) status = s;
+  };
+  GDR_CUDA(cudaMemsetAsync(X, 0, sizeof(c128) * ldx * ns * nrhs, ctx->stream));
+  c128* sig_dev = ctx->get<c128>("pl.sigma", (size_t)ns);
+  GDR_CUDA(cudaMemcpyAsync(sig_dev, sigma.data(), sizeof(c128) * ns, cudaMemcpyHostToDevice, ctx->stream));
+  // ||b_j||
+  std::vector<double> bnorm(nrhs);
+  {
+    const int nblk = (int)std::min<long>((n + 255) / 256, 2L * ctx->num_sms);
+    c128* part = ctx->get<c128>("pl.part", (size_t)nblk * nrhs + 64);
+    unsigned* cnt = ctx->get<unsigned>("pl.cnt", (size_t)4 * nrhs);
+    double* out = ctx->get<double>("pl.bn", (size_t)nrhs);
+    GDR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * 4 * nrhs, ctx->stream));
+    norms2<c128>(ctx, n, nrhs, B, ldb, out, part, nblk, cnt);
+    GDR_CUDA(cudaMemcpyAsync(bnorm.data(), out, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+    GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (auto& v : bnorm) v = std::sqrt(v);
+  }
+  // ---- RHS 1: GMRES-DR(m,k)-Sh
+  cx<R>* bin = ctx->get<cx<R>>("pl.bin", (size_t)ld);
+  to_inner<R>(ctx, n, 1, B, ldb, bin, ld);
+  const double tol1 = mixed ? std::max(p.tol, p.inner_tol) : p.tol;
+  DrResult dr = dr_sh<R>(ctx, A, bin, sigma, m, k, tol1, p.max_mvps, p.max_cycles, X, ldx, use_graph);
+  rep.mvps_rhs1 = dr.mvps;
+  rep.cycles_rhs1 = dr.cycles;
+  if (dr.status == GDR_ENOCONV && p.max_cycles > 0) {
+    worst(GDR_ENOCONV);
+  } else {
+    worst(dr.status);
+  }
+  const int kd = dr.valid_defl ? k : 0;
+  // the kept pair, FP64 copy of V_{k+1}
+  c128* V128 = nullptr;
+  if (kd > 0) {
+    V128 = ctx->get<c128>("pl.V128", (size_t)ld * (kd + 1));
+    if (mixed)
+      cvt_64_to_128(ctx, n, kd + 1, reinterpret_cast<const c64*>(dr.V), dr.ldv, V128, ld);
+    else
+      copy128(ctx, n, kd + 1, reinterpret_cast<const c128*>(dr.V), dr.ldv, V128, ld);
+  }
+  if (defl_out && kd > 0) {
+    gdr_defl* df = new gdr_defl();
+    df->ctx = ctx;
+    df->n = n;
+    df->ldv = ld;
+    df->k = kd;
+    df->prec = mixed ? GDR_PREC_MIXED : GDR_PREC_FP64;
+    GDR_CUDA(cudaMalloc(&df->V128, sizeof(c128) * ld * (kd + 1)));
+    GDR_CUDA(cudaMalloc(&df->V, sizeof(cx<R>) * ld * (kd + 1)));
+    GDR_CUDA(cudaMalloc(&df->Hk, sizeof(c128) * (kd + 1) * kd));
+    GDR_CUDA(cudaMemcpyAsync(df->V128, V128, sizeof(c128) * ld * (kd + 1), cudaMemcpyDeviceToDevice, ctx->stream));
+    GDR_CUDA(cudaMemcpy2DAsync(df->V, ld * sizeof(cx<R>), dr.V, dr.ldv * sizeof(cx<R>), n * sizeof(cx<R>), kd + 1,
+                               cudaMemcpyDeviceToDevice, ctx->stream));
+    GDR_CUDA(cudaMemcpyAsync(df->Hk, dr.Hk, sizeof(c128) * (kd + 1) * kd, cudaMemcpyDeviceToDevice, ctx->stream));
+    df->Hk_host.resize((size_t)(kd + 1) * kd);
+    GDR_CUDA(cudaMemcpyAsync(df->Hk_host.data(), dr.Hk, sizeof(c128) * (kd + 1) * kd, cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+    *defl_out = df;
+  }
+  // keep the deflation pair in a buffer the later stages do not overwrite
+  cx<R>* Vd = nullptr;
+  c128* Hkd = nullptr;
+  if (kd > 0) {
+    Vd = ctx->get<cx<R>>("pl.Vd", (size_t)ld * (kd + 1));
+    Hkd = ctx->get<c128>("pl.Hkd", (size_t)(kd + 1) * kd);
+    GDR_CUDA(cudaMemcpy2DAsync(Vd, ld * sizeof(cx<R>), dr.V, dr.ldv * sizeof(cx<R>), n * sizeof(cx<R>), kd + 1,
+                               cudaMemcpyDeviceToDevice, ctx->stream));
+    GDR_CUDA(cudaMemcpyAsync(Hkd, dr.Hk, sizeof(c128) * (kd + 1) * kd, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  const bool project = kd > 0 && !(p.flags & GDR_FLAG_NO_PROJ);
+  // ---- extra right-hand side v_{k+1} and RHS 2..nrhs: GMRES(m_p)-Proj(k)-Sh
+  if (nrhs > 1) {
+    const int ncol = nrhs;  // column 0: v_{k+1} (if deflating), columns 1..: b^2..b^nrhs
+    cx<R>* rhs = ctx->get<cx<R>>("pl.rhs", (size_t)ld * ncol);
+    c128* XP = ctx->get<c128>("pl.XP", (size_t)ld * ns * ncol);  // slot 0: S (extra), slot j: X for rhs j+1
+    GDR_CUDA(cudaMemsetAsync(XP, 0, sizeof(c128) * ld * ns * ncol, ctx->stream));
+    if (project)
+      GDR_CUDA(cudaMemcpyAsync(rhs, Vd + (long)kd * ld, sizeof(cx<R>) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    to_inner<R>(ctx, n, nrhs - 1, B + ldb, ldb, rhs + ld, ld);
+    std::vector<int> mask(ncol, 1);
+    if (!project) mask[0] = 0;
+    const bool seq = (p.flags & GDR_FLAG_SEQUENTIAL) != 0;
+    const int first = project ? 0 : 1;
+    auto run_cols = [&](int c0, int cn) {
+      ProjJob<R> job;
+      job.ncol = cn;
+      job.ns = ns;
+      job.m_p = mp;
+      job.k = kd;
+      job.project = project;
+      job.Vd = Vd;
+      job.ldvd = ld;
+      job.Hk = Hkd;
+      job.rhs = rhs + (long)c0 * ld;
+      job.ldrhs = ld;
+      job.sigma.resize((size_t)cn * ns);
+      for (int c = 0; c < cn; ++c)
+        for (int i = 0; i < ns; ++i) job.sigma[(size_t)c * ns + i] = sigma[i];
+      job.tol.resize(cn);
+      for (int c = 0; c < cn; ++c)
+        job.tol[c] = (c0 + c == 0) ? p.extra_tol : (mixed ? std::max(p.tol, p.inner_tol) : p.tol);
+      job.mask.assign(mask.begin() + c0, mask.begin() + c0 + cn);
+      job.X = XP + (long)c0 * ns * ld;
+      job.ldx = ld;
+      job.xcs = (long)ns * ld;
+      job.max_mvps = p.max_mvps;
+      ProjResult pr = proj_batch<R>(ctx, A, job, use_graph && !seq);
+      for (int c = 0; c < cn; ++c) {
+        if (c0 + c == 0) rep.mvps_extra += pr.mvps[c];
+        else rep.mvps_proj += pr.mvps[c];
+      }
+      worst(pr.status);
+    };
+    if (seq) {
+      for (int c = first; c < ncol; ++c) run_cols(c, 1);
+    } else {
+      run_cols(first, ncol - first);
+    }
+    // ---- correction phase (FP64): extra solutions s_i = s~_i / (1 - gamma_i), then x_i^j += gamma_i^j s_i
+    c128* RP = ctx->get<c128>("pl.RP", (size_t)ld * ns * ncol);
+    if (project && ns > 1) {
+      std::vector<double> rr;
+      std::vector<double> one(1, 1.0);
+      const c128* v128 = V128 + (long)kd * ld;
+      // extra system residuals v - (A - sigma_i) s~_i
+      true_residuals(ctx, A, ns, sig_dev, 1, v128, ld, XP, ld, RP, ld, rr, one);
+      c128* gam = ctx->get<c128>("pl.gam", (size_t)ns * ncol);
+      const int nblk = (int)std::min<long>((n + 255) / 256, 2L * ctx->num_sms);
+      c128* part = ctx->get<c128>("pl.dpart", (size_t)nblk * ns * ncol + 64);
+      unsigned* cnt = ctx->get<unsigned>("pl.dcnt", (size_t)4 * ns * ncol);
+      GDR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * 4 * ns * ncol, ctx->stream));
+      dots128(ctx, n, ns, v128, 0, RP, ld, gam, part, nblk, cnt);
+      dim3 ge(grid1(ctx, n), (unsigned)(ns - 1));
+      extra_scale_kernel<<<ge, 256, 0, ctx->stream>>>(n, ns, gam, XP, ld);
+      GDR_LAUNCHED(ctx);
+      // RHS 2..: residuals, gamma_i^j = v^H r_i^j, corrections
+      std::vector<double> bn2(bnorm.begin() + 1, bnorm.end());
+      true_residuals(ctx, A, ns, sig_dev, nrhs - 1, B + ldb, ldb, XP + (long)ns * ld, ld, RP + (long)ns * ld, ld, rr,
+                     bn2);
+      dots128(ctx, n, ns * (nrhs - 1), v128, 0, RP + (long)ns * ld, ld, gam + ns, part, nblk, cnt);
+      dim3 gc(grid1(ctx, n), (unsigned)(ns * (nrhs - 1)));
+      correct_kernel<<<gc, 256, 0, ctx->stream>>>(n, ns, gam + ns, XP, ld, XP + (long)ns * ld, ld);
+      GDR_LAUNCHED(ctx);
+    }
+    // results of RHS 2.. into X
+    for (int j = 1; j < nrhs; ++j)
+      copy128(ctx, n, ns, XP + (long)j * ns * ld, ld, X + (long)j * ns * ldx, ldx);
+  }
+  // ---- FP64 true residuals, refinement (MIXED) and cleanup of every (shift, rhs) pair
+  const int np = ns * nrhs;
+  c128* Rres = ctx->get<c128>("pl.Rres", (size_t)ld * np);
+  std::vector<double> relres;
+  true_residuals(ctx, A, ns, sig_dev, nrhs, B, ldb, X, ldx, Rres, ld, relres, bnorm);
+  rep.resid_cols += np;
+  const int max_pass = (p.flags & GDR_FLAG_NO_REFINE) ? -1 : std::max(0, p.refine_max);
+  for (int pass = 0; pass <= max_pass; ++pass) {
+    std::vector<int> mask(np, 0);
+    int nact = 0;
+    for (int q = 0; q < np; ++q)
+      if (!(relres[q] <= p.tol)) {
+        mask[q] = 1;
+        ++nact;
+      }
+    if (nact == 0) break;
+    const bool cleanup = (pass == max_pass) || !mixed;
+    rep.refine_passes++;
+    if (cleanup) rep.pairs_cleaned += nact;
+    // chunk the pairs by memory
+    size_t freeb = 0, totb = 0;
+    GDR_CUDA(cudaMemGetInfo(&freeb, &totb));
+    const size_t elem = cleanup ? sizeof(c128) : sizeof(cx<R>);
+    const size_t per_col = elem * (size_t)ld * (mp + 4) + 4096;
+    int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)np, (freeb / 2) / per_col));
+    for (int q0 = 0; q0 < np; q0 += chunk) {
+      const int cn = std::min(chunk, np - q0);
+      bool any = false;
+      for (int q = q0; q < q0 + cn; ++q) any = any || mask[q];
+      if (!any) continue;
+      std::vector<double> tolc(cn);
+      std::vector<int> mk(mask.begin() + q0, mask.begin() + q0 + cn);
+      for (int c = 0; c < cn; ++c) {
+        const int q = q0 + c;
+        // relative to the residual column: reach tol * ||b|| with margin
+        tolc[c] = std::max(0.3 * p.tol / std::max(relres[q], 1e-300), cleanup ? 0.0 : p.inner_tol);
+        tolc[c] = std::min(tolc[c], 0.5);
+      }
+      auto run_refine = [&](auto tag) {
+        using RR = decltype(tag);
+        cx<RR>* rin = ctx->get<cx<RR>>("rf.rin", (size_t)ld * cn);
+        to_inner<RR>(ctx, n, cn, Rres + (long)q0 * ld, ld, rin, ld);
+        ProjJob<RR> job;
+        job.ncol = cn;
+        job.ns = 1;
+        job.m_p = mp;
+        job.k = kd;
+        job.project = project;
+        cx<RR>* vd = nullptr;
+        if (kd > 0) {
+          if (std::is_same<RR, R>::value) {
+            vd = reinterpret_cast<cx<RR>*>(Vd);
+          } else {  // FP64 cleanup after a complex64 solve: FP64 copy of the kept basis
+            vd = reinterpret_cast<cx<RR>*>(V128);
+          }
+        }
+        job.Vd = vd;
+        job.ldvd = ld;
+        job.Hk = Hkd;
+        job.rhs = rin;
+        job.ldrhs = ld;
+        job.sigma.resize(cn);
+        for (int c = 0; c < cn; ++c) job.sigma[c] = sigma[(q0 + c) % ns];
+        job.tol = tolc;
+        job.mask = mk;
+        job.X = X + (long)q0 * ldx;
+        job.ldx = ldx;
+        job.xcs = ldx;
+        job.max_mvps = p.max_mvps;
+        ProjResult pr = proj_batch<RR>(ctx, A, job, use_graph);
+        for (int c = 0; c < cn; ++c) rep.mvps_refine += pr.mvps[c];
+        if (pr.status == GDR_ENAN || pr.status == GDR_ECUDA) worst(pr.status);
+      };
+      if (cleanup)
+        run_refine(double{});
+      else
+        run_refine(R{});
+    }
+    true_residuals(ctx, A, ns, sig_dev, nrhs, B, ldb, X, ldx, Rres, ld, relres, bnorm);
+    rep.resid_cols += np;
+  }
+  double mx = 0;
+  for (double v : relres) mx = std::max(mx, v);
+  rep.max_relres = mx;
+  if (!(mx <= p.tol)) {
+    if (status == GDR_OK) status = GDR_ENOCONV;
+  } else if (status == GDR_ENOCONV && p.max_cycles <= 0) {
+    status = GDR_OK;  // a stage stopped at its cap but refinement reached tol
+  }
+  return status;
+}
+
+// ------------------------------------------------------------ instances
+
+template DrResult dr_sh<float>(gdr_ctx*, const gdr_op*, const c64*, const std::vector<c128>&, int, int, double, long,
+                               int, c128*, long, bool);
+template DrResult dr_sh<double>(gdr_ctx*, const gdr_op*, const c128*, const std::vector<c128>&, int, int, double, long,
+                                int, c128*, long, bool);
+template ProjResult proj_batch<float>(gdr_ctx*, const gdr_op*, const ProjJob<float>&, bool);
+template ProjResult proj_batch<double>(gdr_ctx*, const gdr_op*, const ProjJob<double>&, bool);
+template gdr_status solve_pipeline<float>(gdr_ctx*, const gdr_op*, const std::vector<c128>&, int, const c128*, long,
+                                          c128*, long, const gdr_params&, gdr_defl**, gdr_report&);
+template gdr_status solve_pipeline<double>(gdr_ctx*, const gdr_op*, const std::vector<c128>&, int, const c128*, long,
+                                           c128*, long, const gdr_params&, gdr_defl**, gdr_report&);

@@ -1,0 +1,60 @@
+// Solver driver interfaces (host side).
+#pragma once
+#include <vector>
+
+#include "kernels.cuh"
+
+struct DrResult {
+  gdr_status status = GDR_OK;
+  long mvps = 0;
+  long cycles = 0;
+  int k_eff = 0;
+  bool broke = false;
+  bool valid_defl = false;
+  void* V = nullptr;       // basis buffer (vector precision); V[:, 0:k+1] is the kept V_{k+1}
+  long ldv = 0;
+  c128* Hk = nullptr;      // kept Hbar_k ((k+1) x k) on the device
+  std::vector<double> norms;
+};
+
+// A batch of columns for GMRES(m_p)-Proj(k)-Sh.
+template <typename R>
+struct ProjJob {
+  int ncol = 0, ns = 1, m_p = 0, k = 0;
+  bool project = true;
+  const cx<R>* Vd = nullptr;   // kept V_{k+1} (n x (k+1), ld ldvd), shared by all columns
+  long ldvd = 0;
+  const c128* Hk = nullptr;    // kept Hbar_k ((k+1) x k)
+  const cx<R>* rhs = nullptr;  // right-hand sides, column c at rhs + c*ldrhs
+  long ldrhs = 0;
+  std::vector<c128> sigma;     // ncol x ns, sigma[c*ns] the base shift of column c
+  std::vector<double> tol;     // relative tolerance per column
+  std::vector<int> mask;       // columns to solve (empty: all)
+  c128* X = nullptr;           // X + c*xcs + i*ldx accumulates shift i of column c (FP64)
+  long ldx = 0, xcs = 0;
+  long max_mvps = 100000;
+};
+
+struct ProjResult {
+  gdr_status status = GDR_OK;
+  long cycles = 0;
+  std::vector<long> mvps;
+  std::vector<int> converged;
+  std::vector<c128> gamma;     // accumulated gamma_i per column (eq. keyder2), diagnostic
+};
+
+template <typename R>
+DrResult dr_sh(gdr_ctx* ctx, const gdr_op* A, const cx<R>* b, const std::vector<c128>& sigma, int m, int k, double tol,
+               long max_mvps, int max_cycles, c128* X, long ldx, bool use_graph);
+
+template <typename R>
+ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool use_graph);
+
+void true_residuals(gdr_ctx* ctx, const gdr_op* A, int ns, const c128* sigma_dev, int nrhs, const c128* B, long ldb,
+                    const c128* X, long ldx, c128* R, long ldr, std::vector<double>& relres,
+                    const std::vector<double>& bnorm);
+
+template <typename R>
+gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>& sigma, int nrhs, const c128* B,
+                          long ldb, c128* X, long ldx, const gdr_params& p, gdr_defl** defl_out, gdr_report& rep);
+
