@@ -386,7 +386,7 @@ gdr_status gdr_dense_gmres_sh(gdr_ctx* ctx, int m, int ns, const double* Hbar, c
     GDR_REQUIRE(m >= 1 && m <= GDR_MAX_M && ns >= 1, "bad sizes");
     GDR_REQUIRE(Hbar && c && sigma && beta && D && s && beta_new && norms, "null argument");
     DenseCycle d{};
-    d.ncol = 1; d.m = m; d.k = 0; d.ns = ns;
+    d.ncol = 1; d.m = m; d.k = 0; d.ns = ns; d.kfull = m + 1;  // general Hbar
     c128* H = ctx->get<c128>("dstep.H", (size_t)(m + 1) * m);
     c128* cv = ctx->get<c128>("dstep.c", (size_t)(m + 1));
     c128* sg = ctx->get<c128>("dstep.sigma", (size_t)ns);
@@ -427,7 +427,7 @@ gdr_status gdr_dense_restart(gdr_ctx* ctx, int m, int k, const double* sigma1, c
     GDR_REQUIRE(m >= 2 && m <= GDR_MAX_M && k >= 1 && k < m, "bad sizes");
     GDR_REQUIRE(sigma1 && Hbar && s && theta && P && Hk && ck, "null argument");
     DenseCycle d{};
-    d.ncol = 1; d.m = m; d.k = k; d.ns = 1;
+    d.ncol = 1; d.m = m; d.k = k; d.ns = 1; d.kfull = m + 1;  // general Hbar
     c128* sg = ctx->get<c128>("rstep.sigma", 1);
     GDR_CUDA(cudaMemcpyAsync(sg, sigma1, sizeof(c128), cudaMemcpyHostToDevice, ctx->stream));
     d.H = reinterpret_cast<const c128*>(Hbar);

@@ -69,12 +69,18 @@ DEV double block_sum(double v, Sh& sh) {
 
 // Householder QR of the first `cols` columns of A (rows x ntot, column-major,
 // lda), reflectors applied to all ntot columns.  R in the upper triangle, v
-// below the diagonal, tau[j].
-DEV void cta_qr(c128* A, int lda, int rows, int cols, int ntot, c128* tau, Sh& sh) {
+// below the diagonal, tau[j].  Column j of the factored part is known to be
+// zero below row max(j+1, kfull) (the GMRES-DR recurrence matrix is upper
+// Hessenberg except for a full leading block; kfull >= rows means dense), so
+// reflector j spans rows j..last(j) only.
+DEV int qr_last(int j, int rows, int kfull) { return min(rows - 1, max(j + 1, kfull)); }
+
+DEV void cta_qr(c128* A, int lda, int rows, int cols, int ntot, c128* tau, Sh& sh, int kfull) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int j = 0; j < cols && j < rows; ++j) {
+    const int last = qr_last(j, rows, kfull);
     double s = 0;
-    for (int i = j + 1 + threadIdx.x; i < rows; i += DT) s += norm2(A[i + (long)j * lda]);
+    for (int i = j + 1 + threadIdx.x; i <= last; i += DT) s += norm2(A[i + (long)j * lda]);
     s = block_sum(s, sh);
     if (threadIdx.x == 0) {
       const c128 alpha = A[j + (long)j * lda];
@@ -91,24 +97,50 @@ DEV void cta_qr(c128* A, int lda, int rows, int cols, int ntot, c128* tau, Sh& s
     const c128 tj = tau[j];
     if (tj.x == 0.0 && tj.y == 0.0) continue;  // uniform across the CTA
     const c128 scal = sh.bc[0];
-    for (int i = j + 1 + threadIdx.x; i < rows; i += DT) A[i + (long)j * lda] = A[i + (long)j * lda] * scal;
+    for (int i = j + 1 + threadIdx.x; i <= last; i += DT) A[i + (long)j * lda] = A[i + (long)j * lda] * scal;
     __syncthreads();
     const c128 ct = conj(tj);
-    for (int cc = j + 1 + warp; cc < ntot; cc += DT / 32) {
-      c128* col = A + (long)cc * lda;
-      c128 w = {0, 0};
-      for (int i = j + lane; i < rows; i += 32) {
-        const c128 vi = (i == j) ? c128{1, 0} : A[i + (long)j * lda];
-        w += cmulc(vi, col[i]);
+    if (last - j < 32) {
+      // short reflector: one thread per column
+      for (int cc = j + 1 + threadIdx.x; cc < ntot; cc += DT) {
+        c128* col = A + (long)cc * lda;
+        c128 w = col[j];
+        for (int i = j + 1; i <= last; ++i) w += cmulc(A[i + (long)j * lda], col[i]);
+        const c128 f = ct * w;
+        col[j] -= f;
+        for (int i = j + 1; i <= last; ++i) col[i] -= A[i + (long)j * lda] * f;
       }
-      w = warp_sum_c(w);
-      const c128 f = ct * w;
-      for (int i = j + lane; i < rows; i += 32) {
-        const c128 vi = (i == j) ? c128{1, 0} : A[i + (long)j * lda];
-        col[i] -= vi * f;
+    } else {
+      for (int cc = j + 1 + warp; cc < ntot; cc += DT / 32) {
+        c128* col = A + (long)cc * lda;
+        c128 w = {0, 0};
+        for (int i = j + lane; i <= last; i += 32) {
+          const c128 vi = (i == j) ? c128{1, 0} : A[i + (long)j * lda];
+          w += cmulc(vi, col[i]);
+        }
+        w = warp_sum_c(w);
+        const c128 f = ct * w;
+        for (int i = j + lane; i <= last; i += 32) {
+          const c128 vi = (i == j) ? c128{1, 0} : A[i + (long)j * lda];
+          col[i] -= vi * f;
+        }
       }
     }
     __syncthreads();
+  }
+}
+
+// y <- Q y for the reflectors of cta_qr (applied in reverse order), one thread.
+DEV void apply_q_serial(const c128* A, int lda, int rows, int cols, const c128* tau, c128* y, int kfull) {
+  for (int j = min(cols, rows) - 1; j >= 0; --j) {
+    const c128 tj = tau[j];
+    if (tj.x == 0.0 && tj.y == 0.0) continue;
+    const int last = qr_last(j, rows, kfull);
+    c128 w = y[j];
+    for (int i = j + 1; i <= last; ++i) w += cmulc(A[i + (long)j * lda], y[i]);
+    const c128 f = tj * w;
+    y[j] -= f;
+    for (int i = j + 1; i <= last; ++i) y[i] -= A[i + (long)j * lda] * f;
   }
 }
 
@@ -166,7 +198,7 @@ DEV void base_ls(const DenseCycle& d, int c, c128* A, Sh& sh) {
   c128* y = tau + (me + 1);
   if (threadIdx.x == 0) sh.ibc[0] = 0;
   __syncthreads();
-  cta_qr(A, lda, rows, me, me + 1, tau, sh);
+  cta_qr(A, lda, rows, me, me + 1, tau, sh, d.kfull);
   for (int i = threadIdx.x; i < me; i += DT) y[i] = A[i + (long)me * lda];
   __syncthreads();
   if (!cta_backsolve(A, lda, me, y, sh)) set_err(st, GDR_EBREAKDOWN);
@@ -226,7 +258,7 @@ DEV void shift_solve(const DenseCycle& d, int c, int i, c128* A, Sh& sh) {
   c128* y = tau + (me + 1);
   if (threadIdx.x == 0) sh.ibc[0] = 0;
   __syncthreads();
-  cta_qr(A, lda, rows, me, me + 2, tau, sh);
+  cta_qr(A, lda, rows, me, me + 2, tau, sh, d.kfull);
   c128 bnew = {0, 0};
   if (!broke) {
     const c128 qc = A[me + (long)me * lda], qs = A[me + (long)(me + 1) * lda];
@@ -248,6 +280,26 @@ DEV void shift_solve(const DenseCycle& d, int c, int i, c128* A, Sh& sh) {
 }
 
 // --------------------------------------------------- harmonic Ritz (D1)
+
+// Givens rotation U = [[cs, sn], [-conj(sn), cs]] with U [x; y] = [r; 0]; rot = {cs, Re sn, Im sn}
+DEV void givens(c128 x, c128 y, double* rot) {
+  const double ax2 = norm2(x), ay2 = norm2(y);
+  if (ay2 == 0.0) {
+    rot[0] = 1.0; rot[1] = 0.0; rot[2] = 0.0;
+  } else if (ax2 == 0.0) {
+    const double inv = 1.0 / sqrt(ay2);
+    rot[0] = 0.0; rot[1] = y.x * inv; rot[2] = -y.y * inv;
+  } else {
+    const double ax = sqrt(ax2);
+    const double inv_r = 1.0 / sqrt(ax2 + ay2);
+    const double inv_ax = 1.0 / ax;
+    rot[0] = ax * inv_r;
+    // sn = (x / |x|) conj(y) / r
+    const c128 ph = {x.x * inv_ax, x.y * inv_ax};
+    const c128 sn = ph * c128{y.x * inv_r, -y.y * inv_r};
+    rot[1] = sn.x; rot[2] = sn.y;
+  }
+}
 
 // selection order of the "smallest" harmonic Ritz values
 DEV bool before(c128 a, c128 b) {
@@ -274,21 +326,28 @@ DEV void harmonic_ritz(const DenseCycle& d, int c, c128* T, Sh& sh) {
   c128* tau = f + m;                             // m
   c128* theta = tau + m;                         // m
   int* sel = reinterpret_cast<int*>(theta + m);  // k
-  // 1) f = H^{-H} hrow^H: QR of [H^H | hrow^H] (H = Hhat[0:m, 0:m], hrow = Hhat[m, :])
+  // 1) f = H^{-H} hrow^H with H = Hhat[0:m, 0:m] = Q R:  R^H z = hrow^H, f = Q z
   const int lda = m;
-  for (int t = threadIdx.x; t < m * m; t += DT) {
-    const int i = t % m, j = t / m;
-    c128 v = H[j + (long)i * (m + 1)];  // (H^H)_{ij} = conj(H_{ji})
-    if (i == j) v -= sig;
-    T[i + (long)j * lda] = conj(v);
-  }
-  for (int i = threadIdx.x; i < m; i += DT) T[i + (long)m * lda] = conj(H[m + (long)i * (m + 1)]);
+  load_shifted(T, lda, H, m + 1, m, m, sig);
   if (threadIdx.x == 0) sh.ibc[0] = 0;
   __syncthreads();
-  cta_qr(T, lda, m, m, m + 1, tau, sh);
-  for (int i = threadIdx.x; i < m; i += DT) f[i] = T[i + (long)m * lda];
+  cta_qr(T, lda, m, m, m, tau, sh, d.kfull);
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < m; ++j) {  // forward substitution with R^H
+      c128 v = conj(H[m + (long)j * (m + 1)]);
+      for (int i = 0; i < j; ++i) v -= cmulc(T[i + (long)j * lda], f[i]);
+      const c128 rjj = T[j + (long)j * lda];
+      if (rjj.x == 0.0 && rjj.y == 0.0) {
+        sh.ibc[0] = 1;
+        f[j] = {0, 0};
+      } else {
+        f[j] = cdiv(v, conj(rjj));
+      }
+    }
+    apply_q_serial(T, lda, m, m, tau, f, d.kfull);
+  }
   __syncthreads();
-  if (!cta_backsolve(T, lda, m, f, sh)) set_err(st, GDR_EBREAKDOWN);
+  if (sh.ibc[0]) set_err(st, GDR_EBREAKDOWN);
   // 2) M = H + f hrow
   for (int t = threadIdx.x; t < m * m; t += DT) {
     const int i = t % m, j = t / m;
@@ -392,88 +451,81 @@ DEV void harmonic_ritz(const DenseCycle& d, int c, c128* T, Sh& sh) {
     __syncthreads();
   }
   const double smallnum = fmax(hnorm * EPS, 1e-300);
+  const double eps2 = EPS * EPS;
+  double* rot = reinterpret_cast<double*>(&sh.bc[1]);  // rot[0] = cs, (rot[1], rot[2]) = sn
   int hi = m - 1, its = 0, total = 0;
   bool failed = false;
   while (hi >= 0) {
     if (threadIdx.x == 0) {
+      // deflation: |h_{l,l-1}|^2 <= eps^2 (|h_{l-1,l-1}|^2 + |h_{l,l}|^2)
       int l = hi;
       for (; l > 0; --l) {
-        const double sub = cabs_(T[l + (long)(l - 1) * lda]);
-        double ref = cabs_(T[l - 1 + (long)(l - 1) * lda]) + cabs_(T[l + (long)l * lda]);
-        if (ref == 0.0) ref = hnorm;
-        if (sub <= EPS * ref || sub <= smallnum * 1e-3) {
+        const double sub = norm2(T[l + (long)(l - 1) * lda]);
+        double ref = norm2(T[l - 1 + (long)(l - 1) * lda]) + norm2(T[l + (long)l * lda]);
+        if (ref == 0.0) ref = hnorm * hnorm;
+        if (sub <= eps2 * ref || sub <= smallnum * smallnum * 1e-6) {
           T[l + (long)(l - 1) * lda] = {0, 0};
           break;
         }
       }
       sh.ibc[1] = l;
+      if (l < hi) {
+        // Wilkinson shift of the trailing 2x2 block (exceptional shift every 10th sweep),
+        // then the first rotation of the sweep
+        ++its;
+        c128 mu;
+        const c128 a = T[hi - 1 + (long)(hi - 1) * lda], b = T[hi - 1 + (long)hi * lda];
+        const c128 cc = T[hi + (long)(hi - 1) * lda], dd = T[hi + (long)hi * lda];
+        if (its % 10 == 0) {
+          mu = dd + c128{fabs(cc.x) + fabs(cc.y), 0};
+        } else {
+          const c128 half = 0.5 * (a - dd);
+          const c128 disc = csqrt_(half * half + b * cc);
+          const c128 l1 = dd + half + disc, l2 = dd + half - disc;
+          mu = (norm2(l1 - dd) <= norm2(l2 - dd)) ? l1 : l2;
+        }
+        givens(T[l + (long)l * lda] - mu, T[l + 1 + (long)l * lda], rot);
+      } else {
+        its = 0;
+      }
     }
     __syncthreads();
     const int lo = sh.ibc[1];
     if (lo == hi) {
       --hi;
-      its = 0;
       continue;
     }
-    ++its;
     ++total;
     if (total > 40 * m) {
       failed = true;
       break;
     }
-    // Wilkinson shift of the trailing 2x2 block (exceptional shift every 10 iterations)
-    c128 mu;
-    {
-      const c128 a = T[hi - 1 + (long)(hi - 1) * lda], b = T[hi - 1 + (long)hi * lda];
-      const c128 cc = T[hi + (long)(hi - 1) * lda], dd = T[hi + (long)hi * lda];
-      if (its % 10 == 0) {
-        mu = dd + c128{fabs(cc.x) + fabs(cc.y), 0};
-      } else {
-        const c128 half = 0.5 * (a - dd);
-        const c128 disc = csqrt_(half * half + b * cc);
-        const c128 l1 = dd + half + disc, l2 = dd + half - disc;
-        mu = (cabs_(l1 - dd) <= cabs_(l2 - dd)) ? l1 : l2;
-      }
-    }
     for (int kk = lo; kk < hi; ++kk) {
-      c128 x, y;
-      if (kk == lo) {
-        x = T[lo + (long)lo * lda] - mu;
-        y = T[lo + 1 + (long)lo * lda];
-      } else {
-        x = T[kk + (long)(kk - 1) * lda];
-        y = T[kk + 1 + (long)(kk - 1) * lda];
-      }
-      // U = [[cs, sn], [-conj(sn), cs]] with U [x; y] = [r; 0]
-      double cs;
-      c128 sn;
-      const double ax = cabs_(x), ay = cabs_(y);
-      if (ay == 0.0) {
-        cs = 1.0;
-        sn = {0, 0};
-      } else if (ax == 0.0) {
-        cs = 0.0;
-        sn = {y.x / ay, -y.y / ay};
-      } else {
-        const double r = hypot(ax, ay);
-        cs = ax / r;
-        const c128 ph = {x.x / ax, x.y / ax};
-        sn = ph * c128{y.x / r, -y.y / r};
-      }
-      __syncthreads();
+      const double cs = rot[0];
+      const c128 sn = {rot[1], rot[2]};
       // left: rows kk, kk+1, columns max(kk-1,0)..m-1
       for (int cc = max(kk - 1, 0) + threadIdx.x; cc < m; cc += DT) {
         const c128 a = T[kk + (long)cc * lda], b = T[kk + 1 + (long)cc * lda];
         T[kk + (long)cc * lda] = cs * a + sn * b;
-        T[kk + 1 + (long)cc * lda] = cs * b - conj(sn) * a;
+        T[kk + 1 + (long)cc * lda] = (cc == kk - 1 && kk > lo) ? c128{0, 0} : cs * b - conj(sn) * a;
       }
       __syncthreads();
-      // right: columns kk, kk+1, rows 0..min(kk+2, hi)
+      // right: columns kk, kk+1, rows 0..min(kk+2, hi); the thread of row kk+2 (or kk+1
+      // at the end of the sweep) also does row kk+1 and forms the next rotation
       const int rlast = min(kk + 2, hi);
+      const int owner = (kk + 2 <= hi) ? kk + 2 : kk + 1;
       for (int r = threadIdx.x; r <= rlast; r += DT) {
+        if (r == kk + 1 && owner != kk + 1) continue;
         const c128 a = T[r + (long)kk * lda], b = T[r + (long)(kk + 1) * lda];
         T[r + (long)kk * lda] = cs * a + b * conj(sn);
         T[r + (long)(kk + 1) * lda] = cs * b - a * sn;
+        if (r == owner && owner == kk + 2) {
+          const c128 a1 = T[kk + 1 + (long)kk * lda], b1 = T[kk + 1 + (long)(kk + 1) * lda];
+          const c128 x = cs * a1 + b1 * conj(sn);
+          T[kk + 1 + (long)kk * lda] = x;
+          T[kk + 1 + (long)(kk + 1) * lda] = cs * b1 - a1 * sn;
+          givens(x, T[kk + 2 + (long)kk * lda], rot);
+        }
       }
       if (t < m) {
         c128* zr = Z + (long)t * m;
@@ -481,7 +533,6 @@ DEV void harmonic_ritz(const DenseCycle& d, int c, c128* T, Sh& sh) {
         zr[kk] = cs * a + b * conj(sn);
         zr[kk + 1] = cs * b - a * sn;
       }
-      if (kk > lo && threadIdx.x == 0) T[kk + 1 + (long)(kk - 1) * lda] = {0, 0};
       __syncthreads();
     }
   }
@@ -763,7 +814,7 @@ __global__ void __launch_bounds__(DT) dense_proj_kernel(ProjArgs a) {
   for (int r = threadIdx.x; r <= k; r += DT) A[r + (long)k * (k + 1)] = a.cproj[(long)c * (k + 2) + r];
   if (threadIdx.x == 0) sh.ibc[0] = 0;
   __syncthreads();
-  cta_qr(A, k + 1, k + 1, k, k + 1, tau, sh);
+  cta_qr(A, k + 1, k + 1, k, k + 1, tau, sh, k + 1);
   for (int r = threadIdx.x; r < k; r += DT) d1[r] = A[r + (long)k * (k + 1)];
   __syncthreads();
   if (!cta_backsolve(A, k + 1, k, d1, sh)) set_err(st, GDR_EBREAKDOWN);
@@ -791,7 +842,7 @@ __global__ void __launch_bounds__(DT) dense_proj_kernel(ProjArgs a) {
   for (int r = threadIdx.x; r < k; r += DT) A[r + (long)k * k] = bi * t[r];
   if (threadIdx.x == 0) sh.ibc[0] = 0;
   __syncthreads();
-  cta_qr(A, k, k, k, k + 1, tau, sh);
+  cta_qr(A, k, k, k, k + 1, tau, sh, k);
   for (int r = threadIdx.x; r < k; r += DT) y[r] = A[r + (long)k * k];
   __syncthreads();
   if (!cta_backsolve(A, k, k, y, sh)) set_err(st, GDR_EBREAKDOWN);

@@ -105,6 +105,7 @@ void op_build_wilson(gdr_ctx* ctx, gdr_op* op, const double* links);
 //  and when want_r: column k+1+ns = s (the new residual r = V_{m+1} s).
 struct DenseCycle {
   int ncol, m, k, ns;
+  int kfull;  // Hbar is zero below row max(j+1, kfull) in column j (k for GMRES-DR, 0 Hessenberg, m+1 dense)
   const c128* H; const c128* cvec; const c128* sigma;
   c128* beta; double* norms; int* sact;     // per column: ns each
   c128* Cf; int ldc; long ccs;              // coefficient matrices

@@ -80,6 +80,19 @@ DEV void block_reduce(cx<R> (&acc)[NV], c128* out, int nvalid) {
   __syncthreads();
 }
 
+// sum over blocks of the partials p[bk * stride] by one warp (fixed order: lanes
+// stride the blocks, then a shuffle tree), result valid in every lane
+DEV c128 warp_sum_partials(const c128* p, long stride, int lane) {
+  c128 s = {0, 0};
+  for (int bk = lane; bk < (int)gridDim.x; bk += 32) s += ldcg128(p + (long)bk * stride);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    s.x += __shfl_xor_sync(FULL, s.x, off);
+    s.y += __shfl_xor_sync(FULL, s.y, off);
+  }
+  return s;
+}
+
 // true in exactly one block per column: the last one to finish
 DEV bool last_block(unsigned* cnt) {
   __shared__ bool last;
@@ -135,11 +148,9 @@ __global__ void __launch_bounds__(NT) gs_dot_kernel(Batch<R> b, int nv, const cx
   }
   if (!last_block(b.cnt + 4 * c)) return;
   const int tot = nv + (wnorm ? 1 : 0);
-  for (int i = threadIdx.x; i < tot; i += NT) {
-    c128 s = {0, 0};
-    for (int bk = 0; bk < (int)gridDim.x; ++bk) s += ldcg128(part + (long)bk * hstride + i);
-    hout[(long)c * hstride + i] = s;
-  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = warp; i < tot; i += NT / 32) hout[(long)c * hstride + i] = warp_sum_partials(part + i, hstride, lane);
+  __syncthreads();
   if (threadIdx.x == 0) b.cnt[4 * c] = 0;
 }
 
@@ -177,12 +188,8 @@ __global__ void __launch_bounds__(NT) gs_update_kernel(Batch<R> b, int nv, cx<R>
   if (!last_block(b.cnt + 4 * c)) return;
   __shared__ double wn_s;
   if (threadIdx.x < 32) {
-    double s = 0;
-    for (int bk = threadIdx.x; bk < (int)gridDim.x; bk += 32) s += ldcg128(part + (long)bk * hstride).x;
-    // fixed-order warp sum
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(FULL, s, off);
-    if (threadIdx.x == 0) wn_s = sqrt(s);
+    const c128 s = warp_sum_partials(part, hstride, threadIdx.x);
+    if (threadIdx.x == 0) wn_s = sqrt(s.x);
   }
   __syncthreads();
   const double wn = wn_s;
@@ -252,11 +259,12 @@ __global__ void __launch_bounds__(NT) norms2_kernel(long n, const T* __restrict_
   block_reduce<double, 1>(d, part + (long)c * gridDim.x + blockIdx.x, 1);
   (void)a;
   if (!last_block(cnt + 4 * c)) return;
-  if (threadIdx.x == 0) {
-    double t = 0;
-    for (int bk = 0; bk < (int)gridDim.x; ++bk) t += ldcg128(part + (long)c * gridDim.x + bk).x;
-    out[c] = t;
-    cnt[4 * c] = 0;
+  if (threadIdx.x < 32) {
+    const c128 t = warp_sum_partials(part + (long)c * gridDim.x, 1, threadIdx.x);
+    if (threadIdx.x == 0) {
+      out[c] = t.x;
+      cnt[4 * c] = 0;
+    }
   }
 }
 
@@ -270,11 +278,12 @@ __global__ void __launch_bounds__(NT) dots128_kernel(long n, const c128* __restr
   for (long i = blockIdx.x * (long)NT + threadIdx.x; i < n; i += (long)gridDim.x * NT) a[0] += cmulc(uc[i], xc[i]);
   block_reduce<double, 1>(a, part + (long)c * gridDim.x + blockIdx.x, 1);
   if (!last_block(cnt + 4 * c)) return;
-  if (threadIdx.x == 0) {
-    c128 t = {0, 0};
-    for (int bk = 0; bk < (int)gridDim.x; ++bk) t += ldcg128(part + (long)c * gridDim.x + bk);
-    out[c] = t;
-    cnt[4 * c] = 0;
+  if (threadIdx.x < 32) {
+    const c128 t = warp_sum_partials(part + (long)c * gridDim.x, 1, threadIdx.x);
+    if (threadIdx.x == 0) {
+      out[c] = t;
+      cnt[4 * c] = 0;
+    }
   }
 }
 

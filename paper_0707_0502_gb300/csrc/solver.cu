@@ -214,7 +214,7 @@ DrResult dr_sh(gdr_ctx* ctx, const gdr_op* A, const cx<R>* b_in, const std::vect
   const int ldc = m + 1;
   const int ncf = k + 1 + ns + 1;
   DenseCycle d{};
-  d.ncol = 1; d.m = m; d.k = k; d.ns = ns;
+  d.ncol = 1; d.m = m; d.k = k; d.ns = ns; d.kfull = k;
   d.H = b.H; d.cvec = b.cvec; d.sigma = b.sigma;
   d.beta = sh.beta; d.norms = sh.norms; d.sact = sh.sact;
   d.Cf = ctx->get<c128>("dr.Cf", (size_t)ldc * ncf); d.ldc = ldc; d.ccs = (long)ldc * ncf;
@@ -315,7 +315,7 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
   // GMRES-Sh dense step
   const int ldc = mp + 1;
   DenseCycle d{};
-  d.ncol = ncol; d.m = mp; d.k = 0; d.ns = ns;
+  d.ncol = ncol; d.m = mp; d.k = 0; d.ns = ns; d.kfull = 0;
   d.H = b.H; d.cvec = b.cvec; d.sigma = b.sigma;
   d.beta = sh.beta; d.norms = sh.norms; d.sact = sh.sact;
   d.Cf = ctx->get<c128>("pj.Cf", (size_t)ldc * (ns + 1) * ncol); d.ldc = ldc; d.ccs = (long)ldc * (ns + 1);
