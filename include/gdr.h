@@ -173,6 +173,26 @@ gdr_status gdr_dense_gmres_sh(gdr_ctx *ctx, int m, int ns, const double *Hbar, c
                               const double *sigma, const double *beta, double *D, double *s,
                               double *beta_new, double *norms);
 
+/* Allocation-free form of gdr_dense_gmres_sh, with the same arguments and
+ * results.  The paper has no counterpart of this call: it exists for callers
+ * that cannot let the library allocate device memory (code running under an
+ * allocator it does not control, such as a host framework's memory pool or a
+ * fixed device-memory budget, or a latency-critical loop where cudaMalloc and
+ * cudaFree would synchronise the device).  Its workspace is one fixed array
+ * in the library's device image (about 180 KB, present on every device that
+ * loads the library until the process exits), so it never calls cudaMalloc,
+ * cudaFree or an allocating library routine.  Limits: m <= GDR_NOALLOC_MAX_M,
+ * ns <= GDR_NOALLOC_MAX_NS; larger sizes return GDR_EINVAL.  The first call on
+ * a device looks up the array's device address, so make it before any stream
+ * capture.  All calls share the one array, which keeps the last call's
+ * contents: calls that overlap on the GPU race and must be serialised by the
+ * caller.  Synchronises the context stream before returning. */
+#define GDR_NOALLOC_MAX_M 96
+#define GDR_NOALLOC_MAX_NS 16
+gdr_status gdr_dense_gmres_sh_noalloc(gdr_ctx *ctx, int m, int ns, const double *Hbar, const double *c,
+                                      const double *sigma, const double *beta, double *D, double *s,
+                                      double *beta_new, double *norms);
+
 /* GMRES-DR restart (Sec. 2.2): harmonic Ritz pairs of Hhat = Hbar - sigma1 Ibar,
  * k of smallest |theta| (ties: larger Im, then larger Re), P_{k+1} = [orth([G;0]), p],
  * p from s; Hk = P^H Hbar P_k ((k+1) x k), ck = P^H s (k+1).

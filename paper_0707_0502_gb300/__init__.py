@@ -79,6 +79,8 @@ _SIGS = {
     "gdr_defl_destroy": (None, [_P]),
     "gdr_arnoldi_step": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int, _P]),
     "gdr_dense_gmres_sh": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "gdr_dense_gmres_sh_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P,
+                                                  _P]),
     "gdr_dense_restart": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P]),
     "gdr_basis_update": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_long, ctypes.c_int, _P, _P, ctypes.c_int,
                                         ctypes.c_int, _P]),
@@ -243,6 +245,14 @@ def gdr_dense_gmres_sh(ctx, m, sigma, Hbar, c, beta, D, s, beta_new, norms):
     sg = _c128_host(sigma)
     _check(lib().gdr_dense_gmres_sh(ctx, int(m), len(sg), _ptr(Hbar), _ptr(c), sg.ctypes.data, _ptr(beta), _ptr(D),
                                     _ptr(s), _ptr(beta_new), _ptr(norms)), ctx)
+
+
+def gdr_dense_gmres_sh_noalloc(ctx, m, sigma, Hbar, c, beta, D, s, beta_new, norms):
+    """Same as gdr_dense_gmres_sh, with no device allocation inside the library
+    (fixed workspace; m <= 96, ns <= 16; calls must not overlap on the GPU)."""
+    sg = _c128_host(sigma)
+    _check(lib().gdr_dense_gmres_sh_noalloc(ctx, int(m), len(sg), _ptr(Hbar), _ptr(c), sg.ctypes.data, _ptr(beta),
+                                            _ptr(D), _ptr(s), _ptr(beta_new), _ptr(norms)), ctx)
 
 
 def gdr_dense_restart(ctx, m, k, sigma1, Hbar, s, theta, P, Hk, ck):
