@@ -18,6 +18,11 @@
 // convention: H = I - tau v v^H, v_0 = 1, H^H [alpha; x] = [beta; 0], beta real.
 #include "kernels.cuh"
 
+// Phase marks for timing studies; empty in the library build.
+#ifndef GDR_DENSE_MARK
+#define GDR_DENSE_MARK(i, v)
+#endif
+
 namespace {
 
 constexpr int DT = 128;  // threads per dense CTA
@@ -53,6 +58,7 @@ DEV double warp_sum_d(double v) {
 struct Sh {  // small shared scratch of a dense CTA
   double red[DT / 32];
   c128 bc[4];
+  c128 nx[4];  // QR sweep: entries (kk+1, kk), (kk+1, kk+1), (kk+2, kk), (kk+2, kk+1) after the left update
   int ibc[4];
 };
 
@@ -176,6 +182,9 @@ DEV void load_shifted(c128* A, int lda, const c128* H, int ldh, int rows, int co
   }
 }
 
+// odd leading dimension: row-wise accesses of 16-byte elements hit distinct banks
+HD int odd_ld(int rows) { return rows | 1; }
+
 DEV void set_err(ColState* st, int code) {
   if (threadIdx.x == 0) atomicCAS(&st->err, 0, code);
 }
@@ -191,7 +200,7 @@ DEV void base_ls(const DenseCycle& d, int c, c128* A, Sh& sh) {
   const c128* cv = d.cvec + (long)c * (m + 1);
   const c128 sig = d.sigma[(long)c * d.ns];
   const int rows = broke ? me : me + 1;
-  const int lda = rows;
+  const int lda = odd_ld(rows);
   load_shifted(A, lda, H, m + 1, rows, me, sig);
   for (int i = threadIdx.x; i < rows; i += DT) A[i + (long)me * lda] = cv[i];
   c128* tau = A + (long)lda * (me + 1);
@@ -248,7 +257,7 @@ DEV void shift_solve(const DenseCycle& d, int c, int i, c128* A, Sh& sh) {
   const c128 sig = d.sigma[(long)c * d.ns + i];
   const c128 beta = d.beta[(long)c * d.ns + i];
   const int rows = broke ? me : me + 1;
-  const int lda = rows;
+  const int lda = odd_ld(rows);
   load_shifted(A, lda, H, m + 1, rows, me, sig);
   for (int r = threadIdx.x; r < rows; r += DT) {
     A[r + (long)me * lda] = cv[r];
@@ -281,24 +290,42 @@ DEV void shift_solve(const DenseCycle& d, int c, int i, c128* A, Sh& sh) {
 
 // --------------------------------------------------- harmonic Ritz (D1)
 
+// 1/sqrt(a) for a > 0: single-precision estimate, then two Newton steps
+// y <- y (3 - a y^2) / 2 in FP64 (quadratic convergence: ~1e-7 -> 1e-14 -> 1e-16).
+// A normal-range float must hold a; otherwise fall back to the FP64 expression.
+DEV double rsqrt_nr(double a) {
+  if (!(a > 1e-36 && a < 1e36)) return 1.0 / sqrt(a);
+  double y = (double)rsqrtf((float)a);
+  y = y * (1.5 - 0.5 * a * y * y);
+  y = y * (1.5 - 0.5 * a * y * y);
+  return y;
+}
+
 // Givens rotation U = [[cs, sn], [-conj(sn), cs]] with U [x; y] = [r; 0]; rot = {cs, Re sn, Im sn}
 DEV void givens(c128 x, c128 y, double* rot) {
   const double ax2 = norm2(x), ay2 = norm2(y);
   if (ay2 == 0.0) {
     rot[0] = 1.0; rot[1] = 0.0; rot[2] = 0.0;
   } else if (ax2 == 0.0) {
-    const double inv = 1.0 / sqrt(ay2);
+    const double inv = rsqrt_nr(ay2);
     rot[0] = 0.0; rot[1] = y.x * inv; rot[2] = -y.y * inv;
   } else {
-    const double ax = sqrt(ax2);
-    const double inv_r = 1.0 / sqrt(ax2 + ay2);
-    const double inv_ax = 1.0 / ax;
-    rot[0] = ax * inv_r;
+    const double inv_r = rsqrt_nr(ax2 + ay2);
+    const double inv_ax = rsqrt_nr(ax2);
+    rot[0] = ax2 * inv_ax * inv_r;  // |x| / r
     // sn = (x / |x|) conj(y) / r
-    const c128 ph = {x.x * inv_ax, x.y * inv_ax};
-    const c128 sn = ph * c128{y.x * inv_r, -y.y * inv_r};
-    rot[1] = sn.x; rot[2] = sn.y;
+    const double f = inv_ax * inv_r;
+    rot[1] = (x.x * y.x + x.y * y.y) * f;
+    rot[2] = (x.y * y.x - x.x * y.y) * f;
   }
+}
+
+// selection order with precomputed magnitudes
+DEV bool before_m(c128 a, double ma, c128 b, double mb) {
+  const double scale = fmax(ma, mb);
+  if (fabs(ma - mb) > 1e-9 * scale) return ma < mb;
+  if (fabs(a.y - b.y) > 1e-9 * scale) return a.y > b.y;
+  return a.x > b.x;
 }
 
 // selection order of the "smallest" harmonic Ritz values
@@ -322,12 +349,13 @@ DEV void harmonic_ritz(const DenseCycle& d, int c, c128* T, Sh& sh) {
   c128* Z = reinterpret_cast<c128*>(scr);        // m x m, row-major, row t owned by thread t
   c128* Y = Z + (long)m * m;                     // m x k   eigenvectors of T
   c128* G = Y + (long)m * k;                     // m x k   eigenvectors of M
-  c128* f = T + (long)m * (m + 2);               // m
+  const int lda = odd_ld(m);
+  c128* f = T + (long)lda * (m + 2);             // m
   c128* tau = f + m;                             // m
   c128* theta = tau + m;                         // m
   int* sel = reinterpret_cast<int*>(theta + m);  // k
+  GDR_DENSE_MARK(0, 0);
   // 1) f = H^{-H} hrow^H with H = Hhat[0:m, 0:m] = Q R:  R^H z = hrow^H, f = Q z
-  const int lda = m;
   load_shifted(T, lda, H, m + 1, m, m, sig);
   if (threadIdx.x == 0) sh.ibc[0] = 0;
   __syncthreads();
@@ -348,6 +376,7 @@ DEV void harmonic_ritz(const DenseCycle& d, int c, c128* T, Sh& sh) {
   }
   __syncthreads();
   if (sh.ibc[0]) set_err(st, GDR_EBREAKDOWN);
+  GDR_DENSE_MARK(1, 0);
   // 2) M = H + f hrow
   for (int t = threadIdx.x; t < m * m; t += DT) {
     const int i = t % m, j = t / m;
@@ -356,6 +385,7 @@ DEV void harmonic_ritz(const DenseCycle& d, int c, c128* T, Sh& sh) {
     T[i + (long)j * lda] = v + f[i] * H[m + (long)j * (m + 1)];
   }
   __syncthreads();
+  GDR_DENSE_MARK(2, 0);
   // 3) Hessenberg reduction M = Q Hh Q^H, reflectors kept below the subdiagonal
   for (int j = 0; j + 2 < m; ++j) {
     double s = 0;
@@ -411,25 +441,34 @@ DEV void harmonic_ritz(const DenseCycle& d, int c, c128* T, Sh& sh) {
     }
     __syncthreads();
   }
-  // 4) Z = Q = H_0 H_1 ... (rows owned by threads), then clear below the subdiagonal
-  const int t = threadIdx.x;
-  if (t < m) {
-    c128* zr = Z + (long)t * m;
-    for (int j = 0; j < m; ++j) zr[j] = {t == j ? 1.0 : 0.0, 0.0};
-    for (int j = 0; j + 2 < m; ++j) {
-      const c128 tj = tau[j];
-      if (tj.x == 0.0 && tj.y == 0.0) continue;
+  GDR_DENSE_MARK(3, 0);
+  // 4) Z = Q = H_0 H_1 ... : Z <- Z H_j for j = 0.., one warp per row of Z
+  //    (I - tau v v^H applied from the right), then clear below the subdiagonal.
+  //    During the QR sweep row t of Z belongs to thread DT-1-t.
+  const int zrow = DT - 1 - threadIdx.x;  // row of Z owned by this thread in the sweep
+  for (int r = warp; r < m; r += DT / 32) {
+    c128* zr = Z + (long)r * m;
+    for (int i = lane; i < m; i += 32) zr[i] = {r == i ? 1.0 : 0.0, 0.0};
+  }
+  __syncthreads();
+  for (int j = 0; j + 2 < m; ++j) {
+    const c128 tj = tau[j];
+    if (tj.x == 0.0 && tj.y == 0.0) continue;
+    for (int r = warp; r < m; r += DT / 32) {
+      c128* zr = Z + (long)r * m;
       c128 w = {0, 0};
-      for (int i = j + 1; i < m; ++i) {
+      for (int i = j + 1 + lane; i < m; i += 32) {
         const c128 vi = (i == j + 1) ? c128{1, 0} : T[i + (long)j * lda];
         w += zr[i] * vi;
       }
+      w = warp_sum_c(w);
       const c128 fct = tj * w;
-      for (int i = j + 1; i < m; ++i) {
+      for (int i = j + 1 + lane; i < m; i += 32) {
         const c128 vi = (i == j + 1) ? c128{1, 0} : T[i + (long)j * lda];
         zr[i] -= fct * conj(vi);
       }
     }
+    __syncwarp();
   }
   __syncthreads();
   for (int q = threadIdx.x; q < m * m; q += DT) {
@@ -437,6 +476,7 @@ DEV void harmonic_ritz(const DenseCycle& d, int c, c128* T, Sh& sh) {
     if (i > j + 1) T[i + (long)j * lda] = {0, 0};
   }
   __syncthreads();
+  GDR_DENSE_MARK(4, 0);
   // 5) complex single-shift QR to Schur form T = Z^H M Z
   double hnorm = 0;
   for (int q = threadIdx.x; q < m * m; q += DT) hnorm = fmax(hnorm, cabs_(T[q]));
@@ -456,18 +496,27 @@ DEV void harmonic_ritz(const DenseCycle& d, int c, c128* T, Sh& sh) {
   int hi = m - 1, its = 0, total = 0;
   bool failed = false;
   while (hi >= 0) {
-    if (threadIdx.x == 0) {
-      // deflation: |h_{l,l-1}|^2 <= eps^2 (|h_{l-1,l-1}|^2 + |h_{l,l}|^2)
-      int l = hi;
-      for (; l > 0; --l) {
-        const double sub = norm2(T[l + (long)(l - 1) * lda]);
-        double ref = norm2(T[l - 1 + (long)(l - 1) * lda]) + norm2(T[l + (long)l * lda]);
-        if (ref == 0.0) ref = hnorm * hnorm;
-        if (sub <= eps2 * ref || sub <= smallnum * smallnum * 1e-6) {
-          T[l + (long)(l - 1) * lda] = {0, 0};
+    if (warp == 0) {
+      // deflation: the largest l in (0, hi] with |h_{l,l-1}|^2 <= eps^2 (|h_{l-1,l-1}|^2 + |h_{l,l}|^2),
+      // tested 32 subdiagonals at a time from the bottom (uniform result in the warp)
+      int l = 0;
+      for (int top = hi; top > 0; top -= 32) {
+        const int cand = top - lane;
+        bool neg = false;
+        if (cand > 0) {
+          const double sub = norm2(T[cand + (long)(cand - 1) * lda]);
+          double ref = norm2(T[cand - 1 + (long)(cand - 1) * lda]) + norm2(T[cand + (long)cand * lda]);
+          if (ref == 0.0) ref = hnorm * hnorm;
+          neg = (sub <= eps2 * ref || sub <= smallnum * smallnum * 1e-6);
+        }
+        const unsigned bal = __ballot_sync(FULL, neg);
+        if (bal) {
+          l = top - (__ffs(bal) - 1);  // lowest lane = largest candidate
           break;
         }
       }
+      if (lane == 0) {
+      if (l > 0) T[l + (long)(l - 1) * lda] = {0, 0};
       sh.ibc[1] = l;
       if (l < hi) {
         // Wilkinson shift of the trailing 2x2 block (exceptional shift every 10th sweep),
@@ -488,6 +537,7 @@ DEV void harmonic_ritz(const DenseCycle& d, int c, c128* T, Sh& sh) {
       } else {
         its = 0;
       }
+      }
     }
     __syncthreads();
     const int lo = sh.ibc[1];
@@ -506,29 +556,34 @@ DEV void harmonic_ritz(const DenseCycle& d, int c, c128* T, Sh& sh) {
       // left: rows kk, kk+1, columns max(kk-1,0)..m-1
       for (int cc = max(kk - 1, 0) + threadIdx.x; cc < m; cc += DT) {
         const c128 a = T[kk + (long)cc * lda], b = T[kk + 1 + (long)cc * lda];
+        const c128 b_new = (cc == kk - 1 && kk > lo) ? c128{0, 0} : cs * b - conj(sn) * a;
         T[kk + (long)cc * lda] = cs * a + sn * b;
-        T[kk + 1 + (long)cc * lda] = (cc == kk - 1 && kk > lo) ? c128{0, 0} : cs * b - conj(sn) * a;
+        T[kk + 1 + (long)cc * lda] = b_new;
+        if ((cc == kk || cc == kk + 1) && kk + 2 <= hi) {  // inputs of the next rotation
+          sh.nx[cc - kk] = b_new;
+          sh.nx[2 + cc - kk] = T[kk + 2 + (long)cc * lda];
+        }
       }
       __syncthreads();
       // right: columns kk, kk+1, rows 0..min(kk+2, hi); the thread of row kk+2 (or kk+1
       // at the end of the sweep) also does row kk+1 and forms the next rotation
       const int rlast = min(kk + 2, hi);
-      const int owner = (kk + 2 <= hi) ? kk + 2 : kk + 1;
+      // (the owner, a thread with no row of this update, forms the next rotation from
+      //  the entries of rows kk+1, kk+2 saved by the left update)
+      c128 x_next = {0, 0}, y_next = {0, 0};
+      const bool own = (threadIdx.x == DT - 1 - m) && (kk + 2 <= hi);
+      if (own) {
+        x_next = cs * sh.nx[0] + sh.nx[1] * conj(sn);
+        y_next = cs * sh.nx[2] + sh.nx[3] * conj(sn);
+      }
       for (int r = threadIdx.x; r <= rlast; r += DT) {
-        if (r == kk + 1 && owner != kk + 1) continue;
         const c128 a = T[r + (long)kk * lda], b = T[r + (long)(kk + 1) * lda];
         T[r + (long)kk * lda] = cs * a + b * conj(sn);
         T[r + (long)(kk + 1) * lda] = cs * b - a * sn;
-        if (r == owner && owner == kk + 2) {
-          const c128 a1 = T[kk + 1 + (long)kk * lda], b1 = T[kk + 1 + (long)(kk + 1) * lda];
-          const c128 x = cs * a1 + b1 * conj(sn);
-          T[kk + 1 + (long)kk * lda] = x;
-          T[kk + 1 + (long)(kk + 1) * lda] = cs * b1 - a1 * sn;
-          givens(x, T[kk + 2 + (long)kk * lda], rot);
-        }
       }
-      if (t < m) {
-        c128* zr = Z + (long)t * m;
+      if (own) givens(x_next, y_next, rot);
+      if (zrow >= 0 && zrow < m) {
+        c128* zr = Z + (long)zrow * m;
         const c128 a = zr[kk], b = zr[kk + 1];
         zr[kk] = cs * a + b * conj(sn);
         zr[kk + 1] = cs * b - a * sn;
@@ -541,6 +596,7 @@ DEV void harmonic_ritz(const DenseCycle& d, int c, c128* T, Sh& sh) {
     return;
   }
   __syncthreads();
+  GDR_DENSE_MARK(5, 0);
   // 6) eigenvalues and selection of the k smallest
   c128* th = d.theta + (long)c * m;
   for (int i = threadIdx.x; i < m; i += DT) {
@@ -548,21 +604,45 @@ DEV void harmonic_ritz(const DenseCycle& d, int c, c128* T, Sh& sh) {
     th[i] = theta[i];
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    // selection sort in index order (same rule as the definition)
-    unsigned char used[GDR_MAX_M];
-    for (int i = 0; i < m; ++i) used[i] = 0;
+  // k rounds of a warp argmin under `before` (ties: lower index), which picks what
+  // the index-order selection sort picks for a consistent order; |theta| computed once
+  if (warp == 0) {
+    double mag[3];
+    unsigned used = 0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int i = lane + 32 * q;
+      mag[q] = (i < m) ? sqrt(norm2(theta[i])) : 0.0;
+    }
     for (int q = 0; q < k; ++q) {
-      int best = -1;
-      for (int i = 0; i < m; ++i) {
-        if (used[i]) continue;
-        if (best < 0 || before(theta[i], theta[best])) best = i;
+      int bi = -1;
+      double bm = 0.0;
+      c128 bt = {0, 0};
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const int i = lane + 32 * r;
+        if (i >= m || (used >> r & 1u)) continue;
+        if (bi < 0 || before_m(theta[i], mag[r], bt, bm)) { bi = i; bm = mag[r]; bt = theta[i]; }
       }
-      used[best] = 1;
-      sel[q] = best;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const int oi = __shfl_xor_sync(FULL, bi, off);
+        const double om = __shfl_xor_sync(FULL, bm, off);
+        const c128 ot = shfl_xor_c(bt, off);
+        bool take = false;
+        if (oi >= 0) {
+          if (bi < 0) take = true;
+          else if (before_m(ot, om, bt, bm)) take = true;
+          else if (!before_m(bt, bm, ot, om) && oi < bi) take = true;
+        }
+        if (take) { bi = oi; bm = om; bt = ot; }
+      }
+      if (lane == 0) sel[q] = bi;
+      if ((bi & 31) == lane) used |= 1u << (bi >> 5);
     }
   }
   __syncthreads();
+  GDR_DENSE_MARK(6, 0);
   // 7) eigenvectors of T (back substitution, one thread per selected value), Y = m x k
   for (int q = threadIdx.x; q < k; q += DT) {
     const int p = sel[q];
@@ -583,7 +663,9 @@ DEV void harmonic_ritz(const DenseCycle& d, int c, c128* T, Sh& sh) {
     for (int i = 0; i <= p; ++i) y[i] = (1.0 / nn) * y[i];
   }
   __syncthreads();
-  // 8) G = Z Y : thread t owns row t of Z
+  GDR_DENSE_MARK(7, 0);
+  // 8) G = Z Y : thread t computes row t of G (Z is complete after the barrier)
+  const int t = threadIdx.x;
   if (t < m) {
     const c128* zr = Z + (long)t * m;
     for (int q = 0; q < k; ++q) {
@@ -595,6 +677,7 @@ DEV void harmonic_ritz(const DenseCycle& d, int c, c128* T, Sh& sh) {
     }
   }
   __syncthreads();
+  GDR_DENSE_MARK(8, 0);
   // 9) P_k = orth([G; 0]) by classical Gram-Schmidt twice, in T (ld m+1)
   const int ldp = m + 1;
   for (int q = threadIdx.x; q < ldp * k; q += DT) {
@@ -631,6 +714,7 @@ DEV void harmonic_ritz(const DenseCycle& d, int c, c128* T, Sh& sh) {
   }
   c128* Pk = d.Pk + (long)c * ldp * k;
   for (int q = threadIdx.x; q < ldp * k; q += DT) Pk[q] = T[q];
+  GDR_DENSE_MARK(9, total);
 }
 
 // restart completion (D2 block 0): p_{k+1} from s, P into Cf, Hbar_k, c_k
@@ -803,21 +887,22 @@ __global__ void __launch_bounds__(DT) dense_proj_kernel(ProjArgs a) {
     for (int r = threadIdx.x; r <= k; r += DT) Cf[r + (long)i * ldc] = {0, 0};
     return;
   }
-  c128* A = reinterpret_cast<c128*>(smem_raw);  // (k+1) x (k+1)
-  c128* tau = A + (long)(k + 1) * (k + 1);
+  c128* A = reinterpret_cast<c128*>(smem_raw);  // (k+1) x (k+1), odd leading dimension
+  const int la = odd_ld(k + 1);
+  c128* tau = A + (long)la * (k + 1);
   c128* d1 = tau + (k + 1);
   c128* t = d1 + (k + 1);   // (Hbar_k - sigma_1 Ibar) d_1, length k+1
   c128* y = t + (k + 1);
   const c128 s1 = a.sigma[(long)c * a.ns];
   // base: min || c - (Hbar_k - s1 Ibar) d ||
-  load_shifted(A, k + 1, a.Hk, k + 1, k + 1, k, s1);
-  for (int r = threadIdx.x; r <= k; r += DT) A[r + (long)k * (k + 1)] = a.cproj[(long)c * (k + 2) + r];
+  load_shifted(A, la, a.Hk, k + 1, k + 1, k, s1);
+  for (int r = threadIdx.x; r <= k; r += DT) A[r + (long)k * la] = a.cproj[(long)c * (k + 2) + r];
   if (threadIdx.x == 0) sh.ibc[0] = 0;
   __syncthreads();
-  cta_qr(A, k + 1, k + 1, k, k + 1, tau, sh, k + 1);
-  for (int r = threadIdx.x; r < k; r += DT) d1[r] = A[r + (long)k * (k + 1)];
+  cta_qr(A, la, k + 1, k, k + 1, tau, sh, k + 1);
+  for (int r = threadIdx.x; r < k; r += DT) d1[r] = A[r + (long)k * la];
   __syncthreads();
-  if (!cta_backsolve(A, k + 1, k, d1, sh)) set_err(st, GDR_EBREAKDOWN);
+  if (!cta_backsolve(A, la, k, d1, sh)) set_err(st, GDR_EBREAKDOWN);
   for (int r = threadIdx.x; r <= k; r += DT) {
     c128 acc = {0, 0};
     for (int j = 0; j < k; ++j) {
@@ -838,14 +923,15 @@ __global__ void __launch_bounds__(DT) dense_proj_kernel(ProjArgs a) {
   // shift i: (H_k - s_i I) d_i = beta_i (H_k - s1 I) d_1 = beta_i t[0:k]
   const c128 si = a.sigma[(long)c * a.ns + i];
   const c128 bi = a.beta[(long)c * a.ns + i];
-  load_shifted(A, k, a.Hk, k + 1, k, k, si);
-  for (int r = threadIdx.x; r < k; r += DT) A[r + (long)k * k] = bi * t[r];
+  const int lb = odd_ld(k);
+  load_shifted(A, lb, a.Hk, k + 1, k, k, si);
+  for (int r = threadIdx.x; r < k; r += DT) A[r + (long)k * lb] = bi * t[r];
   if (threadIdx.x == 0) sh.ibc[0] = 0;
   __syncthreads();
-  cta_qr(A, k, k, k, k + 1, tau, sh, k);
-  for (int r = threadIdx.x; r < k; r += DT) y[r] = A[r + (long)k * k];
+  cta_qr(A, lb, k, k, k + 1, tau, sh, k);
+  for (int r = threadIdx.x; r < k; r += DT) y[r] = A[r + (long)k * lb];
   __syncthreads();
-  if (!cta_backsolve(A, k, k, y, sh)) set_err(st, GDR_EBREAKDOWN);
+  if (!cta_backsolve(A, lb, k, y, sh)) set_err(st, GDR_EBREAKDOWN);
   for (int r = threadIdx.x; r <= k; r += DT) Cf[r + (long)i * ldc] = (r < k) ? y[r] : c128{0, 0};
   // gamma_i += [beta_i t - (Hbar_k - s_i Ibar) d_i]_{k+1}  (last row of Ibar is zero)
   if (threadIdx.x == 0) {
@@ -860,8 +946,8 @@ __global__ void __launch_bounds__(DT) dense_proj_kernel(ProjArgs a) {
 size_t dense_smem_bytes(int m, int k) {
   // largest of: shift solve (m+1) x (m+3) + vectors; harmonic Ritz m x (m+2) + 4m;
   // restart completion P ((m+1) x (k+1)), T1 ((m+1) x k), coefficients
-  const size_t a = (size_t)(m + 1) * (m + 3) + 2 * (m + 2);
-  const size_t b = (size_t)m * (m + 2) + 4 * (size_t)m + 8;
+  const size_t a = (size_t)(m + 2) * (m + 3) + 2 * (m + 2);
+  const size_t b = (size_t)(m + 1) * (m + 2) + 4 * (size_t)m + 8;
   const size_t r = (size_t)(m + 1) * (2 * k + 1) + k + 2;
   return sizeof(c128) * std::max(a, std::max(b, r));
 }
@@ -904,7 +990,7 @@ void dense_projection(gdr_ctx* ctx, int ncol, int k, int ns, const c128* Hk, con
                       const c128* beta, const int* sact, c128* gamma, c128* Cf, long ccs, double*, long,
                       ColState* st) {
   ProjArgs a{k, ns, Hk, cproj, sigma, beta, sact, gamma, Cf, ccs, st};
-  const size_t smem = sizeof(c128) * ((size_t)(k + 1) * (k + 1) + 5 * (size_t)(k + 2));
+  const size_t smem = sizeof(c128) * ((size_t)(k + 2) * (k + 1) + 5 * (size_t)(k + 2));
   GDR_REQUIRE(smem <= ctx->dense_smem_limit, "k too large for the projection kernel");
   dim3 g((unsigned)ns, (unsigned)ncol);
   dense_proj_kernel<<<g, DT, smem, ctx->stream>>>(a);
