@@ -120,6 +120,12 @@ gdr_status gdr_op_csr(gdr_ctx *ctx, long n, long nnz, const int *rowptr, const i
  * row-major, mu = x,y,z,t.  `store` picks the link storage of the complex64 matvec. */
 gdr_status gdr_op_wilson(gdr_ctx *ctx, const int dims[4], double diag_a, const double *links,
                          gdr_link_fmt store, gdr_op **out);
+/* A batch of independent CSR matrices (the uneven-size problems solved together by
+ * gdr_solve_batch).  Problem p has n[p] rows and nnz[p] entries; rowptr, col and vals
+ * are the problems' CSR arrays concatenated (device): problem p's n[p]+1 row pointers
+ * (local, starting at 0), then its column indices (local) and c128 values.  n, nnz: host. */
+gdr_status gdr_op_csr_batch(gdr_ctx *ctx, int nprob, const long *n, const long *nnz, const int *rowptr,
+                            const int *col, const double *vals, gdr_op **out);
 void gdr_op_destroy(gdr_op *op);
 long gdr_op_n(const gdr_op *op);
 
@@ -143,6 +149,17 @@ gdr_status gdr_op_apply(gdr_ctx *ctx, const gdr_op *A, gdr_prec prec, int ncol, 
 gdr_status gdr_solve_multishift(gdr_ctx *ctx, const gdr_op *A, int ns, const double *sigma, int nrhs,
                                 const double *B, double *X, const gdr_params *params,
                                 gdr_defl **defl_out, gdr_report *report);
+
+/* Many independent shifted problems (eq. (1) with nrhs = 1 each) solved together:
+ * every problem runs GMRES-DR(m,k)-Sh as one column of a batched cycle (one kernel
+ * sequence / CUDA graph per cycle for the whole batch), then FP64 true residuals and
+ * per-pair refinement / cleanup as in gdr_solve_multishift.  A from gdr_op_csr_batch.
+ * sigma: host c128 [nprob x ns], problem p's shifts at sigma[p*ns], sigma[p*ns] its
+ * base shift.  B: c128, problem p's right-hand side at offset sum_{q<p} n[q].
+ * X: c128, problem p's n[p] x ns solutions (column-major) at offset ns * sum_{q<p} n[q].
+ * status (optional, host int[nprob]): GDR_OK or GDR_ENOCONV per problem. */
+gdr_status gdr_solve_batch(gdr_ctx *ctx, const gdr_op *A, int ns, const double *sigma, const double *B, double *X,
+                           const gdr_params *params, gdr_report *report, int *status);
 
 /* GMRES(m_p)-Proj(k)-Sh with a kept deflation space (Sec. 4), without the
  * correction phase: X[:, i, j] with residuals beta_i r + g_i v_{k+1}.

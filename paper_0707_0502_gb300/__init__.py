@@ -67,6 +67,9 @@ _SIGS = {
     "gdr_op_csr": (ctypes.c_int, [_P, ctypes.c_long, ctypes.c_long, _P, _P, _P, ctypes.POINTER(_P)]),
     "gdr_op_wilson": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.c_double, _P, ctypes.c_int,
                                      ctypes.POINTER(_P)]),
+    "gdr_op_csr_batch": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P, ctypes.POINTER(_P)]),
+    "gdr_solve_batch": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, _P, ctypes.POINTER(gdr_params),
+                                       ctypes.POINTER(gdr_report), _P]),
     "gdr_op_destroy": (None, [_P]),
     "gdr_op_n": (ctypes.c_long, [_P]),
     "gdr_op_apply": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
@@ -174,6 +177,43 @@ def gdr_op_wilson(ctx, dims, links, diag_a=0.0, store=GDR_LINK_C64):
     h = _P()
     _check(lib().gdr_op_wilson(ctx, d, float(diag_a), _ptr(links), int(store), ctypes.byref(h)), ctx)
     return h
+
+
+def gdr_op_csr_batch(ctx, n, nnz, rowptr, col, vals):
+    """n, nnz: per-problem sizes (host); rowptr/col (int32) and vals (complex128):
+    the problems' CSR arrays concatenated, on the device."""
+    nn = np.ascontiguousarray(np.asarray(n, dtype=np.int64))
+    nz = np.ascontiguousarray(np.asarray(nnz, dtype=np.int64))
+    h = _P()
+    _check(lib().gdr_op_csr_batch(ctx, len(nn), nn.ctypes.data, nz.ctypes.data, _ptr(rowptr), _ptr(col), _ptr(vals),
+                                  ctypes.byref(h)), ctx)
+    return h
+
+
+def gdr_solve_batch(ctx, op, sigma, B, X, params):
+    """sigma: (nprob, ns); B: concatenated right-hand sides; X: concatenated n_p x ns
+    blocks (column-major per problem).  Returns (status, report, per-problem status)."""
+    s = _c128_host(sigma)
+    sg = np.asarray(sigma)
+    nprob, ns = sg.shape
+    rep = gdr_report()
+    per = np.zeros(nprob, dtype=np.int32)
+    st = lib().gdr_solve_batch(ctx, op, int(ns), s.ctypes.data, _ptr(B), _ptr(X), ctypes.byref(params),
+                               ctypes.byref(rep), per.ctypes.data)
+    if st not in (GDR_OK, GDR_ENOCONV):
+        _check(st, ctx)
+    return st, rep.as_dict(), per
+
+
+def make_batch_operator(ctx, problems, device="cuda"):
+    """Batch operator from a list of ``workloads.Problem`` with CSR operators."""
+    import torch
+    rp = np.concatenate([p.op[1] for p in problems]).astype(np.int32)
+    cl = np.concatenate([p.op[2] for p in problems]).astype(np.int32)
+    vl = np.concatenate([p.op[3] for p in problems]).astype(np.complex128)
+    return gdr_op_csr_batch(ctx, [p.n for p in problems], [len(p.op[2]) for p in problems],
+                            torch.as_tensor(rp, device=device), torch.as_tensor(cl, device=device),
+                            torch.as_tensor(vl, device=device))
 
 
 def gdr_op_destroy(op):

@@ -173,8 +173,33 @@ gdr_status gdr_op_wilson(gdr_ctx* ctx, const int dims[4], double diag_a, const d
   return GDR_OK;
 }
 
+gdr_status gdr_op_csr_batch(gdr_ctx* ctx, int nprob, const long* n, const long* nnz, const int* rowptr,
+                            const int* col, const double* vals, gdr_op** out) {
+  if (!ctx || !out) return GDR_EINVAL;
+  *out = nullptr;
+  gdr_op* op = new gdr_op();
+  gdr_status st = guarded(ctx, [&] {
+    GDR_REQUIRE(nprob >= 1 && n && nnz && rowptr, "bad CSR batch arguments");
+    for (int p = 0; p < nprob; ++p) GDR_REQUIRE(n[p] > 0 && nnz[p] >= 0, "bad CSR batch sizes");
+    GDR_CUDA(cudaSetDevice(ctx->device));
+    op->ctx = ctx;
+    op->kind = OP_CSR_BATCH;
+    op->nprob = nprob;
+    op_build_csr_batch(ctx, op, n, nnz, rowptr, col, vals);
+  });
+  if (st != GDR_OK) {
+    gdr_op_destroy(op);
+    return st;
+  }
+  *out = op;
+  return GDR_OK;
+}
+
 void gdr_op_destroy(gdr_op* op) {
   if (!op) return;
+  cudaFree(op->rp_off);
+  cudaFree(op->nz_off);
+  cudaFree(op->nrow);
   cudaFree(op->rowptr);
   cudaFree(op->col);
   cudaFree(op->vals128);
@@ -230,6 +255,53 @@ gdr_status gdr_solve_multishift(gdr_ctx* ctx, const gdr_op* A, int ns, const dou
       result = solve_pipeline<double>(ctx, A, sig, nrhs, Bi, ld, Xi, ld, p, defl_out, rep);
     GDR_CUDA(cudaMemcpy2DAsync(X, n * sizeof(c128), Xi, ld * sizeof(c128), n * sizeof(c128), (size_t)ns * nrhs, kout,
                                ctx->stream));
+    GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+    rep.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    rep.kernel_launches = ctx->launches - launches0;
+  });
+  if (report) *report = rep;
+  return st != GDR_OK ? st : result;
+}
+
+gdr_status gdr_solve_batch(gdr_ctx* ctx, const gdr_op* A, int ns, const double* sigma, const double* B, double* X,
+                           const gdr_params* params, gdr_report* report, int* status) {
+  if (!ctx || !A) return GDR_EINVAL;
+  gdr_report rep{};
+  gdr_status result = GDR_OK;
+  gdr_status st = guarded(ctx, [&] {
+    GDR_REQUIRE(A->kind == OP_CSR_BATCH, "gdr_solve_batch needs an operator from gdr_op_csr_batch");
+    GDR_REQUIRE(params && sigma && B && X && ns >= 1, "bad gdr_solve_batch arguments");
+    const gdr_params& p = *params;
+    check_params(p);
+    GDR_CUDA(cudaSetDevice(ctx->device));
+    const auto t0 = std::chrono::steady_clock::now();
+    const long launches0 = ctx->launches;
+    const int np = A->nprob;
+    const long ld = pad_ld(A->n);
+    std::vector<c128> sig = host_c128(sigma, np * ns);
+    c128* Bi = ctx->get<c128>("api.B", (size_t)ld * np);
+    c128* Xi = ctx->get<c128>("api.X", (size_t)ld * ns * np);
+    const bool host = (p.flags & GDR_FLAG_HOST_PTRS) != 0;
+    const cudaMemcpyKind kin = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const cudaMemcpyKind kout = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    GDR_CUDA(cudaMemsetAsync(Bi, 0, sizeof(c128) * ld * np, ctx->stream));
+    long off = 0;
+    for (int q = 0; q < np; ++q) {
+      const long nq = A->nrow_host[q];
+      GDR_CUDA(cudaMemcpyAsync(Bi + (long)q * ld, B + 2 * off, sizeof(c128) * nq, kin, ctx->stream));
+      off += nq;
+    }
+    if (p.prec == GDR_PREC_MIXED)
+      result = solve_batch_pipeline<float>(ctx, A, ns, sig, Bi, Xi, p, rep, status);
+    else
+      result = solve_batch_pipeline<double>(ctx, A, ns, sig, Bi, Xi, p, rep, status);
+    off = 0;
+    for (int q = 0; q < np; ++q) {
+      const long nq = A->nrow_host[q];
+      GDR_CUDA(cudaMemcpy2DAsync(X + 2 * off * ns, nq * sizeof(c128), Xi + (long)q * ns * ld, ld * sizeof(c128),
+                                 nq * sizeof(c128), ns, kout, ctx->stream));
+      off += nq;
+    }
     GDR_CUDA(cudaStreamSynchronize(ctx->stream));
     rep.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     rep.kernel_launches = ctx->launches - launches0;

@@ -126,7 +126,7 @@ struct gdr_ctx {
   }
 };
 
-enum OpKind { OP_CSR = 0, OP_WILSON = 1 };
+enum OpKind { OP_CSR = 0, OP_WILSON = 1, OP_CSR_BATCH = 2 };
 
 struct gdr_op {
   gdr_ctx* ctx = nullptr;
@@ -138,6 +138,13 @@ struct gdr_op {
   int* col = nullptr;
   c128* vals128 = nullptr;
   c64* vals64 = nullptr;
+  // CSR batch: problem p has nrow[p] rows; its rowptr starts at rowptr + rp_off[p] and
+  // its local column indices / values at col + nz_off[p], vals + nz_off[p]
+  int nprob = 0;
+  long* rp_off = nullptr;
+  long* nz_off = nullptr;
+  int* nrow = nullptr;
+  std::vector<long> nrow_host;
   // Wilson: links stored structure-of-arrays [mu][e][V], e = a*3 + b
   int dims[4] = {0, 0, 0, 0};
   long V = 0;
@@ -178,6 +185,8 @@ size_t set_max_dyn_smem(gdr_ctx* ctx, F* f) {
 
 // ops.cu: Y[:,c] = (A - sigma_c) X[:,c]   (B != nullptr:  Y = B - (A - sigma_c) X)
 // sigma: device c128[ncol] (per column); X/Y/B leading dimensions ldx/ldy/ldb
+// For a CSR batch, column c of X/Y/B belongs to problem c / cpp (cpp columns per problem);
+// for every operator B's column is B + (c / cpp) * ldb.
 template <typename R>
 void op_apply(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma_dev, const cx<R>* X, long ldx,
-              cx<R>* Y, long ldy, const cx<R>* B, long ldb);
+              cx<R>* Y, long ldy, const cx<R>* B, long ldb, int cpp = 1);

@@ -41,6 +41,8 @@ struct Batch {
   ColState* st = nullptr;
   c128* sigma = nullptr;    // ns per column
   int nblk = 0;             // grid size of the reduction kernels
+  const int* nvec = nullptr;  // per-column vector length (device); nullptr: all columns have length n
+  int cpp = 1;                // operator problem of column c is c / cpp (CSR batch)
 };
 
 // krylov.cu --------------------------------------------------------------
@@ -61,7 +63,8 @@ template <typename R>
 void start_cycle(gdr_ctx* ctx, const Batch<R>& b, const cx<R>* r, long rcs);
 // out[c] = ||x_c||^2 (FP64 accumulation), x c128 or cx<R>, `cols` columns of length n at stride xcs
 template <typename T>
-void norms2(gdr_ctx* ctx, long n, int cols, const T* x, long xcs, double* out, c128* part, int nblk, unsigned* cnt);
+void norms2(gdr_ctx* ctx, long n, int cols, const T* x, long xcs, double* out, c128* part, int nblk, unsigned* cnt,
+            const int* nvec = nullptr);
 // dots[c] = u_c^H x_c (FP64)   (ucs = 0 shares u)
 void dots128(gdr_ctx* ctx, long n, int cols, const c128* u, long ucs, const c128* x, long xcs, c128* out,
              c128* part, int nblk, unsigned* cnt);
@@ -74,7 +77,8 @@ void dots128(gdr_ctx* ctx, long n, int cols, const c128* u, long ucs, const c128
 // vcs = 0 shares one basis between all columns.
 template <typename R>
 void combine(gdr_ctx* ctx, long n, int ncol, cx<R>* V, long ldv, long vcs, int nv, const c128* C, int ldc, long ccs,
-             int nout, int nx, int rmode, c128* X, long ldx, long xcs, cx<R>* Rv, long rcs, const ColState* st);
+             int nout, int nx, int rmode, c128* X, long ldx, long xcs, cx<R>* Rv, long rcs, const ColState* st,
+             const int* nvec = nullptr);
 
 void krylov_init(gdr_ctx* ctx);
 
@@ -89,9 +93,11 @@ void scal_cols(gdr_ctx* ctx, long n, int cols, const c128* a, c128* X, long xcs)
 
 // ops.cu -----------------------------------------------------------------
 void op_apply_skip(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, const c128* X, long ldx, c128* Y,
-                   long ldy, const c128* B, long ldb, const int* run, int run_stride);
+                   long ldy, const c128* B, long ldb, const int* run, int run_stride, int cpp = 1);
 void op_apply_skip(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, const c64* X, long ldx, c64* Y,
-                   long ldy, const c64* B, long ldb, const int* run, int run_stride);
+                   long ldy, const c64* B, long ldb, const int* run, int run_stride, int cpp = 1);
+void op_build_csr_batch(gdr_ctx* ctx, gdr_op* op, const long* n, const long* nnz, const int* rowptr, const int* col,
+                        const double* vals);
 void op_build_csr(gdr_ctx* ctx, gdr_op* op, const int* rowptr, const int* col, const double* vals);
 void op_build_wilson(gdr_ctx* ctx, gdr_op* op, const double* links);
 

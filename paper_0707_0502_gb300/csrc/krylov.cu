@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(NT) gs_dot_kernel(Batch<R> b, int nv, const cx
   constexpr int K = U<R>::K;
   const cx<R>* __restrict__ V = b.V + c * b.vcs;
   const cx<R>* __restrict__ w = W + c * wcs;
-  const long n = b.n, nu = nunits<R>(n);
+  const long n = b.nvec ? (long)b.nvec[c] : b.n, nu = nunits<R>(n);
   c128* part = b.part + c * b.pstride;
   const long gt = blockIdx.x * (long)NT + threadIdx.x, gs = (long)gridDim.x * NT;
   for (int i0 = 0; i0 < nv; i0 += JB) {
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(NT) gs_update_kernel(Batch<R> b, int nv, cx<R>
   __syncthreads();
   const cx<R>* __restrict__ V = b.V + c * b.vcs;
   cx<R>* __restrict__ w = W + c * wcs;
-  const long n = b.n, nu = nunits<R>(n);
+  const long n = b.nvec ? (long)b.nvec[c] : b.n, nu = nunits<R>(n);
   const long gt = blockIdx.x * (long)NT + threadIdx.x, gs = (long)gridDim.x * NT;
   cx<R> nrm[1] = {{0, 0}};
   for (long u = gt; u < nu; u += gs) {
@@ -224,7 +224,7 @@ __global__ void scale_kernel(Batch<R> b, int j, const cx<R>* __restrict__ W, lon
   const int c = blockIdx.y;
   if (!b.st[c].run) return;
   constexpr int K = U<R>::K;
-  const long n = b.n, nu = nunits<R>(n);
+  const long n = b.nvec ? (long)b.nvec[c] : b.n, nu = nunits<R>(n);
   const R s = (R)b.st[c].inv_norm;
   const cx<R>* w = W + c * wcs;
   cx<R>* v = b.V + c * b.vcs + (long)j * b.ldv;
@@ -244,9 +244,10 @@ template <> struct Real<c128> { using R = double; };
 
 template <typename T>
 __global__ void __launch_bounds__(NT) norms2_kernel(long n, const T* __restrict__ x, long xcs, double* out,
-                                                    c128* part, unsigned* cnt) {
+                                                    c128* part, unsigned* cnt, const int* nvec) {
   using R = typename Real<T>::R;
   const int c = blockIdx.y;
+  if (nvec) n = nvec[c];
   const T* xc = x + c * xcs;
   cx<R> a[1] = {{0, 0}};
   // FP64 per-thread accumulation for accuracy of ||b||
@@ -297,7 +298,8 @@ __global__ void start_scale_kernel(Batch<R> b, const cx<R>* __restrict__ r, long
   const R s = (R)(1.0 / rn);
   const cx<R>* rc = r + c * rcs;
   cx<R>* v = b.V + c * b.vcs;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < b.n; i += (long)gridDim.x * blockDim.x)
+  const long n = b.nvec ? (long)b.nvec[c] : b.n;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
     v[i] = s * rc[i];
 }
 
@@ -330,10 +332,12 @@ template <typename R>
 __global__ void __launch_bounds__(CT) combine_kernel(long n, cx<R>* V, long ldv, long vcs, int nv,
                                                      const c128* __restrict__ C, int ldc, long ccs, int nout, int nx,
                                                      int rmode, c128* X, long ldx, long xcs, cx<R>* Rv, long rcs,
-                                                     const ColState* st) {
+                                                     const ColState* st, const int* nvec) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int c = blockIdx.y;
   if (st && !st[c].active) return;
+  if (nvec) n = nvec[c];
+  if ((long)blockIdx.x * CR >= n) return;
   const int ntot = nout + nx + (rmode ? 1 : 0);
   cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);             // CR x nv  (row-fast)
   cx<R>* cf = tile + (long)CR * nv;                              // nv x ntot
@@ -434,7 +438,7 @@ void scale_into(gdr_ctx* ctx, const Batch<R>& b, int j, const cx<R>* w, long wcs
 template <typename R>
 void arnoldi_step(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b, int j) {
   op_apply_skip(ctx, A, b.ncol, nullptr, b.V + (long)j * b.ldv, b.vcs, b.W, b.wcs, nullptr, 0, &b.st[0].run,
-                (int)(sizeof(ColState) / sizeof(int)));
+                (int)(sizeof(ColState) / sizeof(int)), b.cpp);
   gs_dot<R>(ctx, b, j + 1, b.W, b.wcs, b.h1, true);
   gs_update<R>(ctx, b, j + 1, b.W, b.wcs, b.h1, false);
   gs_dot<R>(ctx, b, j + 1, b.W, b.wcs, b.h2, false);
@@ -445,7 +449,7 @@ void arnoldi_step(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b, int j) {
 template <typename R>
 void start_cycle(gdr_ctx* ctx, const Batch<R>& b, const cx<R>* r, long rcs) {
   double* rn2 = ctx->get<double>("start_rn2", b.ncol);
-  norms2<cx<R>>(ctx, b.n, b.ncol, r, rcs, rn2, b.part, b.nblk, b.cnt);
+  norms2<cx<R>>(ctx, b.n, b.ncol, r, rcs, rn2, b.part, b.nblk, b.cnt, b.nvec);
   dim3 grid(grid_for(ctx, b.n, 256), (unsigned)b.ncol);
   start_scale_kernel<R><<<grid, 256, 0, ctx->stream>>>(b, r, rcs, rn2);
   GDR_LAUNCHED(ctx);
@@ -454,9 +458,10 @@ void start_cycle(gdr_ctx* ctx, const Batch<R>& b, const cx<R>* r, long rcs) {
 }
 
 template <typename T>
-void norms2(gdr_ctx* ctx, long n, int cols, const T* x, long xcs, double* out, c128* part, int nblk, unsigned* cnt) {
+void norms2(gdr_ctx* ctx, long n, int cols, const T* x, long xcs, double* out, c128* part, int nblk, unsigned* cnt,
+            const int* nvec) {
   dim3 grid((unsigned)nblk, (unsigned)cols);
-  norms2_kernel<T><<<grid, NT, 0, ctx->stream>>>(n, x, xcs, out, part, cnt);
+  norms2_kernel<T><<<grid, NT, 0, ctx->stream>>>(n, x, xcs, out, part, cnt, nvec);
   GDR_LAUNCHED(ctx);
 }
 void dots128(gdr_ctx* ctx, long n, int cols, const c128* u, long ucs, const c128* x, long xcs, c128* out, c128* part,
@@ -468,14 +473,15 @@ void dots128(gdr_ctx* ctx, long n, int cols, const c128* u, long ucs, const c128
 
 template <typename R>
 void combine(gdr_ctx* ctx, long n, int ncol, cx<R>* V, long ldv, long vcs, int nv, const c128* C, int ldc, long ccs,
-             int nout, int nx, int rmode, c128* X, long ldx, long xcs, cx<R>* Rv, long rcs, const ColState* st) {
+             int nout, int nx, int rmode, c128* X, long ldx, long xcs, cx<R>* Rv, long rcs, const ColState* st,
+             const int* nvec) {
   const int ntot = nout + nx + (rmode ? 1 : 0);
   if (ntot == 0 || ncol == 0) return;
   const size_t smem = sizeof(cx<R>) * ((size_t)CR * nv + (size_t)nv * ntot);
   GDR_REQUIRE(smem <= ctx->combine_smem_limit, "combine: too many basis vectors / outputs for shared memory");
   dim3 grid((unsigned)((n + CR - 1) / CR), (unsigned)ncol);
   combine_kernel<R><<<grid, CT, smem, ctx->stream>>>(n, V, ldv, vcs, nv, C, ldc, ccs, nout, nx, rmode, X, ldx, xcs,
-                                                     Rv, rcs, st);
+                                                     Rv, rcs, st, nvec);
   GDR_LAUNCHED(ctx);
 }
 
@@ -520,9 +526,9 @@ template void arnoldi_step<float>(gdr_ctx*, const gdr_op*, const Batch<float>&, 
 template void arnoldi_step<double>(gdr_ctx*, const gdr_op*, const Batch<double>&, int);
 template void start_cycle<float>(gdr_ctx*, const Batch<float>&, const c64*, long);
 template void start_cycle<double>(gdr_ctx*, const Batch<double>&, const c128*, long);
-template void norms2<c64>(gdr_ctx*, long, int, const c64*, long, double*, c128*, int, unsigned*);
-template void norms2<c128>(gdr_ctx*, long, int, const c128*, long, double*, c128*, int, unsigned*);
+template void norms2<c64>(gdr_ctx*, long, int, const c64*, long, double*, c128*, int, unsigned*, const int*);
+template void norms2<c128>(gdr_ctx*, long, int, const c128*, long, double*, c128*, int, unsigned*, const int*);
 template void combine<float>(gdr_ctx*, long, int, c64*, long, long, int, const c128*, int, long, int, int, int, c128*,
-                             long, long, c64*, long, const ColState*);
+                             long, long, c64*, long, const ColState*, const int*);
 template void combine<double>(gdr_ctx*, long, int, c128*, long, long, int, const c128*, int, long, int, int, int,
-                              c128*, long, long, c128*, long, const ColState*);
+                              c128*, long, long, c128*, long, const ColState*, const int*);

@@ -12,6 +12,8 @@
 // Vectors are site-major (site*12 + spin*3 + colour).  Links are stored
 // structure-of-arrays [mu][e][V] (e = a*3 + b) so that a warp's loads of one
 // link element are contiguous.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace {
@@ -22,7 +24,8 @@ template <typename R, typename VT>
 __global__ void csr_kernel(long n, const int* __restrict__ rowptr, const int* __restrict__ col,
                            const VT* __restrict__ vals, const c128* __restrict__ sigma,
                            const cx<R>* __restrict__ X, long ldx, cx<R>* __restrict__ Y, long ldy,
-                           const cx<R>* __restrict__ B, long ldb, const int* __restrict__ run, int run_stride) {
+                           const cx<R>* __restrict__ B, long ldb, const int* __restrict__ run, int run_stride,
+                           int cpp) {
   const long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
   const int c = blockIdx.y;
   if (r >= n) return;
@@ -36,7 +39,35 @@ __global__ void csr_kernel(long n, const int* __restrict__ rowptr, const int* __
     acc += a * x[col[p]];
   }
   if (sigma) acc -= cvt<R>(sigma[c]) * x[r];
-  if (B) acc = B[c * ldb + r] - acc;
+  if (B) acc = B[(c / cpp) * ldb + r] - acc;
+  Y[c * ldy + r] = acc;
+}
+
+// CSR batch: column c uses problem c / cpp (its own rows, local column indices)
+template <typename R, typename VT>
+__global__ void csr_batch_kernel(const long* __restrict__ rp_off, const long* __restrict__ nz_off,
+                                 const int* __restrict__ nrow, const int* __restrict__ rowptr,
+                                 const int* __restrict__ col, const VT* __restrict__ vals,
+                                 const c128* __restrict__ sigma, const cx<R>* __restrict__ X, long ldx,
+                                 cx<R>* __restrict__ Y, long ldy, const cx<R>* __restrict__ B, long ldb,
+                                 const int* __restrict__ run, int run_stride, int cpp) {
+  const long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  const int p = c / cpp;
+  if (r >= nrow[p]) return;
+  if (run && !run[(long)c * run_stride]) return;
+  const int* rp = rowptr + rp_off[p];
+  const int* cl = col + nz_off[p];
+  const VT* vl = vals + nz_off[p];
+  const cx<R>* x = X + c * ldx;
+  cx<R> acc = {0, 0};
+  const int p0 = rp[r], p1 = rp[r + 1];
+  for (int q = p0; q < p1; ++q) {
+    const VT v = vl[q];
+    acc += cx<R>{(R)v.x, (R)v.y} * x[cl[q]];
+  }
+  if (sigma) acc -= cvt<R>(sigma[c]) * x[r];
+  if (B) acc = B[(long)p * ldb + r] - acc;
   Y[c * ldy + r] = acc;
 }
 
@@ -160,7 +191,7 @@ __global__ void __launch_bounds__(128) wilson_kernel(const LT* __restrict__ link
                                                     double diag_a, const c128* __restrict__ sigma,
                                                     const cx<R>* __restrict__ X, long ldx, cx<R>* __restrict__ Y,
                                                     long ldy, const cx<R>* __restrict__ B, long ldb,
-                                                    const int* __restrict__ run, int run_stride) {
+                                                    const int* __restrict__ run, int run_stride, int cpp) {
   const long V = (long)Lx * Ly * Lz * Lt;
   const long site = blockIdx.x * (long)blockDim.x + threadIdx.x;
   const int c = blockIdx.y;
@@ -185,7 +216,7 @@ __global__ void __launch_bounds__(128) wilson_kernel(const LT* __restrict__ link
   const c128 sg = sigma ? sigma[c] : c128{0.0, 0.0};
   const cx<R> dg = {(R)(diag_a - sg.x), (R)(-sg.y)};
   cx<R>* y = Y + c * ldy + site * 12;
-  const cx<R>* b = B ? B + c * ldb + site * 12 : nullptr;
+  const cx<R>* b = B ? B + (c / cpp) * ldb + site * 12 : nullptr;
 #pragma unroll
   for (int i = 0; i < 12; ++i) {
     cx<R> v = dg * p.s[i] - acc.s[i];
@@ -198,58 +229,71 @@ __global__ void __launch_bounds__(128) wilson_kernel(const LT* __restrict__ link
 
 template <typename R>
 static void op_apply_impl(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, const cx<R>* X, long ldx,
-                          cx<R>* Y, long ldy, const cx<R>* B, long ldb, const int* run, int run_stride) {
+                          cx<R>* Y, long ldy, const cx<R>* B, long ldb, const int* run, int run_stride, int cpp) {
   if (ncol <= 0) return;
+  constexpr bool F64 = std::is_same<R, double>::value;
   if (A->kind == OP_CSR) {
     dim3 grid((unsigned)((A->n + 255) / 256), (unsigned)ncol);
-    if (std::is_same<R, double>::value) {
+    if (F64) {
       csr_kernel<double, c128><<<grid, 256, 0, ctx->stream>>>(
           A->n, A->rowptr, A->col, A->vals128, sigma, (const c128*)X, ldx, (c128*)Y, ldy, (const c128*)B, ldb, run,
-          run_stride);
+          run_stride, cpp);
     } else {
       csr_kernel<float, c64><<<grid, 256, 0, ctx->stream>>>(A->n, A->rowptr, A->col, A->vals64, sigma,
                                                              (const c64*)X, ldx, (c64*)Y, ldy, (const c64*)B, ldb,
-                                                             run, run_stride);
+                                                             run, run_stride, cpp);
+    }
+    GDR_LAUNCHED(ctx);
+  } else if (A->kind == OP_CSR_BATCH) {
+    dim3 grid((unsigned)((A->n + 255) / 256), (unsigned)ncol);  // A->n = largest problem
+    if (F64) {
+      csr_batch_kernel<double, c128><<<grid, 256, 0, ctx->stream>>>(
+          A->rp_off, A->nz_off, A->nrow, A->rowptr, A->col, A->vals128, sigma, (const c128*)X, ldx, (c128*)Y, ldy,
+          (const c128*)B, ldb, run, run_stride, cpp);
+    } else {
+      csr_batch_kernel<float, c64><<<grid, 256, 0, ctx->stream>>>(
+          A->rp_off, A->nz_off, A->nrow, A->rowptr, A->col, A->vals64, sigma, (const c64*)X, ldx, (c64*)Y, ldy,
+          (const c64*)B, ldb, run, run_stride, cpp);
     }
     GDR_LAUNCHED(ctx);
   } else {
     dim3 grid((unsigned)((A->V + 127) / 128), (unsigned)ncol);
     const int* d = A->dims;
-    if (std::is_same<R, double>::value) {
+    if (F64) {
       wilson_kernel<double, c128><<<grid, 128, 0, ctx->stream>>>(A->links128, d[0], d[1], d[2], d[3], A->diag_a,
                                                                  sigma, (const c128*)X, ldx, (c128*)Y, ldy,
-                                                                 (const c128*)B, ldb, run, run_stride);
+                                                                 (const c128*)B, ldb, run, run_stride, cpp);
     } else if (A->store == GDR_LINK_BF16) {
       wilson_kernel<float, __nv_bfloat162><<<grid, 128, 0, ctx->stream>>>(
           A->links16, d[0], d[1], d[2], d[3], A->diag_a, sigma, (const c64*)X, ldx, (c64*)Y, ldy, (const c64*)B, ldb,
-          run, run_stride);
+          run, run_stride, cpp);
     } else {
       wilson_kernel<float, c64><<<grid, 128, 0, ctx->stream>>>(A->links64, d[0], d[1], d[2], d[3], A->diag_a, sigma,
                                                                (const c64*)X, ldx, (c64*)Y, ldy, (const c64*)B, ldb,
-                                                               run, run_stride);
+                                                               run, run_stride, cpp);
     }
     GDR_LAUNCHED(ctx);
   }
 }
 
 void op_apply_skip(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, const c128* X, long ldx, c128* Y,
-                   long ldy, const c128* B, long ldb, const int* run, int run_stride) {
-  op_apply_impl<double>(ctx, A, ncol, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride);
+                   long ldy, const c128* B, long ldb, const int* run, int run_stride, int cpp) {
+  op_apply_impl<double>(ctx, A, ncol, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride, cpp);
 }
 void op_apply_skip(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, const c64* X, long ldx, c64* Y,
-                   long ldy, const c64* B, long ldb, const int* run, int run_stride) {
-  op_apply_impl<float>(ctx, A, ncol, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride);
+                   long ldy, const c64* B, long ldb, const int* run, int run_stride, int cpp) {
+  op_apply_impl<float>(ctx, A, ncol, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride, cpp);
 }
 
 template <typename R>
 void op_apply(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, const cx<R>* X, long ldx, cx<R>* Y,
-              long ldy, const cx<R>* B, long ldb) {
-  op_apply_skip(ctx, A, ncol, sigma, X, ldx, Y, ldy, B, ldb, nullptr, 0);
+              long ldy, const cx<R>* B, long ldb, int cpp) {
+  op_apply_skip(ctx, A, ncol, sigma, X, ldx, Y, ldy, B, ldb, nullptr, 0, cpp);
 }
 template void op_apply<double>(gdr_ctx*, const gdr_op*, int, const c128*, const c128*, long, c128*, long, const c128*,
-                               long);
+                               long, int);
 template void op_apply<float>(gdr_ctx*, const gdr_op*, int, const c128*, const c64*, long, c64*, long, const c64*,
-                              long);
+                              long, int);
 
 // ------------------------------------------------------ operator creation
 
@@ -300,5 +344,41 @@ void op_build_wilson(gdr_ctx* ctx, gdr_op* op, const double* links) {
   links_soa_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, ctx->stream>>>((const c128*)links, op->V, op->links128,
                                                                           op->links64, op->links16);
   GDR_LAUNCHED(ctx);
+  GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+
+void op_build_csr_batch(gdr_ctx* ctx, gdr_op* op, const long* n, const long* nnz, const int* rowptr, const int* col,
+                        const double* vals) {
+  std::vector<long> rp(op->nprob), nz(op->nprob);
+  std::vector<int> nr(op->nprob);
+  long rtot = 0, ztot = 0, nmax = 0;
+  for (int p = 0; p < op->nprob; ++p) {
+    rp[p] = rtot;
+    nz[p] = ztot;
+    nr[p] = (int)n[p];
+    rtot += n[p] + 1;
+    ztot += nnz[p];
+    nmax = std::max(nmax, n[p]);
+  }
+  op->n = nmax;
+  op->nnz = ztot;
+  op->nrow_host.assign(n, n + op->nprob);
+  GDR_CUDA(cudaMalloc(&op->rowptr, rtot * sizeof(int)));
+  GDR_CUDA(cudaMalloc(&op->col, std::max<long>(ztot, 1) * sizeof(int)));
+  GDR_CUDA(cudaMalloc(&op->vals128, std::max<long>(ztot, 1) * sizeof(c128)));
+  GDR_CUDA(cudaMalloc(&op->vals64, std::max<long>(ztot, 1) * sizeof(c64)));
+  GDR_CUDA(cudaMalloc(&op->rp_off, op->nprob * sizeof(long)));
+  GDR_CUDA(cudaMalloc(&op->nz_off, op->nprob * sizeof(long)));
+  GDR_CUDA(cudaMalloc(&op->nrow, op->nprob * sizeof(int)));
+  GDR_CUDA(cudaMemcpyAsync(op->rowptr, rowptr, rtot * sizeof(int), cudaMemcpyDeviceToDevice, ctx->stream));
+  if (ztot > 0) {
+    GDR_CUDA(cudaMemcpyAsync(op->col, col, ztot * sizeof(int), cudaMemcpyDeviceToDevice, ctx->stream));
+    GDR_CUDA(cudaMemcpyAsync(op->vals128, vals, ztot * sizeof(c128), cudaMemcpyDeviceToDevice, ctx->stream));
+    vals_to64_kernel<<<(unsigned)((ztot + 255) / 256), 256, 0, ctx->stream>>>(op->vals128, ztot, op->vals64);
+    GDR_LAUNCHED(ctx);
+  }
+  GDR_CUDA(cudaMemcpyAsync(op->rp_off, rp.data(), op->nprob * sizeof(long), cudaMemcpyHostToDevice, ctx->stream));
+  GDR_CUDA(cudaMemcpyAsync(op->nz_off, nz.data(), op->nprob * sizeof(long), cudaMemcpyHostToDevice, ctx->stream));
+  GDR_CUDA(cudaMemcpyAsync(op->nrow, nr.data(), op->nprob * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
   GDR_CUDA(cudaStreamSynchronize(ctx->stream));
 }

@@ -54,9 +54,11 @@ __global__ void set_run_kernel(ColState* st, int ncol) {
 
 // normalise V[:, j] of every column with ||.||^2 in nrm2[c]
 template <typename R>
-__global__ void normalize_kernel(cx<R>* V, long ldv, long vcs, int j, long n, const double* nrm2, const ColState* st) {
+__global__ void normalize_kernel(cx<R>* V, long ldv, long vcs, int j, long n, const double* nrm2, const ColState* st,
+                                 const int* nvec) {
   const int c = blockIdx.y;
   if (st && !st[c].active) return;
+  if (nvec) n = nvec[c];
   const double nn = nrm2[c];
   if (!(nn > 0)) return;
   const R s = (R)(1.0 / sqrt(nn));
@@ -186,9 +188,9 @@ void reorth_column(gdr_ctx* ctx, const Batch<R>& b, int j, double* nrm2) {
   gs_update<R>(ctx, b, j, vj, b.vcs, b.h1, false);
   gs_dot<R>(ctx, b, j, vj, b.vcs, b.h1, false);
   gs_update<R>(ctx, b, j, vj, b.vcs, b.h1, false);
-  norms2<cx<R>>(ctx, b.n, b.ncol, vj, b.vcs, nrm2, b.part, b.nblk, b.cnt);
+  norms2<cx<R>>(ctx, b.n, b.ncol, vj, b.vcs, nrm2, b.part, b.nblk, b.cnt, b.nvec);
   dim3 g(grid1(ctx, b.n), (unsigned)b.ncol);
-  normalize_kernel<R><<<g, 256, 0, ctx->stream>>>(b.V, b.ldv, b.vcs, j, b.n, nrm2, b.st);
+  normalize_kernel<R><<<g, 256, 0, ctx->stream>>>(b.V, b.ldv, b.vcs, j, b.n, nrm2, b.st, b.nvec);
   GDR_LAUNCHED(ctx);
 }
 
@@ -204,74 +206,94 @@ std::vector<ColState> read_states(gdr_ctx* ctx, const ColState* st, int ncol) {
 // ------------------------------------------------------------- GMRES-DR-Sh
 
 template <typename R>
-DrResult dr_sh(gdr_ctx* ctx, const gdr_op* A, const cx<R>* b_in, const std::vector<c128>& sigma, int m, int k,
-               double tol, long max_mvps, int max_cycles, c128* X, long ldx, bool use_graph) {
+DrResult dr_sh(gdr_ctx* ctx, const gdr_op* A, const DrJob<R>& job, bool use_graph) {
   const long n = A->n;
-  const int ns = (int)sigma.size();
-  Batch<R> b = make_batch<R>(ctx, "dr", n, 1, m, ns);
-  Shifted sh = make_shifted(ctx, "dr", 1, ns);
-  GDR_CUDA(cudaMemcpyAsync(b.sigma, sigma.data(), sizeof(c128) * ns, cudaMemcpyHostToDevice, ctx->stream));
+  const int ncol = job.ncol, ns = job.ns, m = job.m, k = job.k;
+  Batch<R> b = make_batch<R>(ctx, "dr", n, ncol, m, ns);
+  b.nvec = job.nvec;
+  b.cpp = job.cpp;
+  Shifted sh = make_shifted(ctx, "dr", ncol, ns);
+  GDR_CUDA(cudaMemcpyAsync(b.sigma, job.sigma.data(), sizeof(c128) * ns * ncol, cudaMemcpyHostToDevice,
+                           ctx->stream));
   const int ldc = m + 1;
   const int ncf = k + 1 + ns + 1;
   DenseCycle d{};
-  d.ncol = 1; d.m = m; d.k = k; d.ns = ns; d.kfull = k;
+  d.ncol = ncol; d.m = m; d.k = k; d.ns = ns; d.kfull = k;
   d.H = b.H; d.cvec = b.cvec; d.sigma = b.sigma;
   d.beta = sh.beta; d.norms = sh.norms; d.sact = sh.sact;
-  d.Cf = ctx->get<c128>("dr.Cf", (size_t)ldc * ncf); d.ldc = ldc; d.ccs = (long)ldc * ncf;
-  d.s = ctx->get<c128>("dr.s", (size_t)(m + 1));
-  d.Pk = ctx->get<c128>("dr.Pk", (size_t)(m + 1) * std::max(k, 1));
-  d.Hk = ctx->get<c128>("dr.Hk", (size_t)(k + 1) * std::max(k, 1));
-  d.ck = ctx->get<c128>("dr.ck", (size_t)(k + 1));
-  d.theta = ctx->get<c128>("dr.theta", (size_t)m);
+  d.ccs = (long)ldc * ncf; d.ldc = ldc;
+  d.Cf = ctx->get<c128>("dr.Cf", (size_t)d.ccs * ncol);
+  d.s = ctx->get<c128>("dr.s", (size_t)(m + 1) * ncol);
+  d.Pk = ctx->get<c128>("dr.Pk", (size_t)(m + 1) * std::max(k, 1) * ncol);
+  d.Hk = ctx->get<c128>("dr.Hk", (size_t)(k + 1) * std::max(k, 1) * ncol);
+  d.ck = ctx->get<c128>("dr.ck", (size_t)(k + 1) * ncol);
+  d.theta = ctx->get<c128>("dr.theta", (size_t)m * ncol);
   d.scratch_per_col = (long)2 * ((long)m * m + 2L * m * std::max(k, 1) + 64);
-  d.scratch = ctx->get<double>("dr.scratch", (size_t)d.scratch_per_col);
+  d.scratch = ctx->get<double>("dr.scratch", (size_t)d.scratch_per_col * ncol);
   d.st = b.st;
   d.want_r = (k == 0);  // GMRES(m): restart from the residual vector r = V_{m+1} s
-  cx<R>* rres = ctx->get<cx<R>>("dr.r", (size_t)b.ldv);
-  double* bn2 = ctx->get<double>("dr.bn2", 4);
-  double* tolv = ctx->get<double>("dr.tol", 4);
-  double* rn2 = ctx->get<double>("start_rn2", 4);
-  (void)rn2;
-  GDR_CUDA(cudaMemcpyAsync(tolv, &tol, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-  norms2<cx<R>>(ctx, n, 1, b_in, 0, bn2, b.part, b.nblk, b.cnt);
-  init_cols_kernel<<<1, 32, 0, ctx->stream>>>(b.st, 1, bn2, tolv, nullptr, ns, sh.sact, sh.beta, sh.gamma, sh.norms);
+  cx<R>* rres = ctx->get<cx<R>>("dr.r", (size_t)b.ldv * ncol);
+  double* bn2 = ctx->get<double>("dr.bn2", (size_t)ncol + 4);
+  double* nrm2 = ctx->get<double>("dr.nrm2", (size_t)ncol + 4);
+  double* tolv = ctx->get<double>("dr.tol", (size_t)ncol + 4);
+  GDR_CUDA(cudaMemcpyAsync(tolv, job.tol.data(), sizeof(double) * ncol, cudaMemcpyHostToDevice, ctx->stream));
+  norms2<cx<R>>(ctx, n, ncol, job.rhs, job.ldrhs, bn2, b.part, b.nblk, b.cnt, b.nvec);
+  init_cols_kernel<<<(ncol + 31) / 32, 32, 0, ctx->stream>>>(b.st, ncol, bn2, tolv, nullptr, ns, sh.sact, sh.beta,
+                                                              sh.gamma, sh.norms);
   GDR_LAUNCHED(ctx);
-  start_cycle<R>(ctx, b, b_in, 0);
+  start_cycle<R>(ctx, b, job.rhs, job.ldrhs);
 
   Graph g_first, g_next;
   DrResult res;
   res.k_eff = k;
+  res.col_mvps.assign(ncol, 0);
+  res.col_conv.assign(ncol, 0);
+  std::vector<int> done(ncol, 0);
   int j0 = 0;
   for (;;) {
     const int jstart = j0;
     auto enqueue = [&]() {
-      set_run_kernel<<<1, 32, 0, ctx->stream>>>(b.st, 1);
+      set_run_kernel<<<(ncol + 31) / 32, 32, 0, ctx->stream>>>(b.st, ncol);
       GDR_LAUNCHED(ctx);
       for (int j = jstart; j < m; ++j) arnoldi_step<R>(ctx, A, b, j);
       dense_cycle(ctx, d);
       // restart (V_{k+1} <- V_{m+1} P_{k+1}) fused with x_i += V_m d_i
-      combine<R>(ctx, n, 1, b.V, b.ldv, b.vcs, m + 1, d.Cf, ldc, d.ccs, k > 0 ? k + 1 : 0, ns, k > 0 ? 0 : 1, X, ldx,
-                 (long)ns * ldx, rres, 0, b.st);
-      if (k > 0) reorth_column<R>(ctx, b, k, bn2 + 1);
+      combine<R>(ctx, n, ncol, b.V, b.ldv, b.vcs, m + 1, d.Cf, ldc, d.ccs, k > 0 ? k + 1 : 0, ns, k > 0 ? 0 : 1,
+                 job.X, job.ldx, job.xcs, rres, b.ldv, b.st, b.nvec);
+      if (k > 0) reorth_column<R>(ctx, b, k, nrm2);
       cycle_finish(ctx, d, b.H, b.cvec);
     };
     run_cycle(ctx, use_graph, jstart == 0 ? g_first : g_next, enqueue);
-    const ColState st = read_states(ctx, b.st, 1)[0];
+    const std::vector<ColState> st = read_states(ctx, b.st, ncol);
     res.cycles++;
-    res.mvps += st.broke ? (st.m_eff - jstart) : (m - jstart);
-    if (st.nan) { res.status = GDR_ENAN; break; }
-    if (st.err) { res.status = (gdr_status)st.err; break; }
-    if (st.conv) { res.status = GDR_OK; res.broke = st.broke; break; }
-    if (res.mvps >= max_mvps || (max_cycles > 0 && res.cycles >= max_cycles)) { res.status = GDR_ENOCONV; break; }
+    bool any_active = false;
+    long mx = 0;
+    for (int c = 0; c < ncol; ++c) {
+      if (done[c]) continue;
+      res.col_mvps[c] += st[c].broke ? (st[c].m_eff - jstart) : (m - jstart);
+      mx = std::max(mx, res.col_mvps[c]);
+      if (st[c].nan) res.status = GDR_ENAN;
+      else if (st[c].err && res.status == GDR_OK) res.status = (gdr_status)st[c].err;
+      if (st[c].conv) res.col_conv[c] = 1;
+      if (st[c].broke && c == 0) res.broke = true;
+      if (st[c].active) any_active = true;
+      else done[c] = 1;
+    }
+    res.mvps = std::max(res.mvps, mx);
+    if (!any_active) break;
+    if (mx >= job.max_mvps || (job.max_cycles > 0 && res.cycles >= job.max_cycles)) {
+      if (res.status == GDR_OK) res.status = GDR_ENOCONV;
+      break;
+    }
     j0 = k;
-    if (k == 0) start_cycle<R>(ctx, b, rres, 0);
+    if (k == 0) start_cycle<R>(ctx, b, rres, b.ldv);
   }
   res.V = b.V;
   res.ldv = b.ldv;
   res.Hk = d.Hk;
   res.valid_defl = (k > 0) && !res.broke && res.status != GDR_ENAN && res.status != GDR_EBREAKDOWN;
-  std::vector<double> nr(ns);
-  GDR_CUDA(cudaMemcpyAsync(nr.data(), sh.norms, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->stream));
+  std::vector<double> nr((size_t)ns * ncol);
+  GDR_CUDA(cudaMemcpyAsync(nr.data(), sh.norms, sizeof(double) * ns * ncol, cudaMemcpyDeviceToHost, ctx->stream));
   GDR_CUDA(cudaStreamSynchronize(ctx->stream));
   res.norms = nr;
   return res;
@@ -284,6 +306,8 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
   const long n = A->n;
   const int ncol = job.ncol, ns = job.ns, mp = job.m_p, k = job.k;
   Batch<R> b = make_batch<R>(ctx, "pj", n, ncol, mp, ns, k + 2);
+  b.nvec = job.nvec;
+  b.cpp = job.cpp;
   Shifted sh = make_shifted(ctx, "pj", ncol, ns);
   GDR_CUDA(cudaMemcpyAsync(b.sigma, job.sigma.data(), sizeof(c128) * ns * ncol, cudaMemcpyHostToDevice,
                            ctx->stream));
@@ -300,7 +324,7 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
   std::vector<int> mk(ncol, 1);
   if (!job.mask.empty()) mk = job.mask;
   GDR_CUDA(cudaMemcpyAsync(mask, mk.data(), sizeof(int) * ncol, cudaMemcpyHostToDevice, ctx->stream));
-  norms2<cx<R>>(ctx, n, ncol, r, ldr, bn2, b.part, b.nblk, b.cnt);
+  norms2<cx<R>>(ctx, n, ncol, r, ldr, bn2, b.part, b.nblk, b.cnt, b.nvec);
   init_cols_kernel<<<(ncol + 31) / 32, 32, 0, ctx->stream>>>(b.st, ncol, bn2, tolv, mask, ns, sh.sact, sh.beta,
                                                               sh.gamma, sh.norms);
   GDR_LAUNCHED(ctx);
@@ -349,7 +373,7 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
     for (int j = 0; j < mp; ++j) arnoldi_step<R>(ctx, A, b, j);
     dense_cycle(ctx, d);
     combine<R>(ctx, n, ncol, b.V, b.ldv, b.vcs, mp + 1, d.Cf, ldc, d.ccs, 0, ns, 1, job.X, job.ldx, job.xcs, r, ldr,
-               b.st);
+               b.st, b.nvec);
     cycle_finish(ctx, d, b.H, b.cvec);
   };
   for (;;) {
@@ -446,7 +470,21 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
   cx<R>* bin = ctx->get<cx<R>>("pl.bin", (size_t)ld);
   to_inner<R>(ctx, n, 1, B, ldb, bin, ld);
   const double tol1 = mixed ? std::max(p.tol, p.inner_tol) : p.tol;
-  DrResult dr = dr_sh<R>(ctx, A, bin, sigma, m, k, tol1, p.max_mvps, p.max_cycles, X, ldx, use_graph);
+  DrJob<R> dj;
+  dj.ncol = 1;
+  dj.ns = ns;
+  dj.m = m;
+  dj.k = k;
+  dj.rhs = bin;
+  dj.ldrhs = ld;
+  dj.sigma = sigma;
+  dj.tol.assign(1, tol1);
+  dj.X = X;
+  dj.ldx = ldx;
+  dj.xcs = (long)ns * ldx;
+  dj.max_mvps = p.max_mvps;
+  dj.max_cycles = p.max_cycles;
+  DrResult dr = dr_sh<R>(ctx, A, dj, use_graph);
   rep.mvps_rhs1 = dr.mvps;
   rep.cycles_rhs1 = dr.cycles;
   if (dr.status == GDR_ENOCONV && p.max_cycles > 0) {
@@ -665,15 +703,144 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
   return status;
 }
 
+// ------------------------------------------------- batch of independent problems
+
+template <typename R>
+gdr_status solve_batch_pipeline(gdr_ctx* ctx, const gdr_op* A, int ns, const std::vector<c128>& sigma,
+                                const c128* B, c128* X, const gdr_params& p, gdr_report& rep, int* prob_status) {
+  const int np = A->nprob;
+  const long n = A->n, ld = pad_ld(n);
+  const bool mixed = std::is_same<R, float>::value;
+  const bool use_graph = !(p.flags & GDR_FLAG_NO_GRAPH);
+  const int m = p.m, k = p.k, mp = p.m_proj > 0 ? p.m_proj : p.m - p.k;
+  const int npair = np * ns;
+  GDR_CUDA(cudaMemsetAsync(X, 0, sizeof(c128) * ld * npair, ctx->stream));
+  // per-pair lengths (pair q = problem q / ns, shift q % ns)
+  std::vector<int> nvp_h(npair);
+  for (int q = 0; q < npair; ++q) nvp_h[q] = (int)A->nrow_host[q / ns];
+  int* nvp = ctx->get<int>("bt.nvp", (size_t)npair);
+  GDR_CUDA(cudaMemcpyAsync(nvp, nvp_h.data(), sizeof(int) * npair, cudaMemcpyHostToDevice, ctx->stream));
+  c128* sig_dev = ctx->get<c128>("bt.sigma", (size_t)npair);
+  GDR_CUDA(cudaMemcpyAsync(sig_dev, sigma.data(), sizeof(c128) * npair, cudaMemcpyHostToDevice, ctx->stream));
+  const int nblk = (int)std::min<long>((n + 255) / 256, 2L * ctx->num_sms);
+  c128* part = ctx->get<c128>("bt.part", (size_t)nblk * npair + 64);
+  unsigned* cnt = ctx->get<unsigned>("bt.cnt", (size_t)4 * npair);
+  double* out = ctx->get<double>("bt.out", (size_t)npair);
+  GDR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * 4 * npair, ctx->stream));
+  std::vector<double> bnorm(np);
+  norms2<c128>(ctx, n, np, B, ld, out, part, nblk, cnt, A->nrow);
+  GDR_CUDA(cudaMemcpyAsync(bnorm.data(), out, sizeof(double) * np, cudaMemcpyDeviceToHost, ctx->stream));
+  GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (auto& v : bnorm) v = std::sqrt(v);
+  // ---- every problem's GMRES-DR(m,k)-Sh, the problems as columns of one batch
+  cx<R>* bin = ctx->get<cx<R>>("bt.bin", (size_t)ld * np);
+  to_inner<R>(ctx, ld, np, B, ld, bin, ld);
+  DrJob<R> dj;
+  dj.ncol = np;
+  dj.ns = ns;
+  dj.m = m;
+  dj.k = k;
+  dj.rhs = bin;
+  dj.ldrhs = ld;
+  dj.sigma = sigma;
+  dj.tol.assign(np, mixed ? std::max(p.tol, p.inner_tol) : p.tol);
+  dj.nvec = A->nrow;
+  dj.cpp = 1;
+  dj.X = X;
+  dj.ldx = ld;
+  dj.xcs = (long)ns * ld;
+  dj.max_mvps = p.max_mvps;
+  dj.max_cycles = p.max_cycles;
+  DrResult dr = dr_sh<R>(ctx, A, dj, use_graph);
+  for (long v : dr.col_mvps) rep.mvps_rhs1 += v;
+  rep.cycles_rhs1 = dr.cycles;
+  gdr_status status = (dr.status == GDR_ENOCONV) ? GDR_OK : dr.status;
+  // ---- FP64 true residuals per (problem, shift), refinement / cleanup by batched GMRES(m_p)
+  c128* Rres = ctx->get<c128>("bt.Rres", (size_t)ld * npair);
+  auto residuals = [&](std::vector<double>& rr) {
+    GDR_CUDA(cudaMemsetAsync(Rres, 0, sizeof(c128) * ld * npair, ctx->stream));
+    op_apply<double>(ctx, A, npair, sig_dev, X, ld, Rres, ld, B, ld, ns);
+    norms2<c128>(ctx, n, npair, Rres, ld, out, part, nblk, cnt, nvp);
+    std::vector<double> h(npair);
+    GDR_CUDA(cudaMemcpyAsync(h.data(), out, sizeof(double) * npair, cudaMemcpyDeviceToHost, ctx->stream));
+    GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+    rr.resize(npair);
+    for (int q = 0; q < npair; ++q) rr[q] = std::sqrt(h[q]) / (bnorm[q / ns] > 0 ? bnorm[q / ns] : 1.0);
+    rep.resid_cols += npair;
+  };
+  std::vector<double> relres;
+  residuals(relres);
+  const int max_pass = (p.flags & GDR_FLAG_NO_REFINE) ? -1 : std::max(0, p.refine_max);
+  for (int pass = 0; pass <= max_pass; ++pass) {
+    std::vector<int> mask(npair, 0);
+    int nact = 0;
+    for (int q = 0; q < npair; ++q)
+      if (!(relres[q] <= p.tol)) {
+        mask[q] = 1;
+        ++nact;
+      }
+    if (nact == 0) break;
+    const bool cleanup = (pass == max_pass) || !mixed;
+    rep.refine_passes++;
+    if (cleanup) rep.pairs_cleaned += nact;
+    std::vector<double> tolc(npair);
+    for (int q = 0; q < npair; ++q)
+      tolc[q] = std::min(0.5, std::max(0.3 * p.tol / std::max(relres[q], 1e-300), cleanup ? 0.0 : p.inner_tol));
+    auto run = [&](auto tag) {
+      using RR = decltype(tag);
+      cx<RR>* rin = ctx->get<cx<RR>>("bt.rin", (size_t)ld * npair);
+      to_inner<RR>(ctx, ld, npair, Rres, ld, rin, ld);
+      ProjJob<RR> job;
+      job.ncol = npair;
+      job.ns = 1;
+      job.m_p = mp;
+      job.k = 0;
+      job.project = false;
+      job.rhs = rin;
+      job.ldrhs = ld;
+      job.sigma = sigma;
+      job.tol = tolc;
+      job.mask = mask;
+      job.nvec = nvp;
+      job.cpp = ns;
+      job.X = X;
+      job.ldx = ld;
+      job.xcs = ld;
+      job.max_mvps = p.max_mvps;
+      ProjResult pr = proj_batch<RR>(ctx, A, job, use_graph);
+      for (long v : pr.mvps) rep.mvps_refine += v;
+      if (pr.status == GDR_ENAN) status = GDR_ENAN;
+    };
+    if (cleanup)
+      run(double{});
+    else
+      run(R{});
+    residuals(relres);
+  }
+  double mx = 0;
+  for (int q = 0; q < npair; ++q) mx = std::max(mx, relres[q]);
+  rep.max_relres = mx;
+  if (prob_status)
+    for (int pb = 0; pb < np; ++pb) {
+      bool ok = true;
+      for (int i = 0; i < ns; ++i) ok = ok && relres[pb * ns + i] <= p.tol;
+      prob_status[pb] = ok ? GDR_OK : GDR_ENOCONV;
+    }
+  if (status == GDR_OK && !(mx <= p.tol)) status = GDR_ENOCONV;
+  return status;
+}
+
 // ------------------------------------------------------------ instances
 
-template DrResult dr_sh<float>(gdr_ctx*, const gdr_op*, const c64*, const std::vector<c128>&, int, int, double, long,
-                               int, c128*, long, bool);
-template DrResult dr_sh<double>(gdr_ctx*, const gdr_op*, const c128*, const std::vector<c128>&, int, int, double, long,
-                                int, c128*, long, bool);
+template DrResult dr_sh<float>(gdr_ctx*, const gdr_op*, const DrJob<float>&, bool);
+template DrResult dr_sh<double>(gdr_ctx*, const gdr_op*, const DrJob<double>&, bool);
 template ProjResult proj_batch<float>(gdr_ctx*, const gdr_op*, const ProjJob<float>&, bool);
 template ProjResult proj_batch<double>(gdr_ctx*, const gdr_op*, const ProjJob<double>&, bool);
 template gdr_status solve_pipeline<float>(gdr_ctx*, const gdr_op*, const std::vector<c128>&, int, const c128*, long,
                                           c128*, long, const gdr_params&, gdr_defl**, gdr_report&);
 template gdr_status solve_pipeline<double>(gdr_ctx*, const gdr_op*, const std::vector<c128>&, int, const c128*, long,
                                            c128*, long, const gdr_params&, gdr_defl**, gdr_report&);
+template gdr_status solve_batch_pipeline<float>(gdr_ctx*, const gdr_op*, int, const std::vector<c128>&, const c128*,
+                                                c128*, const gdr_params&, gdr_report&, int*);
+template gdr_status solve_batch_pipeline<double>(gdr_ctx*, const gdr_op*, int, const std::vector<c128>&, const c128*,
+                                                 c128*, const gdr_params&, gdr_report&, int*);

@@ -4,6 +4,22 @@
 
 #include "kernels.cuh"
 
+// One GMRES-DR(m,k)-Sh run on a batch of columns (independent Krylov spaces in lockstep).
+template <typename R>
+struct DrJob {
+  int ncol = 1, ns = 1, m = 0, k = 0;
+  const cx<R>* rhs = nullptr;  // column c at rhs + c*ldrhs
+  long ldrhs = 0;
+  std::vector<c128> sigma;     // ncol x ns, sigma[c*ns] the base shift of column c
+  std::vector<double> tol;     // relative tolerance per column
+  const int* nvec = nullptr;   // per-column vector length (device), nullptr: all A->n
+  int cpp = 1;                 // operator problem of column c is c / cpp
+  c128* X = nullptr;           // X + c*xcs + i*ldx accumulates shift i of column c (FP64)
+  long ldx = 0, xcs = 0;
+  long max_mvps = 100000;
+  int max_cycles = 0;
+};
+
 struct DrResult {
   gdr_status status = GDR_OK;
   long mvps = 0;
@@ -15,6 +31,8 @@ struct DrResult {
   long ldv = 0;
   c128* Hk = nullptr;      // kept Hbar_k ((k+1) x k) on the device
   std::vector<double> norms;
+  std::vector<long> col_mvps;  // per column
+  std::vector<int> col_conv;
 };
 
 // A batch of columns for GMRES(m_p)-Proj(k)-Sh.
@@ -30,6 +48,8 @@ struct ProjJob {
   std::vector<c128> sigma;     // ncol x ns, sigma[c*ns] the base shift of column c
   std::vector<double> tol;     // relative tolerance per column
   std::vector<int> mask;       // columns to solve (empty: all)
+  const int* nvec = nullptr;   // per-column vector length (device), nullptr: all A->n
+  int cpp = 1;                 // operator problem of column c is c / cpp
   c128* X = nullptr;           // X + c*xcs + i*ldx accumulates shift i of column c (FP64)
   long ldx = 0, xcs = 0;
   long max_mvps = 100000;
@@ -44,8 +64,12 @@ struct ProjResult {
 };
 
 template <typename R>
-DrResult dr_sh(gdr_ctx* ctx, const gdr_op* A, const cx<R>* b, const std::vector<c128>& sigma, int m, int k, double tol,
-               long max_mvps, int max_cycles, c128* X, long ldx, bool use_graph);
+DrResult dr_sh(gdr_ctx* ctx, const gdr_op* A, const DrJob<R>& job, bool use_graph);
+
+// Independent problems of a CSR batch, one right-hand side each (all with ns shifts).
+template <typename R>
+gdr_status solve_batch_pipeline(gdr_ctx* ctx, const gdr_op* A, int ns, const std::vector<c128>& sigma,
+                                const c128* B, c128* X, const gdr_params& p, gdr_report& rep, int* prob_status);
 
 template <typename R>
 ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool use_graph);
