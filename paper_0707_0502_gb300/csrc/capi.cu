@@ -427,7 +427,7 @@ gdr_status gdr_arnoldi_step(gdr_ctx* ctx, const gdr_op* A, gdr_prec prec, void* 
       b.h1 = ctx->get<c128>("step.h1", (size_t)(j + 3));
       b.h2 = ctx->get<c128>("step.h2", (size_t)(j + 3));
       const long units = (n * (long)sizeof(cx<R>) + 15) / 16;
-      b.nblk = (int)std::max<long>(1, std::min<long>((units + 255) / 256, 2L * ctx->num_sms));
+      b.nblk = (int)std::max<long>(1, std::min<long>((units + 255) / 256, 3L * ctx->num_sms));
       b.pstride = (long)b.nblk * (j + 3);
       b.part = ctx->get<c128>("step.part", (size_t)b.pstride + 64);
       b.cnt = ctx->get<unsigned>("step.cnt", 4);

@@ -14,7 +14,7 @@
 namespace {
 
 constexpr int NT = 256;  // threads of the reduction kernels
-constexpr int JB = 8;    // basis vectors per register chunk
+constexpr int JB = 8;    // basis vectors per register chunk (update)
 constexpr unsigned FULL = 0xffffffffu;
 
 // 16-byte units: 2 complex64 or 1 complex128
@@ -106,50 +106,82 @@ DEV bool last_block(unsigned* cnt) {
 
 // ------------------------------------------------------------ Gram-Schmidt
 
+// h = V^H w (+ ||w||^2): a block stages a tile of w in shared memory, each warp
+// takes whole basis vectors and its lanes stream DU units of that vector
+// (coalesced, DU loads in flight per lane); one warp reduction per (vector,
+// tile), accumulated in FP64.  w and V are each read once.
+template <typename R> struct DotTile { static constexpr int DU = (U<R>::K == 2) ? 16 : 8; };
+
 template <typename R>
-__global__ void __launch_bounds__(NT) gs_dot_kernel(Batch<R> b, int nv, const cx<R>* __restrict__ W, long wcs,
+__global__ void __launch_bounds__(NT, 3) gs_dot_kernel(Batch<R> b, int nv, const cx<R>* __restrict__ W, long wcs,
                                                     c128* __restrict__ hout, int hstride, int wnorm) {
   const int c = blockIdx.y;
   if (!b.st[c].run) return;
   constexpr int K = U<R>::K;
+  constexpr int DU = DotTile<R>::DU;
+  constexpr int TU = DU * 32;  // units per tile
+  __shared__ cx<R> wt[TU * K];
+  __shared__ c128 accs[GDR_MAX_M + 2];
   const cx<R>* __restrict__ V = b.V + c * b.vcs;
   const cx<R>* __restrict__ w = W + c * wcs;
   const long n = b.nvec ? (long)b.nvec[c] : b.n, nu = nunits<R>(n);
-  c128* part = b.part + c * b.pstride;
-  const long gt = blockIdx.x * (long)NT + threadIdx.x, gs = (long)gridDim.x * NT;
-  for (int i0 = 0; i0 < nv; i0 += JB) {
-    cx<R> acc[JB];
-#pragma unroll
-    for (int q = 0; q < JB; ++q) acc[q] = {0, 0};
-    for (long u = gt; u < nu; u += gs) {
-      cx<R> wv[K];
-      ldu<R>(w, u, n, wv);
-#pragma unroll
-      for (int q = 0; q < JB; ++q) {
-        if (i0 + q < nv) {
-          cx<R> vv[K];
-          ldu<R>(V + (long)(i0 + q) * b.ldv, u, n, vv);
-#pragma unroll
-          for (int kk = 0; kk < K; ++kk) acc[q] += cmulc(vv[kk], wv[kk]);
-        }
-      }
-    }
-    block_reduce<R, JB>(acc, part + (long)blockIdx.x * hstride + i0, min(JB, nv - i0));
-  }
-  if (wnorm) {
-    cx<R> a[1] = {{0, 0}};
-    for (long u = gt; u < nu; u += gs) {
-      cx<R> wv[K];
-      ldu<R>(w, u, n, wv);
-#pragma unroll
-      for (int kk = 0; kk < K; ++kk) a[0].x += norm2(wv[kk]);
-    }
-    block_reduce<R, 1>(a, part + (long)blockIdx.x * hstride + nv, 1);
-  }
-  if (!last_block(b.cnt + 4 * c)) return;
-  const int tot = nv + (wnorm ? 1 : 0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = warp; i < tot; i += NT / 32) hout[(long)c * hstride + i] = warp_sum_partials(part + i, hstride, lane);
+  const int nvec_tot = nv + (wnorm ? 1 : 0);
+  for (int i = threadIdx.x; i < nvec_tot; i += NT) accs[i] = {0, 0};
+  const long ntiles = (nu + TU - 1) / TU;
+  for (long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const long u0 = t * TU;
+    __syncthreads();  // readers of the previous tile are done
+    for (int q = threadIdx.x; q < TU; q += NT) {
+      cx<R> tmp[K];
+      if (u0 + q < nu) {
+        ldu<R>(w, u0 + q, n, tmp);
+      } else {
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) tmp[kk] = {0, 0};
+      }
+#pragma unroll
+      for (int kk = 0; kk < K; ++kk) wt[q * K + kk] = tmp[kk];
+    }
+    __syncthreads();
+    for (int i = warp; i < nvec_tot; i += NT / 32) {
+      cx<R> a = {0, 0};
+      if (i < nv) {
+        const cx<R>* vi = V + (long)i * b.ldv;
+        cx<R> vv[DU][K];
+#pragma unroll
+        for (int tt = 0; tt < DU; ++tt) {
+          const long u = u0 + lane + 32 * tt;
+          if (u < nu) {
+            ldu<R>(vi, u, n, vv[tt]);
+          } else {
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) vv[tt][kk] = {0, 0};
+          }
+        }
+#pragma unroll
+        for (int tt = 0; tt < DU; ++tt)
+#pragma unroll
+          for (int kk = 0; kk < K; ++kk) a += cmulc(vv[tt][kk], wt[(lane + 32 * tt) * K + kk]);
+      } else {  // ||w||^2
+#pragma unroll
+        for (int tt = 0; tt < DU; ++tt)
+#pragma unroll
+          for (int kk = 0; kk < K; ++kk) a.x += norm2(wt[(lane + 32 * tt) * K + kk]);
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        a.x += __shfl_xor_sync(FULL, a.x, off);
+        a.y += __shfl_xor_sync(FULL, a.y, off);
+      }
+      if (lane == 0) accs[i] += up(a);
+    }
+  }
+  __syncthreads();
+  c128* part = b.part + c * b.pstride;
+  for (int i = threadIdx.x; i < nvec_tot; i += NT) part[(long)blockIdx.x * hstride + i] = accs[i];
+  if (!last_block(b.cnt + 4 * c)) return;
+  for (int i = warp; i < nvec_tot; i += NT / 32) hout[(long)c * hstride + i] = warp_sum_partials(part + i, hstride, lane);
   __syncthreads();
   if (threadIdx.x == 0) b.cnt[4 * c] = 0;
 }
@@ -171,12 +203,21 @@ __global__ void __launch_bounds__(NT) gs_update_kernel(Batch<R> b, int nv, cx<R>
   for (long u = gt; u < nu; u += gs) {
     cx<R> acc[K];
     ldu<R>(w, u, n, acc);
-    for (int i = 0; i < nv; ++i) {
-      cx<R> vv[K];
-      ldu<R>(V + (long)i * b.ldv, u, n, vv);
-      const cx<R> hi = hs[i];
+    // basis vectors in groups of JB: all loads of a group are in flight together
+    for (int i0 = 0; i0 < nv; i0 += JB) {
+      cx<R> vv[JB][K];
 #pragma unroll
-      for (int kk = 0; kk < K; ++kk) acc[kk] -= vv[kk] * hi;
+      for (int q = 0; q < JB; ++q) {
+        if (i0 + q < nv) ldu<R>(V + (long)(i0 + q) * b.ldv, u, n, vv[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < JB; ++q) {
+        if (i0 + q < nv) {
+          const cx<R> hi = hs[i0 + q];
+#pragma unroll
+          for (int kk = 0; kk < K; ++kk) acc[kk] -= vv[q][kk] * hi;
+        }
+      }
     }
     stu<R>(w, u, n, acc);
 #pragma unroll

@@ -179,11 +179,11 @@ DEV void hop_mu(const LT* __restrict__ links, const cx<R>* __restrict__ x, long 
                 long stride, Spinor<R>& acc) {
   const long fwd = (coord == L - 1) ? site - (long)(L - 1) * stride : site + stride;
   const long bwd = (coord == 0) ? site + (long)(L - 1) * stride : site - stride;
-  Spinor<R> p;
-  load_spinor<R>(x, fwd, p);
-  hop<MU, true, R, LT>(links, V, site, p, acc);
-  load_spinor<R>(x, bwd, p);
-  hop<MU, false, R, LT>(links, V, bwd, p, acc);
+  Spinor<R> pf, pb;  // both neighbour spinors in flight before either hop's arithmetic
+  load_spinor<R>(x, fwd, pf);
+  load_spinor<R>(x, bwd, pb);
+  hop<MU, true, R, LT>(links, V, site, pf, acc);
+  hop<MU, false, R, LT>(links, V, bwd, pb, acc);
 }
 
 template <typename R, typename LT>

@@ -128,11 +128,14 @@ void run_cycle(gdr_ctx* ctx, bool use_graph, Graph& g, const std::function<void(
   ctx->launches += g.nodes;
 }
 
+// Grid of the Gram-Schmidt reduction kernels: enough 256-thread blocks for one
+// 16-byte unit per thread, at most 3 per SM (all resident in one wave at the
+// register use of the dot kernel).
 template <typename R>
 int nblk_for(gdr_ctx* ctx, long n) {
   const long units = (n * (long)sizeof(cx<R>) + 15) / 16;
   long g = (units + 255) / 256;
-  g = std::min<long>(g, 2L * ctx->num_sms);
+  g = std::min<long>(g, 3L * ctx->num_sms);
   return (int)std::max<long>(g, 1);
 }
 
