@@ -71,7 +71,9 @@ typedef struct {
   int m_proj;         /* GMRES cycle length in the Proj phase (0: m - k) */
   double tol;         /* relative residual target ||b - (A - sigma_i I) x|| / ||b|| */
   double extra_tol;   /* relative tolerance for the extra right-hand side v_{k+1} */
-  double inner_tol;   /* MIXED: relative reduction asked of each complex64 pass */
+  double inner_tol;   /* MIXED: relative residual of the complex64 GMRES-DR / Proj stages before FP64
+                         refinement; <= 0 chooses it: 1e-3 when the complex64 basis fits in half of
+                         the L2 cache (cycles limited by the FP64 dense steps), else 1e-5 */
   long max_mvps;      /* cap on Arnoldi matvecs per solve stage (per column) */
   int max_cycles;     /* 0: unlimited; else stop RHS 1 after this many cycles */
   int refine_max;     /* MIXED: refinement passes before the FP64 cleanup */
@@ -171,6 +173,15 @@ gdr_status gdr_solve_proj(gdr_ctx *ctx, const gdr_op *A, const gdr_defl *defl, i
  * (k+1) x k, column-major).  Either may be NULL.  *k_out receives k. */
 gdr_status gdr_defl_export(gdr_ctx *ctx, const gdr_defl *defl, double *V, double *Hbar, int *k_out);
 void gdr_defl_destroy(gdr_defl *defl);
+
+/* Per-kernel timing.  gdr_profile(ctx, 1) clears the counters and makes every
+ * later launch of the context bracketed by CUDA events on its stream (CUDA graphs
+ * are not used while it is on); gdr_profile(ctx, 0) switches it off.
+ * gdr_profile_report writes a JSON object {kernel: {"launches", "ms", "bytes"}} into
+ * buf (len bytes, NUL-terminated), "bytes" being the algorithmic bytes the launches
+ * move (0 for the dense FP64 kernels); it synchronises the stream. */
+gdr_status gdr_profile(gdr_ctx *ctx, int enable);
+gdr_status gdr_profile_report(gdr_ctx *ctx, char *buf, long len);
 
 /* --------------------------------------------------------- step-level calls
  * Single steps of the cycle, exposed for parity checks and benchmarks.  All

@@ -78,6 +78,8 @@ _SIGS = {
                                             ctypes.POINTER(gdr_report)]),
     "gdr_solve_proj": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, ctypes.c_int, _P, _P,
                                       ctypes.POINTER(gdr_params), ctypes.POINTER(gdr_report)]),
+    "gdr_profile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gdr_profile_report": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_long]),
     "gdr_defl_export": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_int)]),
     "gdr_defl_destroy": (None, [_P]),
     "gdr_arnoldi_step": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int, _P]),
@@ -257,6 +259,18 @@ def gdr_solve_proj(ctx, op, defl, sigma, B, X, params):
     if st not in (GDR_OK, GDR_ENOCONV):
         _check(st, ctx)
     return st, rep.as_dict()
+
+
+def gdr_profile(ctx, enable):
+    _check(lib().gdr_profile(ctx, 1 if enable else 0), ctx)
+
+
+def gdr_profile_report(ctx):
+    """{kernel: {"launches", "ms", "bytes"}} accumulated since gdr_profile(ctx, True)."""
+    import json
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(lib().gdr_profile_report(ctx, buf, len(buf)), ctx)
+    return json.loads(buf.value.decode())
 
 
 def gdr_defl_export(ctx, defl, V=None, n_k=None):

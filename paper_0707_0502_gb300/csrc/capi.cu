@@ -32,9 +32,20 @@ void check_params(const gdr_params& p) {
   GDR_REQUIRE(p.m >= 2 && p.m <= GDR_MAX_M, "m must be in [2, GDR_MAX_M]");
   GDR_REQUIRE(p.k >= 0 && p.k < p.m, "k must satisfy 0 <= k < m");
   GDR_REQUIRE(p.m_proj >= 0 && p.m_proj <= GDR_MAX_M, "m_proj must be in [0, GDR_MAX_M]");
-  GDR_REQUIRE(p.tol > 0 && p.extra_tol > 0 && p.inner_tol > 0, "tolerances must be positive");
+  GDR_REQUIRE(p.tol > 0 && p.extra_tol > 0, "tolerances must be positive");
   GDR_REQUIRE(p.max_mvps > 0, "max_mvps must be positive");
   GDR_REQUIRE(p.prec == GDR_PREC_FP64 || p.prec == GDR_PREC_MIXED, "unknown precision");
+}
+
+// inner_tol <= 0: loose complex64 stages when the basis is L2-resident (there the
+// FP64 dense steps of each GMRES-DR cycle dominate), tight ones otherwise.
+gdr_params resolve_inner_tol(const gdr_ctx* ctx, long n, const gdr_params& p) {
+  gdr_params r = p;
+  if (!(r.inner_tol > 0)) {
+    const double basis = (double)(p.m + 1) * (double)n * sizeof(c64);
+    r.inner_tol = (basis <= 0.5 * (double)ctx->l2_bytes) ? 1e-3 : 1e-5;
+  }
+  return r;
 }
 
 std::vector<c128> host_c128(const double* p, int count) {
@@ -55,7 +66,7 @@ void gdr_params_default(gdr_params* p) {
   p->m_proj = 0;
   p->tol = 1e-8;
   p->extra_tol = 1e-5;
-  p->inner_tol = 1e-5;
+  p->inner_tol = 0.0;  // automatic
   p->max_mvps = 100000;
   p->max_cycles = 0;
   p->refine_max = 3;
@@ -92,6 +103,7 @@ gdr_status gdr_create(gdr_ctx** out, int device, void* cuda_stream) {
     ctx->device = device;
     ctx->num_sms = prop.multiProcessorCount;
     ctx->max_smem_optin = prop.sharedMemPerBlockOptin;
+    ctx->l2_bytes = prop.l2CacheSize;
     if (cuda_stream) {
       ctx->stream = static_cast<cudaStream_t>(cuda_stream);
     } else {
@@ -249,10 +261,11 @@ gdr_status gdr_solve_multishift(gdr_ctx* ctx, const gdr_op* A, int ns, const dou
     const cudaMemcpyKind kout = (p.flags & GDR_FLAG_HOST_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     GDR_CUDA(cudaMemcpy2DAsync(Bi, ld * sizeof(c128), B, n * sizeof(c128), n * sizeof(c128), nrhs, kin,
                                ctx->stream));
+    const gdr_params pr = resolve_inner_tol(ctx, A->n, p);
     if (p.prec == GDR_PREC_MIXED)
-      result = solve_pipeline<float>(ctx, A, sig, nrhs, Bi, ld, Xi, ld, p, defl_out, rep);
+      result = solve_pipeline<float>(ctx, A, sig, nrhs, Bi, ld, Xi, ld, pr, defl_out, rep);
     else
-      result = solve_pipeline<double>(ctx, A, sig, nrhs, Bi, ld, Xi, ld, p, defl_out, rep);
+      result = solve_pipeline<double>(ctx, A, sig, nrhs, Bi, ld, Xi, ld, pr, defl_out, rep);
     GDR_CUDA(cudaMemcpy2DAsync(X, n * sizeof(c128), Xi, ld * sizeof(c128), n * sizeof(c128), (size_t)ns * nrhs, kout,
                                ctx->stream));
     GDR_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -291,10 +304,11 @@ gdr_status gdr_solve_batch(gdr_ctx* ctx, const gdr_op* A, int ns, const double* 
       GDR_CUDA(cudaMemcpyAsync(Bi + (long)q * ld, B + 2 * off, sizeof(c128) * nq, kin, ctx->stream));
       off += nq;
     }
+    const gdr_params pr = resolve_inner_tol(ctx, A->n * (long)A->nprob, p);
     if (p.prec == GDR_PREC_MIXED)
-      result = solve_batch_pipeline<float>(ctx, A, ns, sig, Bi, Xi, p, rep, status);
+      result = solve_batch_pipeline<float>(ctx, A, ns, sig, Bi, Xi, pr, rep, status);
     else
-      result = solve_batch_pipeline<double>(ctx, A, ns, sig, Bi, Xi, p, rep, status);
+      result = solve_batch_pipeline<double>(ctx, A, ns, sig, Bi, Xi, pr, rep, status);
     off = 0;
     for (int q = 0; q < np; ++q) {
       const long nq = A->nrow_host[q];
@@ -380,6 +394,50 @@ gdr_status gdr_solve_proj(gdr_ctx* ctx, const gdr_op* A, const gdr_defl* defl, i
   });
   if (report) *report = rep;
   return st != GDR_OK ? st : result;
+}
+
+gdr_status gdr_profile(gdr_ctx* ctx, int enable) {
+  if (!ctx) return GDR_EINVAL;
+  return guarded(ctx, [&] {
+    GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (auto& r : ctx->prof_pending) {
+      ctx->ev_pool.push_back(r.a);
+      ctx->ev_pool.push_back(r.b);
+    }
+    ctx->prof_pending.clear();
+    ctx->prof.clear();
+    ctx->profile = enable != 0;
+  });
+}
+
+gdr_status gdr_profile_report(gdr_ctx* ctx, char* buf, long len) {
+  if (!ctx || !buf || len <= 0) return GDR_EINVAL;
+  return guarded(ctx, [&] {
+    GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (auto& r : ctx->prof_pending) {
+      float ms = 0;
+      GDR_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+      auto& g = ctx->prof[r.name];
+      g.launches++;
+      g.ms += ms;
+      g.bytes += r.bytes;
+      ctx->ev_pool.push_back(r.a);
+      ctx->ev_pool.push_back(r.b);
+    }
+    ctx->prof_pending.clear();
+    std::string s = "{";
+    bool first = true;
+    for (auto& kv : ctx->prof) {
+      char line[256];
+      std::snprintf(line, sizeof(line), "%s\"%s\": {\"launches\": %ld, \"ms\": %.6f, \"bytes\": %.0f}",
+                    first ? "" : ", ", kv.first.c_str(), kv.second.launches, kv.second.ms, kv.second.bytes);
+      s += line;
+      first = false;
+    }
+    s += "}";
+    GDR_REQUIRE((long)s.size() < len, "profile report buffer too small");
+    std::memcpy(buf, s.c_str(), s.size() + 1);
+  });
 }
 
 gdr_status gdr_defl_export(gdr_ctx* ctx, const gdr_defl* defl, double* V, double* Hbar, int* k_out) {

@@ -88,6 +88,7 @@ struct gdr_ctx {
   bool own_stream = false;
   int num_sms = 0;
   size_t max_smem_optin = 0;
+  size_t l2_bytes = 0;
   size_t dense_smem_limit = 0;    // dynamic shared memory available to the dense kernels
   size_t combine_smem_limit = 0;  // ... and to the basis-combination kernel
   std::string err;
@@ -95,6 +96,31 @@ struct gdr_ctx {
   void* pinned = nullptr;            // small pinned host buffer for status words
   size_t pinned_bytes = 0;
   long launches = 0;                 // kernels launched (graph replays add their node count)
+
+  // per-kernel timing (gdr_profile): CUDA events around every launch, graphs off
+  struct ProfRec {
+    const char* name;
+    double bytes;
+    cudaEvent_t a, b;
+  };
+  struct ProfAgg {
+    long launches = 0;
+    double ms = 0, bytes = 0;
+  };
+  bool profile = false;
+  std::vector<ProfRec> prof_pending;
+  std::vector<cudaEvent_t> ev_pool;
+  std::map<std::string, ProfAgg> prof;
+  cudaEvent_t take_event() {
+    if (ev_pool.empty()) {
+      cudaEvent_t e;
+      GDR_CUDA(cudaEventCreate(&e));
+      return e;
+    }
+    cudaEvent_t e = ev_pool.back();
+    ev_pool.pop_back();
+    return e;
+  }
 
   // device workspace `name` of at least `bytes`; contents undefined after growth
   void* get(const std::string& name, size_t bytes) {
@@ -180,6 +206,23 @@ size_t set_max_dyn_smem(gdr_ctx* ctx, F* f) {
   GDR_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
   return dyn;
 }
+
+// Brackets one kernel launch with CUDA events when profiling is on.
+struct KProf {
+  gdr_ctx* ctx;
+  int idx = -1;
+  KProf(gdr_ctx* c, const char* name, double bytes) : ctx(c) {
+    if (c->profile) {
+      gdr_ctx::ProfRec r{name, bytes, c->take_event(), c->take_event()};
+      GDR_CUDA(cudaEventRecord(r.a, c->stream));
+      c->prof_pending.push_back(r);
+      idx = (int)c->prof_pending.size() - 1;
+    }
+  }
+  ~KProf() {
+    if (idx >= 0) cudaEventRecord(ctx->prof_pending[idx].b, ctx->stream);
+  }
+};
 
 // ---------------------------------------------------- launchers (per file)
 

@@ -974,11 +974,17 @@ void dense_cycle(gdr_ctx* ctx, const DenseCycle& d) {
   const size_t smem = dense_smem_bytes(d.m, d.k);
   GDR_REQUIRE(smem <= ctx->dense_smem_limit, "basis size m too large for the dense FP64 kernels");
   dim3 g1(d.k > 0 ? 2 : 1, (unsigned)d.ncol);
-  dense_d1_kernel<<<g1, DT, smem, ctx->stream>>>(d);
-  GDR_LAUNCHED(ctx);
+  {
+    KProf kp(ctx, d.k > 0 ? "dense_ls_harmonic_ritz" : "dense_ls", 0.0);
+    dense_d1_kernel<<<g1, DT, smem, ctx->stream>>>(d);
+    GDR_LAUNCHED(ctx);
+  }
   dim3 g2((unsigned)d.ns, (unsigned)d.ncol);
-  dense_d2_kernel<<<g2, DT, smem, ctx->stream>>>(d);
-  GDR_LAUNCHED(ctx);
+  {
+    KProf kp(ctx, "dense_shifts_restart", 0.0);
+    dense_d2_kernel<<<g2, DT, smem, ctx->stream>>>(d);
+    GDR_LAUNCHED(ctx);
+  }
 }
 
 void cycle_finish(gdr_ctx* ctx, const DenseCycle& d, c128* H, c128* cvec) {
@@ -993,6 +999,7 @@ void dense_projection(gdr_ctx* ctx, int ncol, int k, int ns, const c128* Hk, con
   const size_t smem = sizeof(c128) * ((size_t)(k + 2) * (k + 1) + 5 * (size_t)(k + 2));
   GDR_REQUIRE(smem <= ctx->dense_smem_limit, "k too large for the projection kernel");
   dim3 g((unsigned)ns, (unsigned)ncol);
+  KProf kp(ctx, "dense_projection", 0.0);
   dense_proj_kernel<<<g, DT, smem, ctx->stream>>>(a);
   GDR_LAUNCHED(ctx);
 }

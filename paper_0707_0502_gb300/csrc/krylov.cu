@@ -460,18 +460,22 @@ unsigned grid_for(gdr_ctx* ctx, long work, int threads) {
 template <typename R>
 void gs_dot(gdr_ctx* ctx, const Batch<R>& b, int nv, const cx<R>* w, long wcs, c128* h_out, bool wnorm) {
   dim3 grid((unsigned)b.nblk, (unsigned)b.ncol);
+  KProf kp(ctx, sizeof(R) == 4 ? "gs_dot_c64" : "gs_dot_c128", (double)(nv + 1) * b.n * sizeof(cx<R>) * b.ncol);
   gs_dot_kernel<R><<<grid, NT, 0, ctx->stream>>>(b, nv, w, wcs, h_out, b.m + 2, wnorm ? 1 : 0);
   GDR_LAUNCHED(ctx);
 }
 template <typename R>
 void gs_update(gdr_ctx* ctx, const Batch<R>& b, int nv, cx<R>* w, long wcs, const c128* h, bool final_step) {
   dim3 grid((unsigned)b.nblk, (unsigned)b.ncol);
+  KProf kp(ctx, sizeof(R) == 4 ? "gs_update_c64" : "gs_update_c128",
+           (double)(nv + 2) * b.n * sizeof(cx<R>) * b.ncol);
   gs_update_kernel<R><<<grid, NT, 0, ctx->stream>>>(b, nv, w, wcs, h, b.m + 2, final_step ? 1 : 0);
   GDR_LAUNCHED(ctx);
 }
 template <typename R>
 void scale_into(gdr_ctx* ctx, const Batch<R>& b, int j, const cx<R>* w, long wcs) {
   dim3 grid(grid_for(ctx, nunits<R>(b.n), 256), (unsigned)b.ncol);
+  KProf kp(ctx, "scale", 2.0 * b.n * sizeof(cx<R>) * b.ncol);
   scale_kernel<R><<<grid, 256, 0, ctx->stream>>>(b, j, w, wcs);
   GDR_LAUNCHED(ctx);
 }
@@ -502,6 +506,7 @@ template <typename T>
 void norms2(gdr_ctx* ctx, long n, int cols, const T* x, long xcs, double* out, c128* part, int nblk, unsigned* cnt,
             const int* nvec) {
   dim3 grid((unsigned)nblk, (unsigned)cols);
+  KProf kp(ctx, "norms", (double)n * sizeof(T) * cols);
   norms2_kernel<T><<<grid, NT, 0, ctx->stream>>>(n, x, xcs, out, part, cnt, nvec);
   GDR_LAUNCHED(ctx);
 }
@@ -521,6 +526,9 @@ void combine(gdr_ctx* ctx, long n, int ncol, cx<R>* V, long ldv, long vcs, int n
   const size_t smem = sizeof(cx<R>) * ((size_t)CR * nv + (size_t)nv * ntot);
   GDR_REQUIRE(smem <= ctx->combine_smem_limit, "combine: too many basis vectors / outputs for shared memory");
   dim3 grid((unsigned)((n + CR - 1) / CR), (unsigned)ncol);
+  KProf kp(ctx, sizeof(R) == 4 ? "combine_c64" : "combine_c128",
+           (double)ncol * n * ((nv + nout) * sizeof(cx<R>) + 2.0 * nx * sizeof(c128) +
+                               (rmode == 2 ? 2.0 : (rmode == 1 ? 1.0 : 0.0)) * sizeof(cx<R>)));
   combine_kernel<R><<<grid, CT, smem, ctx->stream>>>(n, V, ldv, vcs, nv, C, ldc, ccs, nout, nx, rmode, X, ldx, xcs,
                                                      Rv, rcs, st, nvec);
   GDR_LAUNCHED(ctx);

@@ -228,9 +228,34 @@ __global__ void __launch_bounds__(128) wilson_kernel(const LT* __restrict__ link
 }  // namespace
 
 template <typename R>
+static void op_apply_launch(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, const cx<R>* X, long ldx,
+                            cx<R>* Y, long ldy, const cx<R>* B, long ldb, const int* run, int run_stride, int cpp);
+
+template <typename R>
 static void op_apply_impl(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, const cx<R>* X, long ldx,
                           cx<R>* Y, long ldy, const cx<R>* B, long ldb, const int* run, int run_stride, int cpp) {
   if (ncol <= 0) return;
+  constexpr bool F64 = std::is_same<R, double>::value;
+  const double sv = sizeof(cx<R>);
+  if (A->kind == OP_CSR || A->kind == OP_CSR_BATCH) {
+    // row pointers, column indices, values, x read, y written (+ b read)
+    const double bytes = (double)A->n * 4 + (double)A->nnz * (4 + (F64 ? 16 : 8)) +
+                         (double)ncol * A->n * sv * (B ? 3 : 2);
+    KProf kp(ctx, F64 ? "csr_matvec_c128" : "csr_matvec_c64", bytes);
+    op_apply_launch<R>(ctx, A, ncol, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride, cpp);
+  } else {
+    // per site: 4 links of 18 reals, 24 reals of x read and of y written (+ b read)
+    const double sl = F64 ? 8 : (A->store == GDR_LINK_BF16 ? 2 : 4);
+    const double bytes = (double)A->V * (4 * 18 * sl + (double)ncol * 12 * sv * (B ? 3 : 2));
+    KProf kp(ctx, F64 ? "wilson_matvec_c128" : (A->store == GDR_LINK_BF16 ? "wilson_matvec_c64_bf16links"
+                                                                        : "wilson_matvec_c64"), bytes);
+    op_apply_launch<R>(ctx, A, ncol, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride, cpp);
+  }
+}
+
+template <typename R>
+static void op_apply_launch(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, const cx<R>* X, long ldx,
+                            cx<R>* Y, long ldy, const cx<R>* B, long ldb, const int* run, int run_stride, int cpp) {
   constexpr bool F64 = std::is_same<R, double>::value;
   if (A->kind == OP_CSR) {
     dim3 grid((unsigned)((A->n + 255) / 256), (unsigned)ncol);

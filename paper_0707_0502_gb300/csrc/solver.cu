@@ -102,7 +102,7 @@ struct Graph {
 };
 
 void run_cycle(gdr_ctx* ctx, bool use_graph, Graph& g, const std::function<void()>& enqueue) {
-  if (!use_graph) {
+  if (!use_graph || ctx->profile) {  // per-kernel events need direct launches
     enqueue();
     return;
   }
