@@ -224,10 +224,16 @@ gdr_status gdr_dense_gmres_sh_noalloc(gdr_ctx *ctx, int m, int ns, const double 
 /* GMRES-DR restart (Sec. 2.2): harmonic Ritz pairs of Hhat = Hbar - sigma1 Ibar,
  * k of smallest |theta| (ties: larger Im, then larger Re), P_{k+1} = [orth([G;0]), p],
  * p from s; Hk = P^H Hbar P_k ((k+1) x k), ck = P^H s (k+1).
+ * prec GDR_PREC_FP64: the eigensolve in FP64.  GDR_PREC_MIXED: the form the
+ * solver uses with a complex64 basis -- f refined to FP64 accuracy, the
+ * Hessenberg reduction, QR iteration, eigenvectors and the orthonormalisation of
+ * P_k in FP32 (P_k orthonormal to ~1e-7, theta to FP32 accuracy), falling back
+ * to FP64 where FP32 does not suffice; p, Hk and ck in FP64.
  * In: Hbar c128 (m+1) x m, s c128[m+1], sigma1 host c128.  Out: theta c128[m]
  * (all harmonic Ritz values, unordered), P c128 (m+1) x (k+1), Hk, ck. */
-gdr_status gdr_dense_restart(gdr_ctx *ctx, int m, int k, const double *sigma1, const double *Hbar,
-                             const double *s, double *theta, double *P, double *Hk, double *ck);
+gdr_status gdr_dense_restart(gdr_ctx *ctx, gdr_prec prec, int m, int k, const double *sigma1,
+                             const double *Hbar, const double *s, double *theta, double *P, double *Hk,
+                             double *ck);
 
 /* Basis update (restart, eq. recur1, fused with the multi-shift update):
  * V (n x nv, `prec`) times coefficients C (c128 nv x (nout + nx)):

@@ -86,7 +86,7 @@ _SIGS = {
     "gdr_dense_gmres_sh": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, _P]),
     "gdr_dense_gmres_sh_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P,
                                                   _P]),
-    "gdr_dense_restart": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P]),
+    "gdr_dense_restart": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P]),
     "gdr_basis_update": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_long, ctypes.c_int, _P, _P, ctypes.c_int,
                                         ctypes.c_int, _P]),
 }
@@ -309,10 +309,10 @@ def gdr_dense_gmres_sh_noalloc(ctx, m, sigma, Hbar, c, beta, D, s, beta_new, nor
                                             _ptr(D), _ptr(s), _ptr(beta_new), _ptr(norms)), ctx)
 
 
-def gdr_dense_restart(ctx, m, k, sigma1, Hbar, s, theta, P, Hk, ck):
+def gdr_dense_restart(ctx, prec, m, k, sigma1, Hbar, s, theta, P, Hk, ck):
     sg = _c128_host([sigma1])
-    _check(lib().gdr_dense_restart(ctx, int(m), int(k), sg.ctypes.data, _ptr(Hbar), _ptr(s), _ptr(theta), _ptr(P),
-                                   _ptr(Hk), _ptr(ck)), ctx)
+    _check(lib().gdr_dense_restart(ctx, int(prec), int(m), int(k), sg.ctypes.data, _ptr(Hbar), _ptr(s), _ptr(theta),
+                                   _ptr(P), _ptr(Hk), _ptr(ck)), ctx)
 
 
 def gdr_basis_update(ctx, prec, n, nv, V, C, nout, nx, X):

@@ -550,14 +550,16 @@ gdr_status gdr_dense_gmres_sh(gdr_ctx* ctx, int m, int ns, const double* Hbar, c
   });
 }
 
-gdr_status gdr_dense_restart(gdr_ctx* ctx, int m, int k, const double* sigma1, const double* Hbar, const double* s,
-                             double* theta, double* P, double* Hk, double* ck) {
+gdr_status gdr_dense_restart(gdr_ctx* ctx, gdr_prec prec, int m, int k, const double* sigma1, const double* Hbar,
+                             const double* s, double* theta, double* P, double* Hk, double* ck) {
   if (!ctx) return GDR_EINVAL;
   return guarded(ctx, [&] {
     GDR_REQUIRE(m >= 2 && m <= GDR_MAX_M && k >= 1 && k < m, "bad sizes");
+    GDR_REQUIRE(prec == GDR_PREC_FP64 || prec == GDR_PREC_MIXED, "prec must be GDR_PREC_FP64 or GDR_PREC_MIXED");
     GDR_REQUIRE(sigma1 && Hbar && s && theta && P && Hk && ck, "null argument");
     DenseCycle d{};
     d.ncol = 1; d.m = m; d.k = k; d.ns = 1; d.kfull = m + 1;  // general Hbar
+    d.hr32 = (prec == GDR_PREC_MIXED) ? 1 : 0;
     c128* sg = ctx->get<c128>("rstep.sigma", 1);
     GDR_CUDA(cudaMemcpyAsync(sg, sigma1, sizeof(c128), cudaMemcpyHostToDevice, ctx->stream));
     d.H = reinterpret_cast<const c128*>(Hbar);

@@ -27,46 +27,70 @@ namespace {
 
 constexpr int DT = 128;  // threads per dense CTA
 constexpr unsigned FULL = 0xffffffffu;
-constexpr double EPS = 2.220446049250313e-16;
+// precision-dependent limits of the dense steps
+template <typename R> struct Lim;
+template <> struct Lim<double> {
+  static constexpr double eps = 2.220446049250313e-16;
+  static constexpr double tie = 1e-9;  // relative width of a tie in the selection order
+  static constexpr double tiny = 1e-300;
+};
+template <> struct Lim<float> {
+  static constexpr float eps = 1.1920929e-7f;
+  static constexpr float tie = 2e-5f;
+  static constexpr float tiny = 1e-30f;
+};
 
-DEV c128 cdiv(c128 a, c128 b) {
-  const double d = b.x * b.x + b.y * b.y;
+DEV double sqrt_(double a) { return sqrt(a); }
+DEV float sqrt_(float a) { return sqrtf(a); }
+DEV double fabs_(double a) { return fabs(a); }
+DEV float fabs_(float a) { return fabsf(a); }
+DEV double fmax_(double a, double b) { return fmax(a, b); }
+DEV float fmax_(float a, float b) { return fmaxf(a, b); }
+DEV double copysign_(double a, double b) { return copysign(a, b); }
+DEV float copysign_(float a, float b) { return copysignf(a, b); }
+DEV double hypot_(double a, double b) { return hypot(a, b); }
+DEV float hypot_(float a, float b) { return hypotf(a, b); }
+
+template <typename R> DEV cx<R> cdiv(cx<R> a, cx<R> b) {
+  const R d = b.x * b.x + b.y * b.y;
   return {(a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d};
 }
-DEV double cabs_(c128 a) { return hypot(a.x, a.y); }
-DEV c128 csqrt_(c128 z) {
-  const double r = cabs_(z);
-  if (r == 0.0) return {0, 0};
-  const double re = sqrt(0.5 * (r + fabs(z.x)));
-  if (z.x >= 0) return {re, z.y / (2 * re)};
-  return {fabs(z.y) / (2 * re), copysign(re, z.y)};
+template <typename R> DEV R cabs_(cx<R> a) { return hypot_(a.x, a.y); }
+template <typename R> DEV cx<R> csqrt_(cx<R> z) {
+  const R r = cabs_(z);
+  if (r == R(0)) return {0, 0};
+  const R re = sqrt_(R(0.5) * (r + fabs_(z.x)));
+  if (z.x >= R(0)) return {re, z.y / (2 * re)};
+  return {fabs_(z.y) / (2 * re), copysign_(re, z.y)};
 }
-DEV c128 shfl_xor_c(c128 v, int m) {
+template <typename R> DEV cx<R> shfl_xor_c(cx<R> v, int m) {
   return {__shfl_xor_sync(FULL, v.x, m), __shfl_xor_sync(FULL, v.y, m)};
 }
-DEV c128 warp_sum_c(c128 v) {
+template <typename R> DEV cx<R> warp_sum_c(cx<R> v) {
 #pragma unroll
   for (int m = 16; m > 0; m >>= 1) v += shfl_xor_c(v, m);
   return v;
 }
-DEV double warp_sum_d(double v) {
+template <typename R> DEV R warp_sum_r(R v) {
 #pragma unroll
   for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(FULL, v, m);
   return v;
 }
 
-struct Sh {  // small shared scratch of a dense CTA
-  double red[DT / 32];
-  c128 bc[4];
-  c128 nx[4];  // QR sweep: entries (kk+1, kk), (kk+1, kk+1), (kk+2, kk), (kk+2, kk+1) after the left update
+template <typename R>
+struct ShT {  // small shared scratch of a dense CTA
+  R red[DT / 32];
+  cx<R> bc[4];
+  cx<R> nx[4];  // QR sweep: entries (kk+1, kk), (kk+1, kk+1), (kk+2, kk), (kk+2, kk+1) after the left update
   int ibc[4];
 };
+using Sh = ShT<double>;
 
-DEV double block_sum(double v, Sh& sh) {
-  v = warp_sum_d(v);
+template <typename R> DEV R block_sum(R v, ShT<R>& sh) {
+  v = warp_sum_r(v);
   if ((threadIdx.x & 31) == 0) sh.red[threadIdx.x >> 5] = v;
   __syncthreads();
-  double t = 0;
+  R t = 0;
 #pragma unroll
   for (int w = 0; w < DT / 32; ++w) t += sh.red[w];
   __syncthreads();
@@ -81,53 +105,55 @@ DEV double block_sum(double v, Sh& sh) {
 // reflector j spans rows j..last(j) only.
 DEV int qr_last(int j, int rows, int kfull) { return min(rows - 1, max(j + 1, kfull)); }
 
-DEV void cta_qr(c128* A, int lda, int rows, int cols, int ntot, c128* tau, Sh& sh, int kfull) {
+template <typename R>
+DEV void cta_qr(cx<R>* A, int lda, int rows, int cols, int ntot, cx<R>* tau, ShT<R>& sh, int kfull) {
+  using C = cx<R>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int j = 0; j < cols && j < rows; ++j) {
     const int last = qr_last(j, rows, kfull);
-    double s = 0;
+    R s = 0;
     for (int i = j + 1 + threadIdx.x; i <= last; i += DT) s += norm2(A[i + (long)j * lda]);
     s = block_sum(s, sh);
     if (threadIdx.x == 0) {
-      const c128 alpha = A[j + (long)j * lda];
-      if (s == 0.0 && alpha.y == 0.0) {
+      const C alpha = A[j + (long)j * lda];
+      if (s == R(0) && alpha.y == R(0)) {
         tau[j] = {0, 0};
       } else {
-        const double beta = -copysign(sqrt(norm2(alpha) + s), alpha.x);
+        const R beta = -copysign_(sqrt_(norm2(alpha) + s), alpha.x);
         tau[j] = {(beta - alpha.x) / beta, -alpha.y / beta};
-        sh.bc[0] = cdiv(c128{1, 0}, alpha - c128{beta, 0});
+        sh.bc[0] = cdiv(C{1, 0}, alpha - C{beta, 0});
         A[j + (long)j * lda] = {beta, 0};
       }
     }
     __syncthreads();
-    const c128 tj = tau[j];
-    if (tj.x == 0.0 && tj.y == 0.0) continue;  // uniform across the CTA
-    const c128 scal = sh.bc[0];
+    const C tj = tau[j];
+    if (tj.x == R(0) && tj.y == R(0)) continue;  // uniform across the CTA
+    const C scal = sh.bc[0];
     for (int i = j + 1 + threadIdx.x; i <= last; i += DT) A[i + (long)j * lda] = A[i + (long)j * lda] * scal;
     __syncthreads();
-    const c128 ct = conj(tj);
+    const C ct = conj(tj);
     if (last - j < 32) {
       // short reflector: one thread per column
       for (int cc = j + 1 + threadIdx.x; cc < ntot; cc += DT) {
-        c128* col = A + (long)cc * lda;
-        c128 w = col[j];
+        C* col = A + (long)cc * lda;
+        C w = col[j];
         for (int i = j + 1; i <= last; ++i) w += cmulc(A[i + (long)j * lda], col[i]);
-        const c128 f = ct * w;
+        const C f = ct * w;
         col[j] -= f;
         for (int i = j + 1; i <= last; ++i) col[i] -= A[i + (long)j * lda] * f;
       }
     } else {
       for (int cc = j + 1 + warp; cc < ntot; cc += DT / 32) {
-        c128* col = A + (long)cc * lda;
-        c128 w = {0, 0};
+        C* col = A + (long)cc * lda;
+        C w = {0, 0};
         for (int i = j + lane; i <= last; i += 32) {
-          const c128 vi = (i == j) ? c128{1, 0} : A[i + (long)j * lda];
+          const C vi = (i == j) ? C{1, 0} : A[i + (long)j * lda];
           w += cmulc(vi, col[i]);
         }
         w = warp_sum_c(w);
-        const c128 f = ct * w;
+        const C f = ct * w;
         for (int i = j + lane; i <= last; i += 32) {
-          const c128 vi = (i == j) ? c128{1, 0} : A[i + (long)j * lda];
+          const C vi = (i == j) ? C{1, 0} : A[i + (long)j * lda];
           col[i] -= vi * f;
         }
       }
@@ -137,14 +163,15 @@ DEV void cta_qr(c128* A, int lda, int rows, int cols, int ntot, c128* tau, Sh& s
 }
 
 // y <- Q y for the reflectors of cta_qr (applied in reverse order), one thread.
-DEV void apply_q_serial(const c128* A, int lda, int rows, int cols, const c128* tau, c128* y, int kfull) {
+template <typename R>
+DEV void apply_q_serial(const cx<R>* A, int lda, int rows, int cols, const cx<R>* tau, cx<R>* y, int kfull) {
   for (int j = min(cols, rows) - 1; j >= 0; --j) {
-    const c128 tj = tau[j];
-    if (tj.x == 0.0 && tj.y == 0.0) continue;
+    const cx<R> tj = tau[j];
+    if (tj.x == R(0) && tj.y == R(0)) continue;
     const int last = qr_last(j, rows, kfull);
-    c128 w = y[j];
+    cx<R> w = y[j];
     for (int i = j + 1; i <= last; ++i) w += cmulc(A[i + (long)j * lda], y[i]);
-    const c128 f = tj * w;
+    const cx<R> f = tj * w;
     y[j] -= f;
     for (int i = j + 1; i <= last; ++i) y[i] -= A[i + (long)j * lda] * f;
   }
@@ -172,13 +199,14 @@ DEV bool cta_backsolve(const c128* A, int lda, int nsz, c128* y, Sh& sh) {
   return ok;
 }
 
-// load (Hbar - sig Ibar)[0:rows, 0:cols] into A (lda)
-DEV void load_shifted(c128* A, int lda, const c128* H, int ldh, int rows, int cols, c128 sig) {
+// load (Hbar - sig Ibar)[0:rows, 0:cols] into A (lda), rounded to the precision of A
+template <typename R>
+DEV void load_shifted(cx<R>* A, int lda, const c128* H, int ldh, int rows, int cols, c128 sig) {
   for (int t = threadIdx.x; t < rows * cols; t += DT) {
     const int i = t % rows, j = t / rows;
     c128 v = H[i + (long)j * ldh];
     if (i == j) v -= sig;
-    A[i + (long)j * lda] = v;
+    A[i + (long)j * lda] = cvt<R>(v);
   }
 }
 
@@ -290,9 +318,10 @@ DEV void shift_solve(const DenseCycle& d, int c, int i, c128* A, Sh& sh) {
 
 // --------------------------------------------------- harmonic Ritz (D1)
 
-// 1/sqrt(a) for a > 0: single-precision estimate, then two Newton steps
-// y <- y (3 - a y^2) / 2 in FP64 (quadratic convergence: ~1e-7 -> 1e-14 -> 1e-16).
-// A normal-range float must hold a; otherwise fall back to the FP64 expression.
+// 1/sqrt(a) for a > 0.  FP64: single-precision estimate, then two Newton steps
+// y <- y (3 - a y^2) / 2 (quadratic convergence: ~1e-7 -> 1e-14 -> 1e-16); a
+// normal-range float must hold a, otherwise the FP64 expression is used.
+// FP32: the hardware estimate and one Newton step.
 DEV double rsqrt_nr(double a) {
   if (!(a > 1e-36 && a < 1e36)) return 1.0 / sqrt(a);
   double y = (double)rsqrtf((float)a);
@@ -300,142 +329,229 @@ DEV double rsqrt_nr(double a) {
   y = y * (1.5 - 0.5 * a * y * y);
   return y;
 }
+DEV float rsqrt_nr(float a) {
+  const float y = rsqrtf(a);
+  return y * (1.5f - 0.5f * a * y * y);
+}
 
 // Givens rotation U = [[cs, sn], [-conj(sn), cs]] with U [x; y] = [r; 0]; rot = {cs, Re sn, Im sn}
-DEV void givens(c128 x, c128 y, double* rot) {
-  const double ax2 = norm2(x), ay2 = norm2(y);
-  if (ay2 == 0.0) {
-    rot[0] = 1.0; rot[1] = 0.0; rot[2] = 0.0;
-  } else if (ax2 == 0.0) {
-    const double inv = rsqrt_nr(ay2);
-    rot[0] = 0.0; rot[1] = y.x * inv; rot[2] = -y.y * inv;
+template <typename R> DEV void givens(cx<R> x, cx<R> y, R* rot) {
+  const R ax2 = norm2(x), ay2 = norm2(y);
+  if (ay2 == R(0)) {
+    rot[0] = 1; rot[1] = 0; rot[2] = 0;
+  } else if (ax2 == R(0)) {
+    const R inv = rsqrt_nr(ay2);
+    rot[0] = 0; rot[1] = y.x * inv; rot[2] = -y.y * inv;
   } else {
-    const double inv_r = rsqrt_nr(ax2 + ay2);
-    const double inv_ax = rsqrt_nr(ax2);
+    const R inv_r = rsqrt_nr(ax2 + ay2);
+    const R inv_ax = rsqrt_nr(ax2);
     rot[0] = ax2 * inv_ax * inv_r;  // |x| / r
     // sn = (x / |x|) conj(y) / r
-    const double f = inv_ax * inv_r;
+    const R f = inv_ax * inv_r;
     rot[1] = (x.x * y.x + x.y * y.y) * f;
     rot[2] = (x.y * y.x - x.x * y.y) * f;
   }
 }
 
-// selection order with precomputed magnitudes
-DEV bool before_m(c128 a, double ma, c128 b, double mb) {
-  const double scale = fmax(ma, mb);
-  if (fabs(ma - mb) > 1e-9 * scale) return ma < mb;
-  if (fabs(a.y - b.y) > 1e-9 * scale) return a.y > b.y;
+// selection order of the "smallest" harmonic Ritz values, magnitudes precomputed:
+// |theta| ascending; within a relative tie, larger Im, then larger Re
+template <typename R> DEV bool before_m(cx<R> a, R ma, cx<R> b, R mb) {
+  const R scale = fmax_(ma, mb);
+  if (fabs_(ma - mb) > Lim<R>::tie * scale) return ma < mb;
+  if (fabs_(a.y - b.y) > Lim<R>::tie * scale) return a.y > b.y;
   return a.x > b.x;
 }
 
-// selection order of the "smallest" harmonic Ritz values
-DEV bool before(c128 a, c128 b) {
-  const double ma = cabs_(a), mb = cabs_(b);
-  const double scale = fmax(ma, mb);
-  if (fabs(ma - mb) > 1e-9 * scale) return ma < mb;
-  if (fabs(a.y - b.y) > 1e-9 * scale) return a.y > b.y;
-  return a.x > b.x;
+// Shared-memory layout of the FP32 harmonic Ritz path (byte offsets, 16-byte
+// aligned): T (m x (m+2), odd ld), Z (m rows of odd stride), Y (eigenvectors of
+// T, m x k, odd ld), then f in FP64, the FP64 refinement residual, tau, theta
+// and the selection.
+struct Hr32Layout {
+  long T, Z, Y, fd, rr, tau, theta, sel, total;
+};
+HD long al16(long x) { return (x + 15) & ~15L; }
+HD int odd_ld2(int rows) { return rows | 1; }
+HD Hr32Layout hr32_layout(int m, int k) {
+  const long ld = odd_ld2(m);
+  Hr32Layout L{};
+  long o = 0;
+  L.T = o; o = al16(o + 8 * ld * (m + 2));
+  L.Z = o; o = al16(o + 8 * ld * m);
+  L.Y = o; o = al16(o + 8 * ld * k);
+  L.fd = o; o = al16(o + 16L * m);
+  L.rr = o; o = al16(o + 8L * m);
+  L.tau = o; o = al16(o + 8L * m);
+  L.theta = o; o = al16(o + 8L * m);
+  L.sel = o; o = al16(o + 4L * k);
+  L.total = o;
+  return L;
 }
 
-// Hessenberg reduction + shifted QR with Schur vectors + eigenvectors of the
-// k smallest; writes P_k ((m+1) x k, orthonormal, last row 0) and theta.
-DEV void harmonic_ritz(const DenseCycle& d, int c, c128* T, Sh& sh) {
+// Harmonic Ritz step of the restart in precision R: f = Hhat^{-H} hrow^H, M = Hhat +
+// f hrow, Hessenberg reduction of M with the reflectors accumulated into Z,
+// complex single-shift QR to the Schur form T = Z^H M Z, eigenvectors of T for the
+// k smallest |theta| by back substitution, G = Z Y orthonormalised into P_k
+// ((m+1) x k, last row 0); all m values into theta.
+//
+// R = double: everything in FP64, Z and Y in the per-column global scratch; a
+// failure sets the column's error and returns false.
+// R = float (complex64 basis): T, Z, Y in shared memory (hr32_layout); f is
+// refined to FP64 accuracy by two steps of iterative refinement (FP64
+// residual, FP32 factors).  Returns false, touching no state, when FP32 is not
+// enough (non-finite values, no convergence of the QR iteration, a selected
+// eigenvector nearly dependent on the others); the caller then runs the FP64 form.
+template <typename R>
+DEV bool harmonic_ritz(const DenseCycle& d, int c, unsigned char* smem, ShT<R>& sh) {
+  using C = cx<R>;
+  constexpr bool F32 = sizeof(R) == 4;
   ColState* st = d.st + c;
   const int m = d.m, k = d.k;
   const c128* H = d.H + (long)c * (m + 1) * m;
   const c128 sig = d.sigma[(long)c * d.ns];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* scr = d.scratch + (long)c * d.scratch_per_col;
-  c128* Z = reinterpret_cast<c128*>(scr);        // m x m, row-major, row t owned by thread t
-  c128* Y = Z + (long)m * m;                     // m x k   eigenvectors of T
-  c128* G = Y + (long)m * k;                     // m x k   eigenvectors of M
   const int lda = odd_ld(m);
-  c128* f = T + (long)lda * (m + 2);             // m
-  c128* tau = f + m;                             // m
-  c128* theta = tau + m;                         // m
-  int* sel = reinterpret_cast<int*>(theta + m);  // k
+  C *T, *Z, *Y, *f, *tau, *theta;
+  int* sel;
+  c128* fd = nullptr;  // FP32 path: f in FP64
+  int ldz, ldy;
+  if constexpr (F32) {
+    const Hr32Layout L = hr32_layout(m, k);
+    T = reinterpret_cast<C*>(smem + L.T);
+    Z = reinterpret_cast<C*>(smem + L.Z);
+    Y = reinterpret_cast<C*>(smem + L.Y);
+    fd = reinterpret_cast<c128*>(smem + L.fd);
+    f = reinterpret_cast<C*>(smem + L.rr);
+    tau = reinterpret_cast<C*>(smem + L.tau);
+    theta = reinterpret_cast<C*>(smem + L.theta);
+    sel = reinterpret_cast<int*>(smem + L.sel);
+    ldz = lda;
+    ldy = lda;
+  } else {
+    T = reinterpret_cast<C*>(smem);
+    double* scr = d.scratch + (long)c * d.scratch_per_col;
+    Z = reinterpret_cast<C*>(scr);                // m x m, row-major, row t owned by thread DT-1-t
+    Y = Z + (long)m * m;                          // eigenvectors of T, ld = odd_ld(m)
+    f = T + (long)lda * (m + 2);                  // m
+    tau = f + m;                                  // m
+    theta = tau + m;                              // m
+    sel = reinterpret_cast<int*>(theta + m);      // k
+    ldz = m;
+    ldy = lda;
+  }
+  auto fail = [&]() {
+    if constexpr (!F32) set_err(st, GDR_EBREAKDOWN);
+    return false;
+  };
   GDR_DENSE_MARK(0, 0);
-  // 1) f = H^{-H} hrow^H with H = Hhat[0:m, 0:m] = Q R:  R^H z = hrow^H, f = Q z
+  // 1) f = Hhat^{-H} hrow^H with Hhat = (Hbar - sigma_1 Ibar)[0:m, 0:m] = Q R:
+  //    R^H z = hrow^H, f = Q z (thread 0 solves; the factors stay in T)
   load_shifted(T, lda, H, m + 1, m, m, sig);
   if (threadIdx.x == 0) sh.ibc[0] = 0;
   __syncthreads();
   cta_qr(T, lda, m, m, m, tau, sh, d.kfull);
-  if (threadIdx.x == 0) {
-    for (int j = 0; j < m; ++j) {  // forward substitution with R^H
-      c128 v = conj(H[m + (long)j * (m + 1)]);
-      for (int i = 0; i < j; ++i) v -= cmulc(T[i + (long)j * lda], f[i]);
-      const c128 rjj = T[j + (long)j * lda];
-      if (rjj.x == 0.0 && rjj.y == 0.0) {
+  auto solve_rh = [&](C* v) {  // v <- Hhat^{-H} v, thread 0
+    for (int j = 0; j < m; ++j) {
+      C x = v[j];
+      for (int i = 0; i < j; ++i) x -= cmulc(T[i + (long)j * lda], v[i]);
+      const C rjj = T[j + (long)j * lda];
+      if (rjj.x == R(0) && rjj.y == R(0)) {
         sh.ibc[0] = 1;
-        f[j] = {0, 0};
+        v[j] = {0, 0};
       } else {
-        f[j] = cdiv(v, conj(rjj));
+        v[j] = cdiv(x, conj(rjj));
       }
     }
-    apply_q_serial(T, lda, m, m, tau, f, d.kfull);
-  }
+    apply_q_serial(T, lda, m, m, tau, v, d.kfull);
+  };
+  for (int i = threadIdx.x; i < m; i += DT) f[i] = cvt<R>(conj(H[m + (long)i * (m + 1)]));
   __syncthreads();
-  if (sh.ibc[0]) set_err(st, GDR_EBREAKDOWN);
+  if (threadIdx.x == 0) solve_rh(f);
+  __syncthreads();
+  if (sh.ibc[0]) return fail();
+  if constexpr (F32) {
+    for (int i = threadIdx.x; i < m; i += DT) fd[i] = up(f[i]);
+    for (int it = 0; it < 2; ++it) {
+      __syncthreads();
+      // residual hrow^H - Hhat^H f in FP64 (thread i: row i of Hhat^H = column i of Hhat)
+      for (int i = threadIdx.x; i < m; i += DT) {
+        const c128* hc = H + (long)i * (m + 1);
+        c128 acc = conj(H[m + (long)i * (m + 1)]);
+        for (int j = 0; j < m; ++j) {
+          c128 h = hc[j];
+          if (j == i) h -= sig;
+          acc -= cmulc(h, fd[j]);
+        }
+        f[i] = cvt<R>(acc);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) solve_rh(f);
+      __syncthreads();
+      for (int i = threadIdx.x; i < m; i += DT) fd[i] += up(f[i]);
+    }
+    __syncthreads();
+  } else {
+    fd = reinterpret_cast<c128*>(f);
+  }
   GDR_DENSE_MARK(1, 0);
-  // 2) M = H + f hrow
+  // 2) M = Hhat + f hrow (formed in FP64)
   for (int t = threadIdx.x; t < m * m; t += DT) {
     const int i = t % m, j = t / m;
     c128 v = H[i + (long)j * (m + 1)];
     if (i == j) v -= sig;
-    T[i + (long)j * lda] = v + f[i] * H[m + (long)j * (m + 1)];
+    T[i + (long)j * lda] = cvt<R>(v + fd[i] * H[m + (long)j * (m + 1)]);
   }
   __syncthreads();
   GDR_DENSE_MARK(2, 0);
   // 3) Hessenberg reduction M = Q Hh Q^H, reflectors kept below the subdiagonal
   for (int j = 0; j + 2 < m; ++j) {
-    double s = 0;
+    R s = 0;
     for (int i = j + 2 + threadIdx.x; i < m; i += DT) s += norm2(T[i + (long)j * lda]);
     s = block_sum(s, sh);
     if (threadIdx.x == 0) {
-      const c128 alpha = T[j + 1 + (long)j * lda];
-      if (s == 0.0 && alpha.y == 0.0) {
+      const C alpha = T[j + 1 + (long)j * lda];
+      if (s == R(0) && alpha.y == R(0)) {
         tau[j] = {0, 0};
       } else {
-        const double beta = -copysign(sqrt(norm2(alpha) + s), alpha.x);
+        const R beta = -copysign_(sqrt_(norm2(alpha) + s), alpha.x);
         tau[j] = {(beta - alpha.x) / beta, -alpha.y / beta};
-        sh.bc[0] = cdiv(c128{1, 0}, alpha - c128{beta, 0});
+        sh.bc[0] = cdiv(C{1, 0}, alpha - C{beta, 0});
         T[j + 1 + (long)j * lda] = {beta, 0};
       }
     }
     __syncthreads();
-    const c128 tj = tau[j];
-    if (tj.x == 0.0 && tj.y == 0.0) continue;
-    const c128 scal = sh.bc[0];
+    const C tj = tau[j];
+    if (tj.x == R(0) && tj.y == R(0)) continue;
+    const C scal = sh.bc[0];
     for (int i = j + 2 + threadIdx.x; i < m; i += DT) T[i + (long)j * lda] = T[i + (long)j * lda] * scal;
     __syncthreads();
     // left: rows j+1.., columns j+1..m-1 : (I - conj(tau) v v^H)
-    const c128 ct = conj(tj);
+    const C ct = conj(tj);
     for (int cc = j + 1 + warp; cc < m; cc += DT / 32) {
-      c128* colp = T + (long)cc * lda;
-      c128 w = {0, 0};
+      C* colp = T + (long)cc * lda;
+      C w = {0, 0};
       for (int i = j + 1 + lane; i < m; i += 32) {
-        const c128 vi = (i == j + 1) ? c128{1, 0} : T[i + (long)j * lda];
+        const C vi = (i == j + 1) ? C{1, 0} : T[i + (long)j * lda];
         w += cmulc(vi, colp[i]);
       }
       w = warp_sum_c(w);
-      const c128 fct = ct * w;
+      const C fct = ct * w;
       for (int i = j + 1 + lane; i < m; i += 32) {
-        const c128 vi = (i == j + 1) ? c128{1, 0} : T[i + (long)j * lda];
+        const C vi = (i == j + 1) ? C{1, 0} : T[i + (long)j * lda];
         colp[i] -= vi * fct;
       }
     }
     __syncthreads();
     // right: all rows, columns j+1..m-1 : M (I - tau v v^H)
     for (int r = warp; r < m; r += DT / 32) {
-      c128 w = {0, 0};
+      C w = {0, 0};
       for (int i = j + 1 + lane; i < m; i += 32) {
-        const c128 vi = (i == j + 1) ? c128{1, 0} : T[i + (long)j * lda];
+        const C vi = (i == j + 1) ? C{1, 0} : T[i + (long)j * lda];
         w += T[r + (long)i * lda] * vi;
       }
       w = warp_sum_c(w);
-      const c128 fct = tj * w;
+      const C fct = tj * w;
       for (int i = j + 1 + lane; i < m; i += 32) {
-        const c128 vi = (i == j + 1) ? c128{1, 0} : T[i + (long)j * lda];
+        const C vi = (i == j + 1) ? C{1, 0} : T[i + (long)j * lda];
         T[r + (long)i * lda] -= fct * conj(vi);
       }
     }
@@ -447,24 +563,24 @@ DEV void harmonic_ritz(const DenseCycle& d, int c, c128* T, Sh& sh) {
   //    During the QR sweep row t of Z belongs to thread DT-1-t.
   const int zrow = DT - 1 - threadIdx.x;  // row of Z owned by this thread in the sweep
   for (int r = warp; r < m; r += DT / 32) {
-    c128* zr = Z + (long)r * m;
-    for (int i = lane; i < m; i += 32) zr[i] = {r == i ? 1.0 : 0.0, 0.0};
+    C* zr = Z + (long)r * ldz;
+    for (int i = lane; i < m; i += 32) zr[i] = {R(r == i ? 1 : 0), R(0)};
   }
   __syncthreads();
   for (int j = 0; j + 2 < m; ++j) {
-    const c128 tj = tau[j];
-    if (tj.x == 0.0 && tj.y == 0.0) continue;
+    const C tj = tau[j];
+    if (tj.x == R(0) && tj.y == R(0)) continue;
     for (int r = warp; r < m; r += DT / 32) {
-      c128* zr = Z + (long)r * m;
-      c128 w = {0, 0};
+      C* zr = Z + (long)r * ldz;
+      C w = {0, 0};
       for (int i = j + 1 + lane; i < m; i += 32) {
-        const c128 vi = (i == j + 1) ? c128{1, 0} : T[i + (long)j * lda];
+        const C vi = (i == j + 1) ? C{1, 0} : T[i + (long)j * lda];
         w += zr[i] * vi;
       }
       w = warp_sum_c(w);
-      const c128 fct = tj * w;
+      const C fct = tj * w;
       for (int i = j + 1 + lane; i < m; i += 32) {
-        const c128 vi = (i == j + 1) ? c128{1, 0} : T[i + (long)j * lda];
+        const C vi = (i == j + 1) ? C{1, 0} : T[i + (long)j * lda];
         zr[i] -= fct * conj(vi);
       }
     }
@@ -478,21 +594,24 @@ DEV void harmonic_ritz(const DenseCycle& d, int c, c128* T, Sh& sh) {
   __syncthreads();
   GDR_DENSE_MARK(4, 0);
   // 5) complex single-shift QR to Schur form T = Z^H M Z
-  double hnorm = 0;
-  for (int q = threadIdx.x; q < m * m; q += DT) hnorm = fmax(hnorm, cabs_(T[q]));
+  R hnorm = 0;
+  for (int q = threadIdx.x; q < m * m; q += DT) hnorm = fmax_(hnorm, cabs_(T[(q % m) + (long)(q / m) * lda]));
   {
-    // max over the CTA
-    double v = hnorm;
+    // max over the CTA (NaN propagates as a failure below)
+    R v = hnorm;
 #pragma unroll
-    for (int mm = 16; mm > 0; mm >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, mm));
+    for (int mm = 16; mm > 0; mm >>= 1) v = fmax_(v, __shfl_xor_sync(FULL, v, mm));
     if (lane == 0) sh.red[warp] = v;
     __syncthreads();
-    hnorm = fmax(fmax(sh.red[0], sh.red[1]), fmax(sh.red[2], sh.red[3]));
+    hnorm = fmax_(fmax_(sh.red[0], sh.red[1]), fmax_(sh.red[2], sh.red[3]));
     __syncthreads();
   }
-  const double smallnum = fmax(hnorm * EPS, 1e-300);
-  const double eps2 = EPS * EPS;
-  double* rot = reinterpret_cast<double*>(&sh.bc[1]);  // rot[0] = cs, (rot[1], rot[2]) = sn
+  if constexpr (F32) {
+    if (!(hnorm < 1e30f)) return false;  // overflowed or non-finite in FP32
+  }
+  const R smallnum = fmax_(hnorm * Lim<R>::eps, Lim<R>::tiny);
+  const R eps2 = Lim<R>::eps * Lim<R>::eps;
+  R* rot = reinterpret_cast<R*>(&sh.bc[1]);  // rot[0] = cs, (rot[1], rot[2]) = sn
   int hi = m - 1, its = 0, total = 0;
   bool failed = false;
   while (hi >= 0) {
@@ -504,10 +623,10 @@ DEV void harmonic_ritz(const DenseCycle& d, int c, c128* T, Sh& sh) {
         const int cand = top - lane;
         bool neg = false;
         if (cand > 0) {
-          const double sub = norm2(T[cand + (long)(cand - 1) * lda]);
-          double ref = norm2(T[cand - 1 + (long)(cand - 1) * lda]) + norm2(T[cand + (long)cand * lda]);
-          if (ref == 0.0) ref = hnorm * hnorm;
-          neg = (sub <= eps2 * ref || sub <= smallnum * smallnum * 1e-6);
+          const R sub = norm2(T[cand + (long)(cand - 1) * lda]);
+          R ref = norm2(T[cand - 1 + (long)(cand - 1) * lda]) + norm2(T[cand + (long)cand * lda]);
+          if (ref == R(0)) ref = hnorm * hnorm;
+          neg = (sub <= eps2 * ref || sub <= smallnum * smallnum * R(1e-6));
         }
         const unsigned bal = __ballot_sync(FULL, neg);
         if (bal) {
@@ -516,27 +635,27 @@ DEV void harmonic_ritz(const DenseCycle& d, int c, c128* T, Sh& sh) {
         }
       }
       if (lane == 0) {
-      if (l > 0) T[l + (long)(l - 1) * lda] = {0, 0};
-      sh.ibc[1] = l;
-      if (l < hi) {
-        // Wilkinson shift of the trailing 2x2 block (exceptional shift every 10th sweep),
-        // then the first rotation of the sweep
-        ++its;
-        c128 mu;
-        const c128 a = T[hi - 1 + (long)(hi - 1) * lda], b = T[hi - 1 + (long)hi * lda];
-        const c128 cc = T[hi + (long)(hi - 1) * lda], dd = T[hi + (long)hi * lda];
-        if (its % 10 == 0) {
-          mu = dd + c128{fabs(cc.x) + fabs(cc.y), 0};
+        if (l > 0) T[l + (long)(l - 1) * lda] = {0, 0};
+        sh.ibc[1] = l;
+        if (l < hi) {
+          // Wilkinson shift of the trailing 2x2 block (exceptional shift every 10th sweep),
+          // then the first rotation of the sweep
+          ++its;
+          C mu;
+          const C a = T[hi - 1 + (long)(hi - 1) * lda], b = T[hi - 1 + (long)hi * lda];
+          const C cc = T[hi + (long)(hi - 1) * lda], dd = T[hi + (long)hi * lda];
+          if (its % 10 == 0) {
+            mu = dd + C{fabs_(cc.x) + fabs_(cc.y), 0};
+          } else {
+            const C half = R(0.5) * (a - dd);
+            const C disc = csqrt_(half * half + b * cc);
+            const C l1 = dd + half + disc, l2 = dd + half - disc;
+            mu = (norm2(l1 - dd) <= norm2(l2 - dd)) ? l1 : l2;
+          }
+          givens(T[l + (long)l * lda] - mu, T[l + 1 + (long)l * lda], rot);
         } else {
-          const c128 half = 0.5 * (a - dd);
-          const c128 disc = csqrt_(half * half + b * cc);
-          const c128 l1 = dd + half + disc, l2 = dd + half - disc;
-          mu = (norm2(l1 - dd) <= norm2(l2 - dd)) ? l1 : l2;
+          its = 0;
         }
-        givens(T[l + (long)l * lda] - mu, T[l + 1 + (long)l * lda], rot);
-      } else {
-        its = 0;
-      }
       }
     }
     __syncthreads();
@@ -551,12 +670,12 @@ DEV void harmonic_ritz(const DenseCycle& d, int c, c128* T, Sh& sh) {
       break;
     }
     for (int kk = lo; kk < hi; ++kk) {
-      const double cs = rot[0];
-      const c128 sn = {rot[1], rot[2]};
+      const R cs = rot[0];
+      const C sn = {rot[1], rot[2]};
       // left: rows kk, kk+1, columns max(kk-1,0)..m-1
       for (int cc = max(kk - 1, 0) + threadIdx.x; cc < m; cc += DT) {
-        const c128 a = T[kk + (long)cc * lda], b = T[kk + 1 + (long)cc * lda];
-        const c128 b_new = (cc == kk - 1 && kk > lo) ? c128{0, 0} : cs * b - conj(sn) * a;
+        const C a = T[kk + (long)cc * lda], b = T[kk + 1 + (long)cc * lda];
+        const C b_new = (cc == kk - 1 && kk > lo) ? C{0, 0} : cs * b - conj(sn) * a;
         T[kk + (long)cc * lda] = cs * a + sn * b;
         T[kk + 1 + (long)cc * lda] = b_new;
         if ((cc == kk || cc == kk + 1) && kk + 2 <= hi) {  // inputs of the next rotation
@@ -565,59 +684,55 @@ DEV void harmonic_ritz(const DenseCycle& d, int c, c128* T, Sh& sh) {
         }
       }
       __syncthreads();
-      // right: columns kk, kk+1, rows 0..min(kk+2, hi); the thread of row kk+2 (or kk+1
-      // at the end of the sweep) also does row kk+1 and forms the next rotation
+      // right: columns kk, kk+1, rows 0..min(kk+2, hi).  The owner, a thread with
+      // no row of Z, forms the next rotation from the entries of rows kk+1, kk+2
+      // saved by the left update.
       const int rlast = min(kk + 2, hi);
-      // (the owner, a thread with no row of this update, forms the next rotation from
-      //  the entries of rows kk+1, kk+2 saved by the left update)
-      c128 x_next = {0, 0}, y_next = {0, 0};
+      C x_next = {0, 0}, y_next = {0, 0};
       const bool own = (threadIdx.x == DT - 1 - m) && (kk + 2 <= hi);
       if (own) {
         x_next = cs * sh.nx[0] + sh.nx[1] * conj(sn);
         y_next = cs * sh.nx[2] + sh.nx[3] * conj(sn);
       }
       for (int r = threadIdx.x; r <= rlast; r += DT) {
-        const c128 a = T[r + (long)kk * lda], b = T[r + (long)(kk + 1) * lda];
+        const C a = T[r + (long)kk * lda], b = T[r + (long)(kk + 1) * lda];
         T[r + (long)kk * lda] = cs * a + b * conj(sn);
         T[r + (long)(kk + 1) * lda] = cs * b - a * sn;
       }
       if (own) givens(x_next, y_next, rot);
       if (zrow >= 0 && zrow < m) {
-        c128* zr = Z + (long)zrow * m;
-        const c128 a = zr[kk], b = zr[kk + 1];
+        C* zr = Z + (long)zrow * ldz;
+        const C a = zr[kk], b = zr[kk + 1];
         zr[kk] = cs * a + b * conj(sn);
         zr[kk + 1] = cs * b - a * sn;
       }
       __syncthreads();
     }
   }
-  if (failed) {
-    set_err(st, GDR_EBREAKDOWN);
-    return;
-  }
+  if (failed) return fail();
   __syncthreads();
   GDR_DENSE_MARK(5, 0);
   // 6) eigenvalues and selection of the k smallest
   c128* th = d.theta + (long)c * m;
   for (int i = threadIdx.x; i < m; i += DT) {
     theta[i] = T[i + (long)i * lda];
-    th[i] = theta[i];
+    th[i] = up(theta[i]);
   }
   __syncthreads();
-  // k rounds of a warp argmin under `before` (ties: lower index), which picks what
+  // k rounds of a warp argmin under `before_m` (ties: lower index), which picks what
   // the index-order selection sort picks for a consistent order; |theta| computed once
   if (warp == 0) {
-    double mag[3];
+    R mag[3];
     unsigned used = 0;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       const int i = lane + 32 * q;
-      mag[q] = (i < m) ? sqrt(norm2(theta[i])) : 0.0;
+      mag[q] = (i < m) ? sqrt_(norm2(theta[i])) : R(0);
     }
     for (int q = 0; q < k; ++q) {
       int bi = -1;
-      double bm = 0.0;
-      c128 bt = {0, 0};
+      R bm = 0;
+      C bt = {0, 0};
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         const int i = lane + 32 * r;
@@ -627,8 +742,8 @@ DEV void harmonic_ritz(const DenseCycle& d, int c, c128* T, Sh& sh) {
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
         const int oi = __shfl_xor_sync(FULL, bi, off);
-        const double om = __shfl_xor_sync(FULL, bm, off);
-        const c128 ot = shfl_xor_c(bt, off);
+        const R om = __shfl_xor_sync(FULL, bm, off);
+        const C ot = shfl_xor_c(bt, off);
         bool take = false;
         if (oi >= 0) {
           if (bi < 0) take = true;
@@ -646,75 +761,83 @@ DEV void harmonic_ritz(const DenseCycle& d, int c, c128* T, Sh& sh) {
   // 7) eigenvectors of T (back substitution, one thread per selected value), Y = m x k
   for (int q = threadIdx.x; q < k; q += DT) {
     const int p = sel[q];
-    const c128 lam = theta[p];
-    c128* y = Y + (long)q * m;
+    const C lam = theta[p];
+    C* y = Y + (long)q * ldy;
     for (int i = p + 1; i < m; ++i) y[i] = {0, 0};
     y[p] = {1, 0};
     for (int i = p - 1; i >= 0; --i) {
-      c128 sacc = {0, 0};
+      C sacc = {0, 0};
       for (int j = i + 1; j <= p; ++j) sacc += T[i + (long)j * lda] * y[j];
-      c128 den = T[i + (long)i * lda] - lam;
+      C den = T[i + (long)i * lda] - lam;
       if (cabs_(den) < smallnum) den = {smallnum, 0};
       y[i] = -cdiv(sacc, den);
     }
     // normalise (avoid overflow in later products)
-    double nn = 0;
-    for (int i = 0; i <= p; ++i) nn = fmax(nn, cabs_(y[i]));
-    for (int i = 0; i <= p; ++i) y[i] = (1.0 / nn) * y[i];
+    R nn = 0;
+    for (int i = 0; i <= p; ++i) nn = fmax_(nn, cabs_(y[i]));
+    for (int i = 0; i <= p; ++i) y[i] = (R(1) / nn) * y[i];
   }
   __syncthreads();
   GDR_DENSE_MARK(7, 0);
-  // 8) G = Z Y : thread t computes row t of G (Z is complete after the barrier)
+  // 8) G = Z Y into T (ld m+1, last row 0): thread t computes row t of G
+  const int ldp = m + 1;
   const int t = threadIdx.x;
   if (t < m) {
-    const c128* zr = Z + (long)t * m;
+    const C* zr = Z + (long)t * ldz;
     for (int q = 0; q < k; ++q) {
-      const c128* y = Y + (long)q * m;
+      const C* y = Y + (long)q * ldy;
       const int p = sel[q];
-      c128 acc = {0, 0};
+      C acc = {0, 0};
       for (int j = 0; j <= p; ++j) acc += zr[j] * y[j];
-      G[t + (long)q * m] = acc;
+      T[t + (long)q * ldp] = acc;
     }
+  } else if (t == m) {
+    for (int q = 0; q < k; ++q) T[m + (long)q * ldp] = {0, 0};
   }
   __syncthreads();
   GDR_DENSE_MARK(8, 0);
   // 9) P_k = orth([G; 0]) by classical Gram-Schmidt twice, in T (ld m+1)
-  const int ldp = m + 1;
-  for (int q = threadIdx.x; q < ldp * k; q += DT) {
-    const int i = q % ldp, j = q / ldp;
-    T[q] = (i < m) ? G[i + (long)j * m] : c128{0, 0};
-  }
-  __syncthreads();
-  c128* coef = theta;  // reuse (size >= k)
+  C* coef = theta;  // reuse (size >= k)
   for (int q = 0; q < k; ++q) {
-    c128* pq = T + (long)q * ldp;
+    C* pq = T + (long)q * ldp;
+    R n0 = 0;
+    if constexpr (F32) {
+      for (int i = threadIdx.x; i < m; i += DT) n0 += norm2(pq[i]);
+      n0 = block_sum(n0, sh);
+    }
     for (int pass = 0; pass < 2; ++pass) {
       for (int l = warp; l < q; l += DT / 32) {
-        const c128* pl = T + (long)l * ldp;
-        c128 w = {0, 0};
+        const C* pl = T + (long)l * ldp;
+        C w = {0, 0};
         for (int i = lane; i < m; i += 32) w += cmulc(pl[i], pq[i]);
         w = warp_sum_c(w);
         if (lane == 0) coef[l] = w;
       }
       __syncthreads();
       for (int i = threadIdx.x; i < m; i += DT) {
-        c128 v = pq[i];
+        C v = pq[i];
         for (int l = 0; l < q; ++l) v -= T[i + (long)l * ldp] * coef[l];
         pq[i] = v;
       }
       __syncthreads();
     }
-    double nn = 0;
+    R nn = 0;
     for (int i = threadIdx.x; i < m; i += DT) nn += norm2(pq[i]);
     nn = block_sum(nn, sh);
-    if (!(nn > 0) || !isfinite(nn)) set_err(st, GDR_EBREAKDOWN);
-    const double inv = 1.0 / sqrt(nn);
+    if constexpr (F32) {
+      // nearly dependent on the vectors before it: FP32 orthogonalisation would lose it
+      if (!(nn > R(1e-6) * n0) || !(nn < 1e30f)) return false;
+    } else {
+      if (!(nn > 0) || !isfinite(nn)) set_err(st, GDR_EBREAKDOWN);
+    }
+    const R inv = R(1) / sqrt_(nn);
     for (int i = threadIdx.x; i < m; i += DT) pq[i] = inv * pq[i];
     __syncthreads();
   }
   c128* Pk = d.Pk + (long)c * ldp * k;
-  for (int q = threadIdx.x; q < ldp * k; q += DT) Pk[q] = T[q];
+  for (int q = threadIdx.x; q < ldp * k; q += DT) Pk[q] = up(T[q]);
   GDR_DENSE_MARK(9, total);
+  return true;
 }
 
 // restart completion (D2 block 0): p_{k+1} from s, P into Cf, Hbar_k, c_k
@@ -796,7 +919,11 @@ __global__ void __launch_bounds__(DT) dense_d1_kernel(DenseCycle d) {
     base_ls(d, c, A, sh);
   } else {
     if (st->broke || st->m_eff < d.m || d.k == 0) return;
-    harmonic_ritz(d, c, A, sh);
+    if (d.hr32) {
+      __shared__ ShT<float> shf;
+      if (harmonic_ritz<float>(d, c, smem_raw, shf)) return;
+    }
+    harmonic_ritz<double>(d, c, smem_raw, sh);
   }
 }
 
@@ -820,9 +947,13 @@ __global__ void __launch_bounds__(DT) restart_only_kernel(DenseCycle d, int phas
   __shared__ Sh sh;
   c128* A = reinterpret_cast<c128*>(smem_raw);
   const int c = blockIdx.y;
-  if (phase == 0)
-    harmonic_ritz(d, c, A, sh);
-  else if (d.st[c].err == 0)
+  if (phase == 0) {
+    if (d.hr32) {
+      __shared__ ShT<float> shf;
+      if (harmonic_ritz<float>(d, c, smem_raw, shf)) return;
+    }
+    harmonic_ritz<double>(d, c, smem_raw, sh);
+  } else if (d.st[c].err == 0)
     restart_finish(d, c, A, sh);
 }
 
@@ -960,9 +1091,24 @@ void dense_init(gdr_ctx* ctx) {
   ctx->dense_smem_limit = lim;
 }
 
-void dense_restart(gdr_ctx* ctx, const DenseCycle& d) {
-  const size_t smem = dense_smem_bytes(d.m, d.k);
+// dynamic shared memory of the cycle kernels; drops the FP32 harmonic Ritz form
+// (hr32) when its layout does not fit
+static size_t cycle_smem(gdr_ctx* ctx, DenseCycle& d) {
+  size_t smem = dense_smem_bytes(d.m, d.k);
   GDR_REQUIRE(smem <= ctx->dense_smem_limit, "basis size m too large for the dense FP64 kernels");
+  if (d.hr32 && d.k > 0) {
+    const size_t s32 = (size_t)hr32_layout(d.m, d.k).total;
+    if (s32 <= ctx->dense_smem_limit)
+      smem = std::max(smem, s32);
+    else
+      d.hr32 = 0;
+  }
+  return smem;
+}
+
+void dense_restart(gdr_ctx* ctx, const DenseCycle& dc) {
+  DenseCycle d = dc;
+  const size_t smem = cycle_smem(ctx, d);
   dim3 g(1, (unsigned)d.ncol);
   restart_only_kernel<<<g, DT, smem, ctx->stream>>>(d, 0);
   GDR_LAUNCHED(ctx);
@@ -970,9 +1116,9 @@ void dense_restart(gdr_ctx* ctx, const DenseCycle& d) {
   GDR_LAUNCHED(ctx);
 }
 
-void dense_cycle(gdr_ctx* ctx, const DenseCycle& d) {
-  const size_t smem = dense_smem_bytes(d.m, d.k);
-  GDR_REQUIRE(smem <= ctx->dense_smem_limit, "basis size m too large for the dense FP64 kernels");
+void dense_cycle(gdr_ctx* ctx, const DenseCycle& dc) {
+  DenseCycle d = dc;
+  const size_t smem = cycle_smem(ctx, d);
   dim3 g1(d.k > 0 ? 2 : 1, (unsigned)d.ncol);
   {
     KProf kp(ctx, d.k > 0 ? "dense_ls_harmonic_ritz" : "dense_ls", 0.0);

@@ -122,6 +122,7 @@ struct DenseCycle {
   long scratch_per_col;
   ColState* st;
   bool want_r;
+  int hr32;  // harmonic Ritz eigensolve in FP32 (complex64 basis); FP64 when it cannot be trusted
 };
 void dense_cycle(gdr_ctx* ctx, const DenseCycle& d);
 // cycle bookkeeping after the reduced solves: convergence test, beta/active update,

@@ -235,6 +235,7 @@ DrResult dr_sh(gdr_ctx* ctx, const gdr_op* A, const DrJob<R>& job, bool use_grap
   d.scratch = ctx->get<double>("dr.scratch", (size_t)d.scratch_per_col * ncol);
   d.st = b.st;
   d.want_r = (k == 0);  // GMRES(m): restart from the residual vector r = V_{m+1} s
+  d.hr32 = std::is_same<R, float>::value ? 1 : 0;  // complex64 basis: FP32 eigensolve in the restart
   cx<R>* rres = ctx->get<cx<R>>("dr.r", (size_t)b.ldv * ncol);
   double* bn2 = ctx->get<double>("dr.bn2", (size_t)ncol + 4);
   double* nrm2 = ctx->get<double>("dr.nrm2", (size_t)ncol + 4);
