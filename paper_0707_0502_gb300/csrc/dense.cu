@@ -449,6 +449,7 @@ DEV bool harmonic_ritz(const DenseCycle& d, int c, unsigned char* smem, ShT<R>& 
   if (threadIdx.x == 0) sh.ibc[0] = 0;
   __syncthreads();
   cta_qr(T, lda, m, m, m, tau, sh, d.kfull);
+  GDR_DENSE_MARK(10, 0);
   auto solve_rh = [&](C* v) {  // v <- Hhat^{-H} v, thread 0
     for (int j = 0; j < m; ++j) {
       C x = v[j];
@@ -468,6 +469,7 @@ DEV bool harmonic_ritz(const DenseCycle& d, int c, unsigned char* smem, ShT<R>& 
   if (threadIdx.x == 0) solve_rh(f);
   __syncthreads();
   if (sh.ibc[0]) return fail();
+  GDR_DENSE_MARK(11, 0);
   if constexpr (F32) {
     for (int i = threadIdx.x; i < m; i += DT) fd[i] = up(f[i]);
     for (int it = 0; it < 2; ++it) {
@@ -502,97 +504,164 @@ DEV bool harmonic_ritz(const DenseCycle& d, int c, unsigned char* smem, ShT<R>& 
   }
   __syncthreads();
   GDR_DENSE_MARK(2, 0);
-  // 3) Hessenberg reduction M = Q Hh Q^H, reflectors kept below the subdiagonal
-  for (int j = 0; j + 2 < m; ++j) {
-    R s = 0;
-    for (int i = j + 2 + threadIdx.x; i < m; i += DT) s += norm2(T[i + (long)j * lda]);
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) {
-      const C alpha = T[j + 1 + (long)j * lda];
-      if (s == R(0) && alpha.y == R(0)) {
-        tau[j] = {0, 0};
-      } else {
-        const R beta = -copysign_(sqrt_(norm2(alpha) + s), alpha.x);
-        tau[j] = {(beta - alpha.x) / beta, -alpha.y / beta};
-        sh.bc[0] = cdiv(C{1, 0}, alpha - C{beta, 0});
-        T[j + 1 + (long)j * lda] = {beta, 0};
-      }
-    }
-    __syncthreads();
-    const C tj = tau[j];
-    if (tj.x == R(0) && tj.y == R(0)) continue;
-    const C scal = sh.bc[0];
-    for (int i = j + 2 + threadIdx.x; i < m; i += DT) T[i + (long)j * lda] = T[i + (long)j * lda] * scal;
-    __syncthreads();
-    // left: rows j+1.., columns j+1..m-1 : (I - conj(tau) v v^H)
-    const C ct = conj(tj);
-    for (int cc = j + 1 + warp; cc < m; cc += DT / 32) {
-      C* colp = T + (long)cc * lda;
-      C w = {0, 0};
-      for (int i = j + 1 + lane; i < m; i += 32) {
-        const C vi = (i == j + 1) ? C{1, 0} : T[i + (long)j * lda];
-        w += cmulc(vi, colp[i]);
-      }
-      w = warp_sum_c(w);
-      const C fct = ct * w;
-      for (int i = j + 1 + lane; i < m; i += 32) {
-        const C vi = (i == j + 1) ? C{1, 0} : T[i + (long)j * lda];
-        colp[i] -= vi * fct;
-      }
-    }
-    __syncthreads();
-    // right: all rows, columns j+1..m-1 : M (I - tau v v^H)
-    for (int r = warp; r < m; r += DT / 32) {
-      C w = {0, 0};
-      for (int i = j + 1 + lane; i < m; i += 32) {
-        const C vi = (i == j + 1) ? C{1, 0} : T[i + (long)j * lda];
-        w += T[r + (long)i * lda] * vi;
-      }
-      w = warp_sum_c(w);
-      const C fct = tj * w;
-      for (int i = j + 1 + lane; i < m; i += 32) {
-        const C vi = (i == j + 1) ? C{1, 0} : T[i + (long)j * lda];
-        T[r + (long)i * lda] -= fct * conj(vi);
-      }
-    }
-    __syncthreads();
-  }
-  GDR_DENSE_MARK(3, 0);
-  // 4) Z = Q = H_0 H_1 ... : Z <- Z H_j for j = 0.., one warp per row of Z
-  //    (I - tau v v^H applied from the right), then clear below the subdiagonal.
-  //    During the QR sweep row t of Z belongs to thread DT-1-t.
-  const int zrow = DT - 1 - threadIdx.x;  // row of Z owned by this thread in the sweep
-  for (int r = warp; r < m; r += DT / 32) {
-    C* zr = Z + (long)r * ldz;
-    for (int i = lane; i < m; i += 32) zr[i] = {R(r == i ? 1 : 0), R(0)};
-  }
-  __syncthreads();
-  for (int j = 0; j + 2 < m; ++j) {
-    const C tj = tau[j];
-    if (tj.x == R(0) && tj.y == R(0)) continue;
+  const int zrow = DT - 1 - threadIdx.x;  // FP64 form: row of Z owned by this thread in the sweep
+  if constexpr (F32) {
+    // 3+4) Hessenberg reduction M = Z Hh Z^H with Z accumulated in the same pass.
+    // Per column j: warp 0 forms the reflector (v into vh, tau), then one thread
+    // per column applies it from the left, one thread per row from the right to M
+    // and to Z (no warp reductions; three block barriers per column).
+    C* vh = f;  // f is free once M is formed
     for (int r = warp; r < m; r += DT / 32) {
       C* zr = Z + (long)r * ldz;
-      C w = {0, 0};
-      for (int i = j + 1 + lane; i < m; i += 32) {
-        const C vi = (i == j + 1) ? C{1, 0} : T[i + (long)j * lda];
-        w += zr[i] * vi;
-      }
-      w = warp_sum_c(w);
-      const C fct = tj * w;
-      for (int i = j + 1 + lane; i < m; i += 32) {
-        const C vi = (i == j + 1) ? C{1, 0} : T[i + (long)j * lda];
-        zr[i] -= fct * conj(vi);
-      }
+      for (int i = lane; i < m; i += 32) zr[i] = {R(r == i ? 1 : 0), R(0)};
     }
-    __syncwarp();
+    for (int j = 0; j + 2 < m; ++j) {
+      if (warp == 0) {
+        R s = 0;
+        for (int i = j + 2 + lane; i < m; i += 32) s += norm2(T[i + (long)j * lda]);
+        s = warp_sum_r(s);
+        const C alpha = T[j + 1 + (long)j * lda];
+        const bool triv = (s == R(0) && alpha.y == R(0));
+        C tj = {0, 0}, scal = {0, 0};
+        R beta = 0;
+        if (!triv) {
+          beta = -copysign_(sqrt_(norm2(alpha) + s), alpha.x);
+          tj = {(beta - alpha.x) / beta, -alpha.y / beta};
+          scal = cdiv(C{1, 0}, alpha - C{beta, 0});
+        }
+        for (int i = j + 2 + lane; i < m; i += 32) {
+          vh[i] = triv ? C{0, 0} : T[i + (long)j * lda] * scal;
+          T[i + (long)j * lda] = {0, 0};
+        }
+        if (lane == 0) {
+          vh[j + 1] = {1, 0};
+          tau[j] = tj;
+          if (!triv) T[j + 1 + (long)j * lda] = {beta, 0};
+        }
+      }
+      __syncthreads();
+      const C tj = tau[j];
+      if (tj.x == R(0) && tj.y == R(0)) continue;  // uniform across the CTA
+      // left: rows j+1.., columns j+1..m-1 : (I - conj(tau) v v^H)
+      const C ct = conj(tj);
+      for (int cc = j + 1 + threadIdx.x; cc < m; cc += DT) {
+        C* colp = T + (long)cc * lda;
+        C w = {0, 0};
+        for (int i = j + 1; i < m; ++i) w += cmulc(vh[i], colp[i]);
+        const C fct = ct * w;
+        for (int i = j + 1; i < m; ++i) colp[i] -= vh[i] * fct;
+      }
+      __syncthreads();
+      // right: all rows of M and of Z : X (I - tau v v^H)
+      for (int r = threadIdx.x; r < 2 * m; r += DT) {
+        C w = {0, 0};
+        if (r < m) {
+          for (int i = j + 1; i < m; ++i) w += T[r + (long)i * lda] * vh[i];
+          const C fct = tj * w;
+          for (int i = j + 1; i < m; ++i) T[r + (long)i * lda] -= fct * conj(vh[i]);
+        } else {
+          C* zr = Z + (long)(r - m) * ldz;
+          for (int i = j + 1; i < m; ++i) w += zr[i] * vh[i];
+          const C fct = tj * w;
+          for (int i = j + 1; i < m; ++i) zr[i] -= fct * conj(vh[i]);
+        }
+      }
+      __syncthreads();
+    }
+    GDR_DENSE_MARK(3, 0);
+    GDR_DENSE_MARK(4, 0);
+  } else {
+    // 3) Hessenberg reduction M = Q Hh Q^H, reflectors kept below the subdiagonal
+    for (int j = 0; j + 2 < m; ++j) {
+      R s = 0;
+      for (int i = j + 2 + threadIdx.x; i < m; i += DT) s += norm2(T[i + (long)j * lda]);
+      s = block_sum(s, sh);
+      if (threadIdx.x == 0) {
+        const C alpha = T[j + 1 + (long)j * lda];
+        if (s == R(0) && alpha.y == R(0)) {
+          tau[j] = {0, 0};
+        } else {
+          const R beta = -copysign_(sqrt_(norm2(alpha) + s), alpha.x);
+          tau[j] = {(beta - alpha.x) / beta, -alpha.y / beta};
+          sh.bc[0] = cdiv(C{1, 0}, alpha - C{beta, 0});
+          T[j + 1 + (long)j * lda] = {beta, 0};
+        }
+      }
+      __syncthreads();
+      const C tj = tau[j];
+      if (tj.x == R(0) && tj.y == R(0)) continue;
+      const C scal = sh.bc[0];
+      for (int i = j + 2 + threadIdx.x; i < m; i += DT) T[i + (long)j * lda] = T[i + (long)j * lda] * scal;
+      __syncthreads();
+      // left: rows j+1.., columns j+1..m-1 : (I - conj(tau) v v^H)
+      const C ct = conj(tj);
+      for (int cc = j + 1 + warp; cc < m; cc += DT / 32) {
+        C* colp = T + (long)cc * lda;
+        C w = {0, 0};
+        for (int i = j + 1 + lane; i < m; i += 32) {
+          const C vi = (i == j + 1) ? C{1, 0} : T[i + (long)j * lda];
+          w += cmulc(vi, colp[i]);
+        }
+        w = warp_sum_c(w);
+        const C fct = ct * w;
+        for (int i = j + 1 + lane; i < m; i += 32) {
+          const C vi = (i == j + 1) ? C{1, 0} : T[i + (long)j * lda];
+          colp[i] -= vi * fct;
+        }
+      }
+      __syncthreads();
+      // right: all rows, columns j+1..m-1 : M (I - tau v v^H)
+      for (int r = warp; r < m; r += DT / 32) {
+        C w = {0, 0};
+        for (int i = j + 1 + lane; i < m; i += 32) {
+          const C vi = (i == j + 1) ? C{1, 0} : T[i + (long)j * lda];
+          w += T[r + (long)i * lda] * vi;
+        }
+        w = warp_sum_c(w);
+        const C fct = tj * w;
+        for (int i = j + 1 + lane; i < m; i += 32) {
+          const C vi = (i == j + 1) ? C{1, 0} : T[i + (long)j * lda];
+          T[r + (long)i * lda] -= fct * conj(vi);
+        }
+      }
+      __syncthreads();
+    }
+    GDR_DENSE_MARK(3, 0);
+    // 4) Z = Q = H_0 H_1 ... : Z <- Z H_j for j = 0.., one warp per row of Z
+    //    (I - tau v v^H applied from the right), then clear below the subdiagonal.
+    //    During the QR sweep row t of Z belongs to thread DT-1-t.
+    for (int r = warp; r < m; r += DT / 32) {
+      C* zr = Z + (long)r * ldz;
+      for (int i = lane; i < m; i += 32) zr[i] = {R(r == i ? 1 : 0), R(0)};
+    }
+    __syncthreads();
+    for (int j = 0; j + 2 < m; ++j) {
+      const C tj = tau[j];
+      if (tj.x == R(0) && tj.y == R(0)) continue;
+      for (int r = warp; r < m; r += DT / 32) {
+        C* zr = Z + (long)r * ldz;
+        C w = {0, 0};
+        for (int i = j + 1 + lane; i < m; i += 32) {
+          const C vi = (i == j + 1) ? C{1, 0} : T[i + (long)j * lda];
+          w += zr[i] * vi;
+        }
+        w = warp_sum_c(w);
+        const C fct = tj * w;
+        for (int i = j + 1 + lane; i < m; i += 32) {
+          const C vi = (i == j + 1) ? C{1, 0} : T[i + (long)j * lda];
+          zr[i] -= fct * conj(vi);
+        }
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < m * m; q += DT) {
+      const int i = q % m, j = q / m;
+      if (i > j + 1) T[i + (long)j * lda] = {0, 0};
+    }
+    __syncthreads();
+    GDR_DENSE_MARK(4, 0);
   }
-  __syncthreads();
-  for (int q = threadIdx.x; q < m * m; q += DT) {
-    const int i = q % m, j = q / m;
-    if (i > j + 1) T[i + (long)j * lda] = {0, 0};
-  }
-  __syncthreads();
-  GDR_DENSE_MARK(4, 0);
   // 5) complex single-shift QR to Schur form T = Z^H M Z
   R hnorm = 0;
   for (int q = threadIdx.x; q < m * m; q += DT) hnorm = fmax_(hnorm, cabs_(T[(q % m) + (long)(q / m) * lda]));

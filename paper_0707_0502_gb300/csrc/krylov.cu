@@ -80,11 +80,13 @@ DEV void block_reduce(cx<R> (&acc)[NV], c128* out, int nvalid) {
   __syncthreads();
 }
 
-// sum over blocks of the partials p[bk * stride] by one warp (fixed order: lanes
-// stride the blocks, then a shuffle tree), result valid in every lane
-DEV c128 warp_sum_partials(const c128* p, long stride, int lane) {
+// sum of the partials p[bk * stride], bk < count (default: one per block), by
+// one warp (fixed order: lanes stride the partials, then a shuffle tree),
+// result valid in every lane
+DEV c128 warp_sum_partials(const c128* p, long stride, int lane, int count = -1) {
+  if (count < 0) count = (int)gridDim.x;
   c128 s = {0, 0};
-  for (int bk = lane; bk < (int)gridDim.x; bk += 32) s += ldcg128(p + (long)bk * stride);
+  for (int bk = lane; bk < count; bk += 32) s += ldcg128(p + (long)bk * stride);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     s.x += __shfl_xor_sync(FULL, s.x, off);
@@ -109,12 +111,16 @@ DEV bool last_block(unsigned* cnt) {
 // h = V^H w (+ ||w||^2): a block stages a tile of w in shared memory, each warp
 // takes whole basis vectors and its lanes stream DU units of that vector
 // (coalesced, DU loads in flight per lane); one warp reduction per (vector,
-// tile), accumulated in FP64.  w and V are each read once.
+// tile), accumulated in FP64.  The grid is S tile slots x G vector groups: the
+// block (slot, group) takes the tiles t = slot (mod S) for the vectors of its
+// group, and writes one partial per (slot, vector).  Long vectors use G = 1
+// (w and V each read once); short ones, with fewer tiles than blocks, split the
+// vectors of a tile over G blocks (w re-read G times from L2).
 template <typename R> struct DotTile { static constexpr int DU = (U<R>::K == 2) ? 16 : 8; };
 
 template <typename R>
 __global__ void __launch_bounds__(NT, 3) gs_dot_kernel(Batch<R> b, int nv, const cx<R>* __restrict__ W, long wcs,
-                                                    c128* __restrict__ hout, int hstride, int wnorm) {
+                                                    c128* __restrict__ hout, int hstride, int wnorm, int S, int G) {
   const int c = blockIdx.y;
   if (!b.st[c].run) return;
   constexpr int K = U<R>::K;
@@ -127,9 +133,12 @@ __global__ void __launch_bounds__(NT, 3) gs_dot_kernel(Batch<R> b, int nv, const
   const long n = b.nvec ? (long)b.nvec[c] : b.n, nu = nunits<R>(n);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nvec_tot = nv + (wnorm ? 1 : 0);
-  for (int i = threadIdx.x; i < nvec_tot; i += NT) accs[i] = {0, 0};
+  const int slot = blockIdx.x % S, grp = blockIdx.x / S;
+  const int vpg = (nvec_tot + G - 1) / G;
+  const int i0 = grp * vpg, i1 = min(nvec_tot, i0 + vpg);
+  for (int i = i0 + threadIdx.x; i < i1; i += NT) accs[i] = {0, 0};
   const long ntiles = (nu + TU - 1) / TU;
-  for (long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  for (long t = slot; t < ntiles && i0 < i1; t += S) {
     const long u0 = t * TU;
     __syncthreads();  // readers of the previous tile are done
     for (int q = threadIdx.x; q < TU; q += NT) {
@@ -144,7 +153,7 @@ __global__ void __launch_bounds__(NT, 3) gs_dot_kernel(Batch<R> b, int nv, const
       for (int kk = 0; kk < K; ++kk) wt[q * K + kk] = tmp[kk];
     }
     __syncthreads();
-    for (int i = warp; i < nvec_tot; i += NT / 32) {
+    for (int i = i0 + warp; i < i1; i += NT / 32) {
       cx<R> a = {0, 0};
       if (i < nv) {
         const cx<R>* vi = V + (long)i * b.ldv;
@@ -179,9 +188,10 @@ __global__ void __launch_bounds__(NT, 3) gs_dot_kernel(Batch<R> b, int nv, const
   }
   __syncthreads();
   c128* part = b.part + c * b.pstride;
-  for (int i = threadIdx.x; i < nvec_tot; i += NT) part[(long)blockIdx.x * hstride + i] = accs[i];
+  for (int i = i0 + threadIdx.x; i < i1; i += NT) part[(long)slot * hstride + i] = accs[i];
   if (!last_block(b.cnt + 4 * c)) return;
-  for (int i = warp; i < nvec_tot; i += NT / 32) hout[(long)c * hstride + i] = warp_sum_partials(part + i, hstride, lane);
+  for (int i = warp; i < nvec_tot; i += NT / 32)
+    hout[(long)c * hstride + i] = warp_sum_partials(part + i, hstride, lane, S);
   __syncthreads();
   if (threadIdx.x == 0) b.cnt[4 * c] = 0;
 }
@@ -459,9 +469,18 @@ unsigned grid_for(gdr_ctx* ctx, long work, int threads) {
 
 template <typename R>
 void gs_dot(gdr_ctx* ctx, const Batch<R>& b, int nv, const cx<R>* w, long wcs, c128* h_out, bool wnorm) {
-  dim3 grid((unsigned)b.nblk, (unsigned)b.ncol);
+  // tile slots x vector groups (see gs_dot_kernel); S <= nblk bounds the partials
+  constexpr long TU = DotTile<R>::DU * 32;
+  const long ntiles = (nunits<R>(b.n) + TU - 1) / TU;
+  const int nvec_tot = nv + (wnorm ? 1 : 0);
+  const int S = (int)std::max<long>(1, std::min<long>(ntiles, b.nblk));
+  const long target = 3L * ctx->num_sms;
+  int G = 1;
+  if (S < target) G = (int)std::min<long>((target + S - 1) / S, (nvec_tot + NT / 32 - 1) / (NT / 32));
+  G = std::max(G, 1);
+  dim3 grid((unsigned)(S * G), (unsigned)b.ncol);
   KProf kp(ctx, sizeof(R) == 4 ? "gs_dot_c64" : "gs_dot_c128", (double)(nv + 1) * b.n * sizeof(cx<R>) * b.ncol);
-  gs_dot_kernel<R><<<grid, NT, 0, ctx->stream>>>(b, nv, w, wcs, h_out, b.m + 2, wnorm ? 1 : 0);
+  gs_dot_kernel<R><<<grid, NT, 0, ctx->stream>>>(b, nv, w, wcs, h_out, b.m + 2, wnorm ? 1 : 0, S, G);
   GDR_LAUNCHED(ctx);
 }
 template <typename R>

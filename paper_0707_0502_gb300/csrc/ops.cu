@@ -225,6 +225,59 @@ __global__ void __launch_bounds__(128) wilson_kernel(const LT* __restrict__ link
   }
 }
 
+// Small lattices: a block takes 32 sites and warp w computes the two hops in
+// direction w for them (warp-uniform direction, a quarter of the per-thread
+// dependency chain), the four partial spinors are summed through shared memory
+// and the output, with the diagonal term, is written one component per thread
+// (coalesced).  Used when one thread per site cannot fill the GPU.
+template <typename R, typename LT>
+__global__ void __launch_bounds__(128) wilson_split_kernel(const LT* __restrict__ links, int Lx, int Ly, int Lz,
+                                                          int Lt, double diag_a, const c128* __restrict__ sigma,
+                                                          const cx<R>* __restrict__ X, long ldx,
+                                                          cx<R>* __restrict__ Y, long ldy,
+                                                          const cx<R>* __restrict__ B, long ldb,
+                                                          const int* __restrict__ run, int run_stride, int cpp) {
+  __shared__ cx<R> part[4][32][13];  // odd row length: conflict-free in both phases
+  const long V = (long)Lx * Ly * Lz * Lt;
+  const int c = blockIdx.y;
+  if (run && !run[(long)c * run_stride]) return;
+  const int mu = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long site0 = blockIdx.x * 32L, site = site0 + lane;
+  const cx<R>* x = X + c * ldx;
+  Spinor<R> acc;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) acc.s[i] = {0, 0};
+  if (site < V) {
+    long q = site;
+    const int ix = (int)(q % Lx); q /= Lx;
+    const int iy = (int)(q % Ly); q /= Ly;
+    const int iz = (int)(q % Lz);
+    const int it = (int)(q / Lz);
+    switch (mu) {  // uniform in the warp
+      case 0: hop_mu<0, R, LT>(links, x, V, site, ix, Lx, 1, acc); break;
+      case 1: hop_mu<1, R, LT>(links, x, V, site, iy, Ly, (long)Lx, acc); break;
+      case 2: hop_mu<2, R, LT>(links, x, V, site, iz, Lz, (long)Lx * Ly, acc); break;
+      default: hop_mu<3, R, LT>(links, x, V, site, it, Lt, (long)Lx * Ly * Lz, acc); break;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 12; ++i) part[mu][lane][i] = acc.s[i];
+  __syncthreads();
+  const c128 sg = sigma ? sigma[c] : c128{0.0, 0.0};
+  const cx<R> dg = {(R)(diag_a - sg.x), (R)(-sg.y)};
+  cx<R>* y = Y + c * ldy;
+  const cx<R>* b = B ? B + (c / cpp) * ldb : nullptr;
+  const long nout = min(32L, V - site0) * 12;
+  for (int q = threadIdx.x; q < nout; q += 128) {
+    const int sl = q / 12, comp = q % 12;
+    const cx<R> h = part[0][sl][comp] + part[1][sl][comp] + part[2][sl][comp] + part[3][sl][comp];
+    const long e = site0 * 12 + q;
+    cx<R> v = dg * x[e] - h;
+    if (b) v = b[e] - v;
+    y[e] = v;
+  }
+}
+
 }  // namespace
 
 template <typename R>
@@ -279,6 +332,24 @@ static void op_apply_launch(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128*
       csr_batch_kernel<float, c64><<<grid, 256, 0, ctx->stream>>>(
           A->rp_off, A->nz_off, A->nrow, A->rowptr, A->col, A->vals64, sigma, (const c64*)X, ldx, (c64*)Y, ldy,
           (const c64*)B, ldb, run, run_stride, cpp);
+    }
+    GDR_LAUNCHED(ctx);
+  } else if ((A->V + 127) / 128 * ncol < 2L * ctx->num_sms) {
+    // too few sites for one thread per site: direction-split form
+    dim3 grid((unsigned)((A->V + 31) / 32), (unsigned)ncol);
+    const int* d = A->dims;
+    if (F64) {
+      wilson_split_kernel<double, c128><<<grid, 128, 0, ctx->stream>>>(
+          A->links128, d[0], d[1], d[2], d[3], A->diag_a, sigma, (const c128*)X, ldx, (c128*)Y, ldy, (const c128*)B,
+          ldb, run, run_stride, cpp);
+    } else if (A->store == GDR_LINK_BF16) {
+      wilson_split_kernel<float, __nv_bfloat162><<<grid, 128, 0, ctx->stream>>>(
+          A->links16, d[0], d[1], d[2], d[3], A->diag_a, sigma, (const c64*)X, ldx, (c64*)Y, ldy, (const c64*)B, ldb,
+          run, run_stride, cpp);
+    } else {
+      wilson_split_kernel<float, c64><<<grid, 128, 0, ctx->stream>>>(
+          A->links64, d[0], d[1], d[2], d[3], A->diag_a, sigma, (const c64*)X, ldx, (c64*)Y, ldy, (const c64*)B, ldb,
+          run, run_stride, cpp);
     }
     GDR_LAUNCHED(ctx);
   } else {

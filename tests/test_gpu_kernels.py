@@ -35,7 +35,9 @@ def rel(a, b):
 
 # ---------------------------------------------------------------- matvec a1/a2
 
-WILSON_DIMS = [(2, 2, 2, 2), (4, 4, 4, 4), (3, 4, 2, 6), (8, 4, 4, 2)]
+# small lattices run the direction-split kernel (ragged last block of 32 sites
+# for 2^4 and 3x4x2x6); 16x16x8x8 with 3 columns the thread-per-site kernel
+WILSON_DIMS = [(2, 2, 2, 2), (4, 4, 4, 4), (3, 4, 2, 6), (8, 4, 4, 2), (16, 16, 8, 8)]
 
 
 @pytest.mark.parametrize("dims", WILSON_DIMS)
