@@ -276,7 +276,8 @@ def main():
                        "speedup_mixed_over_fp64": value / world / fp64_value,
                        "mvps_rhs1": reps64[-1]["mvps_rhs1"]},
         "solve": {k: rep[k] for k in ("mvps_rhs1", "cycles_rhs1", "mvps_extra", "mvps_proj", "mvps_refine",
-                                      "refine_passes", "pairs_cleaned", "max_relres")},
+                                      "refine_passes", "pairs_cleaned", "max_relres", "t_total_ms", "t_rhs1_ms",
+                                      "t_proj_ms", "t_refine_ms", "host_syncs", "kernel_launches")},
         "roofline": roof,
         "kernels": ktable,
     }

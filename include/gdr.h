@@ -93,6 +93,10 @@ typedef struct {
   double max_relres;    /* max over (shift, rhs) of the final FP64 true relative residual */
   double t_total_ms;    /* wall time of the solve */
   long kernel_launches; /* kernels of this library launched by the solve (graph nodes counted) */
+  double t_rhs1_ms;     /* wall time of the GMRES-DR(m,k)-Sh stage (right-hand side 1) */
+  double t_proj_ms;     /* extra right-hand side, Proj stage, corrections, first FP64 residuals */
+  double t_refine_ms;   /* refinement passes, FP64 cleanup and their residuals */
+  long host_syncs;      /* host waits on the stream (one per cycle for the convergence test, ...) */
 } gdr_report;
 
 /* ---------------------------------------------------------------- context */

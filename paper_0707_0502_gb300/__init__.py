@@ -41,7 +41,8 @@ class gdr_report(ctypes.Structure):
                 ("mvps_proj", ctypes.c_long), ("mvps_refine", ctypes.c_long), ("resid_cols", ctypes.c_long),
                 ("refine_passes", ctypes.c_int), ("pairs_cleaned", ctypes.c_int),
                 ("max_relres", ctypes.c_double), ("t_total_ms", ctypes.c_double),
-                ("kernel_launches", ctypes.c_long)]
+                ("kernel_launches", ctypes.c_long), ("t_rhs1_ms", ctypes.c_double),
+                ("t_proj_ms", ctypes.c_double), ("t_refine_ms", ctypes.c_double), ("host_syncs", ctypes.c_long)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

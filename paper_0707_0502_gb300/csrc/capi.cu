@@ -479,6 +479,7 @@ gdr_status gdr_arnoldi_step(gdr_ctx* ctx, const gdr_op* A, gdr_prec prec, void* 
       b.ldv = n;
       b.vcs = 0;
       b.W = ctx->get<cx<R>>("step.W", (size_t)pad_ld(n));
+      b.W2 = ctx->get<cx<R>>("step.W2", (size_t)pad_ld(n));
       b.wcs = 0;
       b.H = ctx->get<c128>("step.H", (size_t)(j + 2) * (j + 1));
       b.cvec = nullptr;
@@ -498,7 +499,7 @@ gdr_status gdr_arnoldi_step(gdr_ctx* ctx, const gdr_op* A, gdr_prec prec, void* 
       GDR_CUDA(cudaMemsetAsync(b.cnt, 0, 4 * sizeof(unsigned), ctx->stream));
       GDR_CUDA(cudaMemcpyAsync(b.st, &s, sizeof(s), cudaMemcpyHostToDevice, ctx->stream));
       GDR_CUDA(cudaStreamSynchronize(ctx->stream));
-      arnoldi_step<R>(ctx, A, b, j);
+      arnoldi_step<R>(ctx, A, b, j, j, j);
       GDR_CUDA(cudaMemcpyAsync(hcol, b.H + (long)j * (j + 2), sizeof(c128) * (j + 2), cudaMemcpyDeviceToDevice,
                                ctx->stream));
     };

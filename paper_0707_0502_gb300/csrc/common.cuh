@@ -97,6 +97,7 @@ struct gdr_ctx {
   void* pinned = nullptr;            // small pinned host buffer for status words
   size_t pinned_bytes = 0;
   long launches = 0;                 // kernels launched (graph replays add their node count)
+  long syncs = 0;                    // host waits on the stream by the solver
 
   // per-kernel timing (gdr_profile): CUDA events around every launch, graphs off
   struct ProfRec {

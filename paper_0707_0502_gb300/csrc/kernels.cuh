@@ -29,7 +29,8 @@ struct Batch {
   int ns = 1;            // shifts per column
   cx<R>* V = nullptr;    // basis, column c at V + c*vcs, vectors at stride ldv
   long ldv = 0, vcs = 0;
-  cx<R>* W = nullptr;    // work vector per column (stride wcs)
+  cx<R>* W = nullptr;    // work vectors per column (stride wcs): W receives A v_j,
+  cx<R>* W2 = nullptr;   // W2 the orthogonalised w (next step's unnormalised input)
   long wcs = 0;
   c128* H = nullptr;     // (m+1) x m per column, stride (m+1)*m
   c128* cvec = nullptr;  // m+1 per column
@@ -46,18 +47,27 @@ struct Batch {
 };
 
 // krylov.cu --------------------------------------------------------------
-// h_out[c][0..nv-1] = V_c[:, 0:nv]^H w_c  (+ ||w_c||^2 in h_out[c][nv] if wnorm)
+// h_out[c][0..nv-1] = V_c[:, 0:nv]^H w_c  (+ ||w_c||^2 in h_out[c][nv] if wnorm).  With wprev,
+// v_{nv-1} is taken as wprev_c * inv_norm_c and stored into V on the way.
 template <typename R>
-void gs_dot(gdr_ctx* ctx, const Batch<R>& b, int nv, const cx<R>* w, long wcs, c128* h_out, bool wnorm);
+void gs_dot(gdr_ctx* ctx, const Batch<R>& b, int nv, const cx<R>* w, long wcs, c128* h_out, bool wnorm,
+            const cx<R>* wprev = nullptr);
+// wout_c = w_c - V_c[:, 0:nv] h_c and h_out[c][0..nv-1] = V_c[:, 0:nv]^H wout_c in one pass
+template <typename R>
+void gs_update_dot(gdr_ctx* ctx, const Batch<R>& b, int nv, const cx<R>* w, cx<R>* wout, long wcs, const c128* h,
+                   c128* h_out);
 // w_c -= V_c[:, 0:nv] h_c ; if final: Arnoldi step j = nv-1 is completed (Hbar column, norm, breakdown)
 template <typename R>
 void gs_update(gdr_ctx* ctx, const Batch<R>& b, int nv, cx<R>* w, long wcs, const c128* h, bool final_step);
 // V_c[:, j] = w_c * inv_norm_c   (skips broken / inactive columns)
 template <typename R>
 void scale_into(gdr_ctx* ctx, const Batch<R>& b, int j, const cx<R>* w, long wcs);
-// one full CGS2 Arnoldi step on every column: w = A v_j, two GS passes, v_{j+1}
+// one CGS2 Arnoldi step on every column (Hbar column j, h_{j+1,j}).  Steps after
+// the first of a sweep (j > jstart) take v_j from W2 scaled by 1/h_{j,j-1} and
+// store it into V in their first dot pass; the last step (j == jlast) writes
+// v_{j+1} into V.  Launches: matvec, dot, update+dot, update (+ scale at jlast).
 template <typename R>
-void arnoldi_step(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b, int j);
+void arnoldi_step(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b, int j, int jstart, int jlast);
 // start a cycle from r_c: V_c[:,0] = r_c/||r_c||, cvec_c = ||r_c|| e_1, H_c = 0, state reset
 template <typename R>
 void start_cycle(gdr_ctx* ctx, const Batch<R>& b, const cx<R>* r, long rcs);
@@ -92,10 +102,15 @@ void axpy_cols(gdr_ctx* ctx, long n, int cols, const c128* a, const c128* S, lon
 void scal_cols(gdr_ctx* ctx, long n, int cols, const c128* a, c128* X, long xcs);
 
 // ops.cu -----------------------------------------------------------------
+// y_c = xs_c (A - sigma_c) x_c  [or b - that], skipping columns whose run flag is 0;
+// xs (optional, stride xs_stride doubles) scales each column's result: the
+// Arnoldi step passes 1/h_{j+1,j} and the unnormalised vector
 void op_apply_skip(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, const c128* X, long ldx, c128* Y,
-                   long ldy, const c128* B, long ldb, const int* run, int run_stride, int cpp = 1);
+                   long ldy, const c128* B, long ldb, const int* run, int run_stride, int cpp = 1,
+                   const double* xs = nullptr, int xs_stride = 0);
 void op_apply_skip(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, const c64* X, long ldx, c64* Y,
-                   long ldy, const c64* B, long ldb, const int* run, int run_stride, int cpp = 1);
+                   long ldy, const c64* B, long ldb, const int* run, int run_stride, int cpp = 1,
+                   const double* xs = nullptr, int xs_stride = 0);
 void op_build_csr_batch(gdr_ctx* ctx, gdr_op* op, const long* n, const long* nnz, const int* rowptr, const int* col,
                         const double* vals);
 void op_build_csr(gdr_ctx* ctx, gdr_op* op, const int* rowptr, const int* col, const double* vals);

@@ -120,7 +120,8 @@ template <typename R> struct DotTile { static constexpr int DU = (U<R>::K == 2) 
 
 template <typename R>
 __global__ void __launch_bounds__(NT, 3) gs_dot_kernel(Batch<R> b, int nv, const cx<R>* __restrict__ W, long wcs,
-                                                    c128* __restrict__ hout, int hstride, int wnorm, int S, int G) {
+                                                    c128* __restrict__ hout, int hstride, int wnorm, int S, int G,
+                                                    const cx<R>* __restrict__ Wprev) {
   const int c = blockIdx.y;
   if (!b.st[c].run) return;
   constexpr int K = U<R>::K;
@@ -156,7 +157,10 @@ __global__ void __launch_bounds__(NT, 3) gs_dot_kernel(Batch<R> b, int nv, const
     for (int i = i0 + warp; i < i1; i += NT / 32) {
       cx<R> a = {0, 0};
       if (i < nv) {
-        const cx<R>* vi = V + (long)i * b.ldv;
+        // lazy step: v_{nv-1} is the previous step's unnormalised vector; scale it
+        // and store it into V while it is read
+        const bool lazy = Wprev && i == nv - 1;
+        const cx<R>* vi = lazy ? Wprev + c * wcs : V + (long)i * b.ldv;
         cx<R> vv[DU][K];
 #pragma unroll
         for (int tt = 0; tt < DU; ++tt) {
@@ -166,6 +170,17 @@ __global__ void __launch_bounds__(NT, 3) gs_dot_kernel(Batch<R> b, int nv, const
           } else {
 #pragma unroll
             for (int kk = 0; kk < K; ++kk) vv[tt][kk] = {0, 0};
+          }
+        }
+        if (lazy) {
+          const R sc = (R)b.st[c].inv_norm;
+          cx<R>* vo = b.V + c * b.vcs + (long)i * b.ldv;
+#pragma unroll
+          for (int tt = 0; tt < DU; ++tt) {
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) vv[tt][kk] = sc * vv[tt][kk];
+            const long u = u0 + lane + 32 * tt;
+            if (u < nu) stu<R>(vo, u, n, vv[tt]);
           }
         }
 #pragma unroll
@@ -192,6 +207,105 @@ __global__ void __launch_bounds__(NT, 3) gs_dot_kernel(Batch<R> b, int nv, const
   if (!last_block(b.cnt + 4 * c)) return;
   for (int i = warp; i < nvec_tot; i += NT / 32)
     hout[(long)c * hstride + i] = warp_sum_partials(part + i, hstride, lane, S);
+  __syncthreads();
+  if (threadIdx.x == 0) b.cnt[4 * c] = 0;
+}
+
+// First CGS2 update fused with the second projection: per tile, w' = w - V h
+// (all nv vectors; written to Wout by the group-0 block of the tile and staged
+// in shared memory), then hout = V^H w' for the block's group of vectors, with
+// the tile slot / vector group grid and the partials of gs_dot_kernel.  V is
+// read once from HBM for both (the dot re-reads the tile from L1/L2).
+template <typename R>
+__global__ void __launch_bounds__(NT, 2) gs_update_dot_kernel(Batch<R> b, int nv, const cx<R>* __restrict__ W,
+                                                           cx<R>* __restrict__ Wout, long wcs,
+                                                           const c128* __restrict__ h, c128* __restrict__ hout,
+                                                           int hstride, int S, int G) {
+  const int c = blockIdx.y;
+  if (!b.st[c].run) return;
+  constexpr int K = U<R>::K;
+  constexpr int DU = DotTile<R>::DU;
+  constexpr int TU = DU * 32;
+  __shared__ cx<R> wt[TU * K];
+  __shared__ cx<R> hs[GDR_MAX_M + 2];
+  __shared__ c128 accs[GDR_MAX_M + 2];
+  const cx<R>* __restrict__ V = b.V + c * b.vcs;
+  const cx<R>* __restrict__ w = W + c * wcs;
+  cx<R>* __restrict__ wo = Wout + c * wcs;
+  const long n = b.nvec ? (long)b.nvec[c] : b.n, nu = nunits<R>(n);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int slot = blockIdx.x % S, grp = blockIdx.x / S;
+  const int vpg = (nv + G - 1) / G;
+  const int i0 = grp * vpg, i1 = min(nv, i0 + vpg);
+  for (int i = threadIdx.x; i < nv; i += NT) hs[i] = cvt<R>(h[(long)c * hstride + i]);
+  for (int i = i0 + threadIdx.x; i < i1; i += NT) accs[i] = {0, 0};
+  const long ntiles = (nu + TU - 1) / TU;
+  for (long t = slot; t < ntiles; t += S) {
+    const long u0 = t * TU;
+    __syncthreads();  // hs ready; readers of the previous tile are done
+    for (int q = threadIdx.x; q < TU; q += NT) {
+      const long u = u0 + q;
+      cx<R> acc[K];
+      if (u < nu) {
+        ldu<R>(w, u, n, acc);
+        for (int g0 = 0; g0 < nv; g0 += JB) {
+          cx<R> vv[JB][K];
+#pragma unroll
+          for (int qq = 0; qq < JB; ++qq)
+            if (g0 + qq < nv) ldu<R>(V + (long)(g0 + qq) * b.ldv, u, n, vv[qq]);
+#pragma unroll
+          for (int qq = 0; qq < JB; ++qq) {
+            if (g0 + qq < nv) {
+              const cx<R> hi = hs[g0 + qq];
+#pragma unroll
+              for (int kk = 0; kk < K; ++kk) acc[kk] -= vv[qq][kk] * hi;
+            }
+          }
+        }
+        if (grp == 0) stu<R>(wo, u, n, acc);
+      } else {
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) acc[kk] = {0, 0};
+      }
+#pragma unroll
+      for (int kk = 0; kk < K; ++kk) wt[q * K + kk] = acc[kk];
+    }
+    __syncthreads();
+    for (int i = i0 + warp; i < i1; i += NT / 32) {
+      const cx<R>* vi = V + (long)i * b.ldv;
+      cx<R> a = {0, 0};
+      // the tile in two halves (DU/2 loads in flight per lane; the tile is in L1/L2)
+#pragma unroll
+      for (int t0 = 0; t0 < DU; t0 += DU / 2) {
+        cx<R> vv[DU / 2][K];
+#pragma unroll
+        for (int tt = 0; tt < DU / 2; ++tt) {
+          const long u = u0 + lane + 32 * (t0 + tt);
+          if (u < nu) {
+            ldu<R>(vi, u, n, vv[tt]);
+          } else {
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) vv[tt][kk] = {0, 0};
+          }
+        }
+#pragma unroll
+        for (int tt = 0; tt < DU / 2; ++tt)
+#pragma unroll
+          for (int kk = 0; kk < K; ++kk) a += cmulc(vv[tt][kk], wt[(lane + 32 * (t0 + tt)) * K + kk]);
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        a.x += __shfl_xor_sync(FULL, a.x, off);
+        a.y += __shfl_xor_sync(FULL, a.y, off);
+      }
+      if (lane == 0) accs[i] += up(a);
+    }
+  }
+  __syncthreads();
+  c128* part = b.part + c * b.pstride;
+  for (int i = i0 + threadIdx.x; i < i1; i += NT) part[(long)slot * hstride + i] = accs[i];
+  if (!last_block(b.cnt + 4 * c)) return;
+  for (int i = warp; i < nv; i += NT / 32) hout[(long)c * hstride + i] = warp_sum_partials(part + i, hstride, lane, S);
   __syncthreads();
   if (threadIdx.x == 0) b.cnt[4 * c] = 0;
 }
@@ -467,20 +581,38 @@ unsigned grid_for(gdr_ctx* ctx, long work, int threads) {
 
 // ------------------------------------------------------------- launchers
 
+// tile slots S x vector groups G of the dot kernels; S <= nblk bounds the partials
 template <typename R>
-void gs_dot(gdr_ctx* ctx, const Batch<R>& b, int nv, const cx<R>* w, long wcs, c128* h_out, bool wnorm) {
-  // tile slots x vector groups (see gs_dot_kernel); S <= nblk bounds the partials
+static void dot_grid(gdr_ctx* ctx, const Batch<R>& b, int nvec, int& S, int& G) {
   constexpr long TU = DotTile<R>::DU * 32;
   const long ntiles = (nunits<R>(b.n) + TU - 1) / TU;
-  const int nvec_tot = nv + (wnorm ? 1 : 0);
-  const int S = (int)std::max<long>(1, std::min<long>(ntiles, b.nblk));
+  S = (int)std::max<long>(1, std::min<long>(ntiles, b.nblk));
   const long target = 3L * ctx->num_sms;
-  int G = 1;
-  if (S < target) G = (int)std::min<long>((target + S - 1) / S, (nvec_tot + NT / 32 - 1) / (NT / 32));
+  G = 1;
+  if (S < target) G = (int)std::min<long>((target + S - 1) / S, (nvec + NT / 32 - 1) / (NT / 32));
   G = std::max(G, 1);
+}
+
+template <typename R>
+void gs_dot(gdr_ctx* ctx, const Batch<R>& b, int nv, const cx<R>* w, long wcs, c128* h_out, bool wnorm,
+            const cx<R>* wprev) {
+  int S, G;
+  dot_grid(ctx, b, nv + (wnorm ? 1 : 0), S, G);
   dim3 grid((unsigned)(S * G), (unsigned)b.ncol);
-  KProf kp(ctx, sizeof(R) == 4 ? "gs_dot_c64" : "gs_dot_c128", (double)(nv + 1) * b.n * sizeof(cx<R>) * b.ncol);
-  gs_dot_kernel<R><<<grid, NT, 0, ctx->stream>>>(b, nv, w, wcs, h_out, b.m + 2, wnorm ? 1 : 0, S, G);
+  KProf kp(ctx, sizeof(R) == 4 ? "gs_dot_c64" : "gs_dot_c128",
+           ((double)(nv + 1) + (wprev ? 1.0 : 0.0)) * b.n * sizeof(cx<R>) * b.ncol);
+  gs_dot_kernel<R><<<grid, NT, 0, ctx->stream>>>(b, nv, w, wcs, h_out, b.m + 2, wnorm ? 1 : 0, S, G, wprev);
+  GDR_LAUNCHED(ctx);
+}
+template <typename R>
+void gs_update_dot(gdr_ctx* ctx, const Batch<R>& b, int nv, const cx<R>* w, cx<R>* wout, long wcs, const c128* h,
+                   c128* h_out) {
+  int S, G;
+  dot_grid(ctx, b, nv, S, G);
+  dim3 grid((unsigned)(S * G), (unsigned)b.ncol);
+  KProf kp(ctx, sizeof(R) == 4 ? "gs_update_dot_c64" : "gs_update_dot_c128",
+           (double)(nv + 2) * b.n * sizeof(cx<R>) * b.ncol);
+  gs_update_dot_kernel<R><<<grid, NT, 0, ctx->stream>>>(b, nv, w, wout, wcs, h, h_out, b.m + 2, S, G);
   GDR_LAUNCHED(ctx);
 }
 template <typename R>
@@ -500,14 +632,19 @@ void scale_into(gdr_ctx* ctx, const Batch<R>& b, int j, const cx<R>* w, long wcs
 }
 
 template <typename R>
-void arnoldi_step(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b, int j) {
-  op_apply_skip(ctx, A, b.ncol, nullptr, b.V + (long)j * b.ldv, b.vcs, b.W, b.wcs, nullptr, 0, &b.st[0].run,
-                (int)(sizeof(ColState) / sizeof(int)), b.cpp);
-  gs_dot<R>(ctx, b, j + 1, b.W, b.wcs, b.h1, true);
-  gs_update<R>(ctx, b, j + 1, b.W, b.wcs, b.h1, false);
-  gs_dot<R>(ctx, b, j + 1, b.W, b.wcs, b.h2, false);
-  gs_update<R>(ctx, b, j + 1, b.W, b.wcs, b.h2, true);
-  scale_into<R>(ctx, b, j + 1, b.W, b.wcs);
+void arnoldi_step(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b, int j, int jstart, int jlast) {
+  const int is = (int)(sizeof(ColState) / sizeof(int)), ds = (int)(sizeof(ColState) / sizeof(double));
+  const bool lazy = j > jstart;  // v_j = W2 / h_{j,j-1}, not yet in V
+  if (lazy)
+    op_apply_skip(ctx, A, b.ncol, nullptr, b.W2, b.wcs, b.W, b.wcs, nullptr, 0, &b.st[0].run, is, b.cpp,
+                  &b.st[0].inv_norm, ds);
+  else
+    op_apply_skip(ctx, A, b.ncol, nullptr, b.V + (long)j * b.ldv, b.vcs, b.W, b.wcs, nullptr, 0, &b.st[0].run, is,
+                  b.cpp);
+  gs_dot<R>(ctx, b, j + 1, b.W, b.wcs, b.h1, true, lazy ? b.W2 : nullptr);
+  gs_update_dot<R>(ctx, b, j + 1, b.W, b.W2, b.wcs, b.h1, b.h2);
+  gs_update<R>(ctx, b, j + 1, b.W2, b.wcs, b.h2, true);
+  if (j == jlast) scale_into<R>(ctx, b, j + 1, b.W2, b.wcs);
 }
 
 template <typename R>
@@ -584,14 +721,14 @@ void scal_cols(gdr_ctx* ctx, long n, int cols, const c128* a, c128* X, long xcs)
   GDR_LAUNCHED(ctx);
 }
 
-template void gs_dot<float>(gdr_ctx*, const Batch<float>&, int, const c64*, long, c128*, bool);
-template void gs_dot<double>(gdr_ctx*, const Batch<double>&, int, const c128*, long, c128*, bool);
+template void gs_dot<float>(gdr_ctx*, const Batch<float>&, int, const c64*, long, c128*, bool, const c64*);
+template void gs_dot<double>(gdr_ctx*, const Batch<double>&, int, const c128*, long, c128*, bool, const c128*);
 template void gs_update<float>(gdr_ctx*, const Batch<float>&, int, c64*, long, const c128*, bool);
 template void gs_update<double>(gdr_ctx*, const Batch<double>&, int, c128*, long, const c128*, bool);
 template void scale_into<float>(gdr_ctx*, const Batch<float>&, int, const c64*, long);
 template void scale_into<double>(gdr_ctx*, const Batch<double>&, int, const c128*, long);
-template void arnoldi_step<float>(gdr_ctx*, const gdr_op*, const Batch<float>&, int);
-template void arnoldi_step<double>(gdr_ctx*, const gdr_op*, const Batch<double>&, int);
+template void arnoldi_step<float>(gdr_ctx*, const gdr_op*, const Batch<float>&, int, int, int);
+template void arnoldi_step<double>(gdr_ctx*, const gdr_op*, const Batch<double>&, int, int, int);
 template void start_cycle<float>(gdr_ctx*, const Batch<float>&, const c64*, long);
 template void start_cycle<double>(gdr_ctx*, const Batch<double>&, const c128*, long);
 template void norms2<c64>(gdr_ctx*, long, int, const c64*, long, double*, c128*, int, unsigned*, const int*);

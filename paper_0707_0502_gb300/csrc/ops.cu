@@ -25,7 +25,7 @@ __global__ void csr_kernel(long n, const int* __restrict__ rowptr, const int* __
                            const VT* __restrict__ vals, const c128* __restrict__ sigma,
                            const cx<R>* __restrict__ X, long ldx, cx<R>* __restrict__ Y, long ldy,
                            const cx<R>* __restrict__ B, long ldb, const int* __restrict__ run, int run_stride,
-                           int cpp) {
+                           int cpp, const double* __restrict__ xs, int xs_stride) {
   const long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
   const int c = blockIdx.y;
   if (r >= n) return;
@@ -39,6 +39,7 @@ __global__ void csr_kernel(long n, const int* __restrict__ rowptr, const int* __
     acc += a * x[col[p]];
   }
   if (sigma) acc -= cvt<R>(sigma[c]) * x[r];
+  if (xs) acc = (R)xs[(long)c * xs_stride] * acc;
   if (B) acc = B[(c / cpp) * ldb + r] - acc;
   Y[c * ldy + r] = acc;
 }
@@ -50,7 +51,8 @@ __global__ void csr_batch_kernel(const long* __restrict__ rp_off, const long* __
                                  const int* __restrict__ col, const VT* __restrict__ vals,
                                  const c128* __restrict__ sigma, const cx<R>* __restrict__ X, long ldx,
                                  cx<R>* __restrict__ Y, long ldy, const cx<R>* __restrict__ B, long ldb,
-                                 const int* __restrict__ run, int run_stride, int cpp) {
+                                 const int* __restrict__ run, int run_stride, int cpp,
+                                 const double* __restrict__ xs, int xs_stride) {
   const long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
   const int c = blockIdx.y;
   const int p = c / cpp;
@@ -67,6 +69,7 @@ __global__ void csr_batch_kernel(const long* __restrict__ rp_off, const long* __
     acc += cx<R>{(R)v.x, (R)v.y} * x[cl[q]];
   }
   if (sigma) acc -= cvt<R>(sigma[c]) * x[r];
+  if (xs) acc = (R)xs[(long)c * xs_stride] * acc;
   if (B) acc = B[(long)p * ldb + r] - acc;
   Y[c * ldy + r] = acc;
 }
@@ -191,7 +194,8 @@ __global__ void __launch_bounds__(128) wilson_kernel(const LT* __restrict__ link
                                                     double diag_a, const c128* __restrict__ sigma,
                                                     const cx<R>* __restrict__ X, long ldx, cx<R>* __restrict__ Y,
                                                     long ldy, const cx<R>* __restrict__ B, long ldb,
-                                                    const int* __restrict__ run, int run_stride, int cpp) {
+                                                    const int* __restrict__ run, int run_stride, int cpp,
+                                                    const double* __restrict__ xs, int xs_stride) {
   const long V = (long)Lx * Ly * Lz * Lt;
   const long site = blockIdx.x * (long)blockDim.x + threadIdx.x;
   const int c = blockIdx.y;
@@ -217,9 +221,10 @@ __global__ void __launch_bounds__(128) wilson_kernel(const LT* __restrict__ link
   const cx<R> dg = {(R)(diag_a - sg.x), (R)(-sg.y)};
   cx<R>* y = Y + c * ldy + site * 12;
   const cx<R>* b = B ? B + (c / cpp) * ldb + site * 12 : nullptr;
+  const R sc = xs ? (R)xs[(long)c * xs_stride] : R(1);
 #pragma unroll
   for (int i = 0; i < 12; ++i) {
-    cx<R> v = dg * p.s[i] - acc.s[i];
+    cx<R> v = sc * (dg * p.s[i] - acc.s[i]);
     if (b) v = b[i] - v;
     y[i] = v;
   }
@@ -236,7 +241,8 @@ __global__ void __launch_bounds__(128) wilson_split_kernel(const LT* __restrict_
                                                           const cx<R>* __restrict__ X, long ldx,
                                                           cx<R>* __restrict__ Y, long ldy,
                                                           const cx<R>* __restrict__ B, long ldb,
-                                                          const int* __restrict__ run, int run_stride, int cpp) {
+                                                          const int* __restrict__ run, int run_stride, int cpp,
+                                                          const double* __restrict__ xs, int xs_stride) {
   __shared__ cx<R> part[4][32][13];  // odd row length: conflict-free in both phases
   const long V = (long)Lx * Ly * Lz * Lt;
   const int c = blockIdx.y;
@@ -268,11 +274,12 @@ __global__ void __launch_bounds__(128) wilson_split_kernel(const LT* __restrict_
   cx<R>* y = Y + c * ldy;
   const cx<R>* b = B ? B + (c / cpp) * ldb : nullptr;
   const long nout = min(32L, V - site0) * 12;
+  const R sc = xs ? (R)xs[(long)c * xs_stride] : R(1);
   for (int q = threadIdx.x; q < nout; q += 128) {
     const int sl = q / 12, comp = q % 12;
     const cx<R> h = part[0][sl][comp] + part[1][sl][comp] + part[2][sl][comp] + part[3][sl][comp];
     const long e = site0 * 12 + q;
-    cx<R> v = dg * x[e] - h;
+    cx<R> v = sc * (dg * x[e] - h);
     if (b) v = b[e] - v;
     y[e] = v;
   }
@@ -282,11 +289,13 @@ __global__ void __launch_bounds__(128) wilson_split_kernel(const LT* __restrict_
 
 template <typename R>
 static void op_apply_launch(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, const cx<R>* X, long ldx,
-                            cx<R>* Y, long ldy, const cx<R>* B, long ldb, const int* run, int run_stride, int cpp);
+                            cx<R>* Y, long ldy, const cx<R>* B, long ldb, const int* run, int run_stride, int cpp,
+                            const double* xs, int xs_stride);
 
 template <typename R>
 static void op_apply_impl(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, const cx<R>* X, long ldx,
-                          cx<R>* Y, long ldy, const cx<R>* B, long ldb, const int* run, int run_stride, int cpp) {
+                          cx<R>* Y, long ldy, const cx<R>* B, long ldb, const int* run, int run_stride, int cpp,
+                          const double* xs, int xs_stride) {
   if (ncol <= 0) return;
   constexpr bool F64 = std::is_same<R, double>::value;
   const double sv = sizeof(cx<R>);
@@ -295,31 +304,32 @@ static void op_apply_impl(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* s
     const double bytes = (double)A->n * 4 + (double)A->nnz * (4 + (F64 ? 16 : 8)) +
                          (double)ncol * A->n * sv * (B ? 3 : 2);
     KProf kp(ctx, F64 ? "csr_matvec_c128" : "csr_matvec_c64", bytes);
-    op_apply_launch<R>(ctx, A, ncol, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride, cpp);
+    op_apply_launch<R>(ctx, A, ncol, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride, cpp, xs, xs_stride);
   } else {
     // per site: 4 links of 18 reals, 24 reals of x read and of y written (+ b read)
     const double sl = F64 ? 8 : (A->store == GDR_LINK_BF16 ? 2 : 4);
     const double bytes = (double)A->V * (4 * 18 * sl + (double)ncol * 12 * sv * (B ? 3 : 2));
     KProf kp(ctx, F64 ? "wilson_matvec_c128" : (A->store == GDR_LINK_BF16 ? "wilson_matvec_c64_bf16links"
                                                                         : "wilson_matvec_c64"), bytes);
-    op_apply_launch<R>(ctx, A, ncol, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride, cpp);
+    op_apply_launch<R>(ctx, A, ncol, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride, cpp, xs, xs_stride);
   }
 }
 
 template <typename R>
 static void op_apply_launch(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, const cx<R>* X, long ldx,
-                            cx<R>* Y, long ldy, const cx<R>* B, long ldb, const int* run, int run_stride, int cpp) {
+                            cx<R>* Y, long ldy, const cx<R>* B, long ldb, const int* run, int run_stride, int cpp,
+                          const double* xs, int xs_stride) {
   constexpr bool F64 = std::is_same<R, double>::value;
   if (A->kind == OP_CSR) {
     dim3 grid((unsigned)((A->n + 255) / 256), (unsigned)ncol);
     if (F64) {
       csr_kernel<double, c128><<<grid, 256, 0, ctx->stream>>>(
           A->n, A->rowptr, A->col, A->vals128, sigma, (const c128*)X, ldx, (c128*)Y, ldy, (const c128*)B, ldb, run,
-          run_stride, cpp);
+          run_stride, cpp, xs, xs_stride);
     } else {
       csr_kernel<float, c64><<<grid, 256, 0, ctx->stream>>>(A->n, A->rowptr, A->col, A->vals64, sigma,
                                                              (const c64*)X, ldx, (c64*)Y, ldy, (const c64*)B, ldb,
-                                                             run, run_stride, cpp);
+                                                             run, run_stride, cpp, xs, xs_stride);
     }
     GDR_LAUNCHED(ctx);
   } else if (A->kind == OP_CSR_BATCH) {
@@ -327,11 +337,11 @@ static void op_apply_launch(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128*
     if (F64) {
       csr_batch_kernel<double, c128><<<grid, 256, 0, ctx->stream>>>(
           A->rp_off, A->nz_off, A->nrow, A->rowptr, A->col, A->vals128, sigma, (const c128*)X, ldx, (c128*)Y, ldy,
-          (const c128*)B, ldb, run, run_stride, cpp);
+          (const c128*)B, ldb, run, run_stride, cpp, xs, xs_stride);
     } else {
       csr_batch_kernel<float, c64><<<grid, 256, 0, ctx->stream>>>(
           A->rp_off, A->nz_off, A->nrow, A->rowptr, A->col, A->vals64, sigma, (const c64*)X, ldx, (c64*)Y, ldy,
-          (const c64*)B, ldb, run, run_stride, cpp);
+          (const c64*)B, ldb, run, run_stride, cpp, xs, xs_stride);
     }
     GDR_LAUNCHED(ctx);
   } else if ((A->V + 127) / 128 * ncol < 2L * ctx->num_sms) {
@@ -341,15 +351,15 @@ static void op_apply_launch(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128*
     if (F64) {
       wilson_split_kernel<double, c128><<<grid, 128, 0, ctx->stream>>>(
           A->links128, d[0], d[1], d[2], d[3], A->diag_a, sigma, (const c128*)X, ldx, (c128*)Y, ldy, (const c128*)B,
-          ldb, run, run_stride, cpp);
+          ldb, run, run_stride, cpp, xs, xs_stride);
     } else if (A->store == GDR_LINK_BF16) {
       wilson_split_kernel<float, __nv_bfloat162><<<grid, 128, 0, ctx->stream>>>(
           A->links16, d[0], d[1], d[2], d[3], A->diag_a, sigma, (const c64*)X, ldx, (c64*)Y, ldy, (const c64*)B, ldb,
-          run, run_stride, cpp);
+          run, run_stride, cpp, xs, xs_stride);
     } else {
       wilson_split_kernel<float, c64><<<grid, 128, 0, ctx->stream>>>(
           A->links64, d[0], d[1], d[2], d[3], A->diag_a, sigma, (const c64*)X, ldx, (c64*)Y, ldy, (const c64*)B, ldb,
-          run, run_stride, cpp);
+          run, run_stride, cpp, xs, xs_stride);
     }
     GDR_LAUNCHED(ctx);
   } else {
@@ -358,33 +368,35 @@ static void op_apply_launch(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128*
     if (F64) {
       wilson_kernel<double, c128><<<grid, 128, 0, ctx->stream>>>(A->links128, d[0], d[1], d[2], d[3], A->diag_a,
                                                                  sigma, (const c128*)X, ldx, (c128*)Y, ldy,
-                                                                 (const c128*)B, ldb, run, run_stride, cpp);
+                                                                 (const c128*)B, ldb, run, run_stride, cpp, xs, xs_stride);
     } else if (A->store == GDR_LINK_BF16) {
       wilson_kernel<float, __nv_bfloat162><<<grid, 128, 0, ctx->stream>>>(
           A->links16, d[0], d[1], d[2], d[3], A->diag_a, sigma, (const c64*)X, ldx, (c64*)Y, ldy, (const c64*)B, ldb,
-          run, run_stride, cpp);
+          run, run_stride, cpp, xs, xs_stride);
     } else {
       wilson_kernel<float, c64><<<grid, 128, 0, ctx->stream>>>(A->links64, d[0], d[1], d[2], d[3], A->diag_a, sigma,
                                                                (const c64*)X, ldx, (c64*)Y, ldy, (const c64*)B, ldb,
-                                                               run, run_stride, cpp);
+                                                               run, run_stride, cpp, xs, xs_stride);
     }
     GDR_LAUNCHED(ctx);
   }
 }
 
 void op_apply_skip(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, const c128* X, long ldx, c128* Y,
-                   long ldy, const c128* B, long ldb, const int* run, int run_stride, int cpp) {
-  op_apply_impl<double>(ctx, A, ncol, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride, cpp);
+                   long ldy, const c128* B, long ldb, const int* run, int run_stride, int cpp, const double* xs,
+                   int xs_stride) {
+  op_apply_impl<double>(ctx, A, ncol, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride, cpp, xs, xs_stride);
 }
 void op_apply_skip(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, const c64* X, long ldx, c64* Y,
-                   long ldy, const c64* B, long ldb, const int* run, int run_stride, int cpp) {
-  op_apply_impl<float>(ctx, A, ncol, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride, cpp);
+                   long ldy, const c64* B, long ldb, const int* run, int run_stride, int cpp, const double* xs,
+                   int xs_stride) {
+  op_apply_impl<float>(ctx, A, ncol, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride, cpp, xs, xs_stride);
 }
 
 template <typename R>
 void op_apply(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, const cx<R>* X, long ldx, cx<R>* Y,
               long ldy, const cx<R>* B, long ldb, int cpp) {
-  op_apply_skip(ctx, A, ncol, sigma, X, ldx, Y, ldy, B, ldb, nullptr, 0, cpp);
+  op_apply_skip(ctx, A, ncol, sigma, X, ldx, Y, ldy, B, ldb, nullptr, 0, cpp, nullptr, 0);
 }
 template void op_apply<double>(gdr_ctx*, const gdr_op*, int, const c128*, const c128*, long, c128*, long, const c128*,
                                long, int);

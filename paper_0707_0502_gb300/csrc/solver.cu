@@ -128,6 +128,12 @@ void run_cycle(gdr_ctx* ctx, bool use_graph, Graph& g, const std::function<void(
   ctx->launches += g.nodes;
 }
 
+// host wait on the context stream (counted in the report)
+void stream_sync(gdr_ctx* ctx) {
+  GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+  ctx->syncs++;
+}
+
 // Grid of the Gram-Schmidt reduction kernels: enough 256-thread blocks for one
 // 16-byte unit per thread, at most 3 per SM (all resident in one wave at the
 // register use of the dot kernel).
@@ -152,6 +158,7 @@ Batch<R> make_batch(gdr_ctx* ctx, const std::string& tag, long n, int ncol, int 
   b.V = ctx->get<cx<R>>(tag + ".V", (size_t)b.vcs * ncol);
   b.wcs = b.ldv;
   b.W = ctx->get<cx<R>>(tag + ".W", (size_t)b.wcs * ncol);
+  b.W2 = ctx->get<cx<R>>(tag + ".W2", (size_t)b.wcs * ncol);
   b.H = ctx->get<c128>(tag + ".H", (size_t)(m + 1) * m * ncol);
   b.cvec = ctx->get<c128>(tag + ".c", (size_t)(m + 1) * ncol);
   b.h1 = ctx->get<c128>(tag + ".h1", (size_t)(m + 2) * ncol);
@@ -200,7 +207,7 @@ void reorth_column(gdr_ctx* ctx, const Batch<R>& b, int j, double* nrm2) {
 std::vector<ColState> read_states(gdr_ctx* ctx, const ColState* st, int ncol) {
   ColState* h = static_cast<ColState*>(ctx->host_status(sizeof(ColState) * ncol));
   GDR_CUDA(cudaMemcpyAsync(h, st, sizeof(ColState) * ncol, cudaMemcpyDeviceToHost, ctx->stream));
-  GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+  stream_sync(ctx);
   return std::vector<ColState>(h, h + ncol);
 }
 
@@ -259,7 +266,7 @@ DrResult dr_sh(gdr_ctx* ctx, const gdr_op* A, const DrJob<R>& job, bool use_grap
     auto enqueue = [&]() {
       set_run_kernel<<<(ncol + 31) / 32, 32, 0, ctx->stream>>>(b.st, ncol);
       GDR_LAUNCHED(ctx);
-      for (int j = jstart; j < m; ++j) arnoldi_step<R>(ctx, A, b, j);
+      for (int j = jstart; j < m; ++j) arnoldi_step<R>(ctx, A, b, j, jstart, m - 1);
       dense_cycle(ctx, d);
       // restart (V_{k+1} <- V_{m+1} P_{k+1}) fused with x_i += V_m d_i
       combine<R>(ctx, n, ncol, b.V, b.ldv, b.vcs, m + 1, d.Cf, ldc, d.ccs, k > 0 ? k + 1 : 0, ns, k > 0 ? 0 : 1,
@@ -298,7 +305,7 @@ DrResult dr_sh(gdr_ctx* ctx, const gdr_op* A, const DrJob<R>& job, bool use_grap
   res.valid_defl = (k > 0) && !res.broke && res.status != GDR_ENAN && res.status != GDR_EBREAKDOWN;
   std::vector<double> nr((size_t)ns * ncol);
   GDR_CUDA(cudaMemcpyAsync(nr.data(), sh.norms, sizeof(double) * ns * ncol, cudaMemcpyDeviceToHost, ctx->stream));
-  GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+  stream_sync(ctx);
   res.norms = nr;
   return res;
 }
@@ -374,7 +381,7 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
     }
     // step 5: one GMRES(m_p)-Sh cycle on r
     start_cycle<R>(ctx, b, r, ldr);
-    for (int j = 0; j < mp; ++j) arnoldi_step<R>(ctx, A, b, j);
+    for (int j = 0; j < mp; ++j) arnoldi_step<R>(ctx, A, b, j, 0, mp - 1);
     dense_cycle(ctx, d);
     combine<R>(ctx, n, ncol, b.V, b.ldv, b.vcs, mp + 1, d.Cf, ldc, d.ccs, 0, ns, 1, job.X, job.ldx, job.xcs, r, ldr,
                b.st, b.nvec);
@@ -404,7 +411,7 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
   }
   res.gamma.resize((size_t)ncol * ns);
   GDR_CUDA(cudaMemcpyAsync(res.gamma.data(), sh.gamma, sizeof(c128) * ncol * ns, cudaMemcpyDeviceToHost, ctx->stream));
-  GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+  stream_sync(ctx);
   return res;
 }
 
@@ -426,7 +433,7 @@ void true_residuals(gdr_ctx* ctx, const gdr_op* A, int ns, const c128* sigma_dev
   norms2<c128>(ctx, n, np, R, ldr, out, part, nblk, cnt);
   std::vector<double> h(np);
   GDR_CUDA(cudaMemcpyAsync(h.data(), out, sizeof(double) * np, cudaMemcpyDeviceToHost, ctx->stream));
-  GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+  stream_sync(ctx);
   relres.resize(np);
   for (int p = 0; p < np; ++p) relres[p] = std::sqrt(h[p]) / (bnorm[p / ns] > 0 ? bnorm[p / ns] : 1.0);
 }
@@ -454,6 +461,11 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
   auto worst = [&](gdr_status s) {
     if (s != GDR_OK && (status == GDR_OK || status == GDR_ENOCONV)) status = s;
   };
+  // phase wall times, taken where the stream has just been synchronised
+  using clk = std::chrono::steady_clock;
+  auto ms_since = [](clk::time_point t) { return std::chrono::duration<double, std::milli>(clk::now() - t).count(); };
+  const long syncs0 = ctx->syncs;
+  auto tp = clk::now();
   GDR_CUDA(cudaMemsetAsync(X, 0, sizeof(c128) * ldx * ns * nrhs, ctx->stream));
   c128* sig_dev = ctx->get<c128>("pl.sigma", (size_t)ns);
   GDR_CUDA(cudaMemcpyAsync(sig_dev, sigma.data(), sizeof(c128) * ns, cudaMemcpyHostToDevice, ctx->stream));
@@ -467,7 +479,7 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
     GDR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * 4 * nrhs, ctx->stream));
     norms2<c128>(ctx, n, nrhs, B, ldb, out, part, nblk, cnt);
     GDR_CUDA(cudaMemcpyAsync(bnorm.data(), out, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
-    GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+    stream_sync(ctx);
     for (auto& v : bnorm) v = std::sqrt(v);
   }
   // ---- RHS 1: GMRES-DR(m,k)-Sh
@@ -489,6 +501,8 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
   dj.max_mvps = p.max_mvps;
   dj.max_cycles = p.max_cycles;
   DrResult dr = dr_sh<R>(ctx, A, dj, use_graph);
+  rep.t_rhs1_ms = ms_since(tp);
+  tp = clk::now();
   rep.mvps_rhs1 = dr.mvps;
   rep.cycles_rhs1 = dr.cycles;
   if (dr.status == GDR_ENOCONV && p.max_cycles > 0) {
@@ -523,7 +537,7 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
     df->Hk_host.resize((size_t)(kd + 1) * kd);
     GDR_CUDA(cudaMemcpyAsync(df->Hk_host.data(), dr.Hk, sizeof(c128) * (kd + 1) * kd, cudaMemcpyDeviceToHost,
                              ctx->stream));
-    GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+    stream_sync(ctx);
     *defl_out = df;
   }
   // keep the deflation pair in a buffer the later stages do not overwrite
@@ -621,6 +635,8 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
   std::vector<double> relres;
   true_residuals(ctx, A, ns, sig_dev, nrhs, B, ldb, X, ldx, Rres, ld, relres, bnorm);
   rep.resid_cols += np;
+  rep.t_proj_ms = ms_since(tp);
+  tp = clk::now();
   const int max_pass = (p.flags & GDR_FLAG_NO_REFINE) ? -1 : std::max(0, p.refine_max);
   for (int pass = 0; pass <= max_pass; ++pass) {
     std::vector<int> mask(np, 0);
@@ -699,6 +715,8 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
   double mx = 0;
   for (double v : relres) mx = std::max(mx, v);
   rep.max_relres = mx;
+  rep.t_refine_ms = ms_since(tp);
+  rep.host_syncs = ctx->syncs - syncs0;
   if (!(mx <= p.tol)) {
     if (status == GDR_OK) status = GDR_ENOCONV;
   } else if (status == GDR_ENOCONV && p.max_cycles <= 0) {
@@ -734,7 +752,7 @@ gdr_status solve_batch_pipeline(gdr_ctx* ctx, const gdr_op* A, int ns, const std
   std::vector<double> bnorm(np);
   norms2<c128>(ctx, n, np, B, ld, out, part, nblk, cnt, A->nrow);
   GDR_CUDA(cudaMemcpyAsync(bnorm.data(), out, sizeof(double) * np, cudaMemcpyDeviceToHost, ctx->stream));
-  GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+  stream_sync(ctx);
   for (auto& v : bnorm) v = std::sqrt(v);
   // ---- every problem's GMRES-DR(m,k)-Sh, the problems as columns of one batch
   cx<R>* bin = ctx->get<cx<R>>("bt.bin", (size_t)ld * np);
@@ -767,7 +785,7 @@ gdr_status solve_batch_pipeline(gdr_ctx* ctx, const gdr_op* A, int ns, const std
     norms2<c128>(ctx, n, npair, Rres, ld, out, part, nblk, cnt, nvp);
     std::vector<double> h(npair);
     GDR_CUDA(cudaMemcpyAsync(h.data(), out, sizeof(double) * npair, cudaMemcpyDeviceToHost, ctx->stream));
-    GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+    stream_sync(ctx);
     rr.resize(npair);
     for (int q = 0; q < npair; ++q) rr[q] = std::sqrt(h[q]) / (bnorm[q / ns] > 0 ? bnorm[q / ns] : 1.0);
     rep.resid_cols += npair;
