@@ -60,6 +60,9 @@ typedef enum { GDR_LINK_C128 = 0, GDR_LINK_C64 = 1, GDR_LINK_BF16 = 2 } gdr_link
 #define GDR_FLAG_SEQUENTIAL   4u  /* right-hand sides 2.. one at a time (no column batching) */
 #define GDR_FLAG_NO_PROJ      8u  /* later right-hand sides by plain GMRES(m_p)-Sh (no deflation) */
 #define GDR_FLAG_NO_REFINE   16u  /* no refinement / cleanup after the stages (residuals still reported) */
+#define GDR_FLAG_NO_SWEEP    32u  /* short vectors: one launch per Arnoldi phase instead of the persistent
+                                     per-cycle sweep kernel */
+#define GDR_FLAG_FP64_EIG    64u  /* MIXED: harmonic-Ritz eigensolve in FP64 instead of FP32 */
 
 typedef struct gdr_ctx gdr_ctx;
 typedef struct gdr_op gdr_op;

@@ -26,7 +26,8 @@ GDR_OK, GDR_EINVAL, GDR_ENOMEM, GDR_ECUDA, GDR_ENOCONV, GDR_EBREAKDOWN, GDR_ENAN
 GDR_PREC_FP64, GDR_PREC_MIXED = 0, 1
 GDR_LINK_C128, GDR_LINK_C64, GDR_LINK_BF16 = 0, 1, 2
 GDR_MAX_M = 96
-GDR_FLAG_HOST_PTRS, GDR_FLAG_NO_GRAPH, GDR_FLAG_SEQUENTIAL, GDR_FLAG_NO_PROJ, GDR_FLAG_NO_REFINE = 1, 2, 4, 8, 16
+(GDR_FLAG_HOST_PTRS, GDR_FLAG_NO_GRAPH, GDR_FLAG_SEQUENTIAL, GDR_FLAG_NO_PROJ, GDR_FLAG_NO_REFINE, GDR_FLAG_NO_SWEEP,
+ GDR_FLAG_FP64_EIG) = 1, 2, 4, 8, 16, 32, 64
 
 
 class gdr_params(ctypes.Structure):

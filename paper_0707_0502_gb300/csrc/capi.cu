@@ -113,6 +113,7 @@ gdr_status gdr_create(gdr_ctx** out, int device, void* cuda_stream) {
     }
     dense_init(ctx);
     krylov_init(ctx);
+    sweep_init(ctx);
   });
   if (st != GDR_OK) {
     delete ctx;

@@ -92,6 +92,7 @@ struct gdr_ctx {
   size_t l2_bytes = 0;
   size_t dense_smem_limit = 0;    // dynamic shared memory available to the dense kernels
   size_t combine_smem_limit = 0;  // ... and to the basis-combination kernel
+  int sweep_blocks[3] = {0, 0, 0};  // co-resident blocks per SM of the sweep kernel (c64, bf16 links, c128)
   std::string err;
   std::map<std::string, DevBuf> ws;  // named device workspace
   void* pinned = nullptr;            // small pinned host buffer for status words

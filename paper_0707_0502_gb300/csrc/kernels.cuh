@@ -68,6 +68,17 @@ void scale_into(gdr_ctx* ctx, const Batch<R>& b, int j, const cx<R>* w, long wcs
 // v_{j+1} into V.  Launches: matvec, dot, update+dot, update (+ scale at jlast).
 template <typename R>
 void arnoldi_step(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b, int j, int jstart, int jlast);
+// persistent Arnoldi sweep (sweep.cu): steps jstart..jend-1 of every column in one
+// cooperative launch; v_jend is left unnormalised in W2 (scale_into writes it).
+// sweep_fits: short vectors, where the sweep replaces the per-phase launches.
+// sweep_reserve: its workspace, allocated before any stream capture.
+template <typename R>
+bool sweep_fits(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b);
+template <typename R>
+void sweep_reserve(gdr_ctx* ctx, const Batch<R>& b);
+template <typename R>
+void arnoldi_sweep(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b, int jstart, int jend);
+void sweep_init(gdr_ctx* ctx);
 // start a cycle from r_c: V_c[:,0] = r_c/||r_c||, cvec_c = ||r_c|| e_1, H_c = 0, state reset
 template <typename R>
 void start_cycle(gdr_ctx* ctx, const Batch<R>& b, const cx<R>* r, long rcs);

@@ -242,7 +242,7 @@ DrResult dr_sh(gdr_ctx* ctx, const gdr_op* A, const DrJob<R>& job, bool use_grap
   d.scratch = ctx->get<double>("dr.scratch", (size_t)d.scratch_per_col * ncol);
   d.st = b.st;
   d.want_r = (k == 0);  // GMRES(m): restart from the residual vector r = V_{m+1} s
-  d.hr32 = std::is_same<R, float>::value ? 1 : 0;  // complex64 basis: FP32 eigensolve in the restart
+  d.hr32 = (std::is_same<R, float>::value && job.eig32) ? 1 : 0;  // complex64 basis: FP32 eigensolve in the restart
   cx<R>* rres = ctx->get<cx<R>>("dr.r", (size_t)b.ldv * ncol);
   double* bn2 = ctx->get<double>("dr.bn2", (size_t)ncol + 4);
   double* nrm2 = ctx->get<double>("dr.nrm2", (size_t)ncol + 4);
@@ -254,6 +254,8 @@ DrResult dr_sh(gdr_ctx* ctx, const gdr_op* A, const DrJob<R>& job, bool use_grap
   GDR_LAUNCHED(ctx);
   start_cycle<R>(ctx, b, job.rhs, job.ldrhs);
 
+  const bool sweep = job.sweep && sweep_fits<R>(ctx, A, b);
+  if (sweep) sweep_reserve<R>(ctx, b);
   Graph g_first, g_next;
   DrResult res;
   res.k_eff = k;
@@ -266,7 +268,12 @@ DrResult dr_sh(gdr_ctx* ctx, const gdr_op* A, const DrJob<R>& job, bool use_grap
     auto enqueue = [&]() {
       set_run_kernel<<<(ncol + 31) / 32, 32, 0, ctx->stream>>>(b.st, ncol);
       GDR_LAUNCHED(ctx);
-      for (int j = jstart; j < m; ++j) arnoldi_step<R>(ctx, A, b, j, jstart, m - 1);
+      if (sweep) {
+        arnoldi_sweep<R>(ctx, A, b, jstart, m);
+        scale_into<R>(ctx, b, m, b.W2, b.wcs);
+      } else {
+        for (int j = jstart; j < m; ++j) arnoldi_step<R>(ctx, A, b, j, jstart, m - 1);
+      }
       dense_cycle(ctx, d);
       // restart (V_{k+1} <- V_{m+1} P_{k+1}) fused with x_i += V_m d_i
       combine<R>(ctx, n, ncol, b.V, b.ldv, b.vcs, m + 1, d.Cf, ldc, d.ccs, k > 0 ? k + 1 : 0, ns, k > 0 ? 0 : 1,
@@ -362,6 +369,8 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
   d.st = b.st;
   d.want_r = true;
 
+  const bool sweep = job.sweep && sweep_fits<R>(ctx, A, b);
+  if (sweep) sweep_reserve<R>(ctx, b);
   Graph gr;
   ProjResult res;
   res.mvps.assign(ncol, 0);
@@ -381,7 +390,12 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
     }
     // step 5: one GMRES(m_p)-Sh cycle on r
     start_cycle<R>(ctx, b, r, ldr);
-    for (int j = 0; j < mp; ++j) arnoldi_step<R>(ctx, A, b, j, 0, mp - 1);
+    if (sweep) {
+      arnoldi_sweep<R>(ctx, A, b, 0, mp);
+      scale_into<R>(ctx, b, mp, b.W2, b.wcs);
+    } else {
+      for (int j = 0; j < mp; ++j) arnoldi_step<R>(ctx, A, b, j, 0, mp - 1);
+    }
     dense_cycle(ctx, d);
     combine<R>(ctx, n, ncol, b.V, b.ldv, b.vcs, mp + 1, d.Cf, ldc, d.ccs, 0, ns, 1, job.X, job.ldx, job.xcs, r, ldr,
                b.st, b.nvec);
@@ -500,6 +514,8 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
   dj.xcs = (long)ns * ldx;
   dj.max_mvps = p.max_mvps;
   dj.max_cycles = p.max_cycles;
+  dj.sweep = !(p.flags & GDR_FLAG_NO_SWEEP);
+  dj.eig32 = !(p.flags & GDR_FLAG_FP64_EIG);
   DrResult dr = dr_sh<R>(ctx, A, dj, use_graph);
   rep.t_rhs1_ms = ms_since(tp);
   tp = clk::now();
@@ -587,6 +603,7 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
       job.ldx = ld;
       job.xcs = (long)ns * ld;
       job.max_mvps = p.max_mvps;
+      job.sweep = !(p.flags & GDR_FLAG_NO_SWEEP);
       ProjResult pr = proj_batch<R>(ctx, A, job, use_graph && !seq);
       for (int c = 0; c < cn; ++c) {
         if (c0 + c == 0) rep.mvps_extra += pr.mvps[c];
@@ -700,6 +717,7 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
         job.ldx = ldx;
         job.xcs = ldx;
         job.max_mvps = p.max_mvps;
+        job.sweep = !(p.flags & GDR_FLAG_NO_SWEEP);
         ProjResult pr = proj_batch<RR>(ctx, A, job, use_graph);
         for (int c = 0; c < cn; ++c) rep.mvps_refine += pr.mvps[c];
         if (pr.status == GDR_ENAN || pr.status == GDR_ECUDA) worst(pr.status);
@@ -773,6 +791,8 @@ gdr_status solve_batch_pipeline(gdr_ctx* ctx, const gdr_op* A, int ns, const std
   dj.xcs = (long)ns * ld;
   dj.max_mvps = p.max_mvps;
   dj.max_cycles = p.max_cycles;
+  dj.sweep = !(p.flags & GDR_FLAG_NO_SWEEP);
+  dj.eig32 = !(p.flags & GDR_FLAG_FP64_EIG);
   DrResult dr = dr_sh<R>(ctx, A, dj, use_graph);
   for (long v : dr.col_mvps) rep.mvps_rhs1 += v;
   rep.cycles_rhs1 = dr.cycles;
@@ -829,6 +849,7 @@ gdr_status solve_batch_pipeline(gdr_ctx* ctx, const gdr_op* A, int ns, const std
       job.ldx = ld;
       job.xcs = ld;
       job.max_mvps = p.max_mvps;
+      job.sweep = !(p.flags & GDR_FLAG_NO_SWEEP);
       ProjResult pr = proj_batch<RR>(ctx, A, job, use_graph);
       for (long v : pr.mvps) rep.mvps_refine += v;
       if (pr.status == GDR_ENAN) status = GDR_ENAN;

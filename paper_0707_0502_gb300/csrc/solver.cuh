@@ -18,6 +18,8 @@ struct DrJob {
   long ldx = 0, xcs = 0;
   long max_mvps = 100000;
   int max_cycles = 0;
+  bool sweep = true;           // persistent Arnoldi sweep where it fits (sweep_fits)
+  bool eig32 = true;           // complex64 basis: harmonic-Ritz eigensolve in FP32
 };
 
 struct DrResult {
@@ -53,6 +55,7 @@ struct ProjJob {
   c128* X = nullptr;           // X + c*xcs + i*ldx accumulates shift i of column c (FP64)
   long ldx = 0, xcs = 0;
   long max_mvps = 100000;
+  bool sweep = true;           // persistent Arnoldi sweep where it fits (sweep_fits)
 };
 
 struct ProjResult {
