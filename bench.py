@@ -45,6 +45,26 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x, world):
+    """Largest value of x over the ranks of the default process group (x itself
+    when world == 1): the job's time is its slowest replica's.  The tensor lives
+    where the backend needs it (CUDA for NCCL, host for gloo)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_replica, seconds_max):
+    """Whole-job rate: every rank solves its own replica (weak scaling), so the job
+    processes world * units in the slowest rank's time."""
+    return world * units_per_replica / seconds_max
+
+
 def workload(cid):
     p = W.config(cid)
     return p, {
@@ -230,13 +250,10 @@ def main():
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_s = sum(ms) / 1e3
-    t_max = total_s
+    t_max = max_over_ranks(total_s, world)
     if world > 1:
-        t = torch.tensor([total_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
         dist.barrier()
-    value = world * sols * args.steps / t_max
+    value = job_throughput(world, sols * args.steps, t_max)
     rep = reps[-1]
     launches = rep["kernel_launches"]
 
@@ -260,7 +277,7 @@ def main():
         assert st == g.GDR_OK
         if i >= min(args.warmup, 3):
             e2e_ms.append((t1 - t0) * 1e3)
-    e2e_value = world * sols * len(e2e_ms) / (sum(e2e_ms) / 1e3)
+    e2e_value = job_throughput(world, sols * len(e2e_ms), max_over_ranks(sum(e2e_ms) / 1e3, world))
 
     # ---- dominant kernel roofline (per-kernel CUDA events on the library stream)
     roof, ktable = kernel_roofline(g, ctx, op, p, mixed, stream, B, X)

@@ -188,6 +188,15 @@ void gdr_defl_destroy(gdr_defl *defl);
  * buf (len bytes, NUL-terminated), "bytes" being the algorithmic bytes the launches
  * move (0 for the dense FP64 kernels); it synchronises the stream. */
 gdr_status gdr_profile(gdr_ctx *ctx, int enable);
+
+/* Failure-detection self-test of the grid barrier used by the persistent
+ * Arnoldi sweep (no counterpart in the paper).  Launches `rounds` (>= 1) grid
+ * barriers over a cooperative grid.  phantom = 0: every barrier completes,
+ * GDR_OK.  phantom = 1: each barrier waits for one block more than the grid
+ * has, so the first one ends only by its spin bound (about one second); the
+ * kernel then returns normally and the call reports GDR_ETIMEOUT, leaving the
+ * context usable.  Synchronises the context stream. */
+gdr_status gdr_barrier_selftest(gdr_ctx *ctx, int rounds, int phantom);
 gdr_status gdr_profile_report(gdr_ctx *ctx, char *buf, long len);
 
 /* --------------------------------------------------------- step-level calls

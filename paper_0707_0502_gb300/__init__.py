@@ -88,6 +88,7 @@ _SIGS = {
     "gdr_dense_gmres_sh": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, _P]),
     "gdr_dense_gmres_sh_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P,
                                                   _P]),
+    "gdr_barrier_selftest": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "gdr_dense_restart": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P]),
     "gdr_basis_update": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_long, ctypes.c_int, _P, _P, ctypes.c_int,
                                         ctypes.c_int, _P]),
@@ -315,6 +316,12 @@ def gdr_dense_restart(ctx, prec, m, k, sigma1, Hbar, s, theta, P, Hk, ck):
     sg = _c128_host([sigma1])
     _check(lib().gdr_dense_restart(ctx, int(prec), int(m), int(k), sg.ctypes.data, _ptr(Hbar), _ptr(s), _ptr(theta),
                                    _ptr(P), _ptr(Hk), _ptr(ck)), ctx)
+
+
+def gdr_barrier_selftest(ctx, rounds, phantom):
+    """Status of the grid-barrier self-test (GDR_OK, or GDR_ETIMEOUT with phantom);
+    does not raise for GDR_ETIMEOUT."""
+    return lib().gdr_barrier_selftest(ctx, int(rounds), int(phantom))
 
 
 def gdr_basis_update(ctx, prec, n, nv, V, C, nout, nx, X):

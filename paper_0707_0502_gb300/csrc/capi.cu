@@ -589,6 +589,17 @@ gdr_status gdr_dense_restart(gdr_ctx* ctx, gdr_prec prec, int m, int k, const do
   });
 }
 
+gdr_status gdr_barrier_selftest(gdr_ctx* ctx, int rounds, int phantom) {
+  if (!ctx) return GDR_EINVAL;
+  gdr_status r = GDR_OK;
+  const gdr_status g = guarded(ctx, [&] {
+    GDR_REQUIRE(rounds >= 1 && rounds <= 1000000, "rounds must be in [1, 1e6]");
+    r = barrier_selftest(ctx, rounds, phantom ? 1 : 0);
+    if (r != GDR_OK) ctx->err = "grid barrier gave up (spin bound reached)";
+  });
+  return g != GDR_OK ? g : r;
+}
+
 gdr_status gdr_basis_update(gdr_ctx* ctx, gdr_prec prec, long n, int nv, void* V, const double* C, int nout, int nx,
                             double* X) {
   if (!ctx) return GDR_EINVAL;

@@ -79,6 +79,8 @@ void sweep_reserve(gdr_ctx* ctx, const Batch<R>& b);
 template <typename R>
 void arnoldi_sweep(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b, int jstart, int jend);
 void sweep_init(gdr_ctx* ctx);
+// grid-barrier self-test (gdr_barrier_selftest)
+gdr_status barrier_selftest(gdr_ctx* ctx, int rounds, int phantom);
 // start a cycle from r_c: V_c[:,0] = r_c/||r_c||, cvec_c = ||r_c|| e_1, H_c = 0, state reset
 template <typename R>
 void start_cycle(gdr_ctx* ctx, const Batch<R>& b, const cx<R>* r, long rcs);

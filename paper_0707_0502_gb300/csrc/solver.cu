@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <limits>
 #include <functional>
 #include <type_traits>
 
@@ -496,6 +497,13 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
     stream_sync(ctx);
     for (auto& v : bnorm) v = std::sqrt(v);
   }
+  for (double v : bnorm) {
+    if (!std::isfinite(v)) {  // NaN or Inf in a right-hand side: X stays zero
+      rep.max_relres = v;
+      rep.host_syncs = ctx->syncs - syncs0;
+      return GDR_ENAN;
+    }
+  }
   // ---- RHS 1: GMRES-DR(m,k)-Sh
   cx<R>* bin = ctx->get<cx<R>>("pl.bin", (size_t)ld);
   to_inner<R>(ctx, n, 1, B, ldb, bin, ld);
@@ -772,6 +780,19 @@ gdr_status solve_batch_pipeline(gdr_ctx* ctx, const gdr_op* A, int ns, const std
   GDR_CUDA(cudaMemcpyAsync(bnorm.data(), out, sizeof(double) * np, cudaMemcpyDeviceToHost, ctx->stream));
   stream_sync(ctx);
   for (auto& v : bnorm) v = std::sqrt(v);
+  {
+    bool bad = false;
+    for (int q = 0; q < np; ++q) {
+      if (!std::isfinite(bnorm[q])) {  // NaN or Inf in problem q's right-hand side
+        bad = true;
+        if (prob_status) prob_status[q] = GDR_ENAN;
+      }
+    }
+    if (bad) {
+      rep.max_relres = std::numeric_limits<double>::quiet_NaN();
+      return GDR_ENAN;
+    }
+  }
   // ---- every problem's GMRES-DR(m,k)-Sh, the problems as columns of one batch
   cx<R>* bin = ctx->get<cx<R>>("bt.bin", (size_t)ld * np);
   to_inner<R>(ctx, ld, np, B, ld, bin, ld);

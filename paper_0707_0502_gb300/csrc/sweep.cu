@@ -32,7 +32,7 @@ namespace {
 
 constexpr int ST = 256;                    // threads per block
 constexpr int SDU = 8;                     // 16-byte units per lane of a dot tile (tile = ST units)
-constexpr long BAR_SPINS = 1L << 24;       // barrier give-up count (each poll an L2 round trip)
+constexpr long BAR_SPINS = 1L << 20;       // barrier give-up count: ~1 s (a poll is an L2 round trip + 20 ns)
 
 struct SweepBar {
   unsigned count;
@@ -105,14 +105,14 @@ DEV void red_release_gpu(unsigned* p, unsigned v) {
 // arrives with a release-add (ordering the block's writes, made CTA-visible by
 // __syncthreads, before the arrival) and polls with acquire loads.  False if it
 // gave up (another block's failure or the spin bound).
-DEV bool grid_sync(SweepBar* gb, unsigned& epoch) {
+DEV bool grid_sync(SweepBar* gb, unsigned& epoch, unsigned arrivals = 0) {
   __shared__ int fail;
   __syncthreads();
   ++epoch;
   if (threadIdx.x == 0) {
     fail = 0;
     red_release_gpu(&gb->count, 1u);
-    const unsigned target = epoch * gridDim.x;
+    const unsigned target = epoch * (arrivals ? arrivals : gridDim.x);
     long it = 0;
     while (ld_acquire_gpu(&gb->count) < target) {
       if ((++it & 1023) == 0 && (*(volatile int*)&gb->err || it > BAR_SPINS)) {
@@ -569,6 +569,16 @@ __global__ void __launch_bounds__(ST, 2) arnoldi_sweep_kernel(SweepArgs<R> a) {
     for (int c = 0; c < a.b.ncol; ++c) atomicCAS(&a.b.st[c].err, 0, (int)GDR_ETIMEOUT);
 }
 
+// Barrier self-test: `rounds` grid barriers; with `phantom` one more arrival is
+// expected than there are blocks, so the first barrier can only end by its
+// spin bound.  Block 0 writes the outcome.
+__global__ void barrier_probe_kernel(SweepBar* gb, int rounds, int phantom, int* out) {
+  unsigned epoch = 0;
+  bool ok = true;
+  for (int r = 0; r < rounds && ok; ++r) ok = grid_sync(gb, epoch, gridDim.x + (phantom ? 1u : 0u));
+  if (blockIdx.x == 0 && threadIdx.x == 0) *out = ok ? (int)GDR_OK : (int)GDR_ETIMEOUT;
+}
+
 template <typename R>
 size_t sweep_smem(int kind) {
   constexpr int K = U<R>::K, TU = SDU * 32;
@@ -708,6 +718,32 @@ void arnoldi_sweep(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b, int jstart,
     launch_sweep<R, cx<R>>(ctx, a, grid, smem);
   }
   GDR_LAUNCHED(ctx);
+}
+
+gdr_status barrier_selftest(gdr_ctx* ctx, int rounds, int phantom) {
+  SweepBar* gb = reinterpret_cast<SweepBar*>(ctx->get<int>("probe.bar", 16));
+  int* out = ctx->get<int>("probe.out", 4);
+  GDR_CUDA(cudaMemsetAsync(gb, 0, sizeof(SweepBar), ctx->stream));
+  GDR_CUDA(cudaMemsetAsync(out, 0xff, sizeof(int), ctx->stream));
+  int nb = 0;
+  GDR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, barrier_probe_kernel, ST, 0));
+  GDR_REQUIRE(nb >= 1, "barrier_selftest: kernel does not fit");
+  void* args[] = {&gb, &rounds, &phantom, &out};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(ctx->num_sms * std::min(nb, 2)));
+  cfg.blockDim = dim3(ST);
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  GDR_CUDA(cudaLaunchKernelExC(&cfg, reinterpret_cast<const void*>(barrier_probe_kernel), args));
+  GDR_LAUNCHED(ctx);
+  int h = -1;
+  GDR_CUDA(cudaMemcpyAsync(&h, out, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+  return (gdr_status)h;
 }
 
 template bool sweep_fits<float>(gdr_ctx*, const gdr_op*, const Batch<float>&);
