@@ -37,11 +37,12 @@ UNIT = "solutions/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=CONFIG_ID)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-scale", action="store_true", help="skip the large-lattice kernel measurements")
     return ap.parse_args()
 
 
@@ -281,6 +282,7 @@ def main():
 
     # ---- dominant kernel roofline (per-kernel CUDA events on the library stream)
     roof, ktable = kernel_roofline(g, ctx, op, p, mixed, stream, B, X)
+    scale = kernels_at_scale(g, ctx, stream) if not args.no_scale else None
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -298,6 +300,8 @@ def main():
         "roofline": roof,
         "kernels": ktable,
     }
+    if scale is not None:
+        line["kernels_at_scale"] = scale
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p)
     if rank == 0:
@@ -372,6 +376,60 @@ def kernel_roofline(g, ctx, op, p, params, stream, B, X):
     roof["us_per_launch"] = per_launch_s * 1e6
     roof["share_of_solve"] = v["ms"] / total
     return roof, table
+
+
+def kernels_at_scale(g, ctx, stream):
+    """The HBM-bound kernels on the two large lattices of the workload family
+    (Wilson 16^4, c64 links; 24^3x32, bf16 links): one profiled Arnoldi step at
+    the last column of the basis (j = m - 1, m = 60 / 80; single column, so the
+    algorithmic byte model is exact) and the multi-column matvec of the
+    refinement / Proj stages (8 / 12 columns).  Inputs far larger than L2.  Per
+    kernel: microseconds per launch, GB/s and fraction of measured HBM peak."""
+    import torch
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    out = {}
+    for cid, dims, eps, store, m, ncol in [(3, (16, 16, 16, 16), 0.4, g.GDR_LINK_C64, 60, 8),
+                                           (4, (24, 24, 24, 32), 0.5, g.GDR_LINK_BF16, 80, 12)]:
+        links = W.su3_links(dims, eps, W.rng(cid, 0))
+        with torch.cuda.stream(stream):
+            op = g.gdr_op_wilson(ctx, dims, torch.as_tensor(links).cuda(), 0.0, store)
+            n = 12 * int(np.prod(dims))
+            gen = torch.Generator(device="cuda").manual_seed(cid)
+            V = torch.randn((m + 1, n), dtype=torch.complex64, device="cuda", generator=gen)
+            V /= V.norm(dim=1, keepdim=True)
+            hcol = torch.zeros(m + 1, dtype=torch.complex128, device="cuda")
+            X = torch.randn((ncol, n), dtype=torch.complex64, device="cuda", generator=gen)
+            Y = torch.empty_like(X)
+        del links
+        for _ in range(2):  # warm-up
+            g.gdr_arnoldi_step(ctx, op, g.GDR_PREC_MIXED, V, m - 1, hcol)
+            g.gdr_op_apply(ctx, op, g.GDR_PREC_MIXED, np.zeros(ncol), X, Y)
+        g.gdr_profile(ctx, True)
+        for _ in range(5):
+            g.gdr_arnoldi_step(ctx, op, g.GDR_PREC_MIXED, V, m - 1, hcol)
+            g.gdr_op_apply(ctx, op, g.GDR_PREC_MIXED, np.zeros(ncol), X, Y)
+        prof = g.gdr_profile_report(ctx)
+        g.gdr_profile(ctx, False)
+        key = "x".join(map(str, dims))
+        tab = {}
+        for name, v in prof.items():
+            if v["bytes"] <= 0:
+                continue
+            us = v["ms"] / v["launches"] * 1e3
+            gbs = v["bytes"] / (v["ms"] / 1e3) / 1e9
+            tab[name] = {"launches": v["launches"], "us_per_launch": round(us, 1), "GBs": round(gbs, 1),
+                         "frac_of_measured_hbm": round(gbs / hbm, 3)}
+        out[key] = {"n": n, "arnoldi_step_j": m - 1, "matvec_columns": ncol,
+                    "links": "bf16" if store == g.GDR_LINK_BF16 else "c64", "kernels": tab}
+        g.gdr_op_destroy(op)
+        del V, X, Y
+        torch.cuda.empty_cache()
+    return out
 
 
 if __name__ == "__main__":

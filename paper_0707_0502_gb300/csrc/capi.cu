@@ -500,7 +500,8 @@ gdr_status gdr_arnoldi_step(gdr_ctx* ctx, const gdr_op* A, gdr_prec prec, void* 
       GDR_CUDA(cudaMemsetAsync(b.cnt, 0, 4 * sizeof(unsigned), ctx->stream));
       GDR_CUDA(cudaMemcpyAsync(b.st, &s, sizeof(s), cudaMemcpyHostToDevice, ctx->stream));
       GDR_CUDA(cudaStreamSynchronize(ctx->stream));
-      arnoldi_step<R>(ctx, A, b, j, j, j);
+      cx<R>* wl = nullptr;
+      arnoldi_step<R>(ctx, A, b, j, j, j, wl);
       GDR_CUDA(cudaMemcpyAsync(hcol, b.H + (long)j * (j + 2), sizeof(c128) * (j + 2), cudaMemcpyDeviceToDevice,
                                ctx->stream));
     };

@@ -63,11 +63,13 @@ void gs_update(gdr_ctx* ctx, const Batch<R>& b, int nv, cx<R>* w, long wcs, cons
 template <typename R>
 void scale_into(gdr_ctx* ctx, const Batch<R>& b, int j, const cx<R>* w, long wcs);
 // one CGS2 Arnoldi step on every column (Hbar column j, h_{j+1,j}).  Steps after
-// the first of a sweep (j > jstart) take v_j from W2 scaled by 1/h_{j,j-1} and
-// store it into V in their first dot pass; the last step (j == jlast) writes
-// v_{j+1} into V.  Launches: matvec, dot, update+dot, update (+ scale at jlast).
+// the first of a sweep (j > jstart) take v_j from wlast (the previous step's
+// orthogonalised vector, W or W2) scaled by 1/h_{j,j-1} and store it into V in
+// their first dot pass; wlast is updated to this step's vector; the last step
+// (j == jlast) writes v_{j+1} into V.  Launches: matvec, dot, update+dot, update
+// while the basis fits in L2, else matvec, dot, update, dot, update (+ scale at jlast).
 template <typename R>
-void arnoldi_step(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b, int j, int jstart, int jlast);
+void arnoldi_step(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b, int j, int jstart, int jlast, cx<R>*& wlast);
 // persistent Arnoldi sweep (sweep.cu): steps jstart..jend-1 of every column in one
 // cooperative launch; v_jend is left unnormalised in W2 (scale_into writes it).
 // sweep_fits: short vectors, where the sweep replaces the per-phase launches.

@@ -602,19 +602,33 @@ void scale_into(gdr_ctx* ctx, const Batch<R>& b, int j, const cx<R>* w, long wcs
 }
 
 template <typename R>
-void arnoldi_step(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b, int j, int jstart, int jlast) {
+void arnoldi_step(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b, int j, int jstart, int jlast, cx<R>*& wlast) {
   const int is = (int)(sizeof(ColState) / sizeof(int)), ds = (int)(sizeof(ColState) / sizeof(double));
-  const bool lazy = j > jstart;  // v_j = W2 / h_{j,j-1}, not yet in V
+  const bool lazy = j > jstart;  // v_j = wlast / h_{j,j-1}, not yet in V
+  cx<R>* P = lazy ? wlast : nullptr;
+  cx<R>* Wa = (P == b.W) ? b.W2 : b.W;  // receives A v_j
+  cx<R>* Wb = (Wa == b.W) ? b.W2 : b.W;  // the other buffer (P itself on a lazy step, free after the first dot)
   if (lazy)
-    op_apply_skip(ctx, A, b.ncol, nullptr, b.W2, b.wcs, b.W, b.wcs, nullptr, 0, &b.st[0].run, is, b.cpp,
+    op_apply_skip(ctx, A, b.ncol, nullptr, P, b.wcs, Wa, b.wcs, nullptr, 0, &b.st[0].run, is, b.cpp,
                   &b.st[0].inv_norm, ds);
   else
-    op_apply_skip(ctx, A, b.ncol, nullptr, b.V + (long)j * b.ldv, b.vcs, b.W, b.wcs, nullptr, 0, &b.st[0].run, is,
+    op_apply_skip(ctx, A, b.ncol, nullptr, b.V + (long)j * b.ldv, b.vcs, Wa, b.wcs, nullptr, 0, &b.st[0].run, is,
                   b.cpp);
-  gs_dot<R>(ctx, b, j + 1, b.W, b.wcs, b.h1, true, lazy ? b.W2 : nullptr);
-  gs_update_dot<R>(ctx, b, j + 1, b.W, b.W2, b.wcs, b.h1, b.h2);
-  gs_update<R>(ctx, b, j + 1, b.W2, b.wcs, b.h2, true);
-  if (j == jlast) scale_into<R>(ctx, b, j + 1, b.W2, b.wcs);
+  gs_dot<R>(ctx, b, j + 1, Wa, b.wcs, b.h1, true, P);
+  // fused update + second projection while the basis stays in L2 (its tiles are read
+  // twice); separate passes otherwise (each reads V once from HBM)
+  const bool fuse = (double)(j + 1) * b.n * sizeof(cx<R>) * b.ncol <= 0.5 * (double)ctx->l2_bytes;
+  if (fuse) {
+    gs_update_dot<R>(ctx, b, j + 1, Wa, Wb, b.wcs, b.h1, b.h2);
+    gs_update<R>(ctx, b, j + 1, Wb, b.wcs, b.h2, true);
+    wlast = Wb;
+  } else {
+    gs_update<R>(ctx, b, j + 1, Wa, b.wcs, b.h1, false);
+    gs_dot<R>(ctx, b, j + 1, Wa, b.wcs, b.h2, false);
+    gs_update<R>(ctx, b, j + 1, Wa, b.wcs, b.h2, true);
+    wlast = Wa;
+  }
+  if (j == jlast) scale_into<R>(ctx, b, j + 1, wlast, b.wcs);
 }
 
 template <typename R>
@@ -697,8 +711,8 @@ template void gs_update<float>(gdr_ctx*, const Batch<float>&, int, c64*, long, c
 template void gs_update<double>(gdr_ctx*, const Batch<double>&, int, c128*, long, const c128*, bool);
 template void scale_into<float>(gdr_ctx*, const Batch<float>&, int, const c64*, long);
 template void scale_into<double>(gdr_ctx*, const Batch<double>&, int, const c128*, long);
-template void arnoldi_step<float>(gdr_ctx*, const gdr_op*, const Batch<float>&, int, int, int);
-template void arnoldi_step<double>(gdr_ctx*, const gdr_op*, const Batch<double>&, int, int, int);
+template void arnoldi_step<float>(gdr_ctx*, const gdr_op*, const Batch<float>&, int, int, int, c64*&);
+template void arnoldi_step<double>(gdr_ctx*, const gdr_op*, const Batch<double>&, int, int, int, c128*&);
 template void start_cycle<float>(gdr_ctx*, const Batch<float>&, const c64*, long);
 template void start_cycle<double>(gdr_ctx*, const Batch<double>&, const c128*, long);
 template void norms2<c64>(gdr_ctx*, long, int, const c64*, long, double*, c128*, int, unsigned*, const int*);

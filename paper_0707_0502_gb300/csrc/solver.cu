@@ -273,7 +273,8 @@ DrResult dr_sh(gdr_ctx* ctx, const gdr_op* A, const DrJob<R>& job, bool use_grap
         arnoldi_sweep<R>(ctx, A, b, jstart, m);
         scale_into<R>(ctx, b, m, b.W2, b.wcs);
       } else {
-        for (int j = jstart; j < m; ++j) arnoldi_step<R>(ctx, A, b, j, jstart, m - 1);
+        cx<R>* wl = nullptr;
+        for (int j = jstart; j < m; ++j) arnoldi_step<R>(ctx, A, b, j, jstart, m - 1, wl);
       }
       dense_cycle(ctx, d);
       // restart (V_{k+1} <- V_{m+1} P_{k+1}) fused with x_i += V_m d_i
@@ -395,7 +396,8 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
       arnoldi_sweep<R>(ctx, A, b, 0, mp);
       scale_into<R>(ctx, b, mp, b.W2, b.wcs);
     } else {
-      for (int j = 0; j < mp; ++j) arnoldi_step<R>(ctx, A, b, j, 0, mp - 1);
+      cx<R>* wl = nullptr;
+      for (int j = 0; j < mp; ++j) arnoldi_step<R>(ctx, A, b, j, 0, mp - 1, wl);
     }
     dense_cycle(ctx, d);
     combine<R>(ctx, n, ncol, b.V, b.ldv, b.vcs, mp + 1, d.Cf, ldc, d.ccs, 0, ns, 1, job.X, job.ldx, job.xcs, r, ldr,

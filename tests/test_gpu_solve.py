@@ -43,15 +43,18 @@ def relres(matvec, b, s, x):
     return np.linalg.norm(b - (matvec(x) - s * x)) / np.linalg.norm(b)
 
 
-def test_config1_matched_cycles_fp64(ctx):
-    """All-FP64 GPU path = oracle to 1e-10 after the same number of cycles."""
+@pytest.mark.parametrize("sweep", [True, False])
+def test_config1_matched_cycles_fp64(ctx, sweep):
+    """All-FP64 GPU path = oracle to 1e-10 after the same number of cycles, with the
+    persistent Arnoldi sweep and with one launch per Arnoldi phase."""
     p = W.config(1)
     A = CSROperator(*p.op[1:])
     op = g.make_operator(ctx, p)
+    extra = 0 if sweep else g.GDR_FLAG_NO_SWEEP
     for cycles in (1, 2, 5):
         ref = gmres_dr_sh(A.matvec, p.B[:, 0], p.sigma, p.m, p.k, 1e-30, max_cycles=cycles)
         st, rep, X = solve(ctx, op, p.sigma, p.B, g.GDR_PREC_FP64, p.m, p.k, tol=1e-30, max_cycles=cycles,
-                           flags=g.GDR_FLAG_NO_PROJ | g.GDR_FLAG_NO_REFINE)
+                           flags=g.GDR_FLAG_NO_PROJ | g.GDR_FLAG_NO_REFINE | extra)
         assert rep["cycles_rhs1"] == cycles and rep["mvps_rhs1"] == ref["mvps"]
         for i in range(len(p.sigma)):
             e = np.linalg.norm(X[0, i] - ref["x"][:, i]) / np.linalg.norm(ref["x"][:, i])
@@ -115,4 +118,24 @@ def test_wilson_multishift_multirhs(ctx, wil, prec, nrhs):
             assert relres(A.matvec, B[:, j], s, X[j, i]) <= 1e-8, (i, j)
             xr = ref["X"][:, i, j]
             assert np.linalg.norm(X[j, i] - xr) <= 1e-6 * np.linalg.norm(xr), (i, j)
+    g.gdr_op_destroy(op)
+
+
+@pytest.mark.parametrize("prec", [g.GDR_PREC_FP64, g.GDR_PREC_MIXED])
+def test_wilson16_long_vectors(ctx, prec):
+    """16^4 lattice (786,432 unknowns): long vectors, so the Arnoldi step runs its
+    separate update / dot passes once the basis outgrows L2.  2 shifts, GMRES-DR(30,10);
+    true residuals by the oracle's operator."""
+    from oracle import WilsonOperator
+    dims = (16, 16, 16, 16)
+    links = W.su3_links(dims, 0.4, W.rng(3, 0))
+    A = WilsonOperator(dims, links, diag_a=0.0)
+    kc = W.load_kappa_c()["cfg3:16x16x16x16:eps0.4"]
+    sigma = np.array([-1.0 / (0.9 * kc), -1.0 / 0.12], complex)
+    b = W.gaussian_complex(W.rng(3, 7), A.n, 1)[:, 0]
+    op = g.gdr_op_wilson(ctx, dims, torch.as_tensor(links).cuda(), 0.0, g.GDR_LINK_C64)
+    st, rep, X = solve(ctx, op, sigma, b, prec, 30, 10)
+    assert st == g.GDR_OK, rep
+    for i, s in enumerate(sigma):
+        assert relres(A.matvec, b, s, X[0, i]) <= 1e-8, (i, rep)
     g.gdr_op_destroy(op)
