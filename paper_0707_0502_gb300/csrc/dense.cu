@@ -97,6 +97,41 @@ template <typename R> DEV R block_sum(R v, ShT<R>& sh) {
   return t;
 }
 
+// 1/sqrt(a) for a > 0.  FP64: single-precision estimate, then two Newton steps
+// y <- y (3 - a y^2) / 2 (quadratic convergence: ~1e-7 -> 1e-14 -> 1e-16); a
+// normal-range float must hold a, otherwise the FP64 expression is used.
+// FP32: the hardware estimate and one Newton step.
+DEV double rsqrt_nr(double a) {
+  if (!(a > 1e-36 && a < 1e36)) return 1.0 / sqrt(a);
+  double y = (double)rsqrtf((float)a);
+  y = y * (1.5 - 0.5 * a * y * y);
+  y = y * (1.5 - 0.5 * a * y * y);
+  return y;
+}
+DEV float rsqrt_nr(float a) {
+  const float y = rsqrtf(a);
+  return y * (1.5f - 0.5f * a * y * y);
+}
+
+// Givens rotation U = [[cs, sn], [-conj(sn), cs]] with U [x; y] = [r; 0]; rot = {cs, Re sn, Im sn}
+template <typename R> DEV void givens(cx<R> x, cx<R> y, R* rot) {
+  const R ax2 = norm2(x), ay2 = norm2(y);
+  if (ay2 == R(0)) {
+    rot[0] = 1; rot[1] = 0; rot[2] = 0;
+  } else if (ax2 == R(0)) {
+    const R inv = rsqrt_nr(ay2);
+    rot[0] = 0; rot[1] = y.x * inv; rot[2] = -y.y * inv;
+  } else {
+    const R inv_r = rsqrt_nr(ax2 + ay2);
+    const R inv_ax = rsqrt_nr(ax2);
+    rot[0] = ax2 * inv_ax * inv_r;  // |x| / r
+    // sn = (x / |x|) conj(y) / r
+    const R f = inv_ax * inv_r;
+    rot[1] = (x.x * y.x + x.y * y.y) * f;
+    rot[2] = (x.y * y.x - x.x * y.y) * f;
+  }
+}
+
 // Householder QR of the first `cols` columns of A (rows x ntot, column-major,
 // lda), reflectors applied to all ntot columns.  R in the upper triangle, v
 // below the diagonal, tau[j].  Column j of the factored part is known to be
@@ -177,26 +212,63 @@ DEV void apply_q_serial(const cx<R>* A, int lda, int rows, int cols, const cx<R>
   }
 }
 
-// Solve R y = y (R: upper nsz x nsz of A) in place.  Returns false on a zero pivot.
-DEV bool cta_backsolve(const c128* A, int lda, int nsz, c128* y, Sh& sh) {
-  bool ok = true;
-  for (int j = nsz - 1; j >= 0; --j) {
-    if (threadIdx.x == 0) {
-      const c128 p = A[j + (long)j * lda];
-      if (p.x == 0.0 && p.y == 0.0) {
-        sh.ibc[0] = 1;
-        y[j] = {0, 0};
-      } else {
-        y[j] = cdiv(y[j], p);
-      }
+// Givens QR of the columns j0..cols-1 of an upper Hessenberg block (column j is
+// zero below row j+1), applied to all ntot columns, by warp 0 alone: every lane
+// forms the rotation of column j from its two entries, then rotates its own
+// columns; no block barriers, one FP64 dependency chain per rotation.  R is left
+// in the upper triangle (the eliminated entries hold rounding residue only).
+DEV void warp_givens_qr(c128* A, int lda, int rows, int j0, int cols, int ntot) {
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  for (int j = j0; j < cols && j + 1 < rows; ++j) {
+    double rot[3];
+    givens(A[j + (long)j * lda], A[j + 1 + (long)j * lda], rot);
+    const double cs = rot[0];
+    const c128 sn = {rot[1], rot[2]};
+    for (int cc = j + lane; cc < ntot; cc += 32) {
+      const c128 a = A[j + (long)cc * lda], b = A[j + 1 + (long)cc * lda];
+      A[j + (long)cc * lda] = cs * a + sn * b;
+      A[j + 1 + (long)cc * lda] = cs * b - conj(sn) * a;
     }
-    __syncthreads();
-    const c128 xj = y[j];
-    for (int i = threadIdx.x; i < j; i += DT) y[i] -= A[i + (long)j * lda] * xj;
-    __syncthreads();
+    __syncwarp();
   }
-  if (sh.ibc[0]) ok = false;
-  return ok;
+}
+
+// QR of the GMRES recurrence matrix: Householder reflectors for its dense leading
+// block (columns < kfull - 1), Givens rotations for the Hessenberg columns after it.
+DEV void hess_qr(c128* A, int lda, int rows, int cols, int ntot, c128* tau, Sh& sh, int kfull) {
+  const int jd = max(0, min(cols, kfull - 1));
+  cta_qr(A, lda, rows, jd, ntot, tau, sh, kfull);
+  warp_givens_qr(A, lda, rows, jd, cols, ntot);
+  __syncthreads();
+}
+
+// Solve R y = y in place (R: upper nsz x nsz of A): reciprocals of the diagonal by
+// all threads, then warp 0 substitutes (warp barriers only).  False on a zero pivot.
+DEV bool fast_backsolve(const c128* A, int lda, int nsz, c128* y, c128* rinv, Sh& sh) {
+  if (threadIdx.x == 0) sh.ibc[0] = 0;
+  __syncthreads();
+  for (int j = threadIdx.x; j < nsz; j += DT) {
+    const c128 p = A[j + (long)j * lda];
+    if (p.x == 0.0 && p.y == 0.0) {
+      sh.ibc[0] = 1;
+      rinv[j] = {0, 0};
+    } else {
+      rinv[j] = cdiv(c128{1, 0}, p);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    for (int j = nsz - 1; j >= 0; --j) {
+      const c128 xj = y[j] * rinv[j];
+      __syncwarp();
+      if (threadIdx.x == 0) y[j] = xj;
+      for (int i = threadIdx.x; i < j; i += 32) y[i] -= A[i + (long)j * lda] * xj;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  return sh.ibc[0] == 0;
 }
 
 // load (Hbar - sig Ibar)[0:rows, 0:cols] into A (lda), rounded to the precision of A
@@ -233,12 +305,13 @@ DEV void base_ls(const DenseCycle& d, int c, c128* A, Sh& sh) {
   for (int i = threadIdx.x; i < rows; i += DT) A[i + (long)me * lda] = cv[i];
   c128* tau = A + (long)lda * (me + 1);
   c128* y = tau + (me + 1);
+  c128* rinv = y + (me + 1);
   if (threadIdx.x == 0) sh.ibc[0] = 0;
   __syncthreads();
-  cta_qr(A, lda, rows, me, me + 1, tau, sh, d.kfull);
+  hess_qr(A, lda, rows, me, me + 1, tau, sh, d.kfull);
   for (int i = threadIdx.x; i < me; i += DT) y[i] = A[i + (long)me * lda];
   __syncthreads();
-  if (!cta_backsolve(A, lda, me, y, sh)) set_err(st, GDR_EBREAKDOWN);
+  if (!fast_backsolve(A, lda, me, y, rinv, sh)) set_err(st, GDR_EBREAKDOWN);
   // d_1 -> Cf, s = c - Hhat d_1 from the original Hbar
   c128* Cf = d.Cf + (long)c * d.ccs;
   const int xc = (k > 0 ? k + 1 : 0);
@@ -293,9 +366,10 @@ DEV void shift_solve(const DenseCycle& d, int c, int i, c128* A, Sh& sh) {
   }
   c128* tau = A + (long)lda * (me + 2);
   c128* y = tau + (me + 1);
+  c128* rinv = y + (me + 1);
   if (threadIdx.x == 0) sh.ibc[0] = 0;
   __syncthreads();
-  cta_qr(A, lda, rows, me, me + 2, tau, sh, d.kfull);
+  hess_qr(A, lda, rows, me, me + 2, tau, sh, d.kfull);
   c128 bnew = {0, 0};
   if (!broke) {
     const c128 qc = A[me + (long)me * lda], qs = A[me + (long)(me + 1) * lda];
@@ -308,7 +382,7 @@ DEV void shift_solve(const DenseCycle& d, int c, int i, c128* A, Sh& sh) {
   for (int r = threadIdx.x; r < me; r += DT)
     y[r] = beta * A[r + (long)me * lda] - bnew * A[r + (long)(me + 1) * lda];
   __syncthreads();
-  if (!cta_backsolve(A, lda, me, y, sh)) set_err(st, GDR_EBREAKDOWN);
+  if (!fast_backsolve(A, lda, me, y, rinv, sh)) set_err(st, GDR_EBREAKDOWN);
   for (int r = threadIdx.x; r <= m; r += DT) Cf[r + (long)col * d.ldc] = (r < me) ? y[r] : c128{0, 0};
   if (threadIdx.x == 0) {
     d.beta[(long)c * d.ns + i] = bnew;
@@ -317,41 +391,6 @@ DEV void shift_solve(const DenseCycle& d, int c, int i, c128* A, Sh& sh) {
 }
 
 // --------------------------------------------------- harmonic Ritz (D1)
-
-// 1/sqrt(a) for a > 0.  FP64: single-precision estimate, then two Newton steps
-// y <- y (3 - a y^2) / 2 (quadratic convergence: ~1e-7 -> 1e-14 -> 1e-16); a
-// normal-range float must hold a, otherwise the FP64 expression is used.
-// FP32: the hardware estimate and one Newton step.
-DEV double rsqrt_nr(double a) {
-  if (!(a > 1e-36 && a < 1e36)) return 1.0 / sqrt(a);
-  double y = (double)rsqrtf((float)a);
-  y = y * (1.5 - 0.5 * a * y * y);
-  y = y * (1.5 - 0.5 * a * y * y);
-  return y;
-}
-DEV float rsqrt_nr(float a) {
-  const float y = rsqrtf(a);
-  return y * (1.5f - 0.5f * a * y * y);
-}
-
-// Givens rotation U = [[cs, sn], [-conj(sn), cs]] with U [x; y] = [r; 0]; rot = {cs, Re sn, Im sn}
-template <typename R> DEV void givens(cx<R> x, cx<R> y, R* rot) {
-  const R ax2 = norm2(x), ay2 = norm2(y);
-  if (ay2 == R(0)) {
-    rot[0] = 1; rot[1] = 0; rot[2] = 0;
-  } else if (ax2 == R(0)) {
-    const R inv = rsqrt_nr(ay2);
-    rot[0] = 0; rot[1] = y.x * inv; rot[2] = -y.y * inv;
-  } else {
-    const R inv_r = rsqrt_nr(ax2 + ay2);
-    const R inv_ax = rsqrt_nr(ax2);
-    rot[0] = ax2 * inv_ax * inv_r;  // |x| / r
-    // sn = (x / |x|) conj(y) / r
-    const R f = inv_ax * inv_r;
-    rot[1] = (x.x * y.x + x.y * y.y) * f;
-    rot[2] = (x.y * y.x - x.x * y.y) * f;
-  }
-}
 
 // selection order of the "smallest" harmonic Ritz values, magnitudes precomputed:
 // |theta| ascending; within a relative tie, larger Im, then larger Re
@@ -1093,6 +1132,7 @@ __global__ void __launch_bounds__(DT) dense_proj_kernel(ProjArgs a) {
   c128* d1 = tau + (k + 1);
   c128* t = d1 + (k + 1);   // (Hbar_k - sigma_1 Ibar) d_1, length k+1
   c128* y = t + (k + 1);
+  c128* rinv = y + (k + 1);
   const c128 s1 = a.sigma[(long)c * a.ns];
   // base: min || c - (Hbar_k - s1 Ibar) d ||
   load_shifted(A, la, a.Hk, k + 1, k + 1, k, s1);
@@ -1102,7 +1142,7 @@ __global__ void __launch_bounds__(DT) dense_proj_kernel(ProjArgs a) {
   cta_qr(A, la, k + 1, k, k + 1, tau, sh, k + 1);
   for (int r = threadIdx.x; r < k; r += DT) d1[r] = A[r + (long)k * la];
   __syncthreads();
-  if (!cta_backsolve(A, la, k, d1, sh)) set_err(st, GDR_EBREAKDOWN);
+  if (!fast_backsolve(A, la, k, d1, rinv, sh)) set_err(st, GDR_EBREAKDOWN);
   for (int r = threadIdx.x; r <= k; r += DT) {
     c128 acc = {0, 0};
     for (int j = 0; j < k; ++j) {
@@ -1131,7 +1171,7 @@ __global__ void __launch_bounds__(DT) dense_proj_kernel(ProjArgs a) {
   cta_qr(A, lb, k, k, k + 1, tau, sh, k);
   for (int r = threadIdx.x; r < k; r += DT) y[r] = A[r + (long)k * lb];
   __syncthreads();
-  if (!cta_backsolve(A, lb, k, y, sh)) set_err(st, GDR_EBREAKDOWN);
+  if (!fast_backsolve(A, lb, k, y, rinv, sh)) set_err(st, GDR_EBREAKDOWN);
   for (int r = threadIdx.x; r <= k; r += DT) Cf[r + (long)i * ldc] = (r < k) ? y[r] : c128{0, 0};
   // gamma_i += [beta_i t - (Hbar_k - s_i Ibar) d_i]_{k+1}  (last row of Ibar is zero)
   if (threadIdx.x == 0) {
