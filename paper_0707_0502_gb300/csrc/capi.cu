@@ -488,9 +488,11 @@ gdr_status gdr_arnoldi_step(gdr_ctx* ctx, const gdr_op* A, gdr_prec prec, void* 
       b.h2 = ctx->get<c128>("step.h2", (size_t)(j + 3));
       const long units = (n * (long)sizeof(cx<R>) + 15) / 16;
       b.nblk = (int)std::max<long>(1, std::min<long>((units + 255) / 256, 3L * ctx->num_sms));
-      b.pstride = (long)b.nblk * (j + 3);
+      b.pstride = (long)(b.nblk + 64) * (j + 3);
       b.part = ctx->get<c128>("step.part", (size_t)b.pstride + 64);
       b.cnt = ctx->get<unsigned>("step.cnt", 4);
+      b.gcnt = ctx->get<unsigned>("step.gcnt", 64);
+      GDR_CUDA(cudaMemsetAsync(b.gcnt, 0, 64 * sizeof(unsigned), ctx->stream));
       b.st = ctx->get<ColState>("step.st", 1);
       b.sigma = nullptr;
       ColState s = {};

@@ -39,6 +39,7 @@ struct Batch {
   c128* part = nullptr;  // block partials, per column pstride
   long pstride = 0;
   unsigned* cnt = nullptr;  // last-block counters, per column (4 slots)
+  unsigned* gcnt = nullptr; // slot-group counters of the two-level reductions, per column (64)
   ColState* st = nullptr;
   c128* sigma = nullptr;    // ns per column
   int nblk = 0;             // grid size of the reduction kernels

@@ -77,6 +77,45 @@ DEV bool last_block(unsigned* cnt) {
   return last;
 }
 
+// Two-level deterministic sum of the per-slot partials part[s * hs + i] (s < S,
+// i < nval) into out[i].  Slots come in groups of RG; the last block to finish
+// writing a group's slots (`nblk_group` blocks write into it) sums them, one
+// thread per value, into gpart[g * hs + i]; the last group sums the group results.
+// FP64 adds are costly on this GPU, so no single block sums all S partials.
+constexpr int RG = 16;
+DEV void reduce2(const c128* part, c128* gpart, int hs, int S, int nval, unsigned* gcnt, unsigned* tcnt, int group,
+                 unsigned nblk_group, c128* out) {
+  __shared__ bool last_g, last_t;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last_g = (atomicAdd(&gcnt[group], 1u) == nblk_group - 1);
+  __syncthreads();
+  if (!last_g) return;
+  __threadfence();
+  const int s0 = group * RG, s1 = min(S, s0 + RG);
+  for (int i = threadIdx.x; i < nval; i += NT) {
+    c128 acc = {0, 0};
+    for (int q = s0; q < s1; ++q) acc += ldcg128(part + (long)q * hs + i);
+    gpart[(long)group * hs + i] = acc;
+  }
+  __threadfence();
+  __syncthreads();
+  const int ng = (S + RG - 1) / RG;
+  if (threadIdx.x == 0) {
+    gcnt[group] = 0;
+    last_t = (atomicAdd(tcnt, 1u) == (unsigned)ng - 1);
+  }
+  __syncthreads();
+  if (!last_t) return;
+  __threadfence();
+  for (int i = threadIdx.x; i < nval; i += NT) {
+    c128 acc = {0, 0};
+    for (int g = 0; g < ng; ++g) acc += ldcg128(gpart + (long)g * hs + i);
+    out[i] = acc;
+  }
+  if (threadIdx.x == 0) *tcnt = 0;
+}
+
 // ------------------------------------------------------------ Gram-Schmidt
 
 // h = V^H w (+ ||w||^2): a block stages a tile of w in shared memory, each warp
@@ -174,11 +213,10 @@ __global__ void __launch_bounds__(NT, 3) gs_dot_kernel(Batch<R> b, int nv, const
   __syncthreads();
   c128* part = b.part + c * b.pstride;
   for (int i = i0 + threadIdx.x; i < i1; i += NT) part[(long)slot * hstride + i] = accs[i];
-  if (!last_block(b.cnt + 4 * c)) return;
-  for (int i = warp; i < nvec_tot; i += NT / 32)
-    hout[(long)c * hstride + i] = warp_sum_partials(part + i, hstride, lane, S);
-  __syncthreads();
-  if (threadIdx.x == 0) b.cnt[4 * c] = 0;
+  const int rg = slot / RG;
+  const unsigned nbg = (unsigned)(min(S, (rg + 1) * RG) - rg * RG) * (unsigned)G;
+  reduce2(part, part + (long)b.nblk * hstride, hstride, S, nvec_tot, b.gcnt + 64 * c, b.cnt + 4 * c + 1, rg, nbg,
+          hout + (long)c * hstride);
 }
 
 // First CGS2 update fused with the second projection: per tile, w' = w - V h
@@ -274,10 +312,10 @@ __global__ void __launch_bounds__(NT, 2) gs_update_dot_kernel(Batch<R> b, int nv
   __syncthreads();
   c128* part = b.part + c * b.pstride;
   for (int i = i0 + threadIdx.x; i < i1; i += NT) part[(long)slot * hstride + i] = accs[i];
-  if (!last_block(b.cnt + 4 * c)) return;
-  for (int i = warp; i < nv; i += NT / 32) hout[(long)c * hstride + i] = warp_sum_partials(part + i, hstride, lane, S);
-  __syncthreads();
-  if (threadIdx.x == 0) b.cnt[4 * c] = 0;
+  const int rg = slot / RG;
+  const unsigned nbg = (unsigned)(min(S, (rg + 1) * RG) - rg * RG) * (unsigned)G;
+  reduce2(part, part + (long)b.nblk * hstride, hstride, S, nv, b.gcnt + 64 * c, b.cnt + 4 * c + 1, rg, nbg,
+          hout + (long)c * hstride);
 }
 
 template <typename R>
@@ -556,7 +594,9 @@ template <typename R>
 static void dot_grid(gdr_ctx* ctx, const Batch<R>& b, int nvec, int& S, int& G) {
   constexpr long TU = DotTile<R>::DU * 32;
   const long ntiles = (nunits<R>(b.n) + TU - 1) / TU;
-  S = (int)std::max<long>(1, std::min<long>(ntiles, b.nblk));
+  // as many slots as blocks allow, each slot with the same number of tiles (+-1)
+  const long rounds = std::max<long>(1, (ntiles + b.nblk - 1) / b.nblk);
+  S = (int)std::max<long>(1, std::min<long>((ntiles + rounds - 1) / rounds, b.nblk));
   const long target = 3L * ctx->num_sms;
   G = 1;
   if (S < target) G = (int)std::min<long>((target + S - 1) / S, (nvec + NT / 32 - 1) / (NT / 32));

@@ -165,9 +165,11 @@ Batch<R> make_batch(gdr_ctx* ctx, const std::string& tag, long n, int ncol, int 
   b.h1 = ctx->get<c128>(tag + ".h1", (size_t)(m + 2) * ncol);
   b.h2 = ctx->get<c128>(tag + ".h2", (size_t)(m + 2) * ncol);
   b.nblk = nblk_for<R>(ctx, n);
-  b.pstride = (long)b.nblk * std::max(m + 2, hmin);
+  b.pstride = (long)(b.nblk + 64) * std::max(m + 2, hmin);  // block partials, then slot-group partials
   b.part = ctx->get<c128>(tag + ".part", (size_t)b.pstride * ncol + 64);
   b.cnt = ctx->get<unsigned>(tag + ".cnt", (size_t)4 * ncol);
+  b.gcnt = ctx->get<unsigned>(tag + ".gcnt", (size_t)64 * ncol);
+  GDR_CUDA(cudaMemsetAsync(b.gcnt, 0, sizeof(unsigned) * 64 * ncol, ctx->stream));
   GDR_CUDA(cudaMemsetAsync(b.cnt, 0, sizeof(unsigned) * 4 * ncol, ctx->stream));
   b.st = ctx->get<ColState>(tag + ".st", (size_t)ncol);
   b.sigma = ctx->get<c128>(tag + ".sigma", (size_t)ns * ncol);
