@@ -77,6 +77,9 @@ typedef struct {
   double inner_tol;   /* MIXED: relative residual of the complex64 GMRES-DR / Proj stages before FP64
                          refinement; <= 0 chooses it: 1e-3 when the complex64 basis fits in half of
                          the L2 cache (cycles limited by the FP64 dense steps), else 1e-5 */
+  double refine_tol;  /* MIXED: floor of the relative reduction asked of one complex64 refinement pass
+                         (its target is max(0.3 tol ||b|| / ||r||, refine_tol)); <= 0 chooses
+                         min(inner_tol, 1e-4) */
   long max_mvps;      /* cap on Arnoldi matvecs per solve stage (per column) */
   int max_cycles;     /* 0: unlimited; else stop RHS 1 after this many cycles */
   int refine_max;     /* MIXED: refinement passes before the FP64 cleanup */

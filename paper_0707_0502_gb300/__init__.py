@@ -33,7 +33,7 @@ GDR_MAX_M = 96
 class gdr_params(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("k", ctypes.c_int), ("m_proj", ctypes.c_int),
                 ("tol", ctypes.c_double), ("extra_tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
-                ("max_mvps", ctypes.c_long), ("max_cycles", ctypes.c_int), ("refine_max", ctypes.c_int),
+                ("refine_tol", ctypes.c_double), ("max_mvps", ctypes.c_long), ("max_cycles", ctypes.c_int), ("refine_max", ctypes.c_int),
                 ("prec", ctypes.c_int), ("flags", ctypes.c_uint)]
 
 

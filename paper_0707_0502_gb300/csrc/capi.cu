@@ -45,6 +45,9 @@ gdr_params resolve_inner_tol(const gdr_ctx* ctx, long n, const gdr_params& p) {
     const double basis = (double)(p.m + 1) * (double)n * sizeof(c64);
     r.inner_tol = (basis <= 0.5 * (double)ctx->l2_bytes) ? 1e-3 : 1e-5;
   }
+  // a complex64 refinement pass reliably reduces its residual by 1e-4: one pass then
+  // usually finishes a pair that the stage left at ~1e-4
+  if (!(r.refine_tol > 0)) r.refine_tol = std::min(r.inner_tol, 1e-4);
   return r;
 }
 
@@ -67,6 +70,7 @@ void gdr_params_default(gdr_params* p) {
   p->tol = 1e-8;
   p->extra_tol = 1e-5;
   p->inner_tol = 0.0;  // automatic
+  p->refine_tol = 0.0;  // automatic
   p->max_mvps = 100000;
   p->max_cycles = 0;
   p->refine_max = 3;

@@ -695,7 +695,7 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
       for (int c = 0; c < cn; ++c) {
         const int q = q0 + c;
         // relative to the residual column: reach tol * ||b|| with margin
-        tolc[c] = std::max(0.3 * p.tol / std::max(relres[q], 1e-300), cleanup ? 0.0 : p.inner_tol);
+        tolc[c] = std::max(0.3 * p.tol / std::max(relres[q], 1e-300), cleanup ? 0.0 : p.refine_tol);
         tolc[c] = std::min(tolc[c], 0.5);
       }
       auto run_refine = [&](auto tag) {
@@ -852,7 +852,7 @@ gdr_status solve_batch_pipeline(gdr_ctx* ctx, const gdr_op* A, int ns, const std
     if (cleanup) rep.pairs_cleaned += nact;
     std::vector<double> tolc(npair);
     for (int q = 0; q < npair; ++q)
-      tolc[q] = std::min(0.5, std::max(0.3 * p.tol / std::max(relres[q], 1e-300), cleanup ? 0.0 : p.inner_tol));
+      tolc[q] = std::min(0.5, std::max(0.3 * p.tol / std::max(relres[q], 1e-300), cleanup ? 0.0 : p.refine_tol));
     auto run = [&](auto tag) {
       using RR = decltype(tag);
       cx<RR>* rin = ctx->get<cx<RR>>("bt.rin", (size_t)ld * npair);
