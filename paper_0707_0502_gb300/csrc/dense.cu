@@ -1111,6 +1111,7 @@ struct ProjArgs {
   int k, ns;
   const c128* Hk; const c128* cproj; const c128* sigma; const c128* beta; const int* sact;
   c128* gamma; c128* Cf; long ccs; ColState* st;
+  long hkcs; int hpp;  // column c uses Hk + (c / hpp) * hkcs
 };
 
 __global__ void __launch_bounds__(DT) dense_proj_kernel(ProjArgs a) {
@@ -1118,6 +1119,7 @@ __global__ void __launch_bounds__(DT) dense_proj_kernel(ProjArgs a) {
   __shared__ Sh sh;
   const int c = blockIdx.y, i = blockIdx.x;
   ColState* st = a.st + c;
+  const c128* Hk = a.Hk + (long)(c / a.hpp) * a.hkcs;
   if (!st->active) return;
   const int k = a.k, ldc = k + 1;
   c128* Cf = a.Cf + (long)c * a.ccs;
@@ -1135,7 +1137,7 @@ __global__ void __launch_bounds__(DT) dense_proj_kernel(ProjArgs a) {
   c128* rinv = y + (k + 1);
   const c128 s1 = a.sigma[(long)c * a.ns];
   // base: min || c - (Hbar_k - s1 Ibar) d ||
-  load_shifted(A, la, a.Hk, k + 1, k + 1, k, s1);
+  load_shifted(A, la, Hk, k + 1, k + 1, k, s1);
   for (int r = threadIdx.x; r <= k; r += DT) A[r + (long)k * la] = a.cproj[(long)c * (k + 2) + r];
   if (threadIdx.x == 0) sh.ibc[0] = 0;
   __syncthreads();
@@ -1146,7 +1148,7 @@ __global__ void __launch_bounds__(DT) dense_proj_kernel(ProjArgs a) {
   for (int r = threadIdx.x; r <= k; r += DT) {
     c128 acc = {0, 0};
     for (int j = 0; j < k; ++j) {
-      c128 h = a.Hk[r + (long)j * (k + 1)];
+      c128 h = Hk[r + (long)j * (k + 1)];
       if (r == j) h -= s1;
       acc += h * d1[j];
     }
@@ -1164,7 +1166,7 @@ __global__ void __launch_bounds__(DT) dense_proj_kernel(ProjArgs a) {
   const c128 si = a.sigma[(long)c * a.ns + i];
   const c128 bi = a.beta[(long)c * a.ns + i];
   const int lb = odd_ld(k);
-  load_shifted(A, lb, a.Hk, k + 1, k, k, si);
+  load_shifted(A, lb, Hk, k + 1, k, k, si);
   for (int r = threadIdx.x; r < k; r += DT) A[r + (long)k * lb] = bi * t[r];
   if (threadIdx.x == 0) sh.ibc[0] = 0;
   __syncthreads();
@@ -1176,7 +1178,7 @@ __global__ void __launch_bounds__(DT) dense_proj_kernel(ProjArgs a) {
   // gamma_i += [beta_i t - (Hbar_k - s_i Ibar) d_i]_{k+1}  (last row of Ibar is zero)
   if (threadIdx.x == 0) {
     c128 acc = {0, 0};
-    for (int j = 0; j < k; ++j) acc += a.Hk[k + (long)j * (k + 1)] * y[j];
+    for (int j = 0; j < k; ++j) acc += Hk[k + (long)j * (k + 1)] * y[j];
     a.gamma[(long)c * a.ns + i] += bi * t[k] - acc;
   }
 }
@@ -1249,8 +1251,8 @@ void cycle_finish(gdr_ctx* ctx, const DenseCycle& d, c128* H, c128* cvec) {
 
 void dense_projection(gdr_ctx* ctx, int ncol, int k, int ns, const c128* Hk, const c128* cproj, const c128* sigma,
                       const c128* beta, const int* sact, c128* gamma, c128* Cf, long ccs, double*, long,
-                      ColState* st) {
-  ProjArgs a{k, ns, Hk, cproj, sigma, beta, sact, gamma, Cf, ccs, st};
+                      ColState* st, long hkcs, int hpp) {
+  ProjArgs a{k, ns, Hk, cproj, sigma, beta, sact, gamma, Cf, ccs, st, hkcs, hpp};
   const size_t smem = sizeof(c128) * ((size_t)(k + 2) * (k + 1) + 5 * (size_t)(k + 2));
   GDR_REQUIRE(smem <= ctx->dense_smem_limit, "k too large for the projection kernel");
   dim3 g((unsigned)ns, (unsigned)ncol);

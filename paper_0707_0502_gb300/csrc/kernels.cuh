@@ -45,6 +45,7 @@ struct Batch {
   int nblk = 0;             // grid size of the reduction kernels
   const int* nvec = nullptr;  // per-column vector length (device); nullptr: all columns have length n
   int cpp = 1;                // operator problem of column c is c / cpp (CSR batch)
+  int vpp = 1;                // gs_dot only: column c works on basis c / vpp (shared deflation bases)
 };
 
 // krylov.cu --------------------------------------------------------------
@@ -104,7 +105,7 @@ void dots128(gdr_ctx* ctx, long n, int cols, const c128* u, long ucs, const c128
 template <typename R>
 void combine(gdr_ctx* ctx, long n, int ncol, cx<R>* V, long ldv, long vcs, int nv, const c128* C, int ldc, long ccs,
              int nout, int nx, int rmode, c128* X, long ldx, long xcs, cx<R>* Rv, long rcs, const ColState* st,
-             const int* nvec = nullptr);
+             const int* nvec = nullptr, int vpp = 1);
 
 void krylov_init(gdr_ctx* ctx);
 
@@ -164,9 +165,10 @@ void cycle_finish(gdr_ctx* ctx, const DenseCycle& d, c128* H, c128* cvec);
 // c = V_{k+1}^H r given in cproj (stride k+2 per column), base LS on Hbar_k - sigma_1 Ibar,
 // shifts: (H_k - sigma_i I) d_i = beta_i (H_k - sigma_1 I) d_1; gamma_i accumulated.
 // Writes Cf (ldc = k+1): columns [0, ns) = [d_i ; 0], column ns = -(Hbar_k - sigma_1 Ibar) d_1.
+// Hk: column c uses Hk + (c / hpp) * hkcs (hkcs = 0: one Hbar_k shared by all columns).
 void dense_projection(gdr_ctx* ctx, int ncol, int k, int ns, const c128* Hk, const c128* cproj, const c128* sigma,
                       const c128* beta, const int* sact, c128* gamma, c128* Cf, long ccs, double* scratch,
-                      long scratch_per_col, ColState* st);
+                      long scratch_per_col, ColState* st, long hkcs = 0, int hpp = 1);
 
 size_t dense_smem_bytes(int m, int k);
 // harmonic Ritz restart products alone, for the s already in d.s

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(NT, 3) gs_dot_kernel(Batch<R> b, int nv, const
   constexpr int TU = DU * 32;  // units per tile
   __shared__ cx<R> wt[TU * K];
   __shared__ c128 accs[GDR_MAX_M + 2];
-  const cx<R>* __restrict__ V = b.V + c * b.vcs;
+  const cx<R>* __restrict__ V = b.V + (c / b.vpp) * b.vcs;
   const cx<R>* __restrict__ w = W + c * wcs;
   const long n = b.nvec ? (long)b.nvec[c] : b.n, nu = nunits<R>(n);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -505,7 +505,7 @@ template <typename R>
 __global__ void __launch_bounds__(CT) combine_kernel(long n, cx<R>* V, long ldv, long vcs, int nv,
                                                      const c128* __restrict__ C, int ldc, long ccs, int nout, int nx,
                                                      int rmode, c128* X, long ldx, long xcs, cx<R>* Rv, long rcs,
-                                                     const ColState* st, const int* nvec) {
+                                                     const ColState* st, const int* nvec, int vpp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int c = blockIdx.y;
   if (st && !st[c].active) return;
@@ -514,7 +514,7 @@ __global__ void __launch_bounds__(CT) combine_kernel(long n, cx<R>* V, long ldv,
   const int ntot = nout + nx + (rmode ? 1 : 0);
   cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);             // CR x nv  (row-fast)
   cx<R>* cf = tile + (long)CR * nv;                              // nv x ntot
-  cx<R>* Vc = V + c * vcs;
+  cx<R>* Vc = V + (c / vpp) * vcs;                               // basis of column c (nout == 0 when shared)
   const c128* Cc = C + c * ccs;
   const long r0 = blockIdx.x * (long)CR;
   const int rows = (int)min((long)CR, n - r0);
@@ -700,7 +700,7 @@ void dots128(gdr_ctx* ctx, long n, int cols, const c128* u, long ucs, const c128
 template <typename R>
 void combine(gdr_ctx* ctx, long n, int ncol, cx<R>* V, long ldv, long vcs, int nv, const c128* C, int ldc, long ccs,
              int nout, int nx, int rmode, c128* X, long ldx, long xcs, cx<R>* Rv, long rcs, const ColState* st,
-             const int* nvec) {
+             const int* nvec, int vpp) {
   const int ntot = nout + nx + (rmode ? 1 : 0);
   if (ntot == 0 || ncol == 0) return;
   const size_t smem = sizeof(cx<R>) * ((size_t)CR * nv + (size_t)nv * ntot);
@@ -710,7 +710,7 @@ void combine(gdr_ctx* ctx, long n, int ncol, cx<R>* V, long ldv, long vcs, int n
            (double)ncol * n * ((nv + nout) * sizeof(cx<R>) + 2.0 * nx * sizeof(c128) +
                                (rmode == 2 ? 2.0 : (rmode == 1 ? 1.0 : 0.0)) * sizeof(cx<R>)));
   combine_kernel<R><<<grid, CT, smem, ctx->stream>>>(n, V, ldv, vcs, nv, C, ldc, ccs, nout, nx, rmode, X, ldx, xcs,
-                                                     Rv, rcs, st, nvec);
+                                                     Rv, rcs, st, nvec, vpp);
   GDR_LAUNCHED(ctx);
 }
 
@@ -758,6 +758,6 @@ template void start_cycle<double>(gdr_ctx*, const Batch<double>&, const c128*, l
 template void norms2<c64>(gdr_ctx*, long, int, const c64*, long, double*, c128*, int, unsigned*, const int*);
 template void norms2<c128>(gdr_ctx*, long, int, const c128*, long, double*, c128*, int, unsigned*, const int*);
 template void combine<float>(gdr_ctx*, long, int, c64*, long, long, int, const c128*, int, long, int, int, int, c128*,
-                             long, long, c64*, long, const ColState*, const int*);
+                             long, long, c64*, long, const ColState*, const int*, int);
 template void combine<double>(gdr_ctx*, long, int, c128*, long, long, int, const c128*, int, long, int, int, int,
-                              c128*, long, long, c128*, long, const ColState*, const int*);
+                              c128*, long, long, c128*, long, const ColState*, const int*, int);

@@ -298,6 +298,7 @@ DrResult dr_sh(gdr_ctx* ctx, const gdr_op* A, const DrJob<R>& job, bool use_grap
       else if (st[c].err && res.status == GDR_OK) res.status = (gdr_status)st[c].err;
       if (st[c].conv) res.col_conv[c] = 1;
       if (st[c].broke && c == 0) res.broke = true;
+      if (st[c].broke) res.any_broke = true;
       if (st[c].active) any_active = true;
       else done[c] = 1;
     }
@@ -312,6 +313,7 @@ DrResult dr_sh(gdr_ctx* ctx, const gdr_op* A, const DrJob<R>& job, bool use_grap
   }
   res.V = b.V;
   res.ldv = b.ldv;
+  res.vcs = b.vcs;
   res.Hk = d.Hk;
   res.valid_defl = (k > 0) && !res.broke && res.status != GDR_ENAN && res.status != GDR_EBREAKDOWN;
   std::vector<double> nr((size_t)ns * ncol);
@@ -354,7 +356,8 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
   Batch<R> bd = b;
   bd.V = const_cast<cx<R>*>(job.Vd);
   bd.ldv = job.ldvd;
-  bd.vcs = 0;
+  bd.vcs = job.vdcs;
+  bd.vpp = job.dpp;
   bd.m = k;
   c128* cproj = ctx->get<c128>("pj.cproj", (size_t)(k + 2) * ncol);
   c128* Cp = ctx->get<c128>("pj.Cp", (size_t)(k + 1) * (ns + 1) * ncol);
@@ -387,10 +390,10 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
       // steps 3-4: Minres projection over V_k; c = V_{k+1}^H r
       gs_dot<R>(ctx, bd, k + 1, r, ldr, cproj, false);
       dense_projection(ctx, ncol, k, ns, job.Hk, cproj, b.sigma, sh.beta, sh.sact, sh.gamma, Cp, (long)(k + 1) * (ns + 1),
-                       nullptr, 0, b.st);
+                       nullptr, 0, b.st, job.hkcs, job.dpp);
       // x_i += V_k d_i, r -= V_{k+1} (Hbar_k - sigma_1 Ibar) d_1
-      combine<R>(ctx, n, ncol, bd.V, bd.ldv, 0, k + 1, Cp, k + 1, (long)(k + 1) * (ns + 1), 0, ns, 2, job.X, job.ldx,
-                 job.xcs, r, ldr, b.st);
+      combine<R>(ctx, n, ncol, bd.V, bd.ldv, job.vdcs, k + 1, Cp, k + 1, (long)(k + 1) * (ns + 1), 0, ns, 2, job.X,
+                 job.ldx, job.xcs, r, ldr, b.st, b.nvec, job.dpp);
     }
     // step 5: one GMRES(m_p)-Sh cycle on r
     start_cycle<R>(ctx, b, r, ldr);
@@ -863,6 +866,18 @@ gdr_status solve_batch_pipeline(gdr_ctx* ctx, const gdr_op* A, int ns, const std
       job.m_p = mp;
       job.k = 0;
       job.project = false;
+      // every pair projects over its own problem's kept pair of the GMRES-DR stage
+      // (in the precision of that stage's basis)
+      if (std::is_same<RR, R>::value && dr.valid_defl && !dr.any_broke && k > 0) {
+        job.k = k;
+        job.project = true;
+        job.Vd = reinterpret_cast<const cx<RR>*>(dr.V);
+        job.ldvd = dr.ldv;
+        job.vdcs = dr.vcs;
+        job.Hk = dr.Hk;
+        job.hkcs = (long)(k + 1) * k;
+        job.dpp = ns;
+      }
       job.rhs = rin;
       job.ldrhs = ld;
       job.sigma = sigma;

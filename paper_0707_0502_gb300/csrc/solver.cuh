@@ -31,6 +31,8 @@ struct DrResult {
   bool valid_defl = false;
   void* V = nullptr;       // basis buffer (vector precision); V[:, 0:k+1] is the kept V_{k+1}
   long ldv = 0;
+  long vcs = 0;            // stride between the columns' bases
+  bool any_broke = false;  // some column had a lucky breakdown (no kept pair for it)
   c128* Hk = nullptr;      // kept Hbar_k ((k+1) x k) on the device
   std::vector<double> norms;
   std::vector<long> col_mvps;  // per column
@@ -45,6 +47,8 @@ struct ProjJob {
   const cx<R>* Vd = nullptr;   // kept V_{k+1} (n x (k+1), ld ldvd), shared by all columns
   long ldvd = 0;
   const c128* Hk = nullptr;    // kept Hbar_k ((k+1) x k)
+  long vdcs = 0, hkcs = 0;     // strides between per-problem kept pairs (0: one pair shared by all)
+  int dpp = 1;                 // column c uses kept pair c / dpp
   const cx<R>* rhs = nullptr;  // right-hand sides, column c at rhs + c*ldrhs
   long ldrhs = 0;
   std::vector<c128> sigma;     // ncol x ns, sigma[c*ns] the base shift of column c

@@ -630,8 +630,10 @@ bool sweep_fits(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b) {
   if (b.m + 2 > GDR_MAX_M + 2) return false;
   // the direction-split Wilson form only, i.e. lattices too small for a thread per site
   if (A->kind == OP_WILSON && (A->V + 127) / 128 * b.ncol >= 2L * ctx->num_sms) return false;
-  // short vectors: at most 2^17 elements (1 MB complex64) per column
-  return b.n <= (1L << 17);
+  // short vectors (at most 2^17 elements per column) and the whole batch of bases
+  // within half of L2: there launch and barrier latency, not bandwidth, sets the pace
+  if (b.n > (1L << 17)) return false;
+  return (double)b.ncol * b.n * (b.m + 1) * sizeof(cx<R>) <= 0.5 * (double)ctx->l2_bytes;
 }
 
 template <typename R>
