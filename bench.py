@@ -217,10 +217,14 @@ def main():
         X = torch.zeros((nrhs, ns, p.n), dtype=torch.complex128, device="cuda")
         flush = torch.empty(512 * 2**20, dtype=torch.uint8, device="cuda")
     stream.synchronize()
+    # launch shapes: the first-stage matvec and Arnoldi form tuned here (reported), every
+    # other stage's by GDR_FLAG_AUTOTUNE in the first (untimed) warm-up solve of each leg
+    tune = g.gdr_autotune(ctx, op, g.GDR_PREC_MIXED, 1, p.m)
     mixed = g.gdr_params_default(m=p.m, k=p.k, m_proj=p.m_proj, tol=p.tol, extra_tol=p.extra_tol,
-                                 prec=g.GDR_PREC_MIXED)        # inner_tol: automatic
+                                 prec=g.GDR_PREC_MIXED, flags=g.GDR_FLAG_AUTOTUNE)  # inner_tol: automatic
     plain = g.gdr_params_default(m=p.m, k=p.k, m_proj=p.m_proj, tol=p.tol, extra_tol=p.extra_tol,
-                                 prec=g.GDR_PREC_FP64, flags=g.GDR_FLAG_SEQUENTIAL | g.GDR_FLAG_NO_GRAPH)
+                                 prec=g.GDR_PREC_FP64,
+                                 flags=g.GDR_FLAG_SEQUENTIAL | g.GDR_FLAG_NO_GRAPH | g.GDR_FLAG_AUTOTUNE)
 
     def timed(params, steps, warm, Bx=B, Xx=X):
         reps = []
@@ -299,6 +303,7 @@ def main():
                                       "t_proj_ms", "t_refine_ms", "host_syncs", "kernel_launches")},
         "roofline": roof,
         "kernels": ktable,
+        "autotune": {"stage": "rhs1 matvec (1 column) and Arnoldi form", **tune},
     }
     if scale is not None:
         line["kernels_at_scale"] = scale
@@ -383,8 +388,10 @@ def kernels_at_scale(g, ctx, stream):
     (Wilson 16^4, c64 links; 24^3x32, bf16 links): one profiled Arnoldi step at
     the last column of the basis (j = m - 1, m = 60 / 80; single column, so the
     algorithmic byte model is exact) and the multi-column matvec of the
-    refinement / Proj stages (8 / 12 columns).  Inputs far larger than L2.  Per
-    kernel: microseconds per launch, GB/s and fraction of measured HBM peak."""
+    refinement / Proj stages (8 / 12 columns), each matvec in the launch shape
+    the autotuner chose (its time and the default shape's reported beside).
+    Inputs far larger than L2.  Per kernel: microseconds per launch, GB/s and
+    fraction of measured HBM peak."""
     import torch
     peaks = {}
     try:
@@ -406,6 +413,8 @@ def kernels_at_scale(g, ctx, stream):
             X = torch.randn((ncol, n), dtype=torch.complex64, device="cuda", generator=gen)
             Y = torch.empty_like(X)
         del links
+        tuned = {"1": g.gdr_autotune(ctx, op, g.GDR_PREC_MIXED, 1),
+                 str(ncol): g.gdr_autotune(ctx, op, g.GDR_PREC_MIXED, ncol)}
         for _ in range(2):  # warm-up
             g.gdr_arnoldi_step(ctx, op, g.GDR_PREC_MIXED, V, m - 1, hcol)
             g.gdr_op_apply(ctx, op, g.GDR_PREC_MIXED, np.zeros(ncol), X, Y)
@@ -425,7 +434,8 @@ def kernels_at_scale(g, ctx, stream):
             tab[name] = {"launches": v["launches"], "us_per_launch": round(us, 1), "GBs": round(gbs, 1),
                          "frac_of_measured_hbm": round(gbs / hbm, 3)}
         out[key] = {"n": n, "arnoldi_step_j": m - 1, "matvec_columns": ncol,
-                    "links": "bf16" if store == g.GDR_LINK_BF16 else "c64", "kernels": tab}
+                    "links": "bf16" if store == g.GDR_LINK_BF16 else "c64", "kernels": tab,
+                    "matvec_autotune": tuned}
         g.gdr_op_destroy(op)
         del V, X, Y
         torch.cuda.empty_cache()

@@ -63,6 +63,9 @@ typedef enum { GDR_LINK_C128 = 0, GDR_LINK_C64 = 1, GDR_LINK_BF16 = 2 } gdr_link
 #define GDR_FLAG_NO_SWEEP    32u  /* short vectors: one launch per Arnoldi phase instead of the persistent
                                      per-cycle sweep kernel */
 #define GDR_FLAG_FP64_EIG    64u  /* MIXED: harmonic-Ritz eigensolve in FP64 instead of FP32 */
+#define GDR_FLAG_AUTOTUNE   128u  /* before the first cycle, run gdr_autotune for the matvec and Arnoldi
+                                     form of each stage whose (precision, columns, m) the operator has
+                                     no tuned shape for yet (the tuning time is part of the solve) */
 
 typedef struct gdr_ctx gdr_ctx;
 typedef struct gdr_op gdr_op;
@@ -146,6 +149,52 @@ long gdr_op_n(const gdr_op *op);
  * floats).  sigma: host c128[ncol].  Leading dimension n.  Asynchronous. */
 gdr_status gdr_op_apply(gdr_ctx *ctx, const gdr_op *A, gdr_prec prec, int ncol, const double *sigma,
                         const void *X, void *Y);
+
+/* ------------------------------------------------------------- autotuning
+ * The paper fixes the algorithm, not a kernel layout; these calls choose, by
+ * timing on the device, how the same arithmetic is launched (the result changes
+ * at most in the summation order of a CSR row or of the four hop directions).
+ * A matvec shape belongs to an operator and one (vector precision, column
+ * count); a matvec of another count uses the shape of the nearest tuned count
+ * within a factor 2, else the defaults.  Shapes are not shared between
+ * operators and are lost with gdr_op_destroy. */
+typedef struct {
+  int form;       /* Wilson: 0 one thread per site, 1 direction-split (a warp per direction,
+                     32 sites per block).  CSR: threads per row, 1, 2, 4 or 8 */
+  int threads;    /* threads per block: 64, 128 or 256 (direction-split: 128) */
+  int col_inner;  /* 1: consecutive blocks take one site/row tile for consecutive columns
+                     (links / rows read from HBM once for all columns); 0: column-major grid */
+} gdr_shape;
+
+typedef struct {
+  gdr_shape best;          /* the matvec shape kept (now in effect for this precision and count) */
+  double mv_ms;            /* its time per launch, all columns */
+  double mv_ms_default;    /* the default shape's time per launch */
+  int candidates;          /* matvec shapes timed */
+  int sweep;               /* Arnoldi form kept: 1 persistent sweep, 0 per-phase launches,
+                              -1 not tuned (m = 0, or the sweep does not apply to this shape) */
+  double cycle_ms_sweep;   /* one Arnoldi pass of m steps on ncol columns, each form, replayed */
+  double cycle_ms_launch;  /*   from CUDA graphs (0 when not timed) */
+} gdr_tune_result;
+
+/* Time every candidate matvec shape for `ncol` columns of `prec` vectors on A
+ * (library scratch vectors with counter-based random entries, about 20 ms of
+ * launches per candidate) and keep the fastest on A.  With m > 0, also time one
+ * Arnoldi pass of m steps on ncol columns (random start vectors) as the
+ * persistent sweep and as one launch per phase, where the sweep applies (short
+ * vectors whose bases fit in half of L2), and keep the faster for solves whose
+ * stage has these (prec, ncol, m).  For a CSR batch, ncol must be a positive
+ * multiple of the problem count (column c belongs to problem c / (ncol/nprob)).
+ * out may be NULL.  Synchronises the context stream. */
+gdr_status gdr_autotune(gdr_ctx *ctx, gdr_op *A, gdr_prec prec, int ncol, int m, gdr_tune_result *out);
+
+/* Set the matvec shape of A for (prec, ncol) (shape != NULL; validated: a form
+ * and thread count listed above), or forget it (shape == NULL; ncol <= 0
+ * forgets every shape and Arnoldi choice of A). */
+gdr_status gdr_op_set_shape(gdr_op *A, gdr_prec prec, int ncol, const gdr_shape *shape);
+
+/* The shape a matvec of ncol `prec` columns on A launches with now. */
+gdr_status gdr_op_get_shape(const gdr_op *A, gdr_prec prec, int ncol, gdr_shape *out);
 
 /* ------------------------------------------------------------------ solves */
 

@@ -27,7 +27,7 @@ GDR_PREC_FP64, GDR_PREC_MIXED = 0, 1
 GDR_LINK_C128, GDR_LINK_C64, GDR_LINK_BF16 = 0, 1, 2
 GDR_MAX_M = 96
 (GDR_FLAG_HOST_PTRS, GDR_FLAG_NO_GRAPH, GDR_FLAG_SEQUENTIAL, GDR_FLAG_NO_PROJ, GDR_FLAG_NO_REFINE, GDR_FLAG_NO_SWEEP,
- GDR_FLAG_FP64_EIG) = 1, 2, 4, 8, 16, 32, 64
+ GDR_FLAG_FP64_EIG, GDR_FLAG_AUTOTUNE) = 1, 2, 4, 8, 16, 32, 64, 128
 
 
 class gdr_params(ctypes.Structure):
@@ -47,6 +47,24 @@ class gdr_report(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class gdr_shape(ctypes.Structure):
+    _fields_ = [("form", ctypes.c_int), ("threads", ctypes.c_int), ("col_inner", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class gdr_tune_result(ctypes.Structure):
+    _fields_ = [("best", gdr_shape), ("mv_ms", ctypes.c_double), ("mv_ms_default", ctypes.c_double),
+                ("candidates", ctypes.c_int), ("sweep", ctypes.c_int), ("cycle_ms_sweep", ctypes.c_double),
+                ("cycle_ms_launch", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["best"] = self.best.as_dict()
+        return d
 
 
 class GdrError(RuntimeError):
@@ -75,6 +93,10 @@ _SIGS = {
     "gdr_op_destroy": (None, [_P]),
     "gdr_op_n": (ctypes.c_long, [_P]),
     "gdr_op_apply": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
+    "gdr_autotune": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(gdr_tune_result)]),
+    "gdr_op_set_shape": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(gdr_shape)]),
+    "gdr_op_get_shape": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(gdr_shape)]),
     "gdr_solve_multishift": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int, _P, _P,
                                             ctypes.POINTER(gdr_params), ctypes.POINTER(_P),
                                             ctypes.POINTER(gdr_report)]),
@@ -233,6 +255,32 @@ def gdr_op_apply(ctx, op, prec, sigma, X, Y):
     """Y[c] = (A - sigma_c I) X[c]; X, Y: (ncol, n) complex128 (FP64) or complex64 (MIXED)."""
     s = _c128_host(sigma)
     _check(lib().gdr_op_apply(ctx, op, int(prec), len(s), s.ctypes.data, _ptr(X), _ptr(Y)), ctx)
+
+
+def gdr_autotune(ctx, op, prec, ncol, m=0):
+    """Time the matvec shapes (and, m > 0, the Arnoldi forms) for ncol columns; returns the result dict."""
+    r = gdr_tune_result()
+    _check(lib().gdr_autotune(ctx, op, int(prec), int(ncol), int(m), ctypes.byref(r)), ctx)
+    return r.as_dict()
+
+
+def gdr_op_set_shape(op, prec, ncol, form=None, threads=None, col_inner=0):
+    """Set the matvec shape of op for (prec, ncol); form=None forgets it (ncol <= 0: all)."""
+    if form is None:
+        st = lib().gdr_op_set_shape(op, int(prec), int(ncol), None)
+    else:
+        sh = gdr_shape(int(form), int(threads), int(col_inner))
+        st = lib().gdr_op_set_shape(op, int(prec), int(ncol), ctypes.byref(sh))
+    if st != GDR_OK:
+        raise GdrError(st, "bad shape")
+
+
+def gdr_op_get_shape(op, prec, ncol):
+    sh = gdr_shape()
+    st = lib().gdr_op_get_shape(op, int(prec), int(ncol), ctypes.byref(sh))
+    if st != GDR_OK:
+        raise GdrError(st, "bad arguments")
+    return sh.as_dict()
 
 
 # ------------------------------------------------------------------- solves

@@ -1,6 +1,7 @@
 // extern "C" entry points of include/gdr.h: argument checks, buffer staging
 // and error translation around the solver drivers.  No C++ exception crosses
 // this boundary.
+#include <array>
 #include <chrono>
 #include <cstring>
 #include <type_traits>
@@ -237,11 +238,129 @@ gdr_status gdr_op_apply(gdr_ctx* ctx, const gdr_op* A, gdr_prec prec, int ncol, 
     if (ncol == 0) return;
     c128* sd = ctx->get<c128>("apply.sigma", (size_t)ncol);
     GDR_CUDA(cudaMemcpyAsync(sd, sigma, sizeof(c128) * ncol, cudaMemcpyHostToDevice, ctx->stream));
+    auto run = [&](auto tag) {
+      using R = decltype(tag);
+      const cx<R>* x = static_cast<const cx<R>*>(X);
+      cx<R>* y = static_cast<cx<R>*>(Y);
+      if (A->kind != OP_WILSON) {
+        op_apply<R>(ctx, A, ncol, sd, x, A->n, y, A->n, nullptr, 0);
+        return;
+      }
+      // interface (site-major) order <-> the library's pair-major order
+      cx<R>* xl = ctx->get<cx<R>>("apply.x", (size_t)A->n * ncol);
+      cx<R>* yl = ctx->get<cx<R>>("apply.y", (size_t)A->n * ncol);
+      op_order<cx<R>>(ctx, A, ncol, x, A->n, xl, A->n, true);
+      op_apply<R>(ctx, A, ncol, sd, xl, A->n, yl, A->n, nullptr, 0);
+      op_order<cx<R>>(ctx, A, ncol, yl, A->n, y, A->n, false);
+    };
     if (prec == GDR_PREC_FP64)
-      op_apply<double>(ctx, A, ncol, sd, (const c128*)X, A->n, (c128*)Y, A->n, nullptr, 0);
+      run(double{});
     else
-      op_apply<float>(ctx, A, ncol, sd, (const c64*)X, A->n, (c64*)Y, A->n, nullptr, 0);
+      run(float{});
   });
+}
+
+// Staging of right-hand sides and solutions between the interface order (leading
+// dimension n, host or device memory) and the library order (device, leading dimension
+// ld); Wilson vectors are reordered through a scratch buffer of at most ~256 MB.
+static int stage_chunk(const gdr_op* A, long ld, int cols) {
+  return (int)std::max<long>(1, std::min<long>(cols, (256L << 20) / (ld * (long)sizeof(c128))));
+}
+static void stage_in(gdr_ctx* ctx, const gdr_op* A, int cols, const double* src, c128* dst, long ld,
+                     cudaMemcpyKind kind) {
+  const long n = A->n;
+  if (A->kind != OP_WILSON) {
+    GDR_CUDA(cudaMemcpy2DAsync(dst, ld * sizeof(c128), src, n * sizeof(c128), n * sizeof(c128), cols, kind,
+                               ctx->stream));
+    return;
+  }
+  const int ch = stage_chunk(A, ld, cols);
+  c128* tmp = ctx->get<c128>("api.order", (size_t)ld * ch);
+  for (int c0 = 0; c0 < cols; c0 += ch) {
+    const int nc = std::min(ch, cols - c0);
+    GDR_CUDA(cudaMemcpy2DAsync(tmp, ld * sizeof(c128), src + 2 * (long)c0 * n, n * sizeof(c128), n * sizeof(c128),
+                               nc, kind, ctx->stream));
+    op_order<c128>(ctx, A, nc, tmp, ld, dst + (long)c0 * ld, ld, true);
+  }
+}
+static void stage_out(gdr_ctx* ctx, const gdr_op* A, int cols, const c128* src, long ld, double* dst,
+                      cudaMemcpyKind kind) {
+  const long n = A->n;
+  if (A->kind != OP_WILSON) {
+    GDR_CUDA(cudaMemcpy2DAsync(dst, n * sizeof(c128), src, ld * sizeof(c128), n * sizeof(c128), cols, kind,
+                               ctx->stream));
+    return;
+  }
+  const int ch = stage_chunk(A, ld, cols);
+  c128* tmp = ctx->get<c128>("api.order", (size_t)ld * ch);
+  for (int c0 = 0; c0 < cols; c0 += ch) {
+    const int nc = std::min(ch, cols - c0);
+    op_order<c128>(ctx, A, nc, src + (long)c0 * ld, ld, tmp, ld, false);
+    GDR_CUDA(cudaMemcpy2DAsync(dst + 2 * (long)c0 * n, n * sizeof(c128), tmp, ld * sizeof(c128), n * sizeof(c128),
+                               nc, kind, ctx->stream));
+  }
+}
+
+gdr_status gdr_autotune(gdr_ctx* ctx, gdr_op* A, gdr_prec prec, int ncol, int m, gdr_tune_result* out) {
+  if (!ctx || !A) return GDR_EINVAL;
+  return guarded(ctx, [&] {
+    GDR_REQUIRE(prec == GDR_PREC_FP64 || prec == GDR_PREC_MIXED, "bad precision");
+    GDR_REQUIRE(ncol >= 1 && ncol <= 65535, "ncol must be in [1, 65535]");
+    GDR_REQUIRE(m >= 0 && m <= GDR_MAX_M, "m must be in [0, GDR_MAX_M]");
+    GDR_REQUIRE(A->kind != OP_CSR_BATCH || ncol % A->nprob == 0,
+                "for a CSR batch ncol must be a multiple of the problem count");
+    GDR_CUDA(cudaSetDevice(ctx->device));
+    gdr_tune_result r{};
+    tune_op(ctx, A, prec, ncol, m, r);
+    if (out) *out = r;
+  });
+}
+
+gdr_status gdr_op_set_shape(gdr_op* A, gdr_prec prec, int ncol, const gdr_shape* shape) {
+  if (!A) return GDR_EINVAL;
+  const int fk = prec == GDR_PREC_FP64 ? 1 : 0;
+  if (!shape) {
+    if (ncol <= 0) {
+      A->mv_tuned.clear();
+      A->sweep_tuned.clear();
+    } else {
+      A->mv_tuned.erase({fk, ncol});
+    }
+    return GDR_OK;
+  }
+  if (ncol < 1) return GDR_EINVAL;
+  MvShape s{shape->form, shape->threads, shape->col_inner ? 1 : 0};
+  if (A->kind == OP_WILSON) {
+    if (s.form == 1 && s.threads != 128) return GDR_EINVAL;
+    if (s.form != 0 && s.form != 1) return GDR_EINVAL;
+    if (s.threads != 64 && s.threads != 128 && s.threads != 256) return GDR_EINVAL;
+  } else {
+    if (s.form != 1 && s.form != 2 && s.form != 4 && s.form != 8) return GDR_EINVAL;
+    if (s.threads != 128 && s.threads != 256) return GDR_EINVAL;
+  }
+  A->mv_tuned[{fk, ncol}] = s;
+  return GDR_OK;
+}
+
+gdr_status gdr_op_get_shape(const gdr_op* A, gdr_prec prec, int ncol, gdr_shape* out) {
+  if (!A || !out || ncol < 1) return GDR_EINVAL;
+  const MvShape s = mv_shape(A->ctx, A, prec == GDR_PREC_FP64, ncol);
+  *out = gdr_shape{s.form, s.threads, s.col_inner};
+  return GDR_OK;
+}
+
+// GDR_FLAG_AUTOTUNE: tune every (precision, columns, m) a solve's stages launch
+// with that the operator has no shape for yet
+static void autotune_stages(gdr_ctx* ctx, const gdr_op* A, const gdr_params& p,
+                            const std::vector<std::array<int, 3>>& keys) {
+  if (!(p.flags & GDR_FLAG_AUTOTUNE)) return;
+  gdr_op* Am = const_cast<gdr_op*>(A);  // the tuned shapes are a cache on the handle
+  for (const auto& k : keys) {
+    if (k[1] < 1 || k[1] > 65535) continue;
+    if (A->mv_tuned.count({k[0], k[1]})) continue;
+    gdr_tune_result r{};
+    tune_op(ctx, Am, k[0] ? GDR_PREC_FP64 : GDR_PREC_MIXED, k[1], k[2], r);
+  }
 }
 
 gdr_status gdr_solve_multishift(gdr_ctx* ctx, const gdr_op* A, int ns, const double* sigma, int nrhs, const double* B,
@@ -264,15 +383,21 @@ gdr_status gdr_solve_multishift(gdr_ctx* ctx, const gdr_op* A, int ns, const dou
     c128* Xi = ctx->get<c128>("api.X", (size_t)ld * ns * nrhs);
     const cudaMemcpyKind kin = (p.flags & GDR_FLAG_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     const cudaMemcpyKind kout = (p.flags & GDR_FLAG_HOST_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-    GDR_CUDA(cudaMemcpy2DAsync(Bi, ld * sizeof(c128), B, n * sizeof(c128), n * sizeof(c128), nrhs, kin,
-                               ctx->stream));
+    stage_in(ctx, A, nrhs, B, Bi, ld, kin);
     const gdr_params pr = resolve_inner_tol(ctx, A->n, p);
+    {
+      const int fi = p.prec == GDR_PREC_FP64 ? 1 : 0, mp = pr.m_proj > 0 ? pr.m_proj : pr.m - pr.k;
+      std::vector<std::array<int, 3>> keys{{fi, 1, pr.m}};
+      if (nrhs > 1) keys.push_back({fi, nrhs - 1, mp});
+      if (!fi && !(p.flags & GDR_FLAG_NO_REFINE)) keys.push_back({0, ns * nrhs, mp});
+      keys.push_back({1, ns * nrhs, 0});
+      autotune_stages(ctx, A, p, keys);
+    }
     if (p.prec == GDR_PREC_MIXED)
       result = solve_pipeline<float>(ctx, A, sig, nrhs, Bi, ld, Xi, ld, pr, defl_out, rep);
     else
       result = solve_pipeline<double>(ctx, A, sig, nrhs, Bi, ld, Xi, ld, pr, defl_out, rep);
-    GDR_CUDA(cudaMemcpy2DAsync(X, n * sizeof(c128), Xi, ld * sizeof(c128), n * sizeof(c128), (size_t)ns * nrhs, kout,
-                               ctx->stream));
+    stage_out(ctx, A, ns * nrhs, Xi, ld, X, kout);
     GDR_CUDA(cudaStreamSynchronize(ctx->stream));
     rep.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     rep.kernel_launches = ctx->launches - launches0;
@@ -310,6 +435,13 @@ gdr_status gdr_solve_batch(gdr_ctx* ctx, const gdr_op* A, int ns, const double* 
       off += nq;
     }
     const gdr_params pr = resolve_inner_tol(ctx, A->n * (long)A->nprob, p);
+    {
+      const int fi = p.prec == GDR_PREC_FP64 ? 1 : 0, mp = pr.m_proj > 0 ? pr.m_proj : pr.m - pr.k;
+      std::vector<std::array<int, 3>> keys{{fi, A->nprob, pr.m}};
+      if (!fi && !(p.flags & GDR_FLAG_NO_REFINE)) keys.push_back({0, A->nprob * ns, mp});
+      keys.push_back({1, A->nprob * ns, 0});
+      autotune_stages(ctx, A, p, keys);
+    }
     if (p.prec == GDR_PREC_MIXED)
       result = solve_batch_pipeline<float>(ctx, A, ns, sig, Bi, Xi, pr, rep, status);
     else
@@ -338,6 +470,7 @@ gdr_status gdr_solve_proj(gdr_ctx* ctx, const gdr_op* A, const gdr_defl* defl, i
     GDR_REQUIRE(params && sigma && B && X, "null argument");
     GDR_REQUIRE(ns >= 1 && nrhs >= 1, "ns and nrhs must be >= 1");
     GDR_REQUIRE(defl->n == A->n, "deflation space size differs from the operator");
+    GDR_REQUIRE(defl->wilson_V == (A->kind == OP_WILSON ? A->V : 0), "deflation space from another operator kind");
     const gdr_params& p = *params;
     check_params(p);
     GDR_CUDA(cudaSetDevice(ctx->device));
@@ -345,13 +478,13 @@ gdr_status gdr_solve_proj(gdr_ctx* ctx, const gdr_op* A, const gdr_defl* defl, i
     const long launches0 = ctx->launches;
     const long n = A->n, ld = pad_ld(n);
     const int mp = p.m_proj > 0 ? p.m_proj : p.m - p.k;
+    autotune_stages(ctx, A, p, {{p.prec == GDR_PREC_FP64 ? 1 : 0, nrhs, mp}});
     std::vector<c128> sig = host_c128(sigma, ns);
     c128* Bi = ctx->get<c128>("api.B", (size_t)ld * nrhs);
     c128* Xi = ctx->get<c128>("api.X", (size_t)ld * ns * nrhs);
     const cudaMemcpyKind kin = (p.flags & GDR_FLAG_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     const cudaMemcpyKind kout = (p.flags & GDR_FLAG_HOST_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-    GDR_CUDA(cudaMemcpy2DAsync(Bi, ld * sizeof(c128), B, n * sizeof(c128), n * sizeof(c128), nrhs, kin,
-                               ctx->stream));
+    stage_in(ctx, A, nrhs, B, Bi, ld, kin);
     GDR_CUDA(cudaMemsetAsync(Xi, 0, sizeof(c128) * ld * ns * nrhs, ctx->stream));
     auto run = [&](auto tag) {
       using R = decltype(tag);
@@ -391,8 +524,7 @@ gdr_status gdr_solve_proj(gdr_ctx* ctx, const gdr_op* A, const gdr_defl* defl, i
       run(float{});
     else
       run(double{});
-    GDR_CUDA(cudaMemcpy2DAsync(X, n * sizeof(c128), Xi, ld * sizeof(c128), n * sizeof(c128), (size_t)ns * nrhs, kout,
-                               ctx->stream));
+    stage_out(ctx, A, ns * nrhs, Xi, ld, X, kout);
     GDR_CUDA(cudaStreamSynchronize(ctx->stream));
     rep.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     rep.kernel_launches = ctx->launches - launches0;
@@ -449,7 +581,10 @@ gdr_status gdr_defl_export(gdr_ctx* ctx, const gdr_defl* defl, double* V, double
   if (!ctx || !defl) return GDR_EINVAL;
   return guarded(ctx, [&] {
     if (k_out) *k_out = defl->k;
-    if (V)
+    if (V && defl->wilson_V)
+      wilson_order<c128>(ctx, defl->wilson_V, defl->k + 1, defl->V128, defl->ldv, reinterpret_cast<c128*>(V),
+                         defl->n, false);
+    else if (V)
       GDR_CUDA(cudaMemcpy2DAsync(V, defl->n * sizeof(c128), defl->V128, defl->ldv * sizeof(c128),
                                  defl->n * sizeof(c128), defl->k + 1, cudaMemcpyDeviceToDevice, ctx->stream));
     if (Hbar) std::memcpy(Hbar, defl->Hk_host.data(), sizeof(c128) * defl->Hk_host.size());
@@ -480,7 +615,14 @@ gdr_status gdr_arnoldi_step(gdr_ctx* ctx, const gdr_op* A, gdr_prec prec, void* 
       b.n = n;
       b.m = j + 1;
       b.ns = 1;
-      b.V = static_cast<cx<R>*>(V);
+      // Wilson: the basis in the library's pair-major order for the step, v_{j+1} back
+      cx<R>* Vu = static_cast<cx<R>*>(V);
+      cx<R>* Vl = Vu;
+      if (A->kind == OP_WILSON) {
+        Vl = ctx->get<cx<R>>("step.Vl", (size_t)n * (j + 2));
+        op_order<cx<R>>(ctx, A, j + 1, Vu, n, Vl, n, true);
+      }
+      b.V = Vl;
       b.ldv = n;
       b.vcs = 0;
       b.W = ctx->get<cx<R>>("step.W", (size_t)pad_ld(n));
@@ -508,6 +650,7 @@ gdr_status gdr_arnoldi_step(gdr_ctx* ctx, const gdr_op* A, gdr_prec prec, void* 
       GDR_CUDA(cudaStreamSynchronize(ctx->stream));
       cx<R>* wl = nullptr;
       arnoldi_step<R>(ctx, A, b, j, j, j, wl);
+      if (Vl != Vu) op_order<cx<R>>(ctx, A, 1, Vl + (long)(j + 1) * n, n, Vu + (long)(j + 1) * n, n, false);
       GDR_CUDA(cudaMemcpyAsync(hcol, b.H + (long)j * (j + 2), sizeof(c128) * (j + 2), cudaMemcpyDeviceToDevice,
                                ctx->stream));
     };

@@ -141,6 +141,20 @@ struct gdr_ctx {
     }
     return b.p;
   }
+  // free every workspace buffer whose name starts with `prefix`
+  void release(const std::string& prefix) {
+    bool any = false;
+    for (auto it = ws.begin(); it != ws.end();) {
+      if (it->first.compare(0, prefix.size(), prefix) == 0) {
+        if (!any) GDR_CUDA(cudaStreamSynchronize(stream));
+        any = true;
+        if (it->second.p) GDR_CUDA(cudaFree(it->second.p));
+        it = ws.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
   template <typename T> T* get(const std::string& name, size_t count) {
     return static_cast<T*>(get(name, count * sizeof(T)));
   }
@@ -156,6 +170,14 @@ struct gdr_ctx {
 };
 
 enum OpKind { OP_CSR = 0, OP_WILSON = 1, OP_CSR_BATCH = 2 };
+
+// Launch shape of the operator kernels: set by the autotuner (gdr_autotune) or the
+// caller (gdr_op_set_shape) per vector precision and column count, else defaults.
+struct MvShape {
+  int form = 0;       // Wilson: 0 one thread per site, 1 direction-split; CSR: threads per row (1, 2, 4, 8)
+  int threads = 128;  // threads per block
+  int col_inner = 0;  // 1: consecutive blocks take one site / row tile for consecutive columns
+};
 
 struct gdr_op {
   gdr_ctx* ctx = nullptr;
@@ -182,6 +204,10 @@ struct gdr_op {
   c128* links128 = nullptr;
   c64* links64 = nullptr;
   __nv_bfloat162* links16 = nullptr;
+  // launch shapes chosen per (FP64 vectors, column count), and the Arnoldi form chosen
+  // per (FP64 vectors, column count, m): 1 persistent sweep, 0 per-phase launches
+  std::map<std::pair<int, int>, MvShape> mv_tuned;
+  std::map<std::pair<int, std::pair<int, int>>, int> sweep_tuned;
 };
 
 struct gdr_defl {
@@ -194,6 +220,7 @@ struct gdr_defl {
   c128* V128 = nullptr;  // FP64 copy (always present), ld = ldv
   c128* Hk = nullptr;    // device (k+1) x k
   std::vector<c128> Hk_host;
+  long wilson_V = 0;     // sites of the Wilson operator it came from (vectors in pair-major order), else 0
 };
 
 // leading dimension for basis vectors: multiple of 64 elements

@@ -128,6 +128,30 @@ void op_apply_skip(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, c
 void op_apply_skip(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, const c64* X, long ldx, c64* Y,
                    long ldy, const c64* B, long ldb, const int* run, int run_stride, int cpp = 1,
                    const double* xs = nullptr, int xs_stride = 0);
+// launch shape of the operator kernels for ncol columns (FP64 or complex64 vectors): the
+// shape set for this column count, else the one set for the nearest count within a
+// factor 2, else the defaults (Wilson: direction-split while one thread per site cannot
+// fill the GPU; CSR: one thread per row)
+MvShape mv_shape(const gdr_ctx* ctx, const gdr_op* A, bool f64, int ncol);
+MvShape mv_default(const gdr_ctx* ctx, const gdr_op* A, int ncol);
+// Vector order: the C interface passes Wilson vectors site-major, the library keeps
+// them pair-major (see wilson.cuh).  to_lib: interface -> library order, else back.
+// Other operators: a plain copy (none when in == out).  in and out must differ.
+template <typename T>
+void op_order(gdr_ctx* ctx, const gdr_op* A, int cols, const T* in, long ldi, T* out, long ldo, bool to_lib);
+// the same for Wilson vectors of V sites (c128)
+template <typename T>
+void wilson_order(gdr_ctx* ctx, long V, int cols, const T* in, long ldi, T* out, long ldo, bool to_lib);
+
+// tune.cu ----------------------------------------------------------------
+// x[:, c] (cols columns of n at stride ld) = counter-based uniform [-1, 1) values (timing inputs)
+template <typename R>
+void fill_uniform(gdr_ctx* ctx, long n, int cols, long ld, cx<R>* x, unsigned long long seed);
+// gdr_autotune: the fastest matvec shape for (prec, ncol), kept on A; with m > 0 the
+// Arnoldi form (sweep / per-phase launches) for (prec, ncol, m)
+gdr_status tune_op(gdr_ctx* ctx, gdr_op* A, gdr_prec prec, int ncol, int m, gdr_tune_result& out);
+// the tuned Arnoldi form: 1 sweep, 0 per-phase launches, -1 not tuned
+int sweep_choice(const gdr_op* A, bool f64, int ncol, int m);
 void op_build_csr_batch(gdr_ctx* ctx, gdr_op* op, const long* n, const long* nnz, const int* rowptr, const int* col,
                         const double* vals);
 void op_build_csr(gdr_ctx* ctx, gdr_op* op, const int* rowptr, const int* col, const double* vals);

@@ -12,6 +12,7 @@
 // Vectors are site-major (site*12 + spin*3 + colour).  Links are stored
 // structure-of-arrays [mu][e][V] (e = a*3 + b) so that a warp's loads of one
 // link element are contiguous.
+#include <cmath>
 #include <type_traits>
 
 #include "common.cuh"
@@ -21,24 +22,57 @@ namespace {
 
 // ------------------------------------------------------------- CSR kernel
 
-template <typename R, typename VT>
+// Block -> (tile, column).  col_inner: consecutive blocks take one tile for
+// consecutive columns, so the tile's links or matrix rows are fetched from HBM
+// once and served from L2 to the other columns' blocks running beside it.
+DEV void tile_col(int ncol, int col_inner, long& tile, int& c) {
+  if (col_inner) {
+    tile = blockIdx.x / ncol;
+    c = (int)(blockIdx.x % ncol);
+  } else {
+    tile = blockIdx.x;
+    c = blockIdx.y;
+  }
+}
+
+// sum over the TPR lanes of a row (TPR consecutive lanes of one warp)
+template <int TPR, typename R>
+DEV cx<R> row_sum(cx<R> acc) {
+  if constexpr (TPR > 1) {
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned mask = ((1u << TPR) - 1u) << (lane & ~(unsigned)(TPR - 1));
+#pragma unroll
+    for (int o = TPR / 2; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(mask, acc.x, o, TPR);
+      acc.y += __shfl_xor_sync(mask, acc.y, o, TPR);
+    }
+  }
+  return acc;
+}
+
+// y_r = (A x)_r with TPR threads per row (blockDim.x / TPR rows per block)
+template <typename R, typename VT, int TPR>
 __global__ void csr_kernel(long n, const int* __restrict__ rowptr, const int* __restrict__ col,
                            const VT* __restrict__ vals, const c128* __restrict__ sigma,
                            const cx<R>* __restrict__ X, long ldx, cx<R>* __restrict__ Y, long ldy,
                            const cx<R>* __restrict__ B, long ldb, const int* __restrict__ run, int run_stride,
-                           int cpp, const double* __restrict__ xs, int xs_stride) {
-  const long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  const int c = blockIdx.y;
-  if (r >= n) return;
+                           int cpp, const double* __restrict__ xs, int xs_stride, int ncol, int col_inner) {
+  long tile;
+  int c;
+  tile_col(ncol, col_inner, tile, c);
+  const long r = tile * (blockDim.x / TPR) + threadIdx.x / TPR;
+  if (r >= n) return;  // uniform over the row's lanes
   if (run && !run[(long)c * run_stride]) return;
   const cx<R>* x = X + c * ldx;
   cx<R> acc = {0, 0};
   const int p0 = rowptr[r], p1 = rowptr[r + 1];
-  for (int p = p0; p < p1; ++p) {
+  for (int p = p0 + (int)(threadIdx.x % TPR); p < p1; p += TPR) {
     VT v = vals[p];
     cx<R> a = {(R)v.x, (R)v.y};
     acc += a * x[col[p]];
   }
+  acc = row_sum<TPR>(acc);
+  if (TPR > 1 && threadIdx.x % TPR) return;
   if (sigma) acc -= cvt<R>(sigma[c]) * x[r];
   if (xs) acc = (R)xs[(long)c * xs_stride] * acc;
   if (B) acc = B[(c / cpp) * ldb + r] - acc;
@@ -46,16 +80,18 @@ __global__ void csr_kernel(long n, const int* __restrict__ rowptr, const int* __
 }
 
 // CSR batch: column c uses problem c / cpp (its own rows, local column indices)
-template <typename R, typename VT>
+template <typename R, typename VT, int TPR>
 __global__ void csr_batch_kernel(const long* __restrict__ rp_off, const long* __restrict__ nz_off,
                                  const int* __restrict__ nrow, const int* __restrict__ rowptr,
                                  const int* __restrict__ col, const VT* __restrict__ vals,
                                  const c128* __restrict__ sigma, const cx<R>* __restrict__ X, long ldx,
                                  cx<R>* __restrict__ Y, long ldy, const cx<R>* __restrict__ B, long ldb,
                                  const int* __restrict__ run, int run_stride, int cpp,
-                                 const double* __restrict__ xs, int xs_stride) {
-  const long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  const int c = blockIdx.y;
+                                 const double* __restrict__ xs, int xs_stride, int ncol, int col_inner) {
+  long tile;
+  int c;
+  tile_col(ncol, col_inner, tile, c);
+  const long r = tile * (blockDim.x / TPR) + threadIdx.x / TPR;
   const int p = c / cpp;
   if (r >= nrow[p]) return;
   if (run && !run[(long)c * run_stride]) return;
@@ -65,10 +101,12 @@ __global__ void csr_batch_kernel(const long* __restrict__ rp_off, const long* __
   const cx<R>* x = X + c * ldx;
   cx<R> acc = {0, 0};
   const int p0 = rp[r], p1 = rp[r + 1];
-  for (int q = p0; q < p1; ++q) {
+  for (int q = p0 + (int)(threadIdx.x % TPR); q < p1; q += TPR) {
     const VT v = vl[q];
     acc += cx<R>{(R)v.x, (R)v.y} * x[cl[q]];
   }
+  acc = row_sum<TPR>(acc);
+  if (TPR > 1 && threadIdx.x % TPR) return;
   if (sigma) acc -= cvt<R>(sigma[c]) * x[r];
   if (xs) acc = (R)xs[(long)c * xs_stride] * acc;
   if (B) acc = B[(long)p * ldb + r] - acc;
@@ -77,24 +115,24 @@ __global__ void csr_batch_kernel(const long* __restrict__ rp_off, const long* __
 
 // ---------------------------------------------------------- Wilson kernel
 
-template <typename R, typename LT>
-__global__ void __launch_bounds__(128) wilson_kernel(const LT* __restrict__ links, int Lx, int Ly, int Lz, int Lt,
-                                                    double diag_a, const c128* __restrict__ sigma,
-                                                    const cx<R>* __restrict__ X, long ldx, cx<R>* __restrict__ Y,
-                                                    long ldy, const cx<R>* __restrict__ B, long ldb,
-                                                    const int* __restrict__ run, int run_stride, int cpp,
-                                                    const double* __restrict__ xs, int xs_stride) {
+template <typename R, typename LT, int NT>
+__global__ void __launch_bounds__(NT) wilson_kernel(const LT* __restrict__ links, int Lx, int Ly, int Lz, int Lt,
+                                                   double diag_a, const c128* __restrict__ sigma,
+                                                   const cx<R>* __restrict__ X, long ldx, cx<R>* __restrict__ Y,
+                                                   long ldy, const cx<R>* __restrict__ B, long ldb,
+                                                   const int* __restrict__ run, int run_stride, int cpp,
+                                                   const double* __restrict__ xs, int xs_stride, int ncol,
+                                                   int col_inner) {
   const long V = (long)Lx * Ly * Lz * Lt;
-  const long site = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  const int c = blockIdx.y;
+  long tile;
+  int c;
+  tile_col(ncol, col_inner, tile, c);
+  const long site = tile * NT + threadIdx.x;
   if (site >= V) return;
   if (run && !run[(long)c * run_stride]) return;
   const cx<R>* x = X + c * ldx;
-  long q = site;
-  const int ix = (int)(q % Lx); q /= Lx;
-  const int iy = (int)(q % Ly); q /= Ly;
-  const int iz = (int)(q % Lz);
-  const int it = (int)(q / Lz);
+  int ix, iy, iz, it;
+  site_coords(site, Lx, Ly, Lz, ix, iy, iz, it);
   Spinor<R> acc;
 #pragma unroll
   for (int i = 0; i < 12; ++i) acc.s[i] = {0, 0};
@@ -104,17 +142,23 @@ __global__ void __launch_bounds__(128) wilson_kernel(const LT* __restrict__ link
   hop_mu<3, R, LT>(links, x, V, site, it, Lt, (long)Lx * Ly * Lz, acc);
   // y = (a - sigma_c) x - H x   [ or b - that ]
   Spinor<R> p;
-  load_spinor<R>(x, site, p);
+  load_spinor<R>(x, V, site, p);
   const c128 sg = sigma ? sigma[c] : c128{0.0, 0.0};
   const cx<R> dg = {(R)(diag_a - sg.x), (R)(-sg.y)};
-  cx<R>* y = Y + c * ldy + site * 12;
-  const cx<R>* b = B ? B + (c / cpp) * ldb + site * 12 : nullptr;
+  cx<R>* y = Y + c * ldy;
   const R sc = xs ? (R)xs[(long)c * xs_stride] : R(1);
+  const cx<R>* b = B ? B + (c / cpp) * ldb : nullptr;
 #pragma unroll
-  for (int i = 0; i < 12; ++i) {
-    cx<R> v = sc * (dg * p.s[i] - acc.s[i]);
-    if (b) v = b[i] - v;
-    y[i] = v;
+  for (int i = 0; i < 6; ++i) {
+    cx<R> v0 = sc * (dg * p.s[2 * i] - acc.s[2 * i]);
+    cx<R> v1 = sc * (dg * p.s[2 * i + 1] - acc.s[2 * i + 1]);
+    if (b) {
+      cx<R> b0, b1;
+      load_pair<R>(b, V, site, i, b0, b1);
+      v0 = b0 - v0;
+      v1 = b1 - v1;
+    }
+    store_pair<R>(y, V, site, i, v0, v1);
   }
 }
 
@@ -130,23 +174,23 @@ __global__ void __launch_bounds__(128) wilson_split_kernel(const LT* __restrict_
                                                           cx<R>* __restrict__ Y, long ldy,
                                                           const cx<R>* __restrict__ B, long ldb,
                                                           const int* __restrict__ run, int run_stride, int cpp,
-                                                          const double* __restrict__ xs, int xs_stride) {
+                                                          const double* __restrict__ xs, int xs_stride, int ncol,
+                                                          int col_inner) {
   __shared__ cx<R> part[4][32][13];  // odd row length: conflict-free in both phases
   const long V = (long)Lx * Ly * Lz * Lt;
-  const int c = blockIdx.y;
+  long tile;
+  int c;
+  tile_col(ncol, col_inner, tile, c);
   if (run && !run[(long)c * run_stride]) return;
   const int mu = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long site0 = blockIdx.x * 32L, site = site0 + lane;
+  const long site0 = tile * 32L, site = site0 + lane;
   const cx<R>* x = X + c * ldx;
   Spinor<R> acc;
 #pragma unroll
   for (int i = 0; i < 12; ++i) acc.s[i] = {0, 0};
   if (site < V) {
-    long q = site;
-    const int ix = (int)(q % Lx); q /= Lx;
-    const int iy = (int)(q % Ly); q /= Ly;
-    const int iz = (int)(q % Lz);
-    const int it = (int)(q / Lz);
+    int ix, iy, iz, it;
+    site_coords(site, Lx, Ly, Lz, ix, iy, iz, it);
     switch (mu) {  // uniform in the warp
       case 0: hop_mu<0, R, LT>(links, x, V, site, ix, Lx, 1, acc); break;
       case 1: hop_mu<1, R, LT>(links, x, V, site, iy, Ly, (long)Lx, acc); break;
@@ -161,12 +205,13 @@ __global__ void __launch_bounds__(128) wilson_split_kernel(const LT* __restrict_
   const cx<R> dg = {(R)(diag_a - sg.x), (R)(-sg.y)};
   cx<R>* y = Y + c * ldy;
   const cx<R>* b = B ? B + (c / cpp) * ldb : nullptr;
-  const long nout = min(32L, V - site0) * 12;
   const R sc = xs ? (R)xs[(long)c * xs_stride] : R(1);
-  for (int q = threadIdx.x; q < nout; q += 128) {
-    const int sl = q / 12, comp = q % 12;
+  // output element q: pair q / 64, site q % 64 / 2, half q % 2 (64 consecutive elements of a pair)
+  for (int q = threadIdx.x; q < 6 * 64; q += 128) {
+    const int pr = q >> 6, sl = (q & 63) >> 1, comp = 2 * pr + (q & 1);
+    if (site0 + sl >= V) continue;
     const cx<R> h = part[0][sl][comp] + part[1][sl][comp] + part[2][sl][comp] + part[3][sl][comp];
-    const long e = site0 * 12 + q;
+    const long e = 2 * ((long)pr * V + site0) + (q & 63);
     cx<R> v = sc * (dg * x[e] - h);
     if (b) v = b[e] - v;
     y[e] = v;
@@ -203,70 +248,110 @@ static void op_apply_impl(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* s
   }
 }
 
+MvShape mv_default(const gdr_ctx* ctx, const gdr_op* A, int ncol);
+
+MvShape mv_shape(const gdr_ctx* ctx, const gdr_op* A, bool f64, int ncol) {
+  const int fk = f64 ? 1 : 0;
+  auto it = A->mv_tuned.find({fk, ncol});
+  if (it != A->mv_tuned.end()) return it->second;
+  const MvShape* near = nullptr;
+  double best = std::log(2.0) + 1e-9;
+  for (const auto& kv : A->mv_tuned) {
+    if (kv.first.first != fk) continue;
+    const double r = std::fabs(std::log((double)kv.first.second / (double)ncol));
+    if (r <= best) {
+      best = r;
+      near = &kv.second;
+    }
+  }
+  if (near) return *near;
+  return mv_default(ctx, A, ncol);
+}
+
+MvShape mv_default(const gdr_ctx* ctx, const gdr_op* A, int ncol) {
+  MvShape s;
+  if (A->kind == OP_WILSON) {
+    // too few sites for one thread per site: direction-split form
+    s.form = ((A->V + 127) / 128 * ncol < 2L * ctx->num_sms) ? 1 : 0;
+    s.threads = 128;
+  } else {
+    s.form = 1;
+    s.threads = 256;
+  }
+  s.col_inner = 0;
+  return s;
+}
+
+// grid of `tiles` tiles for ncol columns in the shape's column order
+static dim3 tile_grid(long tiles, int ncol, int col_inner) {
+  return col_inner ? dim3((unsigned)(tiles * ncol), 1) : dim3((unsigned)tiles, (unsigned)ncol);
+}
+
+template <typename R, typename VT, int TPR>
+static void csr_launch(gdr_ctx* ctx, const gdr_op* A, const VT* vals, const MvShape& s, int ncol, const c128* sigma,
+                       const cx<R>* X, long ldx, cx<R>* Y, long ldy, const cx<R>* B, long ldb, const int* run,
+                       int run_stride, int cpp, const double* xs, int xs_stride) {
+  const long rows = s.threads / TPR;
+  const dim3 grid = tile_grid((A->n + rows - 1) / rows, ncol, s.col_inner);  // A->n: largest problem of a batch
+  if (A->kind == OP_CSR)
+    csr_kernel<R, VT, TPR><<<grid, s.threads, 0, ctx->stream>>>(A->n, A->rowptr, A->col, vals, sigma, X, ldx, Y, ldy,
+                                                                 B, ldb, run, run_stride, cpp, xs, xs_stride, ncol,
+                                                                 s.col_inner);
+  else
+    csr_batch_kernel<R, VT, TPR><<<grid, s.threads, 0, ctx->stream>>>(
+        A->rp_off, A->nz_off, A->nrow, A->rowptr, A->col, vals, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride, cpp,
+        xs, xs_stride, ncol, s.col_inner);
+  GDR_LAUNCHED(ctx);
+}
+
+template <typename R, typename LT>
+static void wilson_launch(gdr_ctx* ctx, const gdr_op* A, const LT* links, const MvShape& s, int ncol,
+                          const c128* sigma, const cx<R>* X, long ldx, cx<R>* Y, long ldy, const cx<R>* B, long ldb,
+                          const int* run, int run_stride, int cpp, const double* xs, int xs_stride) {
+  const int* d = A->dims;
+  if (s.form == 1) {
+    wilson_split_kernel<R, LT><<<tile_grid((A->V + 31) / 32, ncol, s.col_inner), 128, 0, ctx->stream>>>(
+        links, d[0], d[1], d[2], d[3], A->diag_a, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride, cpp, xs, xs_stride,
+        ncol, s.col_inner);
+  } else {
+#define GDR_WILSON_SITE(NT)                                                                                         \
+  wilson_kernel<R, LT, NT><<<tile_grid((A->V + NT - 1) / NT, ncol, s.col_inner), NT, 0, ctx->stream>>>(             \
+      links, d[0], d[1], d[2], d[3], A->diag_a, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride, cpp, xs, xs_stride, \
+      ncol, s.col_inner)
+    if (s.threads == 64) GDR_WILSON_SITE(64);
+    else if (s.threads == 256) GDR_WILSON_SITE(256);
+    else GDR_WILSON_SITE(128);
+#undef GDR_WILSON_SITE
+  }
+  GDR_LAUNCHED(ctx);
+}
+
 template <typename R>
 static void op_apply_launch(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, const cx<R>* X, long ldx,
                             cx<R>* Y, long ldy, const cx<R>* B, long ldb, const int* run, int run_stride, int cpp,
-                          const double* xs, int xs_stride) {
+                            const double* xs, int xs_stride) {
   constexpr bool F64 = std::is_same<R, double>::value;
-  if (A->kind == OP_CSR) {
-    dim3 grid((unsigned)((A->n + 255) / 256), (unsigned)ncol);
-    if (F64) {
-      csr_kernel<double, c128><<<grid, 256, 0, ctx->stream>>>(
-          A->n, A->rowptr, A->col, A->vals128, sigma, (const c128*)X, ldx, (c128*)Y, ldy, (const c128*)B, ldb, run,
-          run_stride, cpp, xs, xs_stride);
-    } else {
-      csr_kernel<float, c64><<<grid, 256, 0, ctx->stream>>>(A->n, A->rowptr, A->col, A->vals64, sigma,
-                                                             (const c64*)X, ldx, (c64*)Y, ldy, (const c64*)B, ldb,
-                                                             run, run_stride, cpp, xs, xs_stride);
+  const MvShape s = mv_shape(ctx, A, F64, ncol);
+  if (A->kind == OP_CSR || A->kind == OP_CSR_BATCH) {
+    using VT = typename std::conditional<F64, c128, c64>::type;
+    const VT* vals;
+    if constexpr (F64) vals = A->vals128;
+    else vals = A->vals64;
+    switch (s.form) {
+      case 2: csr_launch<R, VT, 2>(ctx, A, vals, s, ncol, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride, cpp, xs, xs_stride); break;
+      case 4: csr_launch<R, VT, 4>(ctx, A, vals, s, ncol, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride, cpp, xs, xs_stride); break;
+      case 8: csr_launch<R, VT, 8>(ctx, A, vals, s, ncol, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride, cpp, xs, xs_stride); break;
+      default: csr_launch<R, VT, 1>(ctx, A, vals, s, ncol, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride, cpp, xs, xs_stride); break;
     }
-    GDR_LAUNCHED(ctx);
-  } else if (A->kind == OP_CSR_BATCH) {
-    dim3 grid((unsigned)((A->n + 255) / 256), (unsigned)ncol);  // A->n = largest problem
-    if (F64) {
-      csr_batch_kernel<double, c128><<<grid, 256, 0, ctx->stream>>>(
-          A->rp_off, A->nz_off, A->nrow, A->rowptr, A->col, A->vals128, sigma, (const c128*)X, ldx, (c128*)Y, ldy,
-          (const c128*)B, ldb, run, run_stride, cpp, xs, xs_stride);
-    } else {
-      csr_batch_kernel<float, c64><<<grid, 256, 0, ctx->stream>>>(
-          A->rp_off, A->nz_off, A->nrow, A->rowptr, A->col, A->vals64, sigma, (const c64*)X, ldx, (c64*)Y, ldy,
-          (const c64*)B, ldb, run, run_stride, cpp, xs, xs_stride);
-    }
-    GDR_LAUNCHED(ctx);
-  } else if ((A->V + 127) / 128 * ncol < 2L * ctx->num_sms) {
-    // too few sites for one thread per site: direction-split form
-    dim3 grid((unsigned)((A->V + 31) / 32), (unsigned)ncol);
-    const int* d = A->dims;
-    if (F64) {
-      wilson_split_kernel<double, c128><<<grid, 128, 0, ctx->stream>>>(
-          A->links128, d[0], d[1], d[2], d[3], A->diag_a, sigma, (const c128*)X, ldx, (c128*)Y, ldy, (const c128*)B,
-          ldb, run, run_stride, cpp, xs, xs_stride);
-    } else if (A->store == GDR_LINK_BF16) {
-      wilson_split_kernel<float, __nv_bfloat162><<<grid, 128, 0, ctx->stream>>>(
-          A->links16, d[0], d[1], d[2], d[3], A->diag_a, sigma, (const c64*)X, ldx, (c64*)Y, ldy, (const c64*)B, ldb,
-          run, run_stride, cpp, xs, xs_stride);
-    } else {
-      wilson_split_kernel<float, c64><<<grid, 128, 0, ctx->stream>>>(
-          A->links64, d[0], d[1], d[2], d[3], A->diag_a, sigma, (const c64*)X, ldx, (c64*)Y, ldy, (const c64*)B, ldb,
-          run, run_stride, cpp, xs, xs_stride);
-    }
-    GDR_LAUNCHED(ctx);
+  } else if constexpr (F64) {
+    wilson_launch<R, c128>(ctx, A, A->links128, s, ncol, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride, cpp, xs,
+                           xs_stride);
+  } else if (A->store == GDR_LINK_BF16) {
+    wilson_launch<R, __nv_bfloat162>(ctx, A, A->links16, s, ncol, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride, cpp,
+                                     xs, xs_stride);
   } else {
-    dim3 grid((unsigned)((A->V + 127) / 128), (unsigned)ncol);
-    const int* d = A->dims;
-    if (F64) {
-      wilson_kernel<double, c128><<<grid, 128, 0, ctx->stream>>>(A->links128, d[0], d[1], d[2], d[3], A->diag_a,
-                                                                 sigma, (const c128*)X, ldx, (c128*)Y, ldy,
-                                                                 (const c128*)B, ldb, run, run_stride, cpp, xs, xs_stride);
-    } else if (A->store == GDR_LINK_BF16) {
-      wilson_kernel<float, __nv_bfloat162><<<grid, 128, 0, ctx->stream>>>(
-          A->links16, d[0], d[1], d[2], d[3], A->diag_a, sigma, (const c64*)X, ldx, (c64*)Y, ldy, (const c64*)B, ldb,
-          run, run_stride, cpp, xs, xs_stride);
-    } else {
-      wilson_kernel<float, c64><<<grid, 128, 0, ctx->stream>>>(A->links64, d[0], d[1], d[2], d[3], A->diag_a, sigma,
-                                                               (const c64*)X, ldx, (c64*)Y, ldy, (const c64*)B, ldb,
-                                                               run, run_stride, cpp, xs, xs_stride);
-    }
-    GDR_LAUNCHED(ctx);
+    wilson_launch<R, c64>(ctx, A, A->links64, s, ncol, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride, cpp, xs,
+                          xs_stride);
   }
 }
 
@@ -290,6 +375,49 @@ template void op_apply<double>(gdr_ctx*, const gdr_op*, int, const c128*, const 
                                long, int);
 template void op_apply<float>(gdr_ctx*, const gdr_op*, int, const c128*, const c64*, long, c64*, long, const c64*,
                               long, int);
+
+// ------------------------------------------ vector order at the C interface
+
+namespace {
+// site-major (s*12 + q) <-> pair-major (2 ((q/2) V + s) + q%2) Wilson vectors; the
+// pair-major side is walked contiguously
+template <typename T>
+__global__ void wilson_order_kernel(long V, const T* __restrict__ in, long ldi, T* __restrict__ out, long ldo,
+                                    int to_lib) {
+  const int c = blockIdx.y;
+  const long n = 12 * V;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const long pv = i >> 1;
+    const long p = pv / V, site = pv - p * V;
+    const long u = site * 12 + 2 * p + (i & 1);
+    if (to_lib) out[c * ldo + i] = in[c * ldi + u];
+    else out[c * ldo + u] = in[c * ldi + i];
+  }
+}
+}  // namespace
+
+template <typename T>
+void wilson_order(gdr_ctx* ctx, long V, int cols, const T* in, long ldi, T* out, long ldo, bool to_lib) {
+  if (cols <= 0) return;
+  GDR_REQUIRE(in != out, "vector reordering needs distinct buffers");
+  dim3 grid((unsigned)std::min<long>((12 * V + 255) / 256, 8L * ctx->num_sms), (unsigned)cols);
+  wilson_order_kernel<T><<<grid, 256, 0, ctx->stream>>>(V, in, ldi, out, ldo, to_lib ? 1 : 0);
+  GDR_LAUNCHED(ctx);
+}
+template void wilson_order<c128>(gdr_ctx*, long, int, const c128*, long, c128*, long, bool);
+
+template <typename T>
+void op_order(gdr_ctx* ctx, const gdr_op* A, int cols, const T* in, long ldi, T* out, long ldo, bool to_lib) {
+  if (cols <= 0) return;
+  if (A->kind == OP_WILSON) {
+    wilson_order<T>(ctx, A->V, cols, in, ldi, out, ldo, to_lib);
+  } else if (in != out) {
+    GDR_CUDA(cudaMemcpy2DAsync(out, ldo * sizeof(T), in, ldi * sizeof(T), A->n * sizeof(T), cols,
+                               cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+}
+template void op_order<c128>(gdr_ctx*, const gdr_op*, int, const c128*, long, c128*, long, bool);
+template void op_order<c64>(gdr_ctx*, const gdr_op*, int, const c64*, long, c64*, long, bool);
 
 // ------------------------------------------------------ operator creation
 

@@ -257,7 +257,8 @@ DrResult dr_sh(gdr_ctx* ctx, const gdr_op* A, const DrJob<R>& job, bool use_grap
   GDR_LAUNCHED(ctx);
   start_cycle<R>(ctx, b, job.rhs, job.ldrhs);
 
-  const bool sweep = job.sweep && sweep_fits<R>(ctx, A, b);
+  const bool sweep = job.sweep && sweep_fits<R>(ctx, A, b) &&
+                    sweep_choice(A, std::is_same<R, double>::value, ncol, m) != 0;
   if (sweep) sweep_reserve<R>(ctx, b);
   Graph g_first, g_next;
   DrResult res;
@@ -323,6 +324,78 @@ DrResult dr_sh(gdr_ctx* ctx, const gdr_op* A, const DrJob<R>& job, bool use_grap
   return res;
 }
 
+template <typename R>
+void tune_arnoldi(gdr_ctx* ctx, const gdr_op* A, int ncol, int m, double& t_sweep, double& t_launch, int& choice) {
+  t_sweep = t_launch = 0;
+  choice = -1;
+  Batch<R> probe;  // sizes only: no workspace unless the sweep applies
+  probe.n = A->n;
+  probe.ncol = ncol;
+  probe.m = m;
+  if (!sweep_fits<R>(ctx, A, probe)) return;
+  Batch<R> b = make_batch<R>(ctx, "tune", A->n, ncol, m, 1);
+  if (A->kind == OP_CSR_BATCH) {  // column c: problem c / cpp, its own length
+    b.cpp = ncol / A->nprob;
+    std::vector<int> nv(ncol);
+    for (int c = 0; c < ncol; ++c) nv[c] = (int)A->nrow_host[c / b.cpp];
+    int* nvd = ctx->get<int>("tune.nvec", (size_t)ncol);
+    GDR_CUDA(cudaMemcpyAsync(nvd, nv.data(), sizeof(int) * ncol, cudaMemcpyHostToDevice, ctx->stream));
+    b.nvec = nvd;
+  }
+  if (!sweep_fits<R>(ctx, A, b)) return;
+  sweep_reserve<R>(ctx, b);
+  Shifted sh = make_shifted(ctx, "tune", ncol, 1);
+  cx<R>* r = ctx->get<cx<R>>("tune.r", (size_t)b.ldv * ncol);
+  double* bn2 = ctx->get<double>("tune.bn2", (size_t)ncol + 4);
+  double* tolv = ctx->get<double>("tune.tol", (size_t)ncol + 4);
+  GDR_CUDA(cudaMemsetAsync(tolv, 0, sizeof(double) * ncol, ctx->stream));
+  GDR_CUDA(cudaMemsetAsync(r, 0, sizeof(cx<R>) * b.ldv * ncol, ctx->stream));
+  fill_uniform<R>(ctx, b.n, ncol, b.ldv, r, 0x7a11ull);
+  norms2<cx<R>>(ctx, b.n, ncol, r, b.ldv, bn2, b.part, b.nblk, b.cnt, b.nvec);
+  init_cols_kernel<<<(ncol + 31) / 32, 32, 0, ctx->stream>>>(b.st, ncol, bn2, tolv, nullptr, 1, sh.sact, sh.beta,
+                                                              sh.gamma, sh.norms);
+  GDR_LAUNCHED(ctx);
+  start_cycle<R>(ctx, b, r, b.ldv);
+  // one pass j = 0..m-1 in either form, from the same v_0 each time
+  auto pass = [&](bool sw) {
+    set_run_kernel<<<(ncol + 31) / 32, 32, 0, ctx->stream>>>(b.st, ncol);
+    GDR_LAUNCHED(ctx);
+    if (sw) {
+      arnoldi_sweep<R>(ctx, A, b, 0, m);
+      scale_into<R>(ctx, b, m, b.W2, b.wcs);
+    } else {
+      cx<R>* wl = nullptr;
+      for (int j = 0; j < m; ++j) arnoldi_step<R>(ctx, A, b, j, 0, m - 1, wl);
+    }
+  };
+  Graph gs, gl;
+  auto timed = [&](bool sw) {
+    Graph& g = sw ? gs : gl;
+    run_cycle(ctx, true, g, [&] { pass(sw); });  // capture + warm-up
+    cudaEvent_t e0, e1;
+    GDR_CUDA(cudaEventCreate(&e0));
+    GDR_CUDA(cudaEventCreate(&e1));
+    const int reps = 5;
+    GDR_CUDA(cudaEventRecord(e0, ctx->stream));
+    for (int q = 0; q < reps; ++q) run_cycle(ctx, true, g, [&] { pass(sw); });
+    GDR_CUDA(cudaEventRecord(e1, ctx->stream));
+    GDR_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    GDR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return (double)ms / reps;
+  };
+  t_sweep = timed(true);
+  t_launch = timed(false);
+  const std::vector<ColState> st = read_states(ctx, b.st, ncol);
+  for (int c = 0; c < ncol; ++c)
+    if (st[c].nan || st[c].err) throw gdr_error(GDR_ECUDA, "autotune: Arnoldi pass on random vectors failed");
+  choice = t_sweep <= t_launch ? 1 : 0;
+}
+template void tune_arnoldi<float>(gdr_ctx*, const gdr_op*, int, int, double&, double&, int&);
+template void tune_arnoldi<double>(gdr_ctx*, const gdr_op*, int, int, double&, double&, int&);
+
 // ------------------------------------------------- GMRES(m_p)-Proj(k)-Sh
 
 template <typename R>
@@ -376,7 +449,8 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
   d.st = b.st;
   d.want_r = true;
 
-  const bool sweep = job.sweep && sweep_fits<R>(ctx, A, b);
+  const bool sweep = job.sweep && sweep_fits<R>(ctx, A, b) &&
+                    sweep_choice(A, std::is_same<R, double>::value, ncol, mp) != 0;
   if (sweep) sweep_reserve<R>(ctx, b);
   Graph gr;
   ProjResult res;
@@ -558,6 +632,7 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
     df->ldv = ld;
     df->k = kd;
     df->prec = mixed ? GDR_PREC_MIXED : GDR_PREC_FP64;
+    df->wilson_V = A->kind == OP_WILSON ? A->V : 0;
     GDR_CUDA(cudaMalloc(&df->V128, sizeof(c128) * ld * (kd + 1)));
     GDR_CUDA(cudaMalloc(&df->V, sizeof(cx<R>) * ld * (kd + 1)));
     GDR_CUDA(cudaMalloc(&df->Hk, sizeof(c128) * (kd + 1) * kd));

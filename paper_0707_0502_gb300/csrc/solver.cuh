@@ -70,6 +70,12 @@ struct ProjResult {
   std::vector<c128> gamma;     // accumulated gamma_i per column (eq. keyder2), diagnostic
 };
 
+// Time one Arnoldi pass of m steps on ncol columns of A (random start vectors) as the
+// persistent sweep and as per-phase launches, each replayed from a CUDA graph.
+// choice: 1 sweep faster, 0 launches faster, -1 the sweep does not fit (not timed).
+template <typename R>
+void tune_arnoldi(gdr_ctx* ctx, const gdr_op* A, int ncol, int m, double& t_sweep, double& t_launch, int& choice);
+
 template <typename R>
 DrResult dr_sh(gdr_ctx* ctx, const gdr_op* A, const DrJob<R>& job, bool use_graph);
 

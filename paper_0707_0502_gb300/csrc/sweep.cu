@@ -173,11 +173,8 @@ DEV void phase_matvec(const SweepArgs<R>& a, int j, bool lazy, unsigned char* sm
 #pragma unroll
         for (int i = 0; i < 12; ++i) acc.s[i] = {0, 0};
         if (site < V) {
-          long q = site;
-          const int ix = (int)(q % a.Lx); q /= a.Lx;
-          const int iy = (int)(q % a.Ly); q /= a.Ly;
-          const int iz = (int)(q % a.Lz);
-          const int itt = (int)(q / a.Lz);
+          int ix, iy, iz, itt;
+          site_coords(site, a.Lx, a.Ly, a.Lz, ix, iy, iz, itt);
           switch (mu) {
             case 0: hop_mu<0, R, LT, true>(links, x, V, site, ix, a.Lx, 1, acc); break;
             case 1: hop_mu<1, R, LT, true>(links, x, V, site, iy, a.Ly, (long)a.Lx, acc); break;
@@ -192,12 +189,13 @@ DEV void phase_matvec(const SweepArgs<R>& a, int j, bool lazy, unsigned char* sm
       if (live) {
         const cx<R> dg = {(R)a.diag_a, R(0)};
         cx<R>* y = b.W + c * b.wcs;
-        const long nout = min(32L, V - site0) * 12;
-        for (int q = ht; q < nout; q += 128) {
-          const int sl = q / 12, comp = q % 12;
+        // output element q: pair q / 64, site q % 64 / 2, half q % 2 (pair-major vector order)
+        for (int q = ht; q < 6 * 64; q += 128) {
+          const int pr = q >> 6, sl = (q & 63) >> 1, comp = 2 * pr + (q & 1);
+          if (site0 + sl >= V) continue;
           const cx<R> h = part[4 * half][sl][comp] + part[4 * half + 1][sl][comp] + part[4 * half + 2][sl][comp] +
                           part[4 * half + 3][sl][comp];
-          const long e = site0 * 12 + q;
+          const long e = 2 * ((long)pr * V + site0) + (q & 63);
           cx<R> xv;
           if constexpr (sizeof(R) == 4) {
             const float2 t = __ldcg(reinterpret_cast<const float2*>(x) + e);

@@ -3,8 +3,12 @@
 //   (H psi)(x) = sum_mu (1 - gamma_mu) U_mu(x) psi(x+mu) + (1 + gamma_mu) U_mu(x-mu)^H psi(x-mu),
 // with gamma_mu = [[0, B_mu], [B_mu^H, 0]], B_mu unitary 2x2, so that
 //   (1 -+ gamma_mu) psi = [h ; -+ B_mu^H h],  h = u -+ B_mu d,  psi = [u ; d].
-// Vectors are site-major (site*12 + spin*3 + colour); links are stored
-// structure-of-arrays [mu][a*3+b][site].
+// Inside the library a Wilson vector is stored in pair-major order: component
+// q = spin*3 + colour of site s is complex element 2 ((q/2) V + s) + q%2, so the
+// pair (2p, 2p+1) of consecutive sites is contiguous (one float4 per site for
+// complex64, two double2 for complex128) and a warp's loads of one pair are
+// coalesced.  The C interface uses site-major order (s*12 + q); wilson_order
+// converts at the boundary.  Links are stored structure-of-arrays [mu][a*3+b][site].
 #pragma once
 
 #include <cuda_bf16.h>
@@ -57,23 +61,59 @@ template <typename R> struct Spinor { cx<R> s[12]; };
 template <bool CG> DEV float4 ld4(const float4* p) { return CG ? __ldcg(p) : __ldg(p); }
 template <bool CG> DEV double2 ld2(const double2* p) { return CG ? __ldcg(p) : __ldg(p); }
 
-template <typename R, bool CG = false> DEV void load_spinor(const cx<R>* x, long site, Spinor<R>& p) {
+// element index of component q of site s (pair-major order)
+HD long wil_index(long V, long site, int q) { return 2 * ((long)(q >> 1) * V + site) + (q & 1); }
+
+template <typename R, bool CG = false> DEV void load_spinor(const cx<R>* x, long V, long site, Spinor<R>& p) {
   if constexpr (sizeof(R) == 4) {
-    const float4* q = reinterpret_cast<const float4*>(x + site * 12);
+    const float4* q = reinterpret_cast<const float4*>(x) + site;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-      const float4 v = ld4<CG>(q + i);
+      const float4 v = ld4<CG>(q + i * V);
       p.s[2 * i] = {v.x, v.y};
       p.s[2 * i + 1] = {v.z, v.w};
     }
   } else {
-    const double2* q = reinterpret_cast<const double2*>(x + site * 12);
+    const double2* q = reinterpret_cast<const double2*>(x) + 2 * site;
 #pragma unroll
-    for (int i = 0; i < 12; ++i) {
-      const double2 v = ld2<CG>(q + i);
-      p.s[i] = {v.x, v.y};
+    for (int i = 0; i < 6; ++i) {
+      const double2 a = ld2<CG>(q + 2 * i * V), b = ld2<CG>(q + 2 * i * V + 1);
+      p.s[2 * i] = {a.x, a.y};
+      p.s[2 * i + 1] = {b.x, b.y};
     }
   }
+}
+
+// components (2p, 2p+1) of site s
+template <typename R> DEV void load_pair(const cx<R>* x, long V, long site, int p, cx<R>& a, cx<R>& b) {
+  if constexpr (sizeof(R) == 4) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(x) + p * V + site);
+    a = {v.x, v.y};
+    b = {v.z, v.w};
+  } else {
+    const double2* q = reinterpret_cast<const double2*>(x) + 2 * (p * V + site);
+    const double2 u = __ldg(q), w = __ldg(q + 1);
+    a = {u.x, u.y};
+    b = {w.x, w.y};
+  }
+}
+template <typename R> DEV void store_pair(cx<R>* y, long V, long site, int p, cx<R> a, cx<R> b) {
+  if constexpr (sizeof(R) == 4) {
+    reinterpret_cast<float4*>(y)[p * V + site] = make_float4(a.x, a.y, b.x, b.y);
+  } else {
+    double2* q = reinterpret_cast<double2*>(y) + 2 * (p * V + site);
+    q[0] = make_double2(a.x, a.y);
+    q[1] = make_double2(b.x, b.y);
+  }
+}
+
+// lattice coordinates of a site (32-bit division: V < 2^31)
+DEV void site_coords(long site, int Lx, int Ly, int Lz, int& ix, int& iy, int& iz, int& it) {
+  unsigned q = (unsigned)site;
+  ix = (int)(q % (unsigned)Lx); q /= (unsigned)Lx;
+  iy = (int)(q % (unsigned)Ly); q /= (unsigned)Ly;
+  iz = (int)(q % (unsigned)Lz);
+  it = (int)(q / (unsigned)Lz);
 }
 
 // one hop in direction MU; FWD: (1 - gamma) U(x) psi(x+mu), else (1 + gamma) U(x-mu)^H psi(x-mu)
@@ -125,8 +165,8 @@ DEV void hop_mu(const LT* __restrict__ links, const cx<R>* x, long V, long site,
   const long fwd = (coord == L - 1) ? site - (long)(L - 1) * stride : site + stride;
   const long bwd = (coord == 0) ? site + (long)(L - 1) * stride : site - stride;
   Spinor<R> pf, pb;  // both neighbour spinors in flight before either hop's arithmetic
-  load_spinor<R, CG>(x, fwd, pf);
-  load_spinor<R, CG>(x, bwd, pb);
+  load_spinor<R, CG>(x, V, fwd, pf);
+  load_spinor<R, CG>(x, V, bwd, pb);
   hop<MU, true, R, LT>(links, V, site, pf, acc);
   hop<MU, false, R, LT>(links, V, bwd, pb, acc);
 }
