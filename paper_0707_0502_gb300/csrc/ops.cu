@@ -115,8 +115,16 @@ __global__ void csr_batch_kernel(const long* __restrict__ rp_off, const long* __
 
 // ---------------------------------------------------------- Wilson kernel
 
+// Resident warps: the matvec is bound by the latency of its neighbour gathers, so
+// the registers are capped for 24 resident warps per SM (complex64: 80 registers)
+// or 16 (complex128: 128 registers) instead of the compiler's choice (16 warps).
+template <typename R>
+constexpr int wilson_min_blocks(int nt) {
+  return (sizeof(R) == 4 ? 768 : 512) / nt;
+}
+
 template <typename R, typename LT, int NT>
-__global__ void __launch_bounds__(NT) wilson_kernel(const LT* __restrict__ links, int Lx, int Ly, int Lz, int Lt,
+__global__ void __launch_bounds__(NT, wilson_min_blocks<R>(NT)) wilson_kernel(const LT* __restrict__ links, int Lx, int Ly, int Lz, int Lt,
                                                    double diag_a, const c128* __restrict__ sigma,
                                                    const cx<R>* __restrict__ X, long ldx, cx<R>* __restrict__ Y,
                                                    long ldy, const cx<R>* __restrict__ B, long ldb,
