@@ -43,6 +43,17 @@ def parse():
     ap.add_argument("--config", type=int, default=CONFIG_ID)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-scale", action="store_true", help="skip the large-lattice kernel measurements")
+    ap.add_argument("--kernels-only", metavar="LATTICE", default=None,
+                    help="only the large-lattice kernel measurements of one lattice (16x16x16x16 or 24x24x24x32), "
+                         "default launch shapes (no autotuning): the profiling entry point")
+    ap.add_argument("--links", choices=["c64", "bf16"], default=None,
+                    help="with --kernels-only: link storage (default: the lattice's own)")
+    ap.add_argument("--arnoldi-form", choices=["tuned", "launches", "sweep"], default="tuned",
+                    help="Arnoldi form of the short-vector cycles: chosen by the autotuner (default), or pinned "
+                         "(profiling runs pin the form the plain run chose: serialised launches under ncu "
+                         "would bias the tuner)")
+    ap.add_argument("--matvec-only", action="store_true",
+                    help="with --kernels-only: the matvecs alone (no Arnoldi-step basis on the device)")
     return ap.parse_args()
 
 
@@ -191,6 +202,18 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
+    if args.kernels_only:
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        import paper_0707_0502_gb300 as g
+        stream = torch.cuda.Stream()
+        ctx = g.gdr_create(0, stream)
+        out = kernels_at_scale(g, ctx, stream, only=args.kernels_only, link_store=args.links, tune=False,
+                               step=not args.matvec_only)
+        print(json.dumps({"kernels_at_scale": out}), flush=True)
+        g.gdr_destroy(ctx)
+        return
     import torch
     import torch.distributed as dist
 
@@ -219,9 +242,11 @@ def main():
     stream.synchronize()
     # launch shapes: the first-stage matvec and Arnoldi form tuned here (reported), every
     # other stage's by GDR_FLAG_AUTOTUNE in the first (untimed) warm-up solve of each leg
-    tune = g.gdr_autotune(ctx, op, g.GDR_PREC_MIXED, 1, p.m)
+    tune = g.gdr_autotune(ctx, op, g.GDR_PREC_MIXED, 1, p.m if args.arnoldi_form == "tuned" else 0)
+    form_flag = g.GDR_FLAG_NO_SWEEP if args.arnoldi_form == "launches" else 0
     mixed = g.gdr_params_default(m=p.m, k=p.k, m_proj=p.m_proj, tol=p.tol, extra_tol=p.extra_tol,
-                                 prec=g.GDR_PREC_MIXED, flags=g.GDR_FLAG_AUTOTUNE)  # inner_tol: automatic
+                                 prec=g.GDR_PREC_MIXED,
+                                 flags=g.GDR_FLAG_AUTOTUNE | form_flag)  # inner_tol: automatic
     plain = g.gdr_params_default(m=p.m, k=p.k, m_proj=p.m_proj, tol=p.tol, extra_tol=p.extra_tol,
                                  prec=g.GDR_PREC_FP64,
                                  flags=g.GDR_FLAG_SEQUENTIAL | g.GDR_FLAG_NO_GRAPH | g.GDR_FLAG_AUTOTUNE)
@@ -303,7 +328,8 @@ def main():
                                       "t_proj_ms", "t_refine_ms", "host_syncs", "kernel_launches")},
         "roofline": roof,
         "kernels": ktable,
-        "autotune": {"stage": "rhs1 matvec (1 column) and Arnoldi form", **tune},
+        "autotune": {"stage": "rhs1 matvec (1 column) and Arnoldi form", "arnoldi_form": args.arnoldi_form,
+                     **tune},
     }
     if scale is not None:
         line["kernels_at_scale"] = scale
@@ -383,15 +409,15 @@ def kernel_roofline(g, ctx, op, p, params, stream, B, X):
     return roof, table
 
 
-def kernels_at_scale(g, ctx, stream):
+def kernels_at_scale(g, ctx, stream, only=None, link_store=None, tune=True, step=True):
     """The HBM-bound kernels on the two large lattices of the workload family
-    (Wilson 16^4, c64 links; 24^3x32, bf16 links): one profiled Arnoldi step at
-    the last column of the basis (j = m - 1, m = 60 / 80; single column, so the
-    algorithmic byte model is exact) and the multi-column matvec of the
-    refinement / Proj stages (8 / 12 columns), each matvec in the launch shape
-    the autotuner chose (its time and the default shape's reported beside).
-    Inputs far larger than L2.  Per kernel: microseconds per launch, GB/s and
-    fraction of measured HBM peak."""
+    (Wilson 16^4, c64 links; 24^3x32, bf16 links), each profiled alone: one
+    Arnoldi step at the last column of the basis (j = m - 1, m = 60 / 80), the
+    single-column matvec and the multi-column matvec of the refinement / Proj
+    stages (8 / 12 columns), the matvecs in the launch shape the autotuner chose
+    (its time and the default shape's reported beside).  Inputs far larger than
+    L2.  Per kernel: microseconds per launch, GB/s and fraction of measured HBM
+    peak."""
     import torch
     peaks = {}
     try:
@@ -402,42 +428,67 @@ def kernels_at_scale(g, ctx, stream):
     out = {}
     for cid, dims, eps, store, m, ncol in [(3, (16, 16, 16, 16), 0.4, g.GDR_LINK_C64, 60, 8),
                                            (4, (24, 24, 24, 32), 0.5, g.GDR_LINK_BF16, 80, 12)]:
+        if only is not None and only != "x".join(map(str, dims)):
+            continue
+        if link_store is not None:
+            store = g.GDR_LINK_BF16 if link_store == "bf16" else g.GDR_LINK_C64
         links = W.su3_links(dims, eps, W.rng(cid, 0))
+        n = 12 * int(np.prod(dims))
         with torch.cuda.stream(stream):
             op = g.gdr_op_wilson(ctx, dims, torch.as_tensor(links).cuda(), 0.0, store)
-            n = 12 * int(np.prod(dims))
             gen = torch.Generator(device="cuda").manual_seed(cid)
-            V = torch.randn((m + 1, n), dtype=torch.complex64, device="cuda", generator=gen)
-            V /= V.norm(dim=1, keepdim=True)
-            hcol = torch.zeros(m + 1, dtype=torch.complex128, device="cuda")
             X = torch.randn((ncol, n), dtype=torch.complex64, device="cuda", generator=gen)
             Y = torch.empty_like(X)
+            if step:
+                V = torch.randn((m + 1, n), dtype=torch.complex64, device="cuda", generator=gen)
+                V /= V.norm(dim=1, keepdim=True)
+                hcol = torch.zeros(m + 1, dtype=torch.complex128, device="cuda")
         del links
         tuned = {"1": g.gdr_autotune(ctx, op, g.GDR_PREC_MIXED, 1),
-                 str(ncol): g.gdr_autotune(ctx, op, g.GDR_PREC_MIXED, ncol)}
-        for _ in range(2):  # warm-up
-            g.gdr_arnoldi_step(ctx, op, g.GDR_PREC_MIXED, V, m - 1, hcol)
-            g.gdr_op_apply(ctx, op, g.GDR_PREC_MIXED, np.zeros(ncol), X, Y)
-        g.gdr_profile(ctx, True)
-        for _ in range(5):
-            g.gdr_arnoldi_step(ctx, op, g.GDR_PREC_MIXED, V, m - 1, hcol)
-            g.gdr_op_apply(ctx, op, g.GDR_PREC_MIXED, np.zeros(ncol), X, Y)
-        prof = g.gdr_profile_report(ctx)
-        g.gdr_profile(ctx, False)
-        key = "x".join(map(str, dims))
-        tab = {}
-        for name, v in prof.items():
-            if v["bytes"] <= 0:
-                continue
-            us = v["ms"] / v["launches"] * 1e3
-            gbs = v["bytes"] / (v["ms"] / 1e3) / 1e9
-            tab[name] = {"launches": v["launches"], "us_per_launch": round(us, 1), "GBs": round(gbs, 1),
-                         "frac_of_measured_hbm": round(gbs / hbm, 3)}
-        out[key] = {"n": n, "arnoldi_step_j": m - 1, "matvec_columns": ncol,
-                    "links": "bf16" if store == g.GDR_LINK_BF16 else "c64", "kernels": tab,
-                    "matvec_autotune": tuned}
+                 str(ncol): g.gdr_autotune(ctx, op, g.GDR_PREC_MIXED, ncol)} if tune else None
+
+        def profiled(call, reps=5):
+            for _ in range(2):  # warm-up
+                call()
+            g.gdr_profile(ctx, True)
+            for _ in range(reps):
+                call()
+            prof = g.gdr_profile_report(ctx)
+            g.gdr_profile(ctx, False)
+            tab = {}
+            for name, v in prof.items():
+                if v["bytes"] <= 0:
+                    continue
+                us = v["ms"] / v["launches"] * 1e3
+                gbs = v["bytes"] / (v["ms"] / 1e3) / 1e9
+                tab[name] = {"launches": v["launches"], "us_per_launch": round(us, 1), "GBs": round(gbs, 1),
+                             "frac_of_measured_hbm": round(gbs / hbm, 3)}
+            return tab
+
+        res = {}
+        if step:  # Gram-Schmidt kernels and the single-column matvec of one Arnoldi step
+            res[f"arnoldi_step_j{m - 1}"] = profiled(
+                lambda: g.gdr_arnoldi_step(ctx, op, g.GDR_PREC_MIXED, V, m - 1, hcol))
+        X1, Y1 = X[:1], Y[:1]
+        res["matvec_1col"] = profiled(lambda: g.gdr_op_apply(ctx, op, g.GDR_PREC_MIXED, np.zeros(1), X1, Y1))
+        res[f"matvec_{ncol}col"] = profiled(
+            lambda: g.gdr_op_apply(ctx, op, g.GDR_PREC_MIXED, np.zeros(ncol), X, Y))
+        entry = {"n": n, "links": "bf16" if store == g.GDR_LINK_BF16 else "c64", "kernels": res,
+                 "matvec_autotune": tuned}
+        if tuned:  # the tuner's back-to-back timing of the chosen shape (no per-launch events)
+            sl = 2 if store == g.GDR_LINK_BF16 else 4
+            entry["matvec_back_to_back"] = {}
+            for c, t in tuned.items():
+                byt = n // 12 * (4 * 18 * sl + int(c) * 12 * 8 * 2)
+                gbs = byt / (t["mv_ms"] * 1e-3) / 1e9
+                entry["matvec_back_to_back"][c + "col"] = {"us_per_launch": round(t["mv_ms"] * 1e3, 1),
+                                                           "GBs": round(gbs, 1),
+                                                           "frac_of_measured_hbm": round(gbs / hbm, 3)}
+        out["x".join(map(str, dims))] = entry
         g.gdr_op_destroy(op)
-        del V, X, Y
+        del X, Y, X1, Y1
+        if step:
+            del V, hcol
         torch.cuda.empty_cache()
     return out
 

@@ -63,6 +63,11 @@ typedef enum { GDR_LINK_C128 = 0, GDR_LINK_C64 = 1, GDR_LINK_BF16 = 2 } gdr_link
 #define GDR_FLAG_NO_SWEEP    32u  /* short vectors: one launch per Arnoldi phase instead of the persistent
                                      per-cycle sweep kernel */
 #define GDR_FLAG_FP64_EIG    64u  /* MIXED: harmonic-Ritz eigensolve in FP64 instead of FP32 */
+#define GDR_FLAG_RELATED_RHS 256u /* related right-hand sides (Sec. 5, Example 8): RHS 2.. one at a time,
+                                     each started from the Minres projection over the converged solutions
+                                     of the previous ones (B^H B d = B^H b_j, x_i = X_i d, common residual
+                                     b_j - B d), then GMRES(m_p)-Proj(k)-Sh + correction on that residual
+                                     and refinement to tol before the next */
 #define GDR_FLAG_AUTOTUNE   128u  /* before the first cycle, run gdr_autotune for the matvec and Arnoldi
                                      form of each stage whose (precision, columns, m) the operator has
                                      no tuned shape for yet (the tuning time is part of the solve) */
@@ -103,9 +108,11 @@ typedef struct {
   double t_total_ms;    /* wall time of the solve */
   long kernel_launches; /* kernels of this library launched by the solve (graph nodes counted) */
   double t_rhs1_ms;     /* wall time of the GMRES-DR(m,k)-Sh stage (right-hand side 1) */
-  double t_proj_ms;     /* extra right-hand side, Proj stage, corrections, first FP64 residuals */
-  double t_refine_ms;   /* refinement passes, FP64 cleanup and their residuals */
+  double t_proj_ms;     /* extra right-hand side, Proj stage and corrections (GDR_FLAG_RELATED_RHS:
+                           everything after right-hand side 1, its refinement included) */
+  double t_refine_ms;   /* FP64 true residuals, refinement passes and FP64 cleanup */
   long host_syncs;      /* host waits on the stream (one per cycle for the convergence test, ...) */
+  double related_resid; /* GDR_FLAG_RELATED_RHS: largest ||b_j - B d|| / ||b_j|| over j >= 2 (else 0) */
 } gdr_report;
 
 /* ---------------------------------------------------------------- context */

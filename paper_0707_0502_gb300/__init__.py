@@ -27,7 +27,7 @@ GDR_PREC_FP64, GDR_PREC_MIXED = 0, 1
 GDR_LINK_C128, GDR_LINK_C64, GDR_LINK_BF16 = 0, 1, 2
 GDR_MAX_M = 96
 (GDR_FLAG_HOST_PTRS, GDR_FLAG_NO_GRAPH, GDR_FLAG_SEQUENTIAL, GDR_FLAG_NO_PROJ, GDR_FLAG_NO_REFINE, GDR_FLAG_NO_SWEEP,
- GDR_FLAG_FP64_EIG, GDR_FLAG_AUTOTUNE) = 1, 2, 4, 8, 16, 32, 64, 128
+ GDR_FLAG_FP64_EIG, GDR_FLAG_AUTOTUNE, GDR_FLAG_RELATED_RHS) = 1, 2, 4, 8, 16, 32, 64, 128, 256
 
 
 class gdr_params(ctypes.Structure):
@@ -43,7 +43,8 @@ class gdr_report(ctypes.Structure):
                 ("refine_passes", ctypes.c_int), ("pairs_cleaned", ctypes.c_int),
                 ("max_relres", ctypes.c_double), ("t_total_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_long), ("t_rhs1_ms", ctypes.c_double),
-                ("t_proj_ms", ctypes.c_double), ("t_refine_ms", ctypes.c_double), ("host_syncs", ctypes.c_long)]
+                ("t_proj_ms", ctypes.c_double), ("t_refine_ms", ctypes.c_double), ("host_syncs", ctypes.c_long),
+                ("related_resid", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -88,6 +88,85 @@ __global__ void correct_kernel(long n, int ns, const c128* gam, const c128* S, l
     X[(long)p * ldx + r] += g * S[(long)i * lds + r];
 }
 
+// Related right-hand sides (Sec. 5, eqs. relrhs1-relrhs2).  M is the j x (j+1)
+// augmented system [B^H B | B^H b_j] (row-major, FP64, overwritten); d solves it by
+// Gaussian elimination with partial pivoting, one warp (lanes stride the rows).  A
+// column with no usable pivot (linearly dependent right-hand sides) gets d = 0.
+__global__ void related_solve_kernel(int j, c128* M, c128* d) {
+  const int lane = threadIdx.x;
+  const int w = j + 1;
+  for (int p = 0; p < j; ++p) {
+    double best = -1.0;
+    int piv = p;
+    for (int r = p + lane; r < j; r += 32) {
+      const double a = norm2(M[r * w + p]);
+      if (a > best) {
+        best = a;
+        piv = r;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int op = __shfl_xor_sync(0xffffffffu, piv, o);
+      if (ob > best || (ob == best && op < piv)) {
+        best = ob;
+        piv = op;
+      }
+    }
+    if (piv != p)
+      for (int c = p + lane; c < w; c += 32) {
+        const c128 t = M[p * w + c];
+        M[p * w + c] = M[piv * w + c];
+        M[piv * w + c] = t;
+      }
+    __syncwarp();
+    const c128 pv = M[p * w + p];
+    const double pn = norm2(pv);
+    if (pn > 0.0) {
+      const c128 inv = {pv.x / pn, -pv.y / pn};
+      for (int r = p + 1 + lane; r < j; r += 32) {
+        const c128 f = M[r * w + p] * inv;
+        for (int c = p; c < w; ++c) M[r * w + c] -= f * M[p * w + c];
+      }
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    for (int p = j - 1; p >= 0; --p) {
+      c128 acc = M[p * w + j];
+      for (int c = p + 1; c < j; ++c) acc -= M[p * w + c] * d[c];
+      const c128 pv = M[p * w + p];
+      const double pn = norm2(pv);
+      d[p] = pn > 0.0 ? acc * c128{pv.x / pn, -pv.y / pn} : c128{0.0, 0.0};
+    }
+  }
+}
+
+// guesses X_j[:, i] = sum_r d_r X_r[:, i] for every shift i (blockIdx.y < ns) and the
+// common residual res = b_j - sum_r d_r b_r (blockIdx.y == ns); X_r[:, i] at X + (r ns + i) ldx
+__global__ void related_guess_kernel(long n, int ns, int j, const c128* __restrict__ d, c128* X, long ldx,
+                                     const c128* __restrict__ B, long ldb, c128* __restrict__ res) {
+  const int i = blockIdx.y;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    c128 acc = {0.0, 0.0};
+    if (i < ns) {
+      for (int r = 0; r < j; ++r) acc += d[r] * X[((long)r * ns + i) * ldx + e];
+      X[((long)j * ns + i) * ldx + e] = acc;
+    } else {
+      for (int r = 0; r < j; ++r) acc += d[r] * B[(long)r * ldb + e];
+      res[e] = B[(long)j * ldb + e] - acc;
+    }
+  }
+}
+
+// X[:, q] += Y[:, q], q < cols
+__global__ void add_cols_kernel(long n, const c128* __restrict__ Y, long ldy, c128* X, long ldx) {
+  const int q = blockIdx.y;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+    X[(long)q * ldx + e] += Y[(long)q * ldy + e];
+}
+
 unsigned grid1(gdr_ctx* ctx, long n) {
   long g = (n + 255) / 256;
   long cap = (long)ctx->num_sms * 8;
@@ -657,6 +736,103 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
     GDR_CUDA(cudaMemcpyAsync(Hkd, dr.Hk, sizeof(c128) * (kd + 1) * kd, cudaMemcpyDeviceToDevice, ctx->stream));
   }
   const bool project = kd > 0 && !(p.flags & GDR_FLAG_NO_PROJ);
+  const bool related = (p.flags & GDR_FLAG_RELATED_RHS) != 0 && nrhs > 1;
+  const int np = ns * nrhs;
+  c128* Rres = ctx->get<c128>("pl.Rres", (size_t)ld * np);
+  std::vector<double> relres(np, std::numeric_limits<double>::infinity());
+
+  // ---- FP64 true residuals, refinement (MIXED) and cleanup of the (shift, rhs) pairs of
+  //      right-hand sides [r0, r1); relres of those pairs updated
+  auto refine_rhs = [&](int r0, int r1) {
+    const int qg = r0 * ns, nq = (r1 - r0) * ns;
+    const c128* Bq = B + (long)r0 * ldb;
+    c128* Xq = X + (long)qg * ldx;
+    c128* Rq = Rres + (long)qg * ld;
+    std::vector<double> bnq(bnorm.begin() + r0, bnorm.begin() + r1);
+    std::vector<double> rr;
+    auto residuals = [&]() {
+      true_residuals(ctx, A, ns, sig_dev, r1 - r0, Bq, ldb, Xq, ldx, Rq, ld, rr, bnq);
+      rep.resid_cols += nq;
+      for (int q = 0; q < nq; ++q) relres[qg + q] = rr[q];
+    };
+    residuals();
+    const int max_pass = (p.flags & GDR_FLAG_NO_REFINE) ? -1 : std::max(0, p.refine_max);
+    for (int pass = 0; pass <= max_pass; ++pass) {
+      std::vector<int> mask(nq, 0);
+      int nact = 0;
+      for (int q = 0; q < nq; ++q)
+        if (!(rr[q] <= p.tol)) {
+          mask[q] = 1;
+          ++nact;
+        }
+      if (nact == 0) break;
+      const bool cleanup = (pass == max_pass) || !mixed;
+      rep.refine_passes++;
+      if (cleanup) rep.pairs_cleaned += nact;
+      // chunk the pairs by memory
+      size_t freeb = 0, totb = 0;
+      GDR_CUDA(cudaMemGetInfo(&freeb, &totb));
+      const size_t elem = cleanup ? sizeof(c128) : sizeof(cx<R>);
+      const size_t per_col = elem * (size_t)ld * (mp + 4) + 4096;
+      int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)nq, (freeb / 2) / per_col));
+      for (int q0 = 0; q0 < nq; q0 += chunk) {
+        const int cn = std::min(chunk, nq - q0);
+        bool any = false;
+        for (int q = q0; q < q0 + cn; ++q) any = any || mask[q];
+        if (!any) continue;
+        std::vector<double> tolc(cn);
+        std::vector<int> mk(mask.begin() + q0, mask.begin() + q0 + cn);
+        for (int c = 0; c < cn; ++c) {
+          const int q = q0 + c;
+          // relative to the residual column: reach tol * ||b|| with margin
+          tolc[c] = std::max(0.3 * p.tol / std::max(rr[q], 1e-300), cleanup ? 0.0 : p.refine_tol);
+          tolc[c] = std::min(tolc[c], 0.5);
+        }
+        auto run_refine = [&](auto tag) {
+          using RR = decltype(tag);
+          cx<RR>* rin = ctx->get<cx<RR>>("rf.rin", (size_t)ld * cn);
+          to_inner<RR>(ctx, n, cn, Rq + (long)q0 * ld, ld, rin, ld);
+          ProjJob<RR> job;
+          job.ncol = cn;
+          job.ns = 1;
+          job.m_p = mp;
+          job.k = kd;
+          job.project = project;
+          cx<RR>* vd = nullptr;
+          if (kd > 0) {
+            if (std::is_same<RR, R>::value) {
+              vd = reinterpret_cast<cx<RR>*>(Vd);
+            } else {  // FP64 cleanup after a complex64 solve: FP64 copy of the kept basis
+              vd = reinterpret_cast<cx<RR>*>(V128);
+            }
+          }
+          job.Vd = vd;
+          job.ldvd = ld;
+          job.Hk = Hkd;
+          job.rhs = rin;
+          job.ldrhs = ld;
+          job.sigma.resize(cn);
+          for (int c = 0; c < cn; ++c) job.sigma[c] = sigma[(q0 + c) % ns];
+          job.tol = tolc;
+          job.mask = mk;
+          job.X = Xq + (long)q0 * ldx;
+          job.ldx = ldx;
+          job.xcs = ldx;
+          job.max_mvps = p.max_mvps;
+          job.sweep = !(p.flags & GDR_FLAG_NO_SWEEP);
+          ProjResult pr = proj_batch<RR>(ctx, A, job, use_graph);
+          for (int c = 0; c < cn; ++c) rep.mvps_refine += pr.mvps[c];
+          if (pr.status == GDR_ENAN || pr.status == GDR_ECUDA) worst(pr.status);
+        };
+        if (cleanup)
+          run_refine(double{});
+        else
+          run_refine(R{});
+      }
+      residuals();
+    }
+  };
+
   // ---- extra right-hand side v_{k+1} and RHS 2..nrhs: GMRES(m_p)-Proj(k)-Sh
   if (nrhs > 1) {
     const int ncol = nrhs;  // column 0: v_{k+1} (if deflating), columns 1..: b^2..b^nrhs
@@ -665,10 +841,11 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
     GDR_CUDA(cudaMemsetAsync(XP, 0, sizeof(c128) * ld * ns * ncol, ctx->stream));
     if (project)
       GDR_CUDA(cudaMemcpyAsync(rhs, Vd + (long)kd * ld, sizeof(cx<R>) * n, cudaMemcpyDeviceToDevice, ctx->stream));
-    to_inner<R>(ctx, n, nrhs - 1, B + ldb, ldb, rhs + ld, ld);
+    if (!related) to_inner<R>(ctx, n, nrhs - 1, B + ldb, ldb, rhs + ld, ld);
     std::vector<int> mask(ncol, 1);
     if (!project) mask[0] = 0;
-    const bool seq = (p.flags & GDR_FLAG_SEQUENTIAL) != 0;
+    std::vector<double> tol_scale(ncol, 1.0);  // stage tolerance of a column relative to ||b_j|| / ||its rhs||
+    const bool seq = (p.flags & GDR_FLAG_SEQUENTIAL) != 0 || related;
     const int first = project ? 0 : 1;
     auto run_cols = [&](int c0, int cn) {
       ProjJob<R> job;
@@ -687,7 +864,8 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
         for (int i = 0; i < ns; ++i) job.sigma[(size_t)c * ns + i] = sigma[i];
       job.tol.resize(cn);
       for (int c = 0; c < cn; ++c)
-        job.tol[c] = (c0 + c == 0) ? p.extra_tol : (mixed ? std::max(p.tol, p.inner_tol) : p.tol);
+        job.tol[c] = std::min(0.5, tol_scale[c0 + c] * ((c0 + c == 0) ? p.extra_tol
+                                                                      : (mixed ? std::max(p.tol, p.inner_tol) : p.tol)));
       job.mask.assign(mask.begin() + c0, mask.begin() + c0 + cn);
       job.X = XP + (long)c0 * ns * ld;
       job.ldx = ld;
@@ -701,124 +879,103 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
       }
       worst(pr.status);
     };
-    if (seq) {
-      for (int c = first; c < ncol; ++c) run_cols(c, 1);
-    } else {
-      run_cols(first, ncol - first);
-    }
-    // ---- correction phase (FP64): extra solutions s_i = s~_i / (1 - gamma_i), then x_i^j += gamma_i^j s_i
+    // correction phase (FP64): extra solutions s_i = s~_i / (1 - gamma_i), then x_i^j += gamma_i^j s_i
     c128* RP = ctx->get<c128>("pl.RP", (size_t)ld * ns * ncol);
-    if (project && ns > 1) {
+    const bool correct = project && ns > 1;
+    const c128* v128 = correct ? V128 + (long)kd * ld : nullptr;
+    c128* gam = ctx->get<c128>("pl.gam", (size_t)ns * ncol);
+    const int dnblk = (int)std::min<long>((n + 255) / 256, 2L * ctx->num_sms);
+    c128* dpart = ctx->get<c128>("pl.dpart", (size_t)dnblk * ns * ncol + 64);
+    unsigned* dcnt = ctx->get<unsigned>("pl.dcnt", (size_t)4 * ns * ncol);
+    GDR_CUDA(cudaMemsetAsync(dcnt, 0, sizeof(unsigned) * 4 * ns * ncol, ctx->stream));
+    auto scale_extra = [&]() {  // extra system residuals v - (A - sigma_i) s~_i, gamma_i, s_i
       std::vector<double> rr;
       std::vector<double> one(1, 1.0);
-      const c128* v128 = V128 + (long)kd * ld;
-      // extra system residuals v - (A - sigma_i) s~_i
       true_residuals(ctx, A, ns, sig_dev, 1, v128, ld, XP, ld, RP, ld, rr, one);
-      c128* gam = ctx->get<c128>("pl.gam", (size_t)ns * ncol);
-      const int nblk = (int)std::min<long>((n + 255) / 256, 2L * ctx->num_sms);
-      c128* part = ctx->get<c128>("pl.dpart", (size_t)nblk * ns * ncol + 64);
-      unsigned* cnt = ctx->get<unsigned>("pl.dcnt", (size_t)4 * ns * ncol);
-      GDR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * 4 * ns * ncol, ctx->stream));
-      dots128(ctx, n, ns, v128, 0, RP, ld, gam, part, nblk, cnt);
+      dots128(ctx, n, ns, v128, 0, RP, ld, gam, dpart, dnblk, dcnt);
       dim3 ge(grid1(ctx, n), (unsigned)(ns - 1));
       extra_scale_kernel<<<ge, 256, 0, ctx->stream>>>(n, ns, gam, XP, ld);
       GDR_LAUNCHED(ctx);
-      // RHS 2..: residuals, gamma_i^j = v^H r_i^j, corrections
-      std::vector<double> bn2(bnorm.begin() + 1, bnorm.end());
-      true_residuals(ctx, A, ns, sig_dev, nrhs - 1, B + ldb, ldb, XP + (long)ns * ld, ld, RP + (long)ns * ld, ld, rr,
-                     bn2);
-      dots128(ctx, n, ns * (nrhs - 1), v128, 0, RP + (long)ns * ld, ld, gam + ns, part, nblk, cnt);
-      dim3 gc(grid1(ctx, n), (unsigned)(ns * (nrhs - 1)));
-      correct_kernel<<<gc, 256, 0, ctx->stream>>>(n, ns, gam + ns, XP, ld, XP + (long)ns * ld, ld);
+    };
+    // slots [j0, j0 + nr) solved for right-hand sides Bc (FP64, ld ldbc): residuals, gamma_i^j, corrections
+    auto correct_slots = [&](int j0, int nr, const c128* Bc, long ldbc, const std::vector<double>& bn) {
+      std::vector<double> rr;
+      true_residuals(ctx, A, ns, sig_dev, nr, Bc, ldbc, XP + (long)j0 * ns * ld, ld, RP + (long)j0 * ns * ld, ld, rr,
+                     bn);
+      dots128(ctx, n, ns * nr, v128, 0, RP + (long)j0 * ns * ld, ld, gam + (long)j0 * ns, dpart, dnblk, dcnt);
+      dim3 gc(grid1(ctx, n), (unsigned)(ns * nr));
+      correct_kernel<<<gc, 256, 0, ctx->stream>>>(n, ns, gam + (long)j0 * ns, XP, ld, XP + (long)j0 * ns * ld, ld);
       GDR_LAUNCHED(ctx);
-    }
-    // results of RHS 2.. into X
-    for (int j = 1; j < nrhs; ++j)
-      copy128(ctx, n, ns, XP + (long)j * ns * ld, ld, X + (long)j * ns * ldx, ldx);
-  }
-  // ---- FP64 true residuals, refinement (MIXED) and cleanup of every (shift, rhs) pair
-  const int np = ns * nrhs;
-  c128* Rres = ctx->get<c128>("pl.Rres", (size_t)ld * np);
-  std::vector<double> relres;
-  true_residuals(ctx, A, ns, sig_dev, nrhs, B, ldb, X, ldx, Rres, ld, relres, bnorm);
-  rep.resid_cols += np;
-  rep.t_proj_ms = ms_since(tp);
-  tp = clk::now();
-  const int max_pass = (p.flags & GDR_FLAG_NO_REFINE) ? -1 : std::max(0, p.refine_max);
-  for (int pass = 0; pass <= max_pass; ++pass) {
-    std::vector<int> mask(np, 0);
-    int nact = 0;
-    for (int q = 0; q < np; ++q)
-      if (!(relres[q] <= p.tol)) {
-        mask[q] = 1;
-        ++nact;
+    };
+    if (!related) {
+      if (seq) {
+        for (int c = first; c < ncol; ++c) run_cols(c, 1);
+      } else {
+        run_cols(first, ncol - first);
       }
-    if (nact == 0) break;
-    const bool cleanup = (pass == max_pass) || !mixed;
-    rep.refine_passes++;
-    if (cleanup) rep.pairs_cleaned += nact;
-    // chunk the pairs by memory
-    size_t freeb = 0, totb = 0;
-    GDR_CUDA(cudaMemGetInfo(&freeb, &totb));
-    const size_t elem = cleanup ? sizeof(c128) : sizeof(cx<R>);
-    const size_t per_col = elem * (size_t)ld * (mp + 4) + 4096;
-    int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)np, (freeb / 2) / per_col));
-    for (int q0 = 0; q0 < np; q0 += chunk) {
-      const int cn = std::min(chunk, np - q0);
-      bool any = false;
-      for (int q = q0; q < q0 + cn; ++q) any = any || mask[q];
-      if (!any) continue;
-      std::vector<double> tolc(cn);
-      std::vector<int> mk(mask.begin() + q0, mask.begin() + q0 + cn);
-      for (int c = 0; c < cn; ++c) {
-        const int q = q0 + c;
-        // relative to the residual column: reach tol * ||b|| with margin
-        tolc[c] = std::max(0.3 * p.tol / std::max(relres[q], 1e-300), cleanup ? 0.0 : p.refine_tol);
-        tolc[c] = std::min(tolc[c], 0.5);
+      if (correct) {
+        scale_extra();
+        std::vector<double> bn2(bnorm.begin() + 1, bnorm.end());
+        correct_slots(1, nrhs - 1, B + ldb, ldb, bn2);
       }
-      auto run_refine = [&](auto tag) {
-        using RR = decltype(tag);
-        cx<RR>* rin = ctx->get<cx<RR>>("rf.rin", (size_t)ld * cn);
-        to_inner<RR>(ctx, n, cn, Rres + (long)q0 * ld, ld, rin, ld);
-        ProjJob<RR> job;
-        job.ncol = cn;
-        job.ns = 1;
-        job.m_p = mp;
-        job.k = kd;
-        job.project = project;
-        cx<RR>* vd = nullptr;
-        if (kd > 0) {
-          if (std::is_same<RR, R>::value) {
-            vd = reinterpret_cast<cx<RR>*>(Vd);
-          } else {  // FP64 cleanup after a complex64 solve: FP64 copy of the kept basis
-            vd = reinterpret_cast<cx<RR>*>(V128);
+      // results of RHS 2.. into X
+      for (int j = 1; j < nrhs; ++j)
+        copy128(ctx, n, ns, XP + (long)j * ns * ld, ld, X + (long)j * ns * ldx, ldx);
+      rep.t_proj_ms = ms_since(tp);
+      tp = clk::now();
+      refine_rhs(0, nrhs);
+    } else {
+      // Sec. 5: right-hand sides one at a time, each started from the Minres projection over the
+      // converged solutions of the previous ones (B^H B d = B^H b_j, x_i = X_i d, common residual
+      // b_j - B d), then Proj-Sh and the correction on that residual, then refined to tol
+      if (project) run_cols(0, 1);
+      if (correct) scale_extra();
+      refine_rhs(0, 1);
+      c128* M = ctx->get<c128>("rel.M", (size_t)nrhs * (nrhs + 1));
+      c128* dvec = ctx->get<c128>("rel.d", (size_t)nrhs);
+      c128* res = ctx->get<c128>("rel.r", (size_t)ld);
+      double* rn2 = ctx->get<double>("rel.rn", 4);
+      c128* ypart = ctx->get<c128>("rel.part", (size_t)dnblk * (nrhs + 1) + 64);
+      unsigned* ycnt = ctx->get<unsigned>("rel.cnt", (size_t)4 * (nrhs + 1));
+      for (int j = 1; j < nrhs; ++j) {
+        // [B^H B | B^H b_j], row a = b_a^H [b_0 .. b_j]
+        GDR_CUDA(cudaMemsetAsync(ycnt, 0, sizeof(unsigned) * 4 * (nrhs + 1), ctx->stream));
+        for (int a = 0; a < j; ++a)
+          dots128(ctx, n, j + 1, B + (long)a * ldb, 0, B, ldb, M + (long)a * (j + 1), ypart, dnblk, ycnt);
+        related_solve_kernel<<<1, 32, 0, ctx->stream>>>(j, M, dvec);
+        GDR_LAUNCHED(ctx);
+        dim3 gg(grid1(ctx, n), (unsigned)(ns + 1));
+        related_guess_kernel<<<gg, 256, 0, ctx->stream>>>(n, ns, j, dvec, X, ldx, B, ldb, res);
+        GDR_LAUNCHED(ctx);
+        norms2<c128>(ctx, n, 1, res, ld, rn2, ypart, dnblk, ycnt);
+        double rn = 0;
+        GDR_CUDA(cudaMemcpyAsync(&rn, rn2, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        stream_sync(ctx);
+        rn = std::sqrt(rn);
+        rep.related_resid = std::max(rep.related_resid, rn / std::max(bnorm[j], 1e-300));
+        // the Proj stage only where the projected residual misses the stage tolerance
+        // (refinement finishes the pairs either way)
+        if (rn > (mixed ? std::max(p.tol, p.inner_tol) : p.tol) * bnorm[j]) {
+          to_inner<R>(ctx, n, 1, res, ld, rhs + (long)j * ld, ld);
+          tol_scale[j] = bnorm[j] / rn;
+          run_cols(j, 1);
+          if (correct) {
+            std::vector<double> bnr(1, rn);
+            correct_slots(j, 1, res, ld, bnr);
           }
+          dim3 ga(grid1(ctx, n), (unsigned)ns);
+          add_cols_kernel<<<ga, 256, 0, ctx->stream>>>(n, XP + (long)j * ns * ld, ld, X + (long)j * ns * ldx, ldx);
+          GDR_LAUNCHED(ctx);
         }
-        job.Vd = vd;
-        job.ldvd = ld;
-        job.Hk = Hkd;
-        job.rhs = rin;
-        job.ldrhs = ld;
-        job.sigma.resize(cn);
-        for (int c = 0; c < cn; ++c) job.sigma[c] = sigma[(q0 + c) % ns];
-        job.tol = tolc;
-        job.mask = mk;
-        job.X = X + (long)q0 * ldx;
-        job.ldx = ldx;
-        job.xcs = ldx;
-        job.max_mvps = p.max_mvps;
-        job.sweep = !(p.flags & GDR_FLAG_NO_SWEEP);
-        ProjResult pr = proj_batch<RR>(ctx, A, job, use_graph);
-        for (int c = 0; c < cn; ++c) rep.mvps_refine += pr.mvps[c];
-        if (pr.status == GDR_ENAN || pr.status == GDR_ECUDA) worst(pr.status);
-      };
-      if (cleanup)
-        run_refine(double{});
-      else
-        run_refine(R{});
+        refine_rhs(j, j + 1);
+      }
+      rep.t_proj_ms = ms_since(tp);
+      tp = clk::now();
     }
-    true_residuals(ctx, A, ns, sig_dev, nrhs, B, ldb, X, ldx, Rres, ld, relres, bnorm);
-    rep.resid_cols += np;
+  } else {
+    rep.t_proj_ms = ms_since(tp);
+    tp = clk::now();
+    refine_rhs(0, 1);
   }
   double mx = 0;
   for (double v : relres) mx = std::max(mx, v);
