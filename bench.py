@@ -310,7 +310,7 @@ def main():
     e2e_value = job_throughput(world, sols * len(e2e_ms), max_over_ranks(sum(e2e_ms) / 1e3, world))
 
     # ---- dominant kernel roofline (per-kernel CUDA events on the library stream)
-    roof, ktable = kernel_roofline(g, ctx, op, p, mixed, stream, B, X)
+    roof, ktable = kernel_roofline(g, ctx, op, p, mixed, stream, B, X, args.config)
     scale = kernels_at_scale(g, ctx, stream) if not args.no_scale else None
 
     line = {
@@ -360,7 +360,14 @@ def dense_flops(name, m, k, ns, ncol):
     return 0.0
 
 
-def kernel_roofline(g, ctx, op, p, params, stream, B, X):
+# DRAM bytes per launch of a dominant kernel, from one ncu capture of this bench's own
+# launches on the default workload (profiles/gs_update_dot_wilson8x8x8x8.md: average over
+# the 200 launches of one solve; ncu flushes the caches before each captured launch, so
+# this is the cold-cache traffic).  Reset when the kernel changes.
+NCU_TRAFFIC = {(CONFIG_ID, "gs_update_dot_c64"): 10243110}
+
+
+def kernel_roofline(g, ctx, op, p, params, stream, B, X, cid=CONFIG_ID):
     """One extra solve of the workload with per-kernel CUDA events (graphs off):
     every kernel's launches, time and algorithmic bytes; the roofline of the one
     with the largest total time."""
@@ -388,10 +395,13 @@ def kernel_roofline(g, ctx, op, p, params, stream, B, X):
     per_launch_s = v["ms"] / 1e3 / v["launches"]
     if v["bytes"] > 0:
         achieved = v["bytes"] / v["launches"] / per_launch_s / 1e9
+        traffic = NCU_TRAFFIC.get((cid, dom))
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None,
+                "frac": achieved / hbm, "traffic": traffic,
                 "bytes_per_launch": v["bytes"] / v["launches"],
-                "note": "peak = MEASURED_PEAKS.json hbm_gbs (of measured)"}
+                "note": "peak = MEASURED_PEAKS.json hbm_gbs (of measured)"
+                        + ("; traffic: ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, cold caches"
+                           if traffic is not None else "")}
     else:
         ns = len(p.sigma)
         m = p.m if dom != "dense_projection" else p.k
@@ -403,7 +413,7 @@ def kernel_roofline(g, ctx, op, p, params, stream, B, X):
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
                 "frac": achieved / peak, "traffic": None, "flops_per_launch": flops,
                 "note": "FP64 single-CTA kernel: peak = one SM's FP64 rate (2 FMA/clk) at sm_max_mhz; "
-                        "flops from the textbook counts in DESIGN.md"}
+                        "flops from the textbook counts of bench.dense_flops"}
     roof["us_per_launch"] = per_launch_s * 1e6
     roof["share_of_solve"] = v["ms"] / total
     return roof, table
