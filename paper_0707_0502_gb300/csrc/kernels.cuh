@@ -131,7 +131,8 @@ void op_apply_skip(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* sigma, c
 // launch shape of the operator kernels for ncol columns (FP64 or complex64 vectors): the
 // shape set for this column count, else the one set for the nearest count within a
 // factor 2, else the defaults (Wilson: direction-split while one thread per site cannot
-// fill the GPU; CSR: one thread per row)
+// fill the GPU; CSR: one thread per row; several columns of one operator in column-inner
+// block order)
 MvShape mv_shape(const gdr_ctx* ctx, const gdr_op* A, bool f64, int ncol);
 MvShape mv_default(const gdr_ctx* ctx, const gdr_op* A, int ncol);
 // Vector order: the C interface passes Wilson vectors site-major, the library keeps

@@ -286,7 +286,10 @@ MvShape mv_default(const gdr_ctx* ctx, const gdr_op* A, int ncol) {
     s.form = 1;
     s.threads = 256;
   }
-  s.col_inner = 0;
+  // several columns sharing one operator: consecutive blocks take one tile for all
+  // columns, so its links / rows are read from HBM once (column by column, each
+  // column's pass evicts them from L2 on large problems)
+  s.col_inner = (ncol > 1 && A->kind != OP_CSR_BATCH) ? 1 : 0;
   return s;
 }
 

@@ -121,7 +121,8 @@ def test_set_shape_rejects_bad_shapes(ctx):
     assert g.gdr_op_get_shape(op, g.GDR_PREC_FP64, 8)["threads"] == 256   # nearest count within 2x
     assert g.gdr_op_get_shape(op, g.GDR_PREC_FP64, 9)["form"] == 1        # beyond: default (tiny lattice)
     g.gdr_op_set_shape(op, g.GDR_PREC_FP64, 0)                            # forget all
-    assert g.gdr_op_get_shape(op, g.GDR_PREC_FP64, 4)["col_inner"] == 0
+    assert g.gdr_op_get_shape(op, g.GDR_PREC_FP64, 1)["col_inner"] == 0   # defaults: one column
+    assert g.gdr_op_get_shape(op, g.GDR_PREC_FP64, 4)["col_inner"] == 1   # several: column-inner order
     with pytest.raises(g.GdrError):
         g.gdr_autotune(ctx, op, g.GDR_PREC_FP64, 0)
     g.gdr_op_destroy(op)
