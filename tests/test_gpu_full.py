@@ -1,0 +1,79 @@
+"""Parity at the full benchmark sizes, in the launch configuration bench.py times
+(runs on a GB300; -m gpu).
+
+* Config 2 (the bench workload: Wilson 8^4, 49,152 unknowns, six kappa shifts,
+  GMRES-DR(40,20), complex64 stages with FP64 refinement, launch shapes and
+  Arnoldi form from the autotuner): every shift's solution against the oracle's
+  GMRES-DR-Sh solution converged to 1e-12 (agreement <= 1e-6 relative) and its
+  FP64 true residual with the oracle's operator (<= 1e-8).
+* Config 3 (Wilson 16^4, 786,432 unknowns, eight shifts x eight Z2 right-hand
+  sides): too large for an oracle solve inside a test, so every one of the 64
+  (shift, rhs) pairs is checked by the property that defines the result, its
+  FP64 true relative residual computed with the oracle's operator (<= 1e-8)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import WilsonOperator, gmres_dr_sh
+from tests.gpu_util import dev, host
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no GPU", allow_module_level=True)
+
+import paper_0707_0502_gb300 as g  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__
+    __graft_entry__.build()
+    c = g.gdr_create(0)
+    yield c
+    g.gdr_destroy(c)
+
+
+def solve_like_bench(ctx, p, store=g.GDR_LINK_C64):
+    op = g.make_operator(ctx, p, store=store)
+    g.gdr_autotune(ctx, op, g.GDR_PREC_MIXED, 1, p.m)
+    prm = g.gdr_params_default(m=p.m, k=p.k, m_proj=p.m_proj, tol=p.tol, extra_tol=p.extra_tol,
+                               prec=g.GDR_PREC_MIXED, flags=g.GDR_FLAG_AUTOTUNE)
+    nrhs, ns = p.B.shape[1], len(p.sigma)
+    X = torch.zeros((nrhs, ns, p.n), dtype=torch.complex128, device="cuda")
+    st, rep, _ = g.gdr_solve_multishift(ctx, op, p.sigma, dev(np.ascontiguousarray(p.B.T)), X, prm)
+    g.gdr_op_destroy(op)
+    return st, rep, host(X)
+
+
+def operator(p):
+    dims, diag_a, links = p.op[1], p.op[2], p.op[3]
+    return WilsonOperator(dims, links, diag_a=diag_a)
+
+
+def test_config2_bench_workload(ctx):
+    p = W.config(2)
+    st, rep, X = solve_like_bench(ctx, p)
+    assert st == g.GDR_OK and rep["max_relres"] <= 1e-8, rep
+    A = operator(p)
+    b = p.B[:, 0]
+    ref = gmres_dr_sh(A.matvec, b, p.sigma, p.m, p.k, 1e-12)
+    for i, s in enumerate(p.sigma):
+        x = X[0, i]
+        assert np.linalg.norm(b - (A.matvec(x) - s * x)) <= 1e-8 * np.linalg.norm(b), i
+        xr = ref["x"][:, i]
+        assert np.linalg.norm(x - xr) <= 1e-6 * np.linalg.norm(xr), i
+
+
+def test_config3_full_size(ctx):
+    p = W.config(3)
+    st, rep, X = solve_like_bench(ctx, p)
+    assert st == g.GDR_OK and rep["max_relres"] <= 1e-8, rep
+    A = operator(p)
+    for j in range(p.B.shape[1]):
+        b = p.B[:, j]
+        nb = np.linalg.norm(b)
+        for i, s in enumerate(p.sigma):
+            x = X[j, i]
+            assert np.linalg.norm(b - (A.matvec(x) - s * x)) <= 1e-8 * nb, (i, j)
