@@ -16,7 +16,9 @@ Contents
                GMRES-Sh (Sec. 2.1), harmonic Ritz vectors and GMRES-DR(m,k)-Sh
                (Sec. 2.2, Sec. 3), the Minres projection and GMRES(m)-Proj(k)
                (Sec. 2.3), GMRES-Proj-Sh with the extra right-hand side and the
-               correction phase (Sec. 4), related right-hand sides (Sec. 5).
+               correction phase (Sec. 4), the projection over selected approximate
+               eigenvectors (Sec. 4, Theorem 1, Example 4), related right-hand
+               sides (Sec. 5).
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, brute-force definitions on tiny inputs, dense LU, or
@@ -34,5 +36,7 @@ from .krylov import (  # noqa: F401
     extra_rhs_solve,
     correct_solutions,
     related_rhs_projection,
+    kept_eigenpairs,
+    eigvec_projection,
     solve_all_rhs,
 )

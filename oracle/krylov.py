@@ -285,13 +285,50 @@ def minres_projection(Vk1, Hk, sigma1, r0):
     return d, dx, r
 
 
-def gmres_proj_sh(matvec, Vk1, Hk, b, sigma, m_p, tol, max_mvps=100000, record=False, project=True):
+def kept_eigenpairs(Hk, sigma1, k_sel):
+    """Approximate eigenpairs carried by the kept pair A V_k = V_{k+1} Hbar_k (eq. recur1):
+    the harmonic Ritz pairs of span(V_k) with respect to the base shift (the same
+    formula as the restart, on Hbar_k - sigma1 Ibar), the k_sel 'smallest' ones (Sec. 4,
+    Example 4 keeps "the first k").  Returns (theta (k_sel): eigenvalue approximations
+    of A, G (k x k_sel): z_l = V_k g_l with ||g_l|| = 1, res (k_sel): eigen-residual
+    norms ||A z_l - theta_l z_l|| = ||(Hbar_k - theta_l Ibar) g_l||)."""
+    k = Hk.shape[1]
+    theta, idx, G = harmonic_ritz(Hk - sigma1 * _ibar(k + 1, k), k_sel)
+    G = G / np.linalg.norm(G, axis=0)
+    th = theta[idx] + sigma1
+    res = np.array([np.linalg.norm(Hk @ G[:, l] - th[l] * _ibar(k + 1, k) @ G[:, l]) for l in range(k_sel)])
+    return th, G, res
+
+
+def eigvec_projection(Vk1, Hk, th, G, sigma, beta, active, r):
+    """Projection of every shifted system over approximate eigenvectors Z = V_k G with
+    eigenvalues th, as in the proof of Theorem 1 (Sec. 4): d_i = beta_i (Theta - sigma_i)^{-1}
+    (Z^H Z)^{-1} Z^H r, x_i += Z d_i.  Returns (the new base residual r - (A - sigma_1 I) Z d_1,
+    computed through the recurrence, and the n x ns solution increments).  With exact
+    eigenvectors every shifted residual is beta_i times the new base residual; with
+    approximate ones the algorithm assumes it."""
+    k = Hk.shape[1]
+    Z = Vk1[:, :k] @ G
+    w = np.linalg.solve(Z.conj().T @ Z, Z.conj().T @ r)
+    dx = np.zeros((r.shape[0], len(sigma)), dtype=np.complex128)
+    for i in range(len(sigma)):
+        if i == 0 or active[i]:
+            dx[:, i] = Z @ (beta[i] * w / (th - sigma[i]))
+    d1 = w / (th - sigma[0])
+    rnew = r - Vk1 @ ((Hk - sigma[0] * _ibar(k + 1, k)) @ (G @ d1))
+    return rnew, dx
+
+
+def gmres_proj_sh(matvec, Vk1, Hk, b, sigma, m_p, tol, max_mvps=100000, record=False, project=True, eig=None):
     """GMRES(m_p)-Proj(k)-Sh for one right-hand side (Sec. 4, algorithm
     "GMRES-Proj-Sh for the second and subsequent right-hand sides", steps
     2-6).  Zero initial guess.  The non-base residuals are
     beta_i r + g_i v_{k+1}; the v_{k+1} part is ignored by the test and
     removed later by the correction.  ``project=False`` gives plain
-    GMRES(m_p)-Sh (no deflation).
+    GMRES(m_p)-Sh (no deflation).  ``eig=(theta, G)`` replaces the Minres
+    projection over V_k by the projection over the selected approximate
+    eigenvectors V_k G (``eigvec_projection``; Sec. 4, Theorem 1 and Example 4):
+    no v_{k+1} component is tracked and no correction applies.
 
     Returns dict(x, mvps, cycles, converged, norms, beta, gamma_acc, history)."""
     b = np.asarray(b, np.complex128)
@@ -310,7 +347,10 @@ def gmres_proj_sh(matvec, Vk1, Hk, b, sigma, m_p, tol, max_mvps=100000, record=F
     norms = np.full(ns, bnorm)
     converged = np.zeros(ns, dtype=bool)
     while True:
-        if project and k > 0:
+        if project and k > 0 and eig is not None:
+            r, dx = eigvec_projection(Vk1, Hk, eig[0], eig[1], sigma, beta, active, r)
+            x += dx
+        elif project and k > 0:
             # step 3: Minres projection for V_k on the base shift
             d1, dx1, r = minres_projection(Vk1, Hk, sigma[0], r)
             x[:, 0] += dx1
