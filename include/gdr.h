@@ -68,6 +68,11 @@ typedef enum { GDR_LINK_C128 = 0, GDR_LINK_C64 = 1, GDR_LINK_BF16 = 2 } gdr_link
                                      of the previous ones (B^H B d = B^H b_j, x_i = X_i d, common residual
                                      b_j - B d), then GMRES(m_p)-Proj(k)-Sh + correction on that residual
                                      and refinement to tol before the next */
+#define GDR_FLAG_EIG_SELECT  512u /* right-hand sides 2.. by GMRES(m_p)-Proj-Sh projecting over the first
+                                     k_select approximate eigenvectors of the kept pair (harmonic Ritz
+                                     vectors of smallest |theta - sigma_1|) as in Theorem 1 (Sec. 4,
+                                     Example 4), instead of the Minres projection over V_k with the extra
+                                     right-hand side and the correction phase */
 #define GDR_FLAG_AUTOTUNE   128u  /* before the first cycle, run gdr_autotune for the matvec and Arnoldi
                                      form of each stage whose (precision, columns, m) the operator has
                                      no tuned shape for yet (the tuning time is part of the solve) */
@@ -93,6 +98,7 @@ typedef struct {
   int refine_max;     /* MIXED: refinement passes before the FP64 cleanup */
   gdr_prec prec;
   unsigned flags;
+  int k_select;       /* GDR_FLAG_EIG_SELECT: approximate eigenvectors projected over (1..k; <= 0: k) */
 } gdr_params;
 
 typedef struct {
@@ -113,6 +119,8 @@ typedef struct {
   double t_refine_ms;   /* FP64 true residuals, refinement passes and FP64 cleanup */
   long host_syncs;      /* host waits on the stream (one per cycle for the convergence test, ...) */
   double related_resid; /* GDR_FLAG_RELATED_RHS: largest ||b_j - B d|| / ||b_j|| over j >= 2 (else 0) */
+  double eig_resid_max; /* GDR_FLAG_EIG_SELECT: largest eigen-residual ||A z - theta z|| (||z|| = 1)
+                           of the selected approximate eigenvectors (else 0) */
 } gdr_report;
 
 /* ---------------------------------------------------------------- context */

@@ -27,14 +27,14 @@ GDR_PREC_FP64, GDR_PREC_MIXED = 0, 1
 GDR_LINK_C128, GDR_LINK_C64, GDR_LINK_BF16 = 0, 1, 2
 GDR_MAX_M = 96
 (GDR_FLAG_HOST_PTRS, GDR_FLAG_NO_GRAPH, GDR_FLAG_SEQUENTIAL, GDR_FLAG_NO_PROJ, GDR_FLAG_NO_REFINE, GDR_FLAG_NO_SWEEP,
- GDR_FLAG_FP64_EIG, GDR_FLAG_AUTOTUNE, GDR_FLAG_RELATED_RHS) = 1, 2, 4, 8, 16, 32, 64, 128, 256
+ GDR_FLAG_FP64_EIG, GDR_FLAG_AUTOTUNE, GDR_FLAG_RELATED_RHS, GDR_FLAG_EIG_SELECT) = 1, 2, 4, 8, 16, 32, 64, 128, 256, 512
 
 
 class gdr_params(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("k", ctypes.c_int), ("m_proj", ctypes.c_int),
                 ("tol", ctypes.c_double), ("extra_tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
                 ("refine_tol", ctypes.c_double), ("max_mvps", ctypes.c_long), ("max_cycles", ctypes.c_int), ("refine_max", ctypes.c_int),
-                ("prec", ctypes.c_int), ("flags", ctypes.c_uint)]
+                ("prec", ctypes.c_int), ("flags", ctypes.c_uint), ("k_select", ctypes.c_int)]
 
 
 class gdr_report(ctypes.Structure):
@@ -44,7 +44,7 @@ class gdr_report(ctypes.Structure):
                 ("max_relres", ctypes.c_double), ("t_total_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_long), ("t_rhs1_ms", ctypes.c_double),
                 ("t_proj_ms", ctypes.c_double), ("t_refine_ms", ctypes.c_double), ("host_syncs", ctypes.c_long),
-                ("related_resid", ctypes.c_double)]
+                ("related_resid", ctypes.c_double), ("eig_resid_max", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

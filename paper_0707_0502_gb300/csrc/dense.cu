@@ -904,6 +904,13 @@ DEV bool harmonic_ritz(const DenseCycle& d, int c, unsigned char* smem, ShT<R>& 
   }
   __syncthreads();
   GDR_DENSE_MARK(8, 0);
+  if (d.graw) {  // the raw eigenvectors G and their values (selection order), no P_k
+    c128* gout = d.graw + (long)c * ldp * k;
+    for (int q = threadIdx.x; q < ldp * k; q += DT) gout[q] = up(T[q]);
+    for (int q = threadIdx.x; q < k; q += DT) d.gtheta[(long)c * k + q] = up(theta[sel[q]]);
+    __syncthreads();
+    return true;
+  }
   // 9) P_k = orth([G; 0]) by classical Gram-Schmidt twice, in T (ld m+1)
   C* coef = theta;  // reuse (size >= k)
   for (int q = 0; q < k; ++q) {
@@ -1183,6 +1190,162 @@ __global__ void __launch_bounds__(DT) dense_proj_kernel(ProjArgs a) {
   }
 }
 
+// Selected approximate eigenvectors of a kept pair (Sec. 4, Theorem 1, Example 4).
+// d: the kept pair as a cycle of size m = k (dense leading block), d.k = ks, graw /
+// gtheta set.  After the harmonic Ritz step: unit columns of G, theta of A (+ sigma_1),
+// eigen-residuals, and M = (G^H G)^{-1} G^H by Gaussian elimination with partial
+// pivoting on [G^H G | G^H] in the column's FP64 scratch (row-major, width ks + k).
+__global__ void __launch_bounds__(DT) eigsel_setup_kernel(DenseCycle d, c128* M, double* res) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ Sh sh;
+  __shared__ int piv_s;
+  if (!harmonic_ritz<double>(d, 0, smem_raw, sh)) return;
+  const int k = d.m, ks = d.k, ldg = k + 1, w = ks + k;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  c128* G = d.graw;
+  c128* th = d.gtheta;
+  const c128 s1 = d.sigma[0];
+  const c128* H = d.H;  // (k+1) x k
+  for (int q = warp; q < ks; q += DT / 32) {  // unit columns, eigen-residuals
+    c128* g = G + (long)q * ldg;
+    double nn = 0;
+    for (int i = lane; i < k; i += 32) nn += norm2(g[i]);
+    nn = warp_sum_r(nn);
+    const double inv = 1.0 / sqrt(nn);
+    for (int i = lane; i < k; i += 32) g[i] = inv * g[i];
+    __syncwarp();
+    const c128 lam = th[q] + s1;
+    double rr = 0;
+    for (int r = lane; r <= k; r += 32) {
+      c128 acc = (r < k) ? -(lam * g[r]) : c128{0, 0};
+      for (int j = 0; j < k; ++j) acc += H[r + (long)j * (k + 1)] * g[j];
+      rr += norm2(acc);
+    }
+    rr = warp_sum_r(rr);
+    if (lane == 0) {
+      th[q] = lam;
+      res[q] = sqrt(rr);
+    }
+  }
+  __syncthreads();
+  c128* Aug = reinterpret_cast<c128*>(d.scratch);  // ks x (ks + k)
+  for (int q = threadIdx.x; q < ks * w; q += DT) {
+    const int r = q / w, cc = q % w;
+    c128 v = {0, 0};
+    if (cc < ks) {
+      for (int i = 0; i < k; ++i) v += cmulc(G[i + (long)r * ldg], G[i + (long)cc * ldg]);
+    } else {
+      v = conj(G[(cc - ks) + (long)r * ldg]);
+    }
+    Aug[q] = v;
+  }
+  __syncthreads();
+  for (int p = 0; p < ks; ++p) {
+    if (warp == 0) {
+      double best = -1.0;
+      int pv = p;
+      for (int r = p + lane; r < ks; r += 32) {
+        const double a = norm2(Aug[(long)r * w + p]);
+        if (a > best) {
+          best = a;
+          pv = r;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int op = __shfl_xor_sync(0xffffffffu, pv, o);
+        if (ob > best || (ob == best && op < pv)) {
+          best = ob;
+          pv = op;
+        }
+      }
+      if (lane == 0) piv_s = pv;
+    }
+    __syncthreads();
+    const int pv = piv_s;
+    if (pv != p)
+      for (int cc = p + threadIdx.x; cc < w; cc += DT) {
+        const c128 t = Aug[(long)p * w + cc];
+        Aug[(long)p * w + cc] = Aug[(long)pv * w + cc];
+        Aug[(long)pv * w + cc] = t;
+      }
+    __syncthreads();
+    const c128 pval = Aug[(long)p * w + p];
+    const double pn = norm2(pval);
+    if (pn > 0.0) {
+      const c128 inv = {pval.x / pn, -pval.y / pn};
+      const int rows = ks - p - 1, cols = w - p;
+      for (int q = threadIdx.x; q < rows * cols; q += DT) {
+        const int r = p + 1 + q / cols, cc = p + q % cols;
+        const c128 f = Aug[(long)r * w + p] * inv;
+        if (cc > p) Aug[(long)r * w + cc] -= f * Aug[(long)p * w + cc];
+      }
+      __syncthreads();
+      for (int r = p + 1 + threadIdx.x; r < ks; r += DT) Aug[(long)r * w + p] = {0, 0};
+    } else if (threadIdx.x == 0) {
+      set_err(d.st, GDR_EBREAKDOWN);  // dependent eigenvectors
+    }
+    __syncthreads();
+  }
+  // back substitution, one thread per column of G^H: M[l][j], row-major ks x k
+  for (int j = threadIdx.x; j < k; j += DT) {
+    for (int l = ks - 1; l >= 0; --l) {
+      c128 acc = Aug[(long)l * w + ks + j];
+      for (int q = l + 1; q < ks; ++q) acc -= Aug[(long)l * w + q] * M[(long)q * k + j];
+      const c128 pval = Aug[(long)l * w + l];
+      const double pn = norm2(pval);
+      M[(long)l * k + j] = pn > 0.0 ? acc * c128{pval.x / pn, -pval.y / pn} : c128{0, 0};
+    }
+  }
+}
+
+struct EigSelArgs {
+  const c128* G; const c128* M; const c128* theta; int ks;
+};
+
+// Theorem 1 projection for column c (grid.y) and shift i (grid.x)
+__global__ void __launch_bounds__(DT) eigsel_proj_kernel(ProjArgs a, EigSelArgs e) {
+  __shared__ c128 dv[GDR_MAX_M], ev[GDR_MAX_M + 1];
+  const int c = blockIdx.y, i = blockIdx.x;
+  ColState* st = a.st + c;
+  if (!st->active) return;
+  const int k = a.k, ldc = k + 1, ks = e.ks, ldg = k + 1;
+  const c128* Hk = a.Hk + (long)(c / a.hpp) * a.hkcs;
+  c128* Cf = a.Cf + (long)c * a.ccs;
+  const int* sact = a.sact + (long)c * a.ns;
+  if (i > 0 && !sact[i]) {
+    for (int r = threadIdx.x; r <= k; r += DT) Cf[r + (long)i * ldc] = {0, 0};
+    return;
+  }
+  const c128* cp = a.cproj + (long)c * (k + 2);
+  const c128 si = a.sigma[(long)c * a.ns + i];
+  const c128 bi = i == 0 ? c128{1, 0} : a.beta[(long)c * a.ns + i];
+  for (int l = threadIdx.x; l < ks; l += DT) {
+    c128 acc = {0, 0};
+    for (int j = 0; j < k; ++j) acc += e.M[(long)l * k + j] * cp[j];
+    const c128 den = e.theta[l] - si;
+    const double dn = norm2(den);
+    dv[l] = (bi * acc) * c128{den.x / dn, -den.y / dn};
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < k; r += DT) {
+    c128 acc = {0, 0};
+    for (int l = 0; l < ks; ++l) acc += e.G[r + (long)l * ldg] * dv[l];
+    ev[r] = acc;
+    Cf[r + (long)i * ldc] = acc;
+  }
+  if (threadIdx.x == 0) Cf[k + (long)i * ldc] = {0, 0};
+  __syncthreads();
+  if (i == 0) {  // residual column -(Hbar_k - sigma_1 Ibar) e_1
+    for (int r = threadIdx.x; r <= k; r += DT) {
+      c128 acc = (r < k) ? -(si * ev[r]) : c128{0, 0};
+      for (int j = 0; j < k; ++j) acc += Hk[r + (long)j * (k + 1)] * ev[j];
+      Cf[r + (long)a.ns * ldc] = -acc;
+    }
+  }
+}
+
 }  // namespace
 
 size_t dense_smem_bytes(int m, int k) {
@@ -1198,6 +1361,7 @@ void dense_init(gdr_ctx* ctx) {
   size_t lim = set_max_dyn_smem(ctx, dense_d1_kernel);
   lim = std::min(lim, set_max_dyn_smem(ctx, dense_d2_kernel));
   lim = std::min(lim, set_max_dyn_smem(ctx, dense_proj_kernel));
+  lim = std::min(lim, set_max_dyn_smem(ctx, eigsel_setup_kernel));
   lim = std::min(lim, set_max_dyn_smem(ctx, restart_only_kernel));
   ctx->dense_smem_limit = lim;
 }
@@ -1251,12 +1415,61 @@ void cycle_finish(gdr_ctx* ctx, const DenseCycle& d, c128* H, c128* cvec) {
 
 void dense_projection(gdr_ctx* ctx, int ncol, int k, int ns, const c128* Hk, const c128* cproj, const c128* sigma,
                       const c128* beta, const int* sact, c128* gamma, c128* Cf, long ccs, double*, long,
-                      ColState* st, long hkcs, int hpp) {
+                      ColState* st, long hkcs, int hpp, const EigSel* es) {
   ProjArgs a{k, ns, Hk, cproj, sigma, beta, sact, gamma, Cf, ccs, st, hkcs, hpp};
+  if (es) {
+    GDR_REQUIRE(es->ks >= 1 && es->ks <= k && k <= GDR_MAX_M, "bad eigenvector selection");
+    dim3 g((unsigned)ns, (unsigned)ncol);
+    KProf kp(ctx, "dense_projection_eigsel", 0.0);
+    eigsel_proj_kernel<<<g, DT, 0, ctx->stream>>>(a, EigSelArgs{es->G, es->M, es->theta, es->ks});
+    GDR_LAUNCHED(ctx);
+    return;
+  }
   const size_t smem = sizeof(c128) * ((size_t)(k + 2) * (k + 1) + 5 * (size_t)(k + 2));
   GDR_REQUIRE(smem <= ctx->dense_smem_limit, "k too large for the projection kernel");
   dim3 g((unsigned)ns, (unsigned)ncol);
   KProf kp(ctx, "dense_projection", 0.0);
   dense_proj_kernel<<<g, DT, smem, ctx->stream>>>(a);
   GDR_LAUNCHED(ctx);
+}
+
+void eigsel_setup(gdr_ctx* ctx, const c128* Hk, int k, int ks, c128 sigma1, EigSel& out, double* res_host) {
+  GDR_REQUIRE(k >= 1 && k <= GDR_MAX_M && ks >= 1 && ks <= k, "bad eigenvector selection size");
+  DenseCycle d{};
+  d.ncol = 1;
+  d.m = k;
+  d.k = ks;
+  d.ns = 1;
+  d.kfull = k + 1;  // the kept Hbar_k is dense
+  d.H = Hk;
+  c128* sig = ctx->get<c128>("es.sigma", 1);
+  GDR_CUDA(cudaMemcpyAsync(sig, &sigma1, sizeof(c128), cudaMemcpyHostToDevice, ctx->stream));
+  d.sigma = sig;
+  d.theta = ctx->get<c128>("es.theta_all", (size_t)k);
+  d.scratch_per_col = std::max<long>(2L * ((long)k * k + 2L * k * ks + 64), 2L * (long)ks * (ks + k) + 64);
+  d.scratch = ctx->get<double>("es.scratch", (size_t)d.scratch_per_col);
+  d.Pk = ctx->get<c128>("es.Pk", (size_t)(k + 1) * ks);
+  d.graw = ctx->get<c128>("es.G", (size_t)(k + 1) * ks);
+  d.gtheta = ctx->get<c128>("es.theta", (size_t)ks);
+  d.st = ctx->get<ColState>("es.st", 1);
+  ColState s0 = {};
+  s0.active = 1;
+  s0.m_eff = k;
+  GDR_CUDA(cudaMemcpyAsync(d.st, &s0, sizeof(s0), cudaMemcpyHostToDevice, ctx->stream));
+  c128* M = ctx->get<c128>("es.M", (size_t)ks * k);
+  double* res = ctx->get<double>("es.res", (size_t)ks);
+  const size_t smem = dense_smem_bytes(k, ks);
+  GDR_REQUIRE(smem <= ctx->dense_smem_limit, "k too large for the eigenvector selection");
+  KProf kp(ctx, "eigsel_setup", 0.0);
+  eigsel_setup_kernel<<<1, DT, smem, ctx->stream>>>(d, M, res);
+  GDR_LAUNCHED(ctx);
+  ColState s1;
+  GDR_CUDA(cudaMemcpyAsync(&s1, d.st, sizeof(s1), cudaMemcpyDeviceToHost, ctx->stream));
+  if (res_host) GDR_CUDA(cudaMemcpyAsync(res_host, res, sizeof(double) * ks, cudaMemcpyDeviceToHost, ctx->stream));
+  GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (s1.err) throw gdr_error((gdr_status)s1.err, "eigenvector selection: harmonic Ritz step failed");
+  out.G = d.graw;
+  out.M = M;
+  out.theta = d.gtheta;
+  out.ks = ks;
 }

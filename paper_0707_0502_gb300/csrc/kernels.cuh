@@ -180,7 +180,22 @@ struct DenseCycle {
   ColState* st;
   bool want_r;
   int hr32;  // harmonic Ritz eigensolve in FP32 (complex64 basis); FP64 when it cannot be trusted
+  c128* graw = nullptr;    // if set: harmonic Ritz stops after the eigenvectors, G ((m+1) x k per column,
+  c128* gtheta = nullptr;  // last row 0) into graw and their values (selection order) into gtheta
 };
+
+// Projection over selected approximate eigenvectors of a kept pair (Sec. 4, Theorem 1,
+// Example 4): z_l = V_k g_l (||g_l|| = 1), eigenvalues theta_l of A, M = (G^H G)^{-1} G^H.
+struct EigSel {
+  const c128* G = nullptr;      // k x ks, leading dimension k + 1
+  const c128* M = nullptr;      // ks x k, row-major
+  const c128* theta = nullptr;  // ks
+  int ks = 0;
+};
+// The ks 'smallest' harmonic Ritz pairs of the kept pair (Hk: device (k+1) x k, base
+// shift sigma1) and M; buffers from the context workspace; res_host (ks values, may be
+// null) receives the eigen-residual norms ||(Hbar_k - theta_l Ibar) g_l||.  Synchronises.
+void eigsel_setup(gdr_ctx* ctx, const c128* Hk, int k, int ks, c128 sigma1, EigSel& out, double* res_host);
 void dense_cycle(gdr_ctx* ctx, const DenseCycle& d);
 // cycle bookkeeping after the reduced solves: convergence test, beta/active update,
 // the next cycle's Hbar/c (from Hk/ck when k > 0)
@@ -191,9 +206,12 @@ void cycle_finish(gdr_ctx* ctx, const DenseCycle& d, c128* H, c128* cvec);
 // shifts: (H_k - sigma_i I) d_i = beta_i (H_k - sigma_1 I) d_1; gamma_i accumulated.
 // Writes Cf (ldc = k+1): columns [0, ns) = [d_i ; 0], column ns = -(Hbar_k - sigma_1 Ibar) d_1.
 // Hk: column c uses Hk + (c / hpp) * hkcs (hkcs = 0: one Hbar_k shared by all columns).
+// With es (selected eigenvectors): the Theorem 1 projection instead (every column, every
+// shift: d_i = beta_i (Theta - sigma_i)^{-1} M c[0:k], Cf[:, i] = [G d_i ; 0], residual
+// column -(Hbar_k - sigma_1 Ibar) G d_1; gamma untouched).
 void dense_projection(gdr_ctx* ctx, int ncol, int k, int ns, const c128* Hk, const c128* cproj, const c128* sigma,
                       const c128* beta, const int* sact, c128* gamma, c128* Cf, long ccs, double* scratch,
-                      long scratch_per_col, ColState* st, long hkcs = 0, int hpp = 1);
+                      long scratch_per_col, ColState* st, long hkcs = 0, int hpp = 1, const EigSel* es = nullptr);
 
 size_t dense_smem_bytes(int m, int k);
 // harmonic Ritz restart products alone, for the s already in d.s

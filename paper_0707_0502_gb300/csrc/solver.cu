@@ -540,10 +540,10 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
     set_run_kernel<<<(ncol + 31) / 32, 32, 0, ctx->stream>>>(b.st, ncol);
     GDR_LAUNCHED(ctx);
     if (k > 0 && job.project) {
-      // steps 3-4: Minres projection over V_k; c = V_{k+1}^H r
+      // steps 3-4: Minres projection over V_k (or over selected eigenvectors); c = V_{k+1}^H r
       gs_dot<R>(ctx, bd, k + 1, r, ldr, cproj, false);
       dense_projection(ctx, ncol, k, ns, job.Hk, cproj, b.sigma, sh.beta, sh.sact, sh.gamma, Cp, (long)(k + 1) * (ns + 1),
-                       nullptr, 0, b.st, job.hkcs, job.dpp);
+                       nullptr, 0, b.st, job.hkcs, job.dpp, job.eigsel);
       // x_i += V_k d_i, r -= V_{k+1} (Hbar_k - sigma_1 Ibar) d_1
       combine<R>(ctx, n, ncol, bd.V, bd.ldv, job.vdcs, k + 1, Cp, k + 1, (long)(k + 1) * (ns + 1), 0, ns, 2, job.X,
                  job.ldx, job.xcs, r, ldr, b.st, b.nvec, job.dpp);
@@ -737,6 +737,16 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
   }
   const bool project = kd > 0 && !(p.flags & GDR_FLAG_NO_PROJ);
   const bool related = (p.flags & GDR_FLAG_RELATED_RHS) != 0 && nrhs > 1;
+  // Sec. 4, Example 4: right-hand sides 2.. projected over the first k_select approximate
+  // eigenvectors of the kept pair (Theorem 1), no extra right-hand side, no correction
+  EigSel es;
+  const bool eigsel = project && nrhs > 1 && (p.flags & GDR_FLAG_EIG_SELECT) != 0;
+  if (eigsel) {
+    const int ks = (p.k_select > 0 && p.k_select < kd) ? p.k_select : kd;
+    std::vector<double> eres(ks);
+    eigsel_setup(ctx, Hkd, kd, ks, sigma[0], es, eres.data());
+    for (double v : eres) rep.eig_resid_max = std::max(rep.eig_resid_max, v);
+  }
   const int np = ns * nrhs;
   c128* Rres = ctx->get<c128>("pl.Rres", (size_t)ld * np);
   std::vector<double> relres(np, std::numeric_limits<double>::infinity());
@@ -839,14 +849,14 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
     cx<R>* rhs = ctx->get<cx<R>>("pl.rhs", (size_t)ld * ncol);
     c128* XP = ctx->get<c128>("pl.XP", (size_t)ld * ns * ncol);  // slot 0: S (extra), slot j: X for rhs j+1
     GDR_CUDA(cudaMemsetAsync(XP, 0, sizeof(c128) * ld * ns * ncol, ctx->stream));
-    if (project)
+    if (project && !eigsel)
       GDR_CUDA(cudaMemcpyAsync(rhs, Vd + (long)kd * ld, sizeof(cx<R>) * n, cudaMemcpyDeviceToDevice, ctx->stream));
     if (!related) to_inner<R>(ctx, n, nrhs - 1, B + ldb, ldb, rhs + ld, ld);
     std::vector<int> mask(ncol, 1);
-    if (!project) mask[0] = 0;
+    if (!project || eigsel) mask[0] = 0;
     std::vector<double> tol_scale(ncol, 1.0);  // stage tolerance of a column relative to ||b_j|| / ||its rhs||
     const bool seq = (p.flags & GDR_FLAG_SEQUENTIAL) != 0 || related;
-    const int first = project ? 0 : 1;
+    const int first = (project && !eigsel) ? 0 : 1;
     auto run_cols = [&](int c0, int cn) {
       ProjJob<R> job;
       job.ncol = cn;
@@ -872,6 +882,7 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
       job.xcs = (long)ns * ld;
       job.max_mvps = p.max_mvps;
       job.sweep = !(p.flags & GDR_FLAG_NO_SWEEP);
+      if (eigsel) job.eigsel = &es;
       ProjResult pr = proj_batch<R>(ctx, A, job, use_graph && !seq);
       for (int c = 0; c < cn; ++c) {
         if (c0 + c == 0) rep.mvps_extra += pr.mvps[c];
@@ -881,7 +892,7 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
     };
     // correction phase (FP64): extra solutions s_i = s~_i / (1 - gamma_i), then x_i^j += gamma_i^j s_i
     c128* RP = ctx->get<c128>("pl.RP", (size_t)ld * ns * ncol);
-    const bool correct = project && ns > 1;
+    const bool correct = project && ns > 1 && !eigsel;
     const c128* v128 = correct ? V128 + (long)kd * ld : nullptr;
     c128* gam = ctx->get<c128>("pl.gam", (size_t)ns * ncol);
     const int dnblk = (int)std::min<long>((n + 255) / 256, 2L * ctx->num_sms);
@@ -928,7 +939,7 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
       // Sec. 5: right-hand sides one at a time, each started from the Minres projection over the
       // converged solutions of the previous ones (B^H B d = B^H b_j, x_i = X_i d, common residual
       // b_j - B d), then Proj-Sh and the correction on that residual, then refined to tol
-      if (project) run_cols(0, 1);
+      if (project && !eigsel) run_cols(0, 1);
       if (correct) scale_extra();
       refine_rhs(0, 1);
       c128* M = ctx->get<c128>("rel.M", (size_t)nrhs * (nrhs + 1));

@@ -60,6 +60,7 @@ struct ProjJob {
   long ldx = 0, xcs = 0;
   long max_mvps = 100000;
   bool sweep = true;           // persistent Arnoldi sweep where it fits (sweep_fits)
+  const EigSel* eigsel = nullptr;  // project over selected approximate eigenvectors instead (Theorem 1)
 };
 
 struct ProjResult {
