@@ -238,7 +238,9 @@ gdr_status gdr_solve_batch(gdr_ctx *ctx, const gdr_op *A, int ns, const double *
                            const gdr_params *params, gdr_report *report, int *status);
 
 /* GMRES(m_p)-Proj(k)-Sh with a kept deflation space (Sec. 4), without the
- * correction phase: X[:, i, j] with residuals beta_i r + g_i v_{k+1}.
+ * correction phase: X[:, i, j] with residuals beta_i r + g_i v_{k+1}.  With
+ * GDR_FLAG_EIG_SELECT: over the first k_select approximate eigenvectors of the
+ * kept pair (Theorem 1) instead; the report's eig_resid_max is then set.
  * Same argument conventions as gdr_solve_multishift. */
 gdr_status gdr_solve_proj(gdr_ctx *ctx, const gdr_op *A, const gdr_defl *defl, int ns, const double *sigma,
                           int nrhs, const double *B, double *X, const gdr_params *params, gdr_report *report);

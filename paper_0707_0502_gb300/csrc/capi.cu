@@ -516,6 +516,14 @@ gdr_status gdr_solve_proj(gdr_ctx* ctx, const gdr_op* A, const gdr_defl* defl, i
       job.ldx = ld;
       job.xcs = (long)ns * ld;
       job.max_mvps = p.max_mvps;
+      EigSel es;  // Sec. 4, Theorem 1: over the first k_select approximate eigenvectors instead
+      if (job.project && (p.flags & GDR_FLAG_EIG_SELECT)) {
+        const int ks = (p.k_select > 0 && p.k_select < defl->k) ? p.k_select : defl->k;
+        std::vector<double> eres(ks);
+        eigsel_setup(ctx, defl->Hk, defl->k, ks, sig[0], es, eres.data());
+        for (double v : eres) rep.eig_resid_max = std::max(rep.eig_resid_max, v);
+        job.eigsel = &es;
+      }
       ProjResult pr = proj_batch<R>(ctx, A, job, !(p.flags & GDR_FLAG_NO_GRAPH));
       for (long v : pr.mvps) rep.mvps_proj += v;
       result = pr.status;
