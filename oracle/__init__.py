@@ -28,6 +28,8 @@ from .operators import CSROperator, WilsonOperator, gamma_matrices, gamma5  # no
 from .krylov import (  # noqa: F401
     arnoldi_cgs2_step,
     gmres_sh_dense_step,
+    fom_sh_dense_step,
+    ritz,
     harmonic_ritz,
     select_smallest,
     gmres_dr_sh,

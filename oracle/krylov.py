@@ -101,6 +101,45 @@ def gmres_sh_dense_step(Hbar, c, sigma, beta, active):
     return D, s, beta_new, norms
 
 
+def fom_sh_dense_step(Hbar, c, sigma, beta, active):
+    """One FOM-Sh reduced solve (Sec. 3, Examples 2-3: the Galerkin counterpart of
+    GMRES-Sh).  Every shift solves the square system (H_m - sigma_i I) d_i = beta_i c[:m];
+    each residual beta_i c - (Hbar - sigma_i Ibar) d_i is then a multiple of e_{m+1}
+    (the residuals are parallel without any constraint), so with the base residual
+    s = c - (Hbar - sigma_1 Ibar) d_1: beta_i^new = (beta_i c - (Hbar - sigma_i Ibar) d_i)[m] / s[m].
+    Returns D, s, beta_new, norms as gmres_sh_dense_step."""
+    m = Hbar.shape[1]
+    ns = len(sigma)
+    Ib = _ibar(m + 1, m)
+    Hs1 = Hbar - sigma[0] * Ib
+    d1 = np.linalg.solve(Hs1[:m], c[:m])
+    s = c - Hs1 @ d1
+    snorm = np.linalg.norm(s)
+    D = np.zeros((m, ns), dtype=np.complex128)
+    D[:, 0] = d1
+    beta_new = np.array(beta, dtype=np.complex128)
+    for i in range(1, ns):
+        if not active[i]:
+            continue
+        Hsi = Hbar - sigma[i] * Ib
+        di = np.linalg.solve(Hsi[:m], beta[i] * c[:m])
+        beta_new[i] = (beta[i] * c - Hsi @ di)[m] / s[m]
+        D[:, i] = di
+    norms = np.abs(beta_new) * snorm
+    norms[0] = snorm
+    return D, s, beta_new, norms
+
+
+def ritz(Hs, k):
+    """Regular Ritz pairs of the shifted recurrence matrix Hs = Hbar - sigma_1 Ibar:
+    eigenpairs of its square part Hs[:m] (the restart of FOM-DR).  Returns
+    (theta_all, chosen indices, G_chosen (m x k)) like harmonic_ritz."""
+    m = Hs.shape[1]
+    theta, G = sla.eig(Hs[:m, :])
+    idx = select_smallest(theta, k)
+    return theta, idx, G[:, idx]
+
+
 # --------------------------------------------------------------------------
 # harmonic Ritz vectors (Sec. 2.2; formula from the cited GMRES-DR paper)
 # --------------------------------------------------------------------------
@@ -187,7 +226,7 @@ def _solve_invariant(Hbar, c, j1, sigma, beta, active):
     return D
 
 
-def gmres_dr_sh(matvec, b, sigma, m, k, tol, max_mvps=100000, max_cycles=None, record=False):
+def gmres_dr_sh(matvec, b, sigma, m, k, tol, max_mvps=100000, max_cycles=None, record=False, method="gmres"):
     """GMRES-DR(m,k)-Sh for (A - sigma_i I) x_i = b, zero initial guess.
 
     Returns a dict with
@@ -235,14 +274,16 @@ def gmres_dr_sh(matvec, b, sigma, m, k, tol, max_mvps=100000, max_cycles=None, r
             converged = np.ones(ns, dtype=bool)
             break
         # steps 3-5: base least squares, shifted solves, solution updates
-        D, s, beta_new, nrm = gmres_sh_dense_step(Hbar, c, sigma, beta, active)
+        # (method "fom": FOM-Sh / FOM-DR-Sh, Sec. 3 Examples 2-3: Galerkin solves, Ritz restart)
+        step = fom_sh_dense_step if method == "fom" else gmres_sh_dense_step
+        D, s, beta_new, nrm = step(Hbar, c, sigma, beta, active)
         x += V[:, :m] @ D
         upd = active.copy()
         upd[0] = True
         beta = np.where(upd, beta_new, beta)
         norms = np.where(upd, nrm, norms)      # a frozen shift keeps its residual
         Hs1 = Hbar - sigma[0] * _ibar(m + 1, m)
-        theta, idx, G = harmonic_ritz(Hs1, k)
+        theta, idx, G = (ritz if method == "fom" else harmonic_ritz)(Hs1, k)
         if record:
             history.append(dict(mvps=mvps, norms=norms.copy(), beta=beta.copy(), x=x.copy(),
                                 theta=theta, idx=idx, G=G, Vm=V.copy(), Hbar=Hbar.copy(), c=c.copy(),
