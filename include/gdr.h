@@ -73,6 +73,10 @@ typedef enum { GDR_LINK_C128 = 0, GDR_LINK_C64 = 1, GDR_LINK_BF16 = 2 } gdr_link
                                      vectors of smallest |theta - sigma_1|) as in Theorem 1 (Sec. 4,
                                      Example 4), instead of the Minres projection over V_k with the extra
                                      right-hand side and the correction phase */
+#define GDR_FLAG_FOM        1024u /* right-hand side 1 (and every problem of a batch) by FOM(m)-Sh (k = 0)
+                                     or FOM-DR(m,k)-Sh (Sec. 3, Examples 2-3): square Galerkin solves for
+                                     every shift (residuals parallel by construction) and a restart with
+                                     regular Ritz vectors; later stages unchanged */
 #define GDR_FLAG_AUTOTUNE   128u  /* before the first cycle, run gdr_autotune for the matvec and Arnoldi
                                      form of each stage whose (precision, columns, m) the operator has
                                      no tuned shape for yet (the tuning time is part of the solve) */

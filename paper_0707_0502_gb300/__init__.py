@@ -27,7 +27,8 @@ GDR_PREC_FP64, GDR_PREC_MIXED = 0, 1
 GDR_LINK_C128, GDR_LINK_C64, GDR_LINK_BF16 = 0, 1, 2
 GDR_MAX_M = 96
 (GDR_FLAG_HOST_PTRS, GDR_FLAG_NO_GRAPH, GDR_FLAG_SEQUENTIAL, GDR_FLAG_NO_PROJ, GDR_FLAG_NO_REFINE, GDR_FLAG_NO_SWEEP,
- GDR_FLAG_FP64_EIG, GDR_FLAG_AUTOTUNE, GDR_FLAG_RELATED_RHS, GDR_FLAG_EIG_SELECT) = 1, 2, 4, 8, 16, 32, 64, 128, 256, 512
+ GDR_FLAG_FP64_EIG, GDR_FLAG_AUTOTUNE, GDR_FLAG_RELATED_RHS, GDR_FLAG_EIG_SELECT,
+ GDR_FLAG_FOM) = 1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024
 
 
 class gdr_params(ctypes.Structure):

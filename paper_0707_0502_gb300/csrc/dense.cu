@@ -299,7 +299,9 @@ DEV void base_ls(const DenseCycle& d, int c, c128* A, Sh& sh) {
   const c128* H = d.H + (long)c * (m + 1) * m;
   const c128* cv = d.cvec + (long)c * (m + 1);
   const c128 sig = d.sigma[(long)c * d.ns];
-  const int rows = broke ? me : me + 1;
+  // GMRES: least squares on the (m+1) x m recurrence; FOM (and a lucky breakdown): the
+  // square m x m Galerkin system
+  const int rows = (broke || d.fom) ? me : me + 1;
   const int lda = odd_ld(rows);
   load_shifted(A, lda, H, m + 1, rows, me, sig);
   for (int i = threadIdx.x; i < rows; i += DT) A[i + (long)me * lda] = cv[i];
@@ -357,6 +359,38 @@ DEV void shift_solve(const DenseCycle& d, int c, int i, c128* A, Sh& sh) {
   const c128* s = d.s + (long)c * (m + 1);
   const c128 sig = d.sigma[(long)c * d.ns + i];
   const c128 beta = d.beta[(long)c * d.ns + i];
+  if (d.fom) {
+    // FOM: (H_m - sigma_i I) d_i = beta_i c[0:m] (Galerkin); the residual
+    // beta_i c - (Hbar - sigma_i Ibar) d_i is a multiple of e_{m+1}: beta_new relates
+    // its last component to that of the base residual s
+    const int lda = odd_ld(me);
+    load_shifted(A, lda, H, m + 1, me, me, sig);
+    for (int r = threadIdx.x; r < me; r += DT) A[r + (long)me * lda] = cv[r];
+    c128* tau = A + (long)lda * (me + 1);
+    c128* y = tau + (me + 1);
+    c128* rinv = y + (me + 1);
+    if (threadIdx.x == 0) sh.ibc[0] = 0;
+    __syncthreads();
+    hess_qr(A, lda, me, me, me + 1, tau, sh, d.kfull);
+    for (int r = threadIdx.x; r < me; r += DT) y[r] = beta * A[r + (long)me * lda];
+    __syncthreads();
+    if (!fast_backsolve(A, lda, me, y, rinv, sh)) set_err(st, GDR_EBREAKDOWN);
+    __syncthreads();
+    for (int r = threadIdx.x; r <= m; r += DT) Cf[r + (long)col * d.ldc] = (r < me) ? y[r] : c128{0, 0};
+    if (threadIdx.x == 0) {
+      c128 bnew = {0, 0};
+      if (!broke) {
+        c128 t = beta * cv[me];
+        for (int j = 0; j < me; ++j) t -= H[me + (long)j * (m + 1)] * y[j];
+        const c128 sl = s[me];
+        if (sl.x == 0.0 && sl.y == 0.0) set_err(st, GDR_EBREAKDOWN);
+        else bnew = cdiv(t, sl);
+      }
+      d.beta[(long)c * d.ns + i] = bnew;
+      d.norms[(long)c * d.ns + i] = cabs_(bnew) * st->rnorm;
+    }
+    return;
+  }
   const int rows = broke ? me : me + 1;
   const int lda = odd_ld(rows);
   load_shifted(A, lda, H, m + 1, rows, me, sig);
@@ -482,6 +516,7 @@ DEV bool harmonic_ritz(const DenseCycle& d, int c, unsigned char* smem, ShT<R>& 
     return false;
   };
   GDR_DENSE_MARK(0, 0);
+  if (!d.fom) {  // regular Ritz values (FOM-DR restart): M = Hhat, no f
   // 1) f = Hhat^{-H} hrow^H with Hhat = (Hbar - sigma_1 Ibar)[0:m, 0:m] = Q R:
   //    R^H z = hrow^H, f = Q z (thread 0 solves; the factors stay in T)
   load_shifted(T, lda, H, m + 1, m, m, sig);
@@ -533,13 +568,15 @@ DEV bool harmonic_ritz(const DenseCycle& d, int c, unsigned char* smem, ShT<R>& 
   } else {
     fd = reinterpret_cast<c128*>(f);
   }
+  }  // !d.fom
   GDR_DENSE_MARK(1, 0);
-  // 2) M = Hhat + f hrow (formed in FP64)
+  // 2) M = Hhat + f hrow (formed in FP64; M = Hhat for regular Ritz values)
   for (int t = threadIdx.x; t < m * m; t += DT) {
     const int i = t % m, j = t / m;
     c128 v = H[i + (long)j * (m + 1)];
     if (i == j) v -= sig;
-    T[i + (long)j * lda] = cvt<R>(v + fd[i] * H[m + (long)j * (m + 1)]);
+    if (!d.fom) v += fd[i] * H[m + (long)j * (m + 1)];
+    T[i + (long)j * lda] = cvt<R>(v);
   }
   __syncthreads();
   GDR_DENSE_MARK(2, 0);

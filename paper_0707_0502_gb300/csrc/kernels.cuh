@@ -180,6 +180,7 @@ struct DenseCycle {
   ColState* st;
   bool want_r;
   int hr32;  // harmonic Ritz eigensolve in FP32 (complex64 basis); FP64 when it cannot be trusted
+  int fom = 0;             // FOM-Sh / FOM-DR-Sh (Sec. 3): square Galerkin solves, regular Ritz restart
   c128* graw = nullptr;    // if set: harmonic Ritz stops after the eigenvectors, G ((m+1) x k per column,
   c128* gtheta = nullptr;  // last row 0) into graw and their values (selection order) into gtheta
 };

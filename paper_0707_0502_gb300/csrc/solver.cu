@@ -325,6 +325,7 @@ DrResult dr_sh(gdr_ctx* ctx, const gdr_op* A, const DrJob<R>& job, bool use_grap
   d.st = b.st;
   d.want_r = (k == 0);  // GMRES(m): restart from the residual vector r = V_{m+1} s
   d.hr32 = (std::is_same<R, float>::value && job.eig32) ? 1 : 0;  // complex64 basis: FP32 eigensolve in the restart
+  d.fom = job.fom ? 1 : 0;
   cx<R>* rres = ctx->get<cx<R>>("dr.r", (size_t)b.ldv * ncol);
   double* bn2 = ctx->get<double>("dr.bn2", (size_t)ncol + 4);
   double* nrm2 = ctx->get<double>("dr.nrm2", (size_t)ncol + 4);
@@ -684,6 +685,7 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
   dj.max_cycles = p.max_cycles;
   dj.sweep = !(p.flags & GDR_FLAG_NO_SWEEP);
   dj.eig32 = !(p.flags & GDR_FLAG_FP64_EIG);
+  dj.fom = (p.flags & GDR_FLAG_FOM) != 0;
   DrResult dr = dr_sh<R>(ctx, A, dj, use_graph);
   rep.t_rhs1_ms = ms_since(tp);
   tp = clk::now();
@@ -1064,6 +1066,7 @@ gdr_status solve_batch_pipeline(gdr_ctx* ctx, const gdr_op* A, int ns, const std
   dj.max_cycles = p.max_cycles;
   dj.sweep = !(p.flags & GDR_FLAG_NO_SWEEP);
   dj.eig32 = !(p.flags & GDR_FLAG_FP64_EIG);
+  dj.fom = (p.flags & GDR_FLAG_FOM) != 0;
   DrResult dr = dr_sh<R>(ctx, A, dj, use_graph);
   for (long v : dr.col_mvps) rep.mvps_rhs1 += v;
   rep.cycles_rhs1 = dr.cycles;

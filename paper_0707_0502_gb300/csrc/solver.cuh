@@ -20,6 +20,7 @@ struct DrJob {
   int max_cycles = 0;
   bool sweep = true;           // persistent Arnoldi sweep where it fits (sweep_fits)
   bool eig32 = true;           // complex64 basis: harmonic-Ritz eigensolve in FP32
+  bool fom = false;            // FOM-Sh / FOM-DR-Sh instead of GMRES-Sh / GMRES-DR-Sh (Sec. 3)
 };
 
 struct DrResult {
