@@ -164,26 +164,55 @@ def cpu_cores():
         return os.cpu_count()
 
 
-def cpu_baseline(p):
-    dt, out = oracle_solve(p)
+def cpu_baseline(p, solve_mvps=None):
+    """The oracle on the host cores.  Small workloads (up to 10^5 unknowns x rhs): one
+    complete solve.  Larger ones (configurations 3, 4): a bounded sample -- one timed
+    GMRES-DR(m,k)-Sh cycle of right-hand side 1 (m matvecs with their CGS2 and dense
+    steps) -- scaled to the matvec count of the whole solve (``solve_mvps``, the FP64 GPU
+    run's, which follows the same algorithm)."""
     sols = len(p.sigma) * p.B.shape[1]
-    return {"value": sols / dt, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-            "sample": f"one complete oracle solve of the workload ({sols} shifted solutions, "
-                      f"{out['mvps_rhs1']} mvps for rhs 1) in {dt:.2f} s, numpy/BLAS threads = cores"}
+    if p.n * p.B.shape[1] <= 100000 or not solve_mvps:
+        dt, out = oracle_solve(p)
+        return {"value": sols / dt, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                "sample": f"one complete oracle solve of the workload ({sols} shifted solutions, "
+                          f"{out['mvps_rhs1']} mvps for rhs 1) in {dt:.2f} s, numpy/BLAS threads = cores"}
+    from oracle import WilsonOperator, gmres_dr_sh
+    A = WilsonOperator(p.op[1], p.op[3], p.op[2])
+    t = time.perf_counter()
+    gmres_dr_sh(A.matvec, p.B[:, 0], p.sigma, p.m, p.k, p.tol, max_cycles=1)
+    dt = time.perf_counter() - t
+    est = dt / p.m * solve_mvps
+    return {"value": sols / est, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"estimated: one oracle GMRES-DR({p.m},{p.k})-Sh cycle of rhs 1 ({p.m} matvecs) took "
+                      f"{dt:.1f} s, scaled to the {solve_mvps} matvecs of the whole FP64 solve "
+                      f"({sols} shifted solutions), numpy/BLAS threads = cores"}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    p, cfg = workload(args.config)
+    if args.config == 5:  # the oracle on every problem of the batch, one after the other
+        from oracle import CSROperator, gmres_dr_sh
+        probs = W.config(5)
+        cfg = {"workload": "64 convection-diffusion CSR problems, sides 32-256, 4 shifts each, GMRES-DR(30,10)",
+               "config_id": 5}
+
+        def batch_solve():
+            t0 = time.perf_counter()
+            for q in probs:
+                gmres_dr_sh(CSROperator(*q.op[1:]).matvec, q.B[:, 0], q.sigma, q.m, q.k, 1e-8)
+            return time.perf_counter() - t0, None
+        solve, sols = batch_solve, sum(len(q.sigma) for q in probs)
+    else:
+        p, cfg = workload(args.config)
+        solve, sols = (lambda: oracle_solve(p)), len(p.sigma) * p.B.shape[1]
     times = []
     for _ in range(args.warmup):
-        oracle_solve(p)
+        solve()
     for _ in range(args.steps):
-        dt, _ = oracle_solve(p)
+        dt, _ = solve()
         times.append(dt)
-    sols = len(p.sigma) * p.B.shape[1]
     value = sols * len(times) / sum(times)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
@@ -197,10 +226,117 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ our arm
 
+def main_batch(args):
+    """Configuration 5: 64 independent convection-diffusion problems (sides 32..256,
+    4 shifts each) in one batched GMRES-DR(30,10)-Sh solve (gdr_solve_batch), mixed
+    precision against the plain FP64 batch; one step = one solve of the whole batch."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_0707_0502_gb300 as g
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    probs = W.config(5)
+    nprob, ns = len(probs), len(probs[0].sigma)
+    ntot = sum(p.n for p in probs)
+    sols = nprob * ns
+    p0 = probs[0]
+    stream = torch.cuda.Stream()
+    ctx = g.gdr_create(0, stream)
+    with torch.cuda.stream(stream):
+        op = g.make_batch_operator(ctx, probs)
+        Bh = np.concatenate([p.B[:, 0] for p in probs])
+        B = torch.as_tensor(Bh, device="cuda")
+        X = torch.zeros(ntot * ns, dtype=torch.complex128, device="cuda")
+        flush = torch.empty(512 * 2**20, dtype=torch.uint8, device="cuda")
+    stream.synchronize()
+    sig = np.stack([p.sigma for p in probs])
+    tune = g.gdr_autotune(ctx, op, g.GDR_PREC_MIXED, nprob, p0.m)
+    mixed = g.gdr_params_default(m=p0.m, k=p0.k, m_proj=p0.m_proj, tol=1e-8, prec=g.GDR_PREC_MIXED,
+                                 flags=g.GDR_FLAG_AUTOTUNE)
+    plain = g.gdr_params_default(m=p0.m, k=p0.k, m_proj=p0.m_proj, tol=1e-8, prec=g.GDR_PREC_FP64,
+                                 flags=g.GDR_FLAG_NO_GRAPH | g.GDR_FLAG_AUTOTUNE)
+
+    def timed(params, steps, warm, Bx=B, Xx=X):
+        for _ in range(warm):
+            g.gdr_solve_batch(ctx, op, sig, Bx, Xx, params)
+        ms, reps = [], []
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, rep, per = g.gdr_solve_batch(ctx, op, sig, Bx, Xx, params)
+            e1.record(stream)
+            e1.synchronize()
+            assert st == g.GDR_OK and (per == 0).all() and rep["max_relres"] <= 1e-8, (st, rep)
+            ms.append(e0.elapsed_time(e1))
+            reps.append(rep)
+        return ms, reps
+
+    clocks = Clocks(0)
+    clocks.start()
+    ms, reps = timed(mixed, args.steps, args.warmup)
+    clk = clocks.stop()
+    value = job_throughput(world, sols * args.steps, sum(ms) / 1e3)
+    ms64, reps64 = timed(plain, max(1, min(args.steps, 3)), 1)
+    fp64_value = sols * len(ms64) / (sum(ms64) / 1e3)
+    Bp = torch.as_tensor(Bh).pin_memory()
+    Xp = torch.zeros(ntot * ns, dtype=torch.complex128).pin_memory()
+    hostp = g.gdr_params_default(m=p0.m, k=p0.k, m_proj=p0.m_proj, tol=1e-8, prec=g.GDR_PREC_MIXED,
+                                 flags=g.GDR_FLAG_HOST_PTRS)
+    e2e_ms = []
+    for i in range(min(args.warmup, 2) + min(args.steps, 3)):
+        stream.synchronize()
+        t0 = time.perf_counter()
+        st, _, _ = g.gdr_solve_batch(ctx, op, sig, Bp.numpy(), Xp.numpy(), hostp)
+        if i >= min(args.warmup, 2):
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    roof, ktable = kernel_roofline(g, ctx, op, p0, mixed, stream, B, X, 5,
+                                   solve=lambda: g.gdr_solve_batch(ctx, op, sig, B, X, mixed))
+    rep = reps[-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sum(ms) / len(ms), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic",
+        "config": {"workload": f"64 convection-diffusion CSR problems, sides 32-256 ({ntot} unknowns), 4 shifts "
+                               f"each, GMRES-DR({p0.m},{p0.k}), one batched solve", "config_id": 5,
+                   "l2": "flushed before every timed step (512 MB write)"},
+        "clocks": clk, "gpu_launches": rep["kernel_launches"] * args.steps,
+        "e2e": {"value": sols * len(e2e_ms) / (sum(e2e_ms) / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": int(Bh.nbytes), "d2h_bytes_per_step": int(ntot * ns * 16)},
+        "fp64_plain": {"value": fp64_value, "unit": UNIT, "ms_per_step": sum(ms64) / len(ms64),
+                       "speedup_mixed_over_fp64": value / world / fp64_value},
+        "solve": {k: rep[k] for k in ("mvps_rhs1", "cycles_rhs1", "mvps_refine", "refine_passes", "max_relres",
+                                      "t_total_ms", "kernel_launches")},
+        "roofline": roof, "kernels": ktable, "autotune": tune,
+    }
+    if not args.no_cpu_baseline:
+        from oracle import CSROperator, gmres_dr_sh
+        t, done, names = 0.0, 0, []
+        for p in probs:  # a bounded sample: problems in batch order until ~15 s
+            A = CSROperator(*p.op[1:])
+            t0 = time.perf_counter()
+            gmres_dr_sh(A.matvec, p.B[:, 0], p.sigma, p.m, p.k, 1e-8)
+            t += time.perf_counter() - t0
+            done += 1
+            names.append(p.n)
+            if t > 15.0:
+                break
+        line["cpu_baseline"] = {"value": done * ns / t, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                                "sample": f"oracle GMRES-DR({p0.m},{p0.k})-Sh of the first {done} problems of the "
+                                          f"batch (n = {names}), {t:.1f} s, numpy/BLAS threads = cores"}
+    print(json.dumps(line), flush=True)
+    g.gdr_op_destroy(op)
+    g.gdr_destroy(ctx)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.config == 5:
+        main_batch(args)
         return
     if args.kernels_only:
         import torch
@@ -334,7 +470,8 @@ def main():
     if scale is not None:
         line["kernels_at_scale"] = scale
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(p)
+        r64 = reps64[-1]
+        line["cpu_baseline"] = cpu_baseline(p, r64["mvps_rhs1"] + r64["mvps_extra"] + r64["mvps_proj"])
     if rank == 0:
         print(json.dumps(line), flush=True)
     g.gdr_op_destroy(op)
@@ -367,7 +504,7 @@ def dense_flops(name, m, k, ns, ncol):
 NCU_TRAFFIC = {(CONFIG_ID, "gs_update_dot_c64"): 10243110}
 
 
-def kernel_roofline(g, ctx, op, p, params, stream, B, X, cid=CONFIG_ID):
+def kernel_roofline(g, ctx, op, p, params, stream, B, X, cid=CONFIG_ID, solve=None):
     """One extra solve of the workload with per-kernel CUDA events (graphs off):
     every kernel's launches, time and algorithmic bytes; the roofline of the one
     with the largest total time."""
@@ -380,7 +517,10 @@ def kernel_roofline(g, ctx, op, p, params, stream, B, X, cid=CONFIG_ID):
     hbm = peaks.get("hbm_gbs", 6800.0)
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     g.gdr_profile(ctx, True)
-    st, rep, _ = g.gdr_solve_multishift(ctx, op, p.sigma, B, X, params)
+    if solve is not None:
+        solve()
+    else:
+        g.gdr_solve_multishift(ctx, op, p.sigma, B, X, params)
     prof = g.gdr_profile_report(ctx)
     g.gdr_profile(ctx, False)
     total = sum(v["ms"] for v in prof.values())

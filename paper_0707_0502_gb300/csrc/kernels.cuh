@@ -46,7 +46,26 @@ struct Batch {
   const int* nvec = nullptr;  // per-column vector length (device); nullptr: all columns have length n
   int cpp = 1;                // operator problem of column c is c / cpp (CSR batch)
   int vpp = 1;                // gs_dot only: column c works on basis c / vpp (shared deflation bases)
+  // host-side sums for the algorithmic byte counts of the profiler (0: n per column / per basis)
+  double ntot = 0;            // the columns' vector lengths
+  double vtot = 0;            // the lengths of the distinct bases gs_dot reads (vpp > 1)
 };
+
+// profiler only (gdr_profile on, graphs off): the share of the elements of `ncol` columns
+// whose run flag (device, stride run_stride ints) is set, weighted by the per-column lengths
+// nvec (device, may be null: equal lengths); kernels skip the other columns.  1 when the
+// profiler is off.  Synchronises the stream.
+double run_share(gdr_ctx* ctx, int ncol, const int* run, int run_stride, const int* nvec);
+template <typename R> inline double run_share(gdr_ctx* ctx, const Batch<R>& b) {
+  return run_share(ctx, b.ncol, &b.st[0].run, (int)(sizeof(ColState) / sizeof(int)), b.nvec);
+}
+
+// algorithmic element counts of a batch: all its columns, and the bases gs_dot reads
+template <typename R> inline double col_len(const Batch<R>& b) { return b.ntot > 0 ? b.ntot : (double)b.n * b.ncol; }
+template <typename R> inline double basis_len(const Batch<R>& b) {
+  if (b.vtot > 0) return b.vtot;
+  return b.vpp > 1 ? (double)b.n * ((b.ncol + b.vpp - 1) / b.vpp) : col_len(b);
+}
 
 // krylov.cu --------------------------------------------------------------
 // h_out[c][0..nv-1] = V_c[:, 0:nv]^H w_c  (+ ||w_c||^2 in h_out[c][nv] if wnorm).  With wprev,
@@ -103,9 +122,11 @@ void dots128(gdr_ctx* ctx, long n, int cols, const c128* u, long ucs, const c128
 // C_c is c128 nv x (nout+nx+(rmode?1:0)), column-major with leading dim ldc, column stride ccs.
 // vcs = 0 shares one basis between all columns.
 template <typename R>
+// lenh / vlenh: host sums of the columns' lengths / of the distinct bases' lengths for the
+// profiler's byte count (0: n per column; one basis when vcs = 0)
 void combine(gdr_ctx* ctx, long n, int ncol, cx<R>* V, long ldv, long vcs, int nv, const c128* C, int ldc, long ccs,
              int nout, int nx, int rmode, c128* X, long ldx, long xcs, cx<R>* Rv, long rcs, const ColState* st,
-             const int* nvec = nullptr, int vpp = 1);
+             const int* nvec = nullptr, int vpp = 1, double lenh = 0, double vlenh = 0);
 
 void krylov_init(gdr_ctx* ctx);
 

@@ -589,6 +589,22 @@ unsigned grid_for(gdr_ctx* ctx, long work, int threads) {
 
 // ------------------------------------------------------------- launchers
 
+double run_share(gdr_ctx* ctx, int ncol, const int* run, int run_stride, const int* nvec) {
+  if (!ctx->profile || ncol <= 0 || run == nullptr) return 1.0;
+  std::vector<int> rf((size_t)ncol * run_stride), nv(nvec ? ncol : 0);
+  GDR_CUDA(cudaMemcpyAsync(rf.data(), run, sizeof(int) * ((size_t)(ncol - 1) * run_stride + 1),
+                           cudaMemcpyDeviceToHost, ctx->stream));
+  if (nvec) GDR_CUDA(cudaMemcpyAsync(nv.data(), nvec, sizeof(int) * ncol, cudaMemcpyDeviceToHost, ctx->stream));
+  GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+  double all = 0, on = 0;
+  for (int c = 0; c < ncol; ++c) {
+    const double len = nvec ? (double)nv[c] : 1.0;
+    all += len;
+    if (rf[(size_t)c * run_stride]) on += len;
+  }
+  return all > 0 ? on / all : 1.0;
+}
+
 // tile slots S x vector groups G of the dot kernels; S <= nblk bounds the partials
 template <typename R>
 static void dot_grid(gdr_ctx* ctx, const Batch<R>& b, int nvec, int& S, int& G) {
@@ -610,7 +626,7 @@ void gs_dot(gdr_ctx* ctx, const Batch<R>& b, int nv, const cx<R>* w, long wcs, c
   dot_grid(ctx, b, nv + (wnorm ? 1 : 0), S, G);
   dim3 grid((unsigned)(S * G), (unsigned)b.ncol);
   KProf kp(ctx, sizeof(R) == 4 ? "gs_dot_c64" : "gs_dot_c128",
-           ((double)(nv + 1) + (wprev ? 1.0 : 0.0)) * b.n * sizeof(cx<R>) * b.ncol);
+           ((double)nv * basis_len(b) + (wprev ? 2.0 : 1.0) * col_len(b)) * sizeof(cx<R>) * run_share(ctx, b));
   gs_dot_kernel<R><<<grid, NT, 0, ctx->stream>>>(b, nv, w, wcs, h_out, b.m + 2, wnorm ? 1 : 0, S, G, wprev);
   GDR_LAUNCHED(ctx);
 }
@@ -621,7 +637,7 @@ void gs_update_dot(gdr_ctx* ctx, const Batch<R>& b, int nv, const cx<R>* w, cx<R
   dot_grid(ctx, b, nv, S, G);
   dim3 grid((unsigned)(S * G), (unsigned)b.ncol);
   KProf kp(ctx, sizeof(R) == 4 ? "gs_update_dot_c64" : "gs_update_dot_c128",
-           (double)(nv + 2) * b.n * sizeof(cx<R>) * b.ncol);
+           (double)(nv + 2) * col_len(b) * sizeof(cx<R>) * run_share(ctx, b));
   gs_update_dot_kernel<R><<<grid, NT, 0, ctx->stream>>>(b, nv, w, wout, wcs, h, h_out, b.m + 2, S, G);
   GDR_LAUNCHED(ctx);
 }
@@ -629,14 +645,14 @@ template <typename R>
 void gs_update(gdr_ctx* ctx, const Batch<R>& b, int nv, cx<R>* w, long wcs, const c128* h, bool final_step) {
   dim3 grid((unsigned)b.nblk, (unsigned)b.ncol);
   KProf kp(ctx, sizeof(R) == 4 ? "gs_update_c64" : "gs_update_c128",
-           (double)(nv + 2) * b.n * sizeof(cx<R>) * b.ncol);
+           (double)(nv + 2) * col_len(b) * sizeof(cx<R>) * run_share(ctx, b));
   gs_update_kernel<R><<<grid, NT, 0, ctx->stream>>>(b, nv, w, wcs, h, b.m + 2, final_step ? 1 : 0);
   GDR_LAUNCHED(ctx);
 }
 template <typename R>
 void scale_into(gdr_ctx* ctx, const Batch<R>& b, int j, const cx<R>* w, long wcs) {
   dim3 grid(grid_for(ctx, nunits<R>(b.n), 256), (unsigned)b.ncol);
-  KProf kp(ctx, "scale", 2.0 * b.n * sizeof(cx<R>) * b.ncol);
+  KProf kp(ctx, "scale", 2.0 * col_len(b) * sizeof(cx<R>) * run_share(ctx, b));
   scale_kernel<R><<<grid, 256, 0, ctx->stream>>>(b, j, w, wcs);
   GDR_LAUNCHED(ctx);
 }
@@ -700,15 +716,19 @@ void dots128(gdr_ctx* ctx, long n, int cols, const c128* u, long ucs, const c128
 template <typename R>
 void combine(gdr_ctx* ctx, long n, int ncol, cx<R>* V, long ldv, long vcs, int nv, const c128* C, int ldc, long ccs,
              int nout, int nx, int rmode, c128* X, long ldx, long xcs, cx<R>* Rv, long rcs, const ColState* st,
-             const int* nvec, int vpp) {
+             const int* nvec, int vpp, double lenh, double vlenh) {
   const int ntot = nout + nx + (rmode ? 1 : 0);
   if (ntot == 0 || ncol == 0) return;
   const size_t smem = sizeof(cx<R>) * ((size_t)CR * nv + (size_t)nv * ntot);
   GDR_REQUIRE(smem <= ctx->combine_smem_limit, "combine: too many basis vectors / outputs for shared memory");
   dim3 grid((unsigned)((n + CR - 1) / CR), (unsigned)ncol);
+  // V read once per distinct basis, the rest per column
+  const double cl = lenh > 0 ? lenh : (double)n * ncol;
+  const double vl = vlenh > 0 ? vlenh : (vcs == 0 ? (double)n : (vpp > 1 ? (double)n * ((ncol + vpp - 1) / vpp) : cl));
+  const double act = st ? run_share(ctx, ncol, &st[0].run, (int)(sizeof(ColState) / sizeof(int)), nvec) : 1.0;
   KProf kp(ctx, sizeof(R) == 4 ? "combine_c64" : "combine_c128",
-           (double)ncol * n * ((nv + nout) * sizeof(cx<R>) + 2.0 * nx * sizeof(c128) +
-                               (rmode == 2 ? 2.0 : (rmode == 1 ? 1.0 : 0.0)) * sizeof(cx<R>)));
+           act * (vl * nv * sizeof(cx<R>) + cl * (nout * sizeof(cx<R>) + 2.0 * nx * sizeof(c128) +
+                                                 (rmode == 2 ? 2.0 : (rmode == 1 ? 1.0 : 0.0)) * sizeof(cx<R>))));
   combine_kernel<R><<<grid, CT, smem, ctx->stream>>>(n, V, ldv, vcs, nv, C, ldc, ccs, nout, nx, rmode, X, ldx, xcs,
                                                      Rv, rcs, st, nvec, vpp);
   GDR_LAUNCHED(ctx);
@@ -758,6 +778,6 @@ template void start_cycle<double>(gdr_ctx*, const Batch<double>&, const c128*, l
 template void norms2<c64>(gdr_ctx*, long, int, const c64*, long, double*, c128*, int, unsigned*, const int*);
 template void norms2<c128>(gdr_ctx*, long, int, const c128*, long, double*, c128*, int, unsigned*, const int*);
 template void combine<float>(gdr_ctx*, long, int, c64*, long, long, int, const c128*, int, long, int, int, int, c128*,
-                             long, long, c64*, long, const ColState*, const int*, int);
+                             long, long, c64*, long, const ColState*, const int*, int, double, double);
 template void combine<double>(gdr_ctx*, long, int, c128*, long, long, int, const c128*, int, long, int, int, int,
-                              c128*, long, long, c128*, long, const ColState*, const int*, int);
+                              c128*, long, long, c128*, long, const ColState*, const int*, int, double, double);

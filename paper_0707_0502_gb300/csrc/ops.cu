@@ -18,6 +18,8 @@
 #include "common.cuh"
 #include "wilson.cuh"
 
+double run_share(gdr_ctx* ctx, int ncol, const int* run, int run_stride, const int* nvec);
+
 namespace {
 
 // ------------------------------------------------------------- CSR kernel
@@ -240,16 +242,17 @@ static void op_apply_impl(gdr_ctx* ctx, const gdr_op* A, int ncol, const c128* s
   if (ncol <= 0) return;
   constexpr bool F64 = std::is_same<R, double>::value;
   const double sv = sizeof(cx<R>);
+  const double act = run_share(ctx, ncol, run, run_stride, nullptr);  // profiler: columns still running
   if (A->kind == OP_CSR || A->kind == OP_CSR_BATCH) {
     // row pointers, column indices, values, x read, y written (+ b read)
     const double bytes = (double)A->n * 4 + (double)A->nnz * (4 + (F64 ? 16 : 8)) +
-                         (double)ncol * A->n * sv * (B ? 3 : 2);
+                         act * (double)ncol * A->n * sv * (B ? 3 : 2);
     KProf kp(ctx, F64 ? "csr_matvec_c128" : "csr_matvec_c64", bytes);
     op_apply_launch<R>(ctx, A, ncol, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride, cpp, xs, xs_stride);
   } else {
     // per site: 4 links of 18 reals, 24 reals of x read and of y written (+ b read)
     const double sl = F64 ? 8 : (A->store == GDR_LINK_BF16 ? 2 : 4);
-    const double bytes = (double)A->V * (4 * 18 * sl + (double)ncol * 12 * sv * (B ? 3 : 2));
+    const double bytes = (double)A->V * (4 * 18 * sl + act * (double)ncol * 12 * sv * (B ? 3 : 2));
     KProf kp(ctx, F64 ? "wilson_matvec_c128" : (A->store == GDR_LINK_BF16 ? "wilson_matvec_c64_bf16links"
                                                                         : "wilson_matvec_c64"), bytes);
     op_apply_launch<R>(ctx, A, ncol, sigma, X, ldx, Y, ldy, B, ldb, run, run_stride, cpp, xs, xs_stride);

@@ -263,6 +263,17 @@ struct Shifted {  // per-column shift bookkeeping
   double* norms;
 };
 
+// vector length of column c (a CSR batch: the rows of problem c / cpp), and the sum over
+// every `every`-th of ncol columns (host side: the profiler's algorithmic byte counts)
+double len_of(const gdr_op* A, int c, int cpp) {
+  return A->kind == OP_CSR_BATCH ? (double)A->nrow_host[c / cpp] : (double)A->n;
+}
+double len_sum(const gdr_op* A, int ncol, int cpp, int every = 1) {
+  double t = 0;
+  for (int c = 0; c < ncol; c += every) t += len_of(A, c, cpp);
+  return t;
+}
+
 Shifted make_shifted(gdr_ctx* ctx, const std::string& tag, int ncol, int ns) {
   Shifted s;
   s.sact = ctx->get<int>(tag + ".sact", (size_t)ncol * ns);
@@ -304,6 +315,7 @@ DrResult dr_sh(gdr_ctx* ctx, const gdr_op* A, const DrJob<R>& job, bool use_grap
   Batch<R> b = make_batch<R>(ctx, "dr", n, ncol, m, ns);
   b.nvec = job.nvec;
   b.cpp = job.cpp;
+  b.ntot = len_sum(A, ncol, job.cpp);
   Shifted sh = make_shifted(ctx, "dr", ncol, ns);
   GDR_CUDA(cudaMemcpyAsync(b.sigma, job.sigma.data(), sizeof(c128) * ns * ncol, cudaMemcpyHostToDevice,
                            ctx->stream));
@@ -362,7 +374,7 @@ DrResult dr_sh(gdr_ctx* ctx, const gdr_op* A, const DrJob<R>& job, bool use_grap
       dense_cycle(ctx, d);
       // restart (V_{k+1} <- V_{m+1} P_{k+1}) fused with x_i += V_m d_i
       combine<R>(ctx, n, ncol, b.V, b.ldv, b.vcs, m + 1, d.Cf, ldc, d.ccs, k > 0 ? k + 1 : 0, ns, k > 0 ? 0 : 1,
-                 job.X, job.ldx, job.xcs, rres, b.ldv, b.st, b.nvec);
+                 job.X, job.ldx, job.xcs, rres, b.ldv, b.st, b.nvec, 1, col_len(b));
       if (k > 0) reorth_column<R>(ctx, b, k, nrm2);
       cycle_finish(ctx, d, b.H, b.cvec);
     };
@@ -422,6 +434,7 @@ void tune_arnoldi(gdr_ctx* ctx, const gdr_op* A, int ncol, int m, double& t_swee
     GDR_CUDA(cudaMemcpyAsync(nvd, nv.data(), sizeof(int) * ncol, cudaMemcpyHostToDevice, ctx->stream));
     b.nvec = nvd;
   }
+  b.ntot = len_sum(A, ncol, b.cpp);
   if (!sweep_fits<R>(ctx, A, b)) return;
   sweep_reserve<R>(ctx, b);
   Shifted sh = make_shifted(ctx, "tune", ncol, 1);
@@ -485,6 +498,7 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
   Batch<R> b = make_batch<R>(ctx, "pj", n, ncol, mp, ns, k + 2);
   b.nvec = job.nvec;
   b.cpp = job.cpp;
+  b.ntot = len_sum(A, ncol, job.cpp);
   Shifted sh = make_shifted(ctx, "pj", ncol, ns);
   GDR_CUDA(cudaMemcpyAsync(b.sigma, job.sigma.data(), sizeof(c128) * ns * ncol, cudaMemcpyHostToDevice,
                            ctx->stream));
@@ -511,6 +525,7 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
   bd.ldv = job.ldvd;
   bd.vcs = job.vdcs;
   bd.vpp = job.dpp;
+  bd.vtot = job.vdcs == 0 ? (double)len_of(A, 0, job.cpp) : len_sum(A, ncol, job.cpp, job.dpp);
   bd.m = k;
   c128* cproj = ctx->get<c128>("pj.cproj", (size_t)(k + 2) * ncol);
   c128* Cp = ctx->get<c128>("pj.Cp", (size_t)(k + 1) * (ns + 1) * ncol);
@@ -547,7 +562,7 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
                        nullptr, 0, b.st, job.hkcs, job.dpp, job.eigsel);
       // x_i += V_k d_i, r -= V_{k+1} (Hbar_k - sigma_1 Ibar) d_1
       combine<R>(ctx, n, ncol, bd.V, bd.ldv, job.vdcs, k + 1, Cp, k + 1, (long)(k + 1) * (ns + 1), 0, ns, 2, job.X,
-                 job.ldx, job.xcs, r, ldr, b.st, b.nvec, job.dpp);
+                 job.ldx, job.xcs, r, ldr, b.st, b.nvec, job.dpp, col_len(b), basis_len(bd));
     }
     // step 5: one GMRES(m_p)-Sh cycle on r
     start_cycle<R>(ctx, b, r, ldr);
@@ -560,7 +575,7 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
     }
     dense_cycle(ctx, d);
     combine<R>(ctx, n, ncol, b.V, b.ldv, b.vcs, mp + 1, d.Cf, ldc, d.ccs, 0, ns, 1, job.X, job.ldx, job.xcs, r, ldr,
-               b.st, b.nvec);
+               b.st, b.nvec, 1, col_len(b));
     cycle_finish(ctx, d, b.H, b.cvec);
   };
   for (;;) {

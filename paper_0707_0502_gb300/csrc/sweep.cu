@@ -695,7 +695,7 @@ void arnoldi_sweep(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b, int jstart,
   // algorithmic bytes: per step the matvec, dot (+ v_j store), update+dot and update passes
   double bytes = 0.0;
   {
-    const double sv = sizeof(cx<R>), nn = (double)b.n * b.ncol;
+    const double sv = sizeof(cx<R>), nn = col_len(b);
     double mv;
     if (A->kind == OP_WILSON) {
       const double sl = sizeof(R) == 8 ? 8 : (bf16 ? 2 : 4);
@@ -708,7 +708,7 @@ void arnoldi_sweep(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b, int jstart,
       bytes += mv + nn * sv * ((nv + 1 + (j > jstart ? 2 : 0)) + (nv + 2) + (nv + 2));
     }
   }
-  KProf kp(ctx, sizeof(R) == 4 ? "arnoldi_sweep_c64" : "arnoldi_sweep_c128", bytes);
+  KProf kp(ctx, sizeof(R) == 4 ? "arnoldi_sweep_c64" : "arnoldi_sweep_c128", bytes * run_share(ctx, b));
   if constexpr (sizeof(R) == 4) {
     if (bf16)
       launch_sweep<R, __nv_bfloat162>(ctx, a, grid, smem);
