@@ -39,12 +39,20 @@ void check_params(const gdr_params& p) {
 }
 
 // inner_tol <= 0: loose complex64 stages when the basis is L2-resident (there the
-// FP64 dense steps of each GMRES-DR cycle dominate), tight ones otherwise.
-gdr_params resolve_inner_tol(const gdr_ctx* ctx, long n, const gdr_params& p) {
+// FP64 dense steps of each GMRES-DR cycle dominate); otherwise as tight as the
+// operator's precision makes worthwhile, since each (shift, rhs) pair is refined on
+// its own while the stage serves all shifts at once (measured on GB300: 16^4 with
+// complex64 links 537 -> 480 ms at 3e-7; the 64-problem CSR batch 641 -> 611 ms at
+// 1e-6; bf16 links limit what a complex64 stage and a refinement pass reach, so a
+// tighter stage there only adds work: 24^3x32 11.2 s at 1e-5, 12.0 s at 1e-6).
+gdr_params resolve_inner_tol(const gdr_ctx* ctx, const gdr_op* A, long n, const gdr_params& p) {
   gdr_params r = p;
   if (!(r.inner_tol > 0)) {
     const double basis = (double)(p.m + 1) * (double)n * sizeof(c64);
-    r.inner_tol = (basis <= 0.5 * (double)ctx->l2_bytes) ? 1e-3 : 1e-5;
+    if (basis <= 0.5 * (double)ctx->l2_bytes) r.inner_tol = 1e-3;
+    else if (A->kind == OP_WILSON && A->store == GDR_LINK_BF16) r.inner_tol = 1e-5;
+    else if (A->kind == OP_CSR_BATCH) r.inner_tol = 1e-6;
+    else r.inner_tol = 3e-7;
   }
   // a complex64 refinement pass reliably reduces its residual by 1e-4: one pass then
   // usually finishes a pair that the stage left at ~1e-4
@@ -384,7 +392,7 @@ gdr_status gdr_solve_multishift(gdr_ctx* ctx, const gdr_op* A, int ns, const dou
     const cudaMemcpyKind kin = (p.flags & GDR_FLAG_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     const cudaMemcpyKind kout = (p.flags & GDR_FLAG_HOST_PTRS) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     stage_in(ctx, A, nrhs, B, Bi, ld, kin);
-    const gdr_params pr = resolve_inner_tol(ctx, A->n, p);
+    const gdr_params pr = resolve_inner_tol(ctx, A, A->n, p);
     {
       const int fi = p.prec == GDR_PREC_FP64 ? 1 : 0, mp = pr.m_proj > 0 ? pr.m_proj : pr.m - pr.k;
       std::vector<std::array<int, 3>> keys{{fi, 1, pr.m}};
@@ -434,7 +442,7 @@ gdr_status gdr_solve_batch(gdr_ctx* ctx, const gdr_op* A, int ns, const double* 
       GDR_CUDA(cudaMemcpyAsync(Bi + (long)q * ld, B + 2 * off, sizeof(c128) * nq, kin, ctx->stream));
       off += nq;
     }
-    const gdr_params pr = resolve_inner_tol(ctx, A->n * (long)A->nprob, p);
+    const gdr_params pr = resolve_inner_tol(ctx, A, A->n * (long)A->nprob, p);
     {
       const int fi = p.prec == GDR_PREC_FP64 ? 1 : 0, mp = pr.m_proj > 0 ? pr.m_proj : pr.m - pr.k;
       std::vector<std::array<int, 3>> keys{{fi, A->nprob, pr.m}};
