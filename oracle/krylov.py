@@ -9,7 +9,7 @@ V_{m+1} (r_0 = V_{m+1} c), beta_i are the collinearity factors
 r_{0,i} = beta_i r_{0,1} (Sec. 2.1).  Indices in code are 0-based: v_j in the
 code is v_{j+1} in the paper.
 
-Readings of the paper used here (each also listed in the design doc):
+Readings of the paper used here:
   * orthogonalisation is classical Gram-Schmidt with one full
     reorthogonalisation (CGS2); v_{k+1} is reorthogonalised after a restart;
   * harmonic Ritz vectors (Sec. 2.2 cites GMRES-DR for the formula) are taken
