@@ -104,6 +104,8 @@ typedef struct {
   gdr_prec prec;
   unsigned flags;
   int k_select;       /* GDR_FLAG_EIG_SELECT: approximate eigenvectors projected over (1..k; <= 0: k) */
+  int m_refine;       /* cycle length of the refinement / cleanup solves (not in the paper); <= 0:
+                         min(m, m_p + (m - m_p) / 2) for vectors of at most 2^17 elements, else m_p */
 } gdr_params;
 
 typedef struct {

@@ -35,7 +35,8 @@ class gdr_params(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("k", ctypes.c_int), ("m_proj", ctypes.c_int),
                 ("tol", ctypes.c_double), ("extra_tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
                 ("refine_tol", ctypes.c_double), ("max_mvps", ctypes.c_long), ("max_cycles", ctypes.c_int), ("refine_max", ctypes.c_int),
-                ("prec", ctypes.c_int), ("flags", ctypes.c_uint), ("k_select", ctypes.c_int)]
+                ("prec", ctypes.c_int), ("flags", ctypes.c_uint), ("k_select", ctypes.c_int),
+                ("m_refine", ctypes.c_int)]
 
 
 class gdr_report(ctypes.Structure):

@@ -33,6 +33,7 @@ void check_params(const gdr_params& p) {
   GDR_REQUIRE(p.m >= 2 && p.m <= GDR_MAX_M, "m must be in [2, GDR_MAX_M]");
   GDR_REQUIRE(p.k >= 0 && p.k < p.m, "k must satisfy 0 <= k < m");
   GDR_REQUIRE(p.m_proj >= 0 && p.m_proj <= GDR_MAX_M, "m_proj must be in [0, GDR_MAX_M]");
+  GDR_REQUIRE(p.m_refine <= GDR_MAX_M, "m_refine must be at most GDR_MAX_M");
   GDR_REQUIRE(p.tol > 0 && p.extra_tol > 0, "tolerances must be positive");
   GDR_REQUIRE(p.max_mvps > 0, "max_mvps must be positive");
   GDR_REQUIRE(p.prec == GDR_PREC_FP64 || p.prec == GDR_PREC_MIXED, "unknown precision");
