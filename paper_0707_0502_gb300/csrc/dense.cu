@@ -1151,6 +1151,45 @@ __global__ void cycle_finish_kernel(DenseCycle d, c128* Hn, c128* cn) {
 
 // ------------------------------------------------------------ projection
 
+// The projection's solution operators depend only on Hbar_k and the shifts, which stay
+// fixed for every cycle of a batch: they are formed once (two setup launches) and each
+// cycle applies them to c = V_{k+1}^H r with short dot products.  Per column c, (ns + 1)
+// blocks of (k+1) x (k+1), column-major with leading dimension k+1, at ops + c (ns+1)(k+1)^2:
+//   block 0  : P_1 = (Hbar_k - sigma_1 Ibar)^+ (least-squares solution operator) in rows
+//              0..k-1, row k zero
+//   block ns : T_1 = (Hbar_k - sigma_1 Ibar) P_1
+//   block i  : S_i = (H_k - sigma_i I)^{-1} T_1[0:k, :] in rows 0..k-1 and, in row k,
+//              g_i = T_1[k, :] - h_{k+1} S_i (h_{k+1}: the last row of Hbar_k)
+// so that d_1 = P_1 c, (Hbar_k - sigma_1 Ibar) d_1 = T_1 c, d_i = beta_i S_i c solves
+// (H_k - sigma_i I) d_i = beta_i (H_k - sigma_1 I) d_1 and the v_{k+1} component of the
+// shifted residual grows by beta_i g_i c (the last row of Ibar is zero).
+
+// x <- Q^H x for the reflectors of cta_qr (in factorisation order), one thread.
+DEV void apply_qh_serial(const c128* A, int lda, int rows, int cols, const c128* tau, c128* x, int kfull) {
+  for (int j = 0; j < min(cols, rows); ++j) {
+    const c128 tj = tau[j];
+    if (tj.x == 0.0 && tj.y == 0.0) continue;
+    const int last = qr_last(j, rows, kfull);
+    c128 w = x[j];
+    for (int i = j + 1; i <= last; ++i) w += cmulc(A[i + (long)j * lda], x[i]);
+    const c128 f = conj(tj) * w;
+    x[j] -= f;
+    for (int i = j + 1; i <= last; ++i) x[i] -= A[i + (long)j * lda] * f;
+  }
+}
+
+// x[0:n] <- R^{-1} x[0:n] (R: upper n x n of A), one thread; false on a zero pivot.
+DEV bool backsolve_serial(const c128* A, int lda, int n, c128* x) {
+  for (int l = n - 1; l >= 0; --l) {
+    c128 v = x[l];
+    for (int q = l + 1; q < n; ++q) v -= A[l + (long)q * lda] * x[q];
+    const c128 p = A[l + (long)l * lda];
+    if (p.x == 0.0 && p.y == 0.0) return false;
+    x[l] = cdiv(v, p);
+  }
+  return true;
+}
+
 struct ProjArgs {
   int k, ns;
   const c128* Hk; const c128* cproj; const c128* sigma; const c128* beta; const int* sact;
@@ -1158,72 +1197,128 @@ struct ProjArgs {
   long hkcs; int hpp;  // column c uses Hk + (c / hpp) * hkcs
 };
 
-__global__ void __launch_bounds__(DT) dense_proj_kernel(ProjArgs a) {
+// setup 1 (one CTA per column): Householder QR of Hbar_k - sigma_1 Ibar in shared memory;
+// thread j forms column j of P_1 (Q^H e_j, back substitution) and of T_1
+__global__ void __launch_bounds__(DT) proj_base_setup_kernel(ProjArgs a, c128* ops) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Sh sh;
+  const int c = blockIdx.x;
+  ColState* st = a.st + c;
+  if (!st->active) return;
+  const int k = a.k, ld = k + 1, la = odd_ld(k + 1);
+  const long bs = (long)ld * ld;
+  const c128* Hk = a.Hk + (long)(c / a.hpp) * a.hkcs;
+  const c128 s1 = a.sigma[(long)c * a.ns];
+  c128* A = reinterpret_cast<c128*>(smem_raw);
+  c128* tau = A + (long)la * k;
+  load_shifted(A, la, Hk, k + 1, k + 1, k, s1);
+  if (threadIdx.x == 0) sh.ibc[0] = 0;
+  __syncthreads();
+  cta_qr(A, la, k + 1, k, k, tau, sh, k + 1);
+  c128* P = ops + (long)c * (a.ns + 1) * bs;
+  c128* T = P + (long)a.ns * bs;
+  bool ok = true;
+  for (int j = threadIdx.x; j <= k; j += DT) {
+    c128* x = P + (long)j * ld;
+    for (int r = 0; r <= k; ++r) x[r] = {r == j ? 1.0 : 0.0, 0.0};
+    apply_qh_serial(A, la, k + 1, k, tau, x, k + 1);
+    x[k] = {0, 0};
+    ok = backsolve_serial(A, la, k, x) && ok;
+    c128* t = T + (long)j * ld;
+    for (int r = 0; r <= k; ++r) {
+      c128 acc0 = {0, 0}, acc1 = {0, 0};
+      int l = 0;
+      for (; l + 1 < k; l += 2) {
+        c128 h0 = Hk[r + (long)l * (k + 1)], h1 = Hk[r + (long)(l + 1) * (k + 1)];
+        if (r == l) h0 -= s1;
+        if (r == l + 1) h1 -= s1;
+        acc0 += h0 * x[l];
+        acc1 += h1 * x[l + 1];
+      }
+      if (l < k) {
+        c128 h0 = Hk[r + (long)l * (k + 1)];
+        if (r == l) h0 -= s1;
+        acc0 += h0 * x[l];
+      }
+      t[r] = acc0 + acc1;
+    }
+  }
+  if (__syncthreads_or(!ok)) set_err(st, GDR_EBREAKDOWN);
+}
+
+// setup 2 (one CTA per column and shift i >= 1): QR of H_k - sigma_i I; thread j solves
+// column j of S_i from T_1[0:k, j] and forms g_i[j]
+__global__ void __launch_bounds__(DT) proj_shift_setup_kernel(ProjArgs a, c128* ops) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ Sh sh;
+  const int c = blockIdx.y, i = blockIdx.x + 1;
+  ColState* st = a.st + c;
+  if (!st->active) return;
+  const int k = a.k, ld = k + 1, lb = odd_ld(k);
+  const long bs = (long)ld * ld;
+  const c128* Hk = a.Hk + (long)(c / a.hpp) * a.hkcs;
+  const c128 si = a.sigma[(long)c * a.ns + i];
+  c128* A = reinterpret_cast<c128*>(smem_raw);
+  c128* tau = A + (long)lb * k;
+  load_shifted(A, lb, Hk, k + 1, k, k, si);
+  if (threadIdx.x == 0) sh.ibc[0] = 0;
+  __syncthreads();
+  cta_qr(A, lb, k, k, k, tau, sh, k);
+  c128* S = ops + (long)c * (a.ns + 1) * bs + (long)i * bs;
+  const c128* T = ops + (long)c * (a.ns + 1) * bs + (long)a.ns * bs;
+  bool ok = true;
+  for (int j = threadIdx.x; j <= k; j += DT) {
+    c128* x = S + (long)j * ld;
+    const c128* t = T + (long)j * ld;
+    for (int r = 0; r < k; ++r) x[r] = t[r];
+    apply_qh_serial(A, lb, k, k, tau, x, k);
+    ok = backsolve_serial(A, lb, k, x) && ok;
+    c128 g = t[k];
+    for (int l = 0; l < k; ++l) g -= Hk[k + (long)l * (k + 1)] * x[l];
+    x[k] = g;
+  }
+  if (__syncthreads_or(!ok)) set_err(st, GDR_EBREAKDOWN);
+}
+
+// one cycle's projection (one CTA per column and shift): the operators applied to c
+__global__ void __launch_bounds__(DT) dense_proj_kernel(ProjArgs a, const c128* ops) {
+  __shared__ c128 cs[GDR_MAX_M + 2];
   const int c = blockIdx.y, i = blockIdx.x;
   ColState* st = a.st + c;
-  const c128* Hk = a.Hk + (long)(c / a.hpp) * a.hkcs;
   if (!st->active) return;
-  const int k = a.k, ldc = k + 1;
+  const int k = a.k, ld = k + 1, ldc = k + 1;
+  const long bs = (long)ld * ld;
   c128* Cf = a.Cf + (long)c * a.ccs;
-  const int* sact = a.sact + (long)c * a.ns;
-  if (i > 0 && !sact[i]) {
+  if (i > 0 && !a.sact[(long)c * a.ns + i]) {
     for (int r = threadIdx.x; r <= k; r += DT) Cf[r + (long)i * ldc] = {0, 0};
     return;
   }
-  c128* A = reinterpret_cast<c128*>(smem_raw);  // (k+1) x (k+1), odd leading dimension
-  const int la = odd_ld(k + 1);
-  c128* tau = A + (long)la * (k + 1);
-  c128* d1 = tau + (k + 1);
-  c128* t = d1 + (k + 1);   // (Hbar_k - sigma_1 Ibar) d_1, length k+1
-  c128* y = t + (k + 1);
-  c128* rinv = y + (k + 1);
-  const c128 s1 = a.sigma[(long)c * a.ns];
-  // base: min || c - (Hbar_k - s1 Ibar) d ||
-  load_shifted(A, la, Hk, k + 1, k + 1, k, s1);
-  for (int r = threadIdx.x; r <= k; r += DT) A[r + (long)k * la] = a.cproj[(long)c * (k + 2) + r];
-  if (threadIdx.x == 0) sh.ibc[0] = 0;
+  for (int r = threadIdx.x; r <= k; r += DT) cs[r] = a.cproj[(long)c * (k + 2) + r];
   __syncthreads();
-  cta_qr(A, la, k + 1, k, k + 1, tau, sh, k + 1);
-  for (int r = threadIdx.x; r < k; r += DT) d1[r] = A[r + (long)k * la];
-  __syncthreads();
-  if (!fast_backsolve(A, la, k, d1, rinv, sh)) set_err(st, GDR_EBREAKDOWN);
-  for (int r = threadIdx.x; r <= k; r += DT) {
-    c128 acc = {0, 0};
-    for (int j = 0; j < k; ++j) {
-      c128 h = Hk[r + (long)j * (k + 1)];
-      if (r == j) h -= s1;
-      acc += h * d1[j];
+  const c128* ob = ops + (long)c * (a.ns + 1) * bs;
+  const c128 bi = (i > 0) ? a.beta[(long)c * a.ns + i] : c128{1, 0};
+  const int nrow = (i == 0) ? 2 * ld : ld;
+  for (int r = threadIdx.x; r < nrow; r += DT) {
+    const bool tpart = r >= ld;  // base CTA: rows of T_1 after those of P_1
+    const int q = tpart ? r - ld : r;
+    const c128* M = ob + (long)(tpart ? a.ns : i) * bs + q;
+    c128 acc0 = {0, 0}, acc1 = {0, 0};
+    int j = 0;
+    for (; j + 1 <= k; j += 2) {
+      acc0 += M[(long)j * ld] * cs[j];
+      acc1 += M[(long)(j + 1) * ld] * cs[j + 1];
     }
-    t[r] = acc;
-  }
-  __syncthreads();
-  if (i == 0) {
-    for (int r = threadIdx.x; r <= k; r += DT) {
-      Cf[r + (long)0 * ldc] = (r < k) ? d1[r] : c128{0, 0};
-      Cf[r + (long)a.ns * ldc] = -t[r];
+    if (j <= k) acc0 += M[(long)j * ld] * cs[j];
+    const c128 v = acc0 + acc1;
+    if (i == 0) {
+      if (tpart) Cf[q + (long)a.ns * ldc] = -v;
+      else Cf[q] = (q < k) ? v : c128{0, 0};
+    } else if (q < k) {
+      Cf[q + (long)i * ldc] = bi * v;
+    } else {
+      Cf[k + (long)i * ldc] = {0, 0};
+      a.gamma[(long)c * a.ns + i] += bi * v;
     }
-    return;
-  }
-  // shift i: (H_k - s_i I) d_i = beta_i (H_k - s1 I) d_1 = beta_i t[0:k]
-  const c128 si = a.sigma[(long)c * a.ns + i];
-  const c128 bi = a.beta[(long)c * a.ns + i];
-  const int lb = odd_ld(k);
-  load_shifted(A, lb, Hk, k + 1, k, k, si);
-  for (int r = threadIdx.x; r < k; r += DT) A[r + (long)k * lb] = bi * t[r];
-  if (threadIdx.x == 0) sh.ibc[0] = 0;
-  __syncthreads();
-  cta_qr(A, lb, k, k, k + 1, tau, sh, k);
-  for (int r = threadIdx.x; r < k; r += DT) y[r] = A[r + (long)k * lb];
-  __syncthreads();
-  if (!fast_backsolve(A, lb, k, y, rinv, sh)) set_err(st, GDR_EBREAKDOWN);
-  for (int r = threadIdx.x; r <= k; r += DT) Cf[r + (long)i * ldc] = (r < k) ? y[r] : c128{0, 0};
-  // gamma_i += [beta_i t - (Hbar_k - s_i Ibar) d_i]_{k+1}  (last row of Ibar is zero)
-  if (threadIdx.x == 0) {
-    c128 acc = {0, 0};
-    for (int j = 0; j < k; ++j) acc += Hk[k + (long)j * (k + 1)] * y[j];
-    a.gamma[(long)c * a.ns + i] += bi * t[k] - acc;
   }
 }
 
@@ -1397,7 +1492,8 @@ size_t dense_smem_bytes(int m, int k) {
 void dense_init(gdr_ctx* ctx) {
   size_t lim = set_max_dyn_smem(ctx, dense_d1_kernel);
   lim = std::min(lim, set_max_dyn_smem(ctx, dense_d2_kernel));
-  lim = std::min(lim, set_max_dyn_smem(ctx, dense_proj_kernel));
+  lim = std::min(lim, set_max_dyn_smem(ctx, proj_base_setup_kernel));
+  lim = std::min(lim, set_max_dyn_smem(ctx, proj_shift_setup_kernel));
   lim = std::min(lim, set_max_dyn_smem(ctx, eigsel_setup_kernel));
   lim = std::min(lim, set_max_dyn_smem(ctx, restart_only_kernel));
   ctx->dense_smem_limit = lim;
@@ -1450,8 +1546,24 @@ void cycle_finish(gdr_ctx* ctx, const DenseCycle& d, c128* H, c128* cvec) {
   GDR_LAUNCHED(ctx);
 }
 
+void proj_setup(gdr_ctx* ctx, int ncol, int k, int ns, const c128* Hk, const c128* sigma, ColState* st, c128* ops,
+                long hkcs, int hpp) {
+  GDR_REQUIRE(k >= 1 && k <= GDR_MAX_M, "bad projection size");
+  ProjArgs a{k, ns, Hk, nullptr, sigma, nullptr, nullptr, nullptr, nullptr, 0, st, hkcs, hpp};
+  const size_t smem = sizeof(c128) * ((size_t)odd_ld(k + 1) * k + (size_t)(k + 1));
+  GDR_REQUIRE(smem <= ctx->dense_smem_limit, "k too large for the projection setup");
+  KProf kp(ctx, "dense_projection_setup", 0.0);
+  proj_base_setup_kernel<<<ncol, DT, smem, ctx->stream>>>(a, ops);
+  GDR_LAUNCHED(ctx);
+  if (ns > 1) {
+    dim3 g((unsigned)(ns - 1), (unsigned)ncol);
+    proj_shift_setup_kernel<<<g, DT, smem, ctx->stream>>>(a, ops);
+    GDR_LAUNCHED(ctx);
+  }
+}
+
 void dense_projection(gdr_ctx* ctx, int ncol, int k, int ns, const c128* Hk, const c128* cproj, const c128* sigma,
-                      const c128* beta, const int* sact, c128* gamma, c128* Cf, long ccs, double*, long,
+                      const c128* beta, const int* sact, c128* gamma, c128* Cf, long ccs, const c128* ops,
                       ColState* st, long hkcs, int hpp, const EigSel* es) {
   ProjArgs a{k, ns, Hk, cproj, sigma, beta, sact, gamma, Cf, ccs, st, hkcs, hpp};
   if (es) {
@@ -1462,11 +1574,10 @@ void dense_projection(gdr_ctx* ctx, int ncol, int k, int ns, const c128* Hk, con
     GDR_LAUNCHED(ctx);
     return;
   }
-  const size_t smem = sizeof(c128) * ((size_t)(k + 2) * (k + 1) + 5 * (size_t)(k + 2));
-  GDR_REQUIRE(smem <= ctx->dense_smem_limit, "k too large for the projection kernel");
+  GDR_REQUIRE(ops != nullptr && k <= GDR_MAX_M, "projection operators not formed");
   dim3 g((unsigned)ns, (unsigned)ncol);
   KProf kp(ctx, "dense_projection", 0.0);
-  dense_proj_kernel<<<g, DT, smem, ctx->stream>>>(a);
+  dense_proj_kernel<<<g, DT, 0, ctx->stream>>>(a, ops);
   GDR_LAUNCHED(ctx);
 }
 

@@ -231,9 +231,16 @@ void cycle_finish(gdr_ctx* ctx, const DenseCycle& d, c128* H, c128* cvec);
 // With es (selected eigenvectors): the Theorem 1 projection instead (every column, every
 // shift: d_i = beta_i (Theta - sigma_i)^{-1} M c[0:k], Cf[:, i] = [G d_i ; 0], residual
 // column -(Hbar_k - sigma_1 Ibar) G d_1; gamma untouched).
+// ops: the operators proj_setup formed for the same Hk, shifts and columns (unused with es).
 void dense_projection(gdr_ctx* ctx, int ncol, int k, int ns, const c128* Hk, const c128* cproj, const c128* sigma,
-                      const c128* beta, const int* sact, c128* gamma, c128* Cf, long ccs, double* scratch,
-                      long scratch_per_col, ColState* st, long hkcs = 0, int hpp = 1, const EigSel* es = nullptr);
+                      const c128* beta, const int* sact, c128* gamma, c128* Cf, long ccs, const c128* ops,
+                      ColState* st, long hkcs = 0, int hpp = 1, const EigSel* es = nullptr);
+// The projection's solution operators for every active column (ops: ncol (ns + 1) (k+1)^2
+// entries): P_1 = (Hbar_k - sigma_1 Ibar)^+, T_1 = (Hbar_k - sigma_1 Ibar) P_1 and, per
+// shift i >= 1, S_i = (H_k - sigma_i I)^{-1} T_1[0:k, :] with the row g_i = T_1[k, :] -
+// h_{k+1} S_i; formed once for a batch whose Hbar_k and shifts stay fixed.
+void proj_setup(gdr_ctx* ctx, int ncol, int k, int ns, const c128* Hk, const c128* sigma, ColState* st, c128* ops,
+                long hkcs = 0, int hpp = 1);
 
 size_t dense_smem_bytes(int m, int k);
 // harmonic Ritz restart products alone, for the s already in d.s

@@ -529,6 +529,11 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
   bd.m = k;
   c128* cproj = ctx->get<c128>("pj.cproj", (size_t)(k + 2) * ncol);
   c128* Cp = ctx->get<c128>("pj.Cp", (size_t)(k + 1) * (ns + 1) * ncol);
+  c128* pops = nullptr;  // the projection's solution operators, formed once for all cycles
+  if (k > 0 && job.project && !job.eigsel) {
+    pops = ctx->get<c128>("pj.ops", (size_t)(k + 1) * (k + 1) * (ns + 1) * ncol);
+    proj_setup(ctx, ncol, k, ns, job.Hk, b.sigma, b.st, pops, job.hkcs, job.dpp);
+  }
   // GMRES-Sh dense step
   const int ldc = mp + 1;
   DenseCycle d{};
@@ -559,7 +564,7 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
       // steps 3-4: Minres projection over V_k (or over selected eigenvectors); c = V_{k+1}^H r
       gs_dot<R>(ctx, bd, k + 1, r, ldr, cproj, false);
       dense_projection(ctx, ncol, k, ns, job.Hk, cproj, b.sigma, sh.beta, sh.sact, sh.gamma, Cp, (long)(k + 1) * (ns + 1),
-                       nullptr, 0, b.st, job.hkcs, job.dpp, job.eigsel);
+                       pops, b.st, job.hkcs, job.dpp, job.eigsel);
       // x_i += V_k d_i, r -= V_{k+1} (Hbar_k - sigma_1 Ibar) d_1
       combine<R>(ctx, n, ncol, bd.V, bd.ldv, job.vdcs, k + 1, Cp, k + 1, (long)(k + 1) * (ns + 1), 0, ns, 2, job.X,
                  job.ldx, job.xcs, r, ldr, b.st, b.nvec, job.dpp, col_len(b), basis_len(bd));
