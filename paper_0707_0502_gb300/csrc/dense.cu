@@ -197,21 +197,6 @@ DEV void cta_qr(cx<R>* A, int lda, int rows, int cols, int ntot, cx<R>* tau, ShT
   }
 }
 
-// y <- Q y for the reflectors of cta_qr (applied in reverse order), one thread.
-template <typename R>
-DEV void apply_q_serial(const cx<R>* A, int lda, int rows, int cols, const cx<R>* tau, cx<R>* y, int kfull) {
-  for (int j = min(cols, rows) - 1; j >= 0; --j) {
-    const cx<R> tj = tau[j];
-    if (tj.x == R(0) && tj.y == R(0)) continue;
-    const int last = qr_last(j, rows, kfull);
-    cx<R> w = y[j];
-    for (int i = j + 1; i <= last; ++i) w += cmulc(A[i + (long)j * lda], y[i]);
-    const cx<R> f = tj * w;
-    y[j] -= f;
-    for (int i = j + 1; i <= last; ++i) y[i] -= A[i + (long)j * lda] * f;
-  }
-}
-
 // Givens QR of the columns j0..cols-1 of an upper Hessenberg block (column j is
 // zero below row j+1), applied to all ntot columns, by warp 0 alone: every lane
 // forms the rotation of column j from its two entries, then rotates its own
@@ -435,6 +420,43 @@ template <typename R> DEV bool before_m(cx<R> a, R ma, cx<R> b, R mb) {
   return a.x > b.x;
 }
 
+// v <- Hhat^{-H} v for Hhat = Q R as cta_qr leaves it (R in T, reflectors below it, tau),
+// by one warp: forward substitution with R^H, right-looking (every lane forms z_j, the
+// lanes update the entries below it), then v <- Q z with the reflectors in reverse order
+// (warp-reduced dots).  A zero diagonal entry of R sets *zero_pivot (z_j := 0).
+template <typename R>
+DEV void solve_rh_warp(const cx<R>* T, int lda, int m, const cx<R>* tau, cx<R>* v, int kfull, int* zero_pivot) {
+  using C = cx<R>;
+  const int lane = threadIdx.x & 31;
+  for (int j = 0; j < m; ++j) {
+    const C rjj = T[j + (long)j * lda];
+    C z = {0, 0};
+    if (rjj.x == R(0) && rjj.y == R(0)) {
+      if (lane == 0) *zero_pivot = 1;
+    } else {
+      z = cdiv(v[j], conj(rjj));
+    }
+    __syncwarp();
+    if (lane == 0) v[j] = z;
+    for (int i = j + 1 + lane; i < m; i += 32) v[i] -= cmulc(T[j + (long)i * lda], z);
+    __syncwarp();
+  }
+  for (int j = m - 1; j >= 0; --j) {
+    const C tj = tau[j];
+    if (tj.x == R(0) && tj.y == R(0)) continue;
+    const int last = qr_last(j, m, kfull);
+    C w = {0, 0};
+    for (int i = j + 1 + lane; i <= last; i += 32) w += cmulc(T[i + (long)j * lda], v[i]);
+    w = warp_sum_c(w);
+    w += v[j];
+    const C f = tj * w;
+    __syncwarp();
+    if (lane == 0) v[j] -= f;
+    for (int i = j + 1 + lane; i <= last; i += 32) v[i] -= T[i + (long)j * lda] * f;
+    __syncwarp();
+  }
+}
+
 // Shared-memory layout of the FP32 harmonic Ritz path (byte offsets, 16-byte
 // aligned): T (m x (m+2), odd ld), Z (m rows of odd stride), Y (eigenvectors of
 // T, m x k, odd ld), then f in FP64, the FP64 refinement residual, tau, theta
@@ -524,23 +546,12 @@ DEV bool harmonic_ritz(const DenseCycle& d, int c, unsigned char* smem, ShT<R>& 
   __syncthreads();
   cta_qr(T, lda, m, m, m, tau, sh, d.kfull);
   GDR_DENSE_MARK(10, 0);
-  auto solve_rh = [&](C* v) {  // v <- Hhat^{-H} v, thread 0
-    for (int j = 0; j < m; ++j) {
-      C x = v[j];
-      for (int i = 0; i < j; ++i) x -= cmulc(T[i + (long)j * lda], v[i]);
-      const C rjj = T[j + (long)j * lda];
-      if (rjj.x == R(0) && rjj.y == R(0)) {
-        sh.ibc[0] = 1;
-        v[j] = {0, 0};
-      } else {
-        v[j] = cdiv(x, conj(rjj));
-      }
-    }
-    apply_q_serial(T, lda, m, m, tau, v, d.kfull);
+  auto solve_rh = [&](C* v) {  // v <- Hhat^{-H} v, warp 0
+    if (warp == 0) solve_rh_warp(T, lda, m, tau, v, d.kfull, &sh.ibc[0]);
   };
   for (int i = threadIdx.x; i < m; i += DT) f[i] = cvt<R>(conj(H[m + (long)i * (m + 1)]));
   __syncthreads();
-  if (threadIdx.x == 0) solve_rh(f);
+  solve_rh(f);
   __syncthreads();
   if (sh.ibc[0]) return fail();
   GDR_DENSE_MARK(11, 0);
@@ -560,7 +571,7 @@ DEV bool harmonic_ritz(const DenseCycle& d, int c, unsigned char* smem, ShT<R>& 
         f[i] = cvt<R>(acc);
       }
       __syncthreads();
-      if (threadIdx.x == 0) solve_rh(f);
+      solve_rh(f);
       __syncthreads();
       for (int i = threadIdx.x; i < m; i += DT) fd[i] += up(f[i]);
     }
@@ -1152,7 +1163,7 @@ __global__ void cycle_finish_kernel(DenseCycle d, c128* Hn, c128* cn) {
 // ------------------------------------------------------------ projection
 
 // The projection's solution operators depend only on Hbar_k and the shifts, which stay
-// fixed for every cycle of a batch: they are formed once (two setup launches) and each
+// fixed for every cycle of a batch: they are formed once (one setup launch) and each
 // cycle applies them to c = V_{k+1}^H r with short dot products.  Per column c, (ns + 1)
 // blocks of (k+1) x (k+1), column-major with leading dimension k+1, at ops + c (ns+1)(k+1)^2:
 //   block 0  : P_1 = (Hbar_k - sigma_1 Ibar)^+ (least-squares solution operator) in rows
@@ -1164,32 +1175,6 @@ __global__ void cycle_finish_kernel(DenseCycle d, c128* Hn, c128* cn) {
 // (H_k - sigma_i I) d_i = beta_i (H_k - sigma_1 I) d_1 and the v_{k+1} component of the
 // shifted residual grows by beta_i g_i c (the last row of Ibar is zero).
 
-// x <- Q^H x for the reflectors of cta_qr (in factorisation order), one thread.
-DEV void apply_qh_serial(const c128* A, int lda, int rows, int cols, const c128* tau, c128* x, int kfull) {
-  for (int j = 0; j < min(cols, rows); ++j) {
-    const c128 tj = tau[j];
-    if (tj.x == 0.0 && tj.y == 0.0) continue;
-    const int last = qr_last(j, rows, kfull);
-    c128 w = x[j];
-    for (int i = j + 1; i <= last; ++i) w += cmulc(A[i + (long)j * lda], x[i]);
-    const c128 f = conj(tj) * w;
-    x[j] -= f;
-    for (int i = j + 1; i <= last; ++i) x[i] -= A[i + (long)j * lda] * f;
-  }
-}
-
-// x[0:n] <- R^{-1} x[0:n] (R: upper n x n of A), one thread; false on a zero pivot.
-DEV bool backsolve_serial(const c128* A, int lda, int n, c128* x) {
-  for (int l = n - 1; l >= 0; --l) {
-    c128 v = x[l];
-    for (int q = l + 1; q < n; ++q) v -= A[l + (long)q * lda] * x[q];
-    const c128 p = A[l + (long)l * lda];
-    if (p.x == 0.0 && p.y == 0.0) return false;
-    x[l] = cdiv(v, p);
-  }
-  return true;
-}
-
 struct ProjArgs {
   int k, ns;
   const c128* Hk; const c128* cproj; const c128* sigma; const c128* beta; const int* sact;
@@ -1197,85 +1182,177 @@ struct ProjArgs {
   long hkcs; int hpp;  // column c uses Hk + (c / hpp) * hkcs
 };
 
-// setup 1 (one CTA per column): Householder QR of Hbar_k - sigma_1 Ibar in shared memory;
-// thread j forms column j of P_1 (Q^H e_j, back substitution) and of T_1
-__global__ void __launch_bounds__(DT) proj_base_setup_kernel(ProjArgs a, c128* ops) {
+// Gauss-Jordan elimination with partial pivoting on the k x w matrix W (column-major,
+// leading dimension k) whose first k columns hold a square system: on return columns
+// k..w-1 hold the system's inverse times the block they held.  Warp 0 finds the pivot
+// (largest |W[i, j]|, i >= j, the lower row on a tie); all threads swap and scale the
+// pivot row, then eliminate column j from the other rows in the columns after j.
+// False (uniform over the CTA) on a zero pivot.
+constexpr int GT = 256;  // threads of the Gauss-Jordan projection setup
+DEV bool cta_gauss_jordan(c128* W, int k, int w, int* piv_s, c128* inv_s) {
+  const int lane = threadIdx.x & 31;
+  for (int j = 0; j < k; ++j) {
+    if (threadIdx.x < 32) {
+      double best = -1.0;
+      int bi = j;
+      for (int i = j + lane; i < k; i += 32) {
+        const double v = norm2(W[i + (long)j * k]);
+        if (v > best) {
+          best = v;
+          bi = i;
+        }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ov = __shfl_xor_sync(FULL, best, off);
+        const int oi = __shfl_xor_sync(FULL, bi, off);
+        if (ov > best || (ov == best && oi < bi)) {
+          best = ov;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        *piv_s = (best > 0.0 && isfinite(best)) ? bi : -1;
+        if (best > 0.0) *inv_s = cdiv(c128{1, 0}, W[bi + (long)j * k]);
+      }
+    }
+    __syncthreads();
+    const int p = *piv_s;
+    if (p < 0) return false;
+    const c128 inv = *inv_s;
+    for (int cc = j + threadIdx.x; cc < w; cc += GT) {
+      const c128 top = W[j + (long)cc * k], pr = W[p + (long)cc * k];
+      if (p != j) W[p + (long)cc * k] = top;
+      W[j + (long)cc * k] = pr * inv;
+    }
+    __syncthreads();
+    const int nc = w - j - 1;
+    for (int t = threadIdx.x; t < k * nc; t += GT) {
+      const int i = t % k, cc = j + 1 + t / k;
+      if (i != j) W[i + (long)cc * k] -= W[i + (long)j * k] * W[j + (long)cc * k];
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+HD size_t proj_gj_smem(int k) { return sizeof(c128) * ((size_t)k * (2 * k + 1) + (size_t)(k + 1)); }
+
+// The projection operators by Gauss-Jordan (one CTA per column and shift, GT threads):
+// P_1 from the normal equations (Hbar_k - sigma_1 Ibar)^H (Hbar_k - sigma_1 Ibar) P_1 =
+// (Hbar_k - sigma_1 Ibar)^H and one Newton-Schulz step, T_1 = (Hbar_k - sigma_1 Ibar) P_1
+// formed from that P_1 (so T_1 c is the image of P_1 c to FP64 rounding whatever P_1's
+// accuracy: the residual update stays consistent with the solution update), then for shift
+// i >= 1 S_i from [H_k - sigma_i I | T_1[0:k, :]] and g_i.  CTA 0 writes blocks 0 and ns;
+// CTA i forms its own T_1 in block i and overwrites it with [S_i; g_i].
+__global__ void __launch_bounds__(GT) proj_gj_setup_kernel(ProjArgs a, c128* ops) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ Sh sh;
-  const int c = blockIdx.x;
+  __shared__ int piv_s;
+  __shared__ c128 inv_s;
+  const int c = blockIdx.y, i = blockIdx.x;
   ColState* st = a.st + c;
   if (!st->active) return;
-  const int k = a.k, ld = k + 1, la = odd_ld(k + 1);
+  const int k = a.k, ld = k + 1, w = 2 * k + 1;
   const long bs = (long)ld * ld;
   const c128* Hk = a.Hk + (long)(c / a.hpp) * a.hkcs;
   const c128 s1 = a.sigma[(long)c * a.ns];
-  c128* A = reinterpret_cast<c128*>(smem_raw);
-  c128* tau = A + (long)la * k;
-  load_shifted(A, la, Hk, k + 1, k + 1, k, s1);
-  if (threadIdx.x == 0) sh.ibc[0] = 0;
-  __syncthreads();
-  cta_qr(A, la, k + 1, k, k, tau, sh, k + 1);
-  c128* P = ops + (long)c * (a.ns + 1) * bs;
-  c128* T = P + (long)a.ns * bs;
-  bool ok = true;
-  for (int j = threadIdx.x; j <= k; j += DT) {
-    c128* x = P + (long)j * ld;
-    for (int r = 0; r <= k; ++r) x[r] = {r == j ? 1.0 : 0.0, 0.0};
-    apply_qh_serial(A, la, k + 1, k, tau, x, k + 1);
-    x[k] = {0, 0};
-    ok = backsolve_serial(A, la, k, x) && ok;
-    c128* t = T + (long)j * ld;
-    for (int r = 0; r <= k; ++r) {
-      c128 acc0 = {0, 0}, acc1 = {0, 0};
-      int l = 0;
-      for (; l + 1 < k; l += 2) {
-        c128 h0 = Hk[r + (long)l * (k + 1)], h1 = Hk[r + (long)(l + 1) * (k + 1)];
-        if (r == l) h0 -= s1;
-        if (r == l + 1) h1 -= s1;
-        acc0 += h0 * x[l];
-        acc1 += h1 * x[l + 1];
+  c128* W = reinterpret_cast<c128*>(smem_raw);  // k x w
+  c128* trow = W + (long)k * w;                 // row k of T_1
+  c128* ob = ops + (long)c * (a.ns + 1) * bs;
+  auto A1 = [&](int r, int l) {
+    c128 h = Hk[r + (long)l * (k + 1)];
+    if (r == l) h -= s1;
+    return h;
+  };
+  for (int t = threadIdx.x; t < k * w; t += GT) {
+    const int p = t % k, q = t / k;
+    if (q < k) {
+      c128 v0 = {0, 0}, v1 = {0, 0};
+      int r = 0;
+      for (; r + 1 <= k; r += 2) {
+        v0 += cmulc(A1(r, p), A1(r, q));
+        v1 += cmulc(A1(r + 1, p), A1(r + 1, q));
       }
-      if (l < k) {
-        c128 h0 = Hk[r + (long)l * (k + 1)];
-        if (r == l) h0 -= s1;
-        acc0 += h0 * x[l];
-      }
-      t[r] = acc0 + acc1;
+      if (r <= k) v0 += cmulc(A1(r, p), A1(r, q));
+      W[t] = v0 + v1;
+    } else {
+      W[t] = conj(A1(q - k, p));
     }
   }
-  if (__syncthreads_or(!ok)) set_err(st, GDR_EBREAKDOWN);
-}
-
-// setup 2 (one CTA per column and shift i >= 1): QR of H_k - sigma_i I; thread j solves
-// column j of S_i from T_1[0:k, j] and forms g_i[j]
-__global__ void __launch_bounds__(DT) proj_shift_setup_kernel(ProjArgs a, c128* ops) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ Sh sh;
-  const int c = blockIdx.y, i = blockIdx.x + 1;
-  ColState* st = a.st + c;
-  if (!st->active) return;
-  const int k = a.k, ld = k + 1, lb = odd_ld(k);
-  const long bs = (long)ld * ld;
-  const c128* Hk = a.Hk + (long)(c / a.hpp) * a.hkcs;
-  const c128 si = a.sigma[(long)c * a.ns + i];
-  c128* A = reinterpret_cast<c128*>(smem_raw);
-  c128* tau = A + (long)lb * k;
-  load_shifted(A, lb, Hk, k + 1, k, k, si);
-  if (threadIdx.x == 0) sh.ibc[0] = 0;
   __syncthreads();
-  cta_qr(A, lb, k, k, k, tau, sh, k);
-  c128* S = ops + (long)c * (a.ns + 1) * bs + (long)i * bs;
-  const c128* T = ops + (long)c * (a.ns + 1) * bs + (long)a.ns * bs;
-  bool ok = true;
-  for (int j = threadIdx.x; j <= k; j += DT) {
-    c128* x = S + (long)j * ld;
-    const c128* t = T + (long)j * ld;
-    for (int r = 0; r < k; ++r) x[r] = t[r];
-    apply_qh_serial(A, lb, k, k, tau, x, k);
-    ok = backsolve_serial(A, lb, k, x) && ok;
-    c128 g = t[k];
-    for (int l = 0; l < k; ++l) g -= Hk[k + (long)l * (k + 1)] * x[l];
-    x[k] = g;
+  bool ok = cta_gauss_jordan(W, k, w, &piv_s, &inv_s);
+  c128* P = W + (long)k * k;  // P_1, k x (k+1), leading dimension k
+  c128* Tb = ob + (long)(i == 0 ? a.ns : i) * bs;
+  auto form_t1 = [&]() {  // Tb = (Hbar_k - sigma_1 Ibar) P_1
+    for (int t = threadIdx.x; t < ld * ld; t += GT) {
+      const int r = t % ld, j = t / ld;
+      c128 v0 = {0, 0}, v1 = {0, 0};
+      int l = 0;
+      for (; l + 1 < k; l += 2) {
+        v0 += A1(r, l) * P[l + (long)j * k];
+        v1 += A1(r, l + 1) * P[l + 1 + (long)j * k];
+      }
+      if (l < k) v0 += A1(r, l) * P[l + (long)j * k];
+      Tb[t] = v0 + v1;
+    }
+  };
+  form_t1();
+  __syncthreads();
+  // one Newton-Schulz step P_1 <- P_1 (2 I - T_1) towards the pseudo-inverse: the normal
+  // equations square the condition number, the step squares P_1's relative error again
+  // (QR accuracy up to kappa ~ 1e7); the new P_1 goes to W's free left block (columns
+  // 0..k-1) and to trow (column k), then back
+  for (int t = threadIdx.x; t < k * ld; t += GT) {
+    const int l = t % k, j = t / k;
+    c128 v0 = P[l + (long)j * k] + P[l + (long)j * k], v1 = {0, 0};
+    int r = 0;
+    for (; r + 1 <= k; r += 2) {
+      v0 -= P[l + (long)r * k] * Tb[r + (long)j * ld];
+      v1 -= P[l + (long)(r + 1) * k] * Tb[r + 1 + (long)j * ld];
+    }
+    if (r <= k) v0 -= P[l + (long)r * k] * Tb[r + (long)j * ld];
+    if (j < k) W[l + (long)j * k] = v0 + v1;
+    else trow[l] = v0 + v1;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < k * ld; t += GT) {
+    const int l = t % k, j = t / k;
+    P[l + (long)j * k] = (j < k) ? W[l + (long)j * k] : trow[l];
+  }
+  __syncthreads();
+  form_t1();
+  if (i == 0) {
+    for (int t = threadIdx.x; t < ld * ld; t += GT) {
+      const int r = t % ld, j = t / ld;
+      ob[t] = (r < k) ? P[r + (long)j * k] : c128{0, 0};
+    }
+    if (__syncthreads_or(!ok)) set_err(st, GDR_EBREAKDOWN);
+    return;
+  }
+  __syncthreads();  // this CTA's T_1 is complete
+  const c128 si = a.sigma[(long)c * a.ns + i];
+  for (int t = threadIdx.x; t < k * w; t += GT) {
+    const int p = t % k, q = t / k;
+    if (q < k) {
+      c128 h = Hk[p + (long)q * (k + 1)];
+      if (p == q) h -= si;
+      W[t] = h;
+    } else {
+      W[t] = Tb[p + (long)(q - k) * ld];
+    }
+  }
+  for (int j = threadIdx.x; j < ld; j += GT) trow[j] = Tb[k + (long)j * ld];
+  __syncthreads();
+  ok = cta_gauss_jordan(W, k, w, &piv_s, &inv_s) && ok;
+  for (int t = threadIdx.x; t < ld * ld; t += GT) {
+    const int r = t % ld, j = t / ld;
+    if (r < k) {
+      Tb[t] = P[r + (long)j * k];  // S_i (W's right block)
+    } else {
+      c128 g = trow[j];
+      for (int l = 0; l < k; ++l) g -= Hk[k + (long)l * (k + 1)] * P[l + (long)j * k];
+      Tb[t] = g;
+    }
   }
   if (__syncthreads_or(!ok)) set_err(st, GDR_EBREAKDOWN);
 }
@@ -1492,8 +1569,7 @@ size_t dense_smem_bytes(int m, int k) {
 void dense_init(gdr_ctx* ctx) {
   size_t lim = set_max_dyn_smem(ctx, dense_d1_kernel);
   lim = std::min(lim, set_max_dyn_smem(ctx, dense_d2_kernel));
-  lim = std::min(lim, set_max_dyn_smem(ctx, proj_base_setup_kernel));
-  lim = std::min(lim, set_max_dyn_smem(ctx, proj_shift_setup_kernel));
+  lim = std::min(lim, set_max_dyn_smem(ctx, proj_gj_setup_kernel));
   lim = std::min(lim, set_max_dyn_smem(ctx, eigsel_setup_kernel));
   lim = std::min(lim, set_max_dyn_smem(ctx, restart_only_kernel));
   ctx->dense_smem_limit = lim;
@@ -1550,16 +1626,12 @@ void proj_setup(gdr_ctx* ctx, int ncol, int k, int ns, const c128* Hk, const c12
                 long hkcs, int hpp) {
   GDR_REQUIRE(k >= 1 && k <= GDR_MAX_M, "bad projection size");
   ProjArgs a{k, ns, Hk, nullptr, sigma, nullptr, nullptr, nullptr, nullptr, 0, st, hkcs, hpp};
-  const size_t smem = sizeof(c128) * ((size_t)odd_ld(k + 1) * k + (size_t)(k + 1));
+  const size_t smem = proj_gj_smem(k);
   GDR_REQUIRE(smem <= ctx->dense_smem_limit, "k too large for the projection setup");
   KProf kp(ctx, "dense_projection_setup", 0.0);
-  proj_base_setup_kernel<<<ncol, DT, smem, ctx->stream>>>(a, ops);
+  dim3 g((unsigned)ns, (unsigned)ncol);
+  proj_gj_setup_kernel<<<g, GT, smem, ctx->stream>>>(a, ops);
   GDR_LAUNCHED(ctx);
-  if (ns > 1) {
-    dim3 g((unsigned)(ns - 1), (unsigned)ncol);
-    proj_shift_setup_kernel<<<g, DT, smem, ctx->stream>>>(a, ops);
-    GDR_LAUNCHED(ctx);
-  }
 }
 
 void dense_projection(gdr_ctx* ctx, int ncol, int k, int ns, const c128* Hk, const c128* cproj, const c128* sigma,

@@ -165,3 +165,27 @@ def test_deflation_saves_matvecs_example7_shape(ctx):
     # right-hand side 1: deflated restarting vs plain restarting
     assert dr["mvps_rhs1"] < g40["mvps_rhs1"], (dr["mvps_rhs1"], g40["mvps_rhs1"])
     g.gdr_op_destroy(op)
+
+
+@pytest.mark.parametrize("prec", [g.GDR_PREC_FP64, g.GDR_PREC_MIXED])
+def test_projection_large_k(ctx, prec):
+    """A kept pair of k = 76 (m = 84, near the largest pair the dense kernels take): the
+    projection operators of GMRES-Proj-Sh come from Gauss-Jordan on a 76 x 153 system in
+    shared memory.  Every (shift, rhs) pair reaches 1e-8 and matches the oracle's
+    GMRES-DR-Sh + GMRES-Proj-Sh solution."""
+    rowptr, col, vals = W.paper_example1_matrix()
+    A = CSROperator(rowptr, col, vals)
+    op = g.gdr_op_csr(ctx, dev(rowptr), dev(col), dev(vals))
+    sig = np.array([0, -0.4, -2], complex)
+    gen = np.random.default_rng([41, 0])
+    B = gen.standard_normal((1000, 3)).astype(complex)
+    st, rep, X = solve(ctx, op, sig, B, prec, 84, 76, tol=1e-8, m_proj=8)
+    assert st == g.GDR_OK, rep
+    assert rep["mvps_rhs1"] > 84 and rep["mvps_proj"] > 0  # restarted: the kept pair exists
+    ref = solve_all_rhs(A.matvec, B, sig, 84, 76, 8, 1e-12, 1e-6)
+    for j in range(3):
+        for i, s in enumerate(sig):
+            assert relres(A.matvec, B[:, j], s, X[j, i]) <= 1e-8, (i, j)
+            xr = ref["X"][:, i, j]
+            assert np.linalg.norm(X[j, i] - xr) <= 1e-6 * np.linalg.norm(xr), (i, j)
+    g.gdr_op_destroy(op)
