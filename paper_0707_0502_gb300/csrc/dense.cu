@@ -1003,8 +1003,11 @@ DEV bool harmonic_ritz(const DenseCycle& d, int c, unsigned char* smem, ShT<R>& 
   return true;
 }
 
-// restart completion (D2 block 0): p_{k+1} from s, P into Cf, Hbar_k, c_k
-DEV void restart_finish(const DenseCycle& d, int c, c128* A, Sh& sh) {
+// restart completion (D2): p_{k+1} from s, P into Cf, Hbar_k, c_k.  The products are split
+// over nslice CTAs by columns of P_k (slice s: columns [k s / nslice, k (s+1) / nslice) of
+// T1 = Hbar P_k, Hbar_k and Cf); every slice forms p_{k+1} itself (it enters row k of
+// Hbar_k), slice 0 also writes c_k and p_{k+1} into Cf.
+DEV void restart_finish(const DenseCycle& d, int c, c128* A, Sh& sh, int slice = 0, int nslice = 1) {
   const int m = d.m, k = d.k, ldp = m + 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   ColState* st = d.st + c;
@@ -1041,34 +1044,37 @@ DEV void restart_finish(const DenseCycle& d, int c, c128* A, Sh& sh) {
   const double inv = 1.0 / sqrt(nn);
   for (int i = threadIdx.x; i < ldp; i += DT) p[i] = inv * p[i];
   __syncthreads();
-  // T1 = Hbar (m+1 x m) * P_k[0:m, :]
-  for (int q = threadIdx.x; q < ldp * k; q += DT) {
-    const int i = q % ldp, j = q / ldp;
+  const int j0 = (int)((long)k * slice / nslice), nj = (int)((long)k * (slice + 1) / nslice) - j0;
+  // T1[:, 0:nj] = Hbar (m+1 x m) * P_k[0:m, j0:j0+nj]
+  for (int q = threadIdx.x; q < ldp * nj; q += DT) {
+    const int i = q % ldp, j = j0 + q / ldp;
     c128 acc = {0, 0};
     for (int l = 0; l < m; ++l) acc += H[i + (long)l * (m + 1)] * P[l + (long)j * ldp];
     T1[q] = acc;
   }
   __syncthreads();
-  // Hbar_k = P^H T1  ((k+1) x k), c_k = P^H s
+  // Hbar_k[:, j0:j0+nj] = P^H T1  ((k+1) rows), c_k = P^H s
   c128* Hk = d.Hk + (long)c * (k + 1) * k;
-  for (int q = threadIdx.x; q < (k + 1) * k; q += DT) {
-    const int i = q % (k + 1), j = q / (k + 1);
+  for (int q = threadIdx.x; q < (k + 1) * nj; q += DT) {
+    const int i = q % (k + 1), jj = q / (k + 1);
     c128 acc = {0, 0};
-    for (int l = 0; l < ldp; ++l) acc += cmulc(P[l + (long)i * ldp], T1[l + (long)j * ldp]);
-    Hk[q] = acc;
+    for (int l = 0; l < ldp; ++l) acc += cmulc(P[l + (long)i * ldp], T1[l + (long)jj * ldp]);
+    Hk[i + (long)(j0 + jj) * (k + 1)] = acc;
   }
+  // P into the coefficient matrix (restart part of `combine`)
+  c128* Cf = d.Cf + (long)c * d.ccs;
+  for (int q = threadIdx.x; q < ldp * nj; q += DT) {
+    const int i = q % ldp, j = j0 + q / ldp;
+    Cf[i + (long)j * d.ldc] = P[i + (long)j * ldp];
+  }
+  if (slice != 0) return;
   c128* ck = d.ck + (long)c * (k + 1);
   for (int i = threadIdx.x; i <= k; i += DT) {
     c128 acc = {0, 0};
     for (int l = 0; l < ldp; ++l) acc += cmulc(P[l + (long)i * ldp], s[l]);
     ck[i] = acc;
   }
-  // P into the coefficient matrix (restart part of `combine`)
-  c128* Cf = d.Cf + (long)c * d.ccs;
-  for (int q = threadIdx.x; q < ldp * (k + 1); q += DT) {
-    const int i = q % ldp, j = q / ldp;
-    Cf[i + (long)j * d.ldc] = P[q];
-  }
+  for (int i = threadIdx.x; i < ldp; i += DT) Cf[i + (long)k * d.ldc] = p[i];
 }
 
 __global__ void __launch_bounds__(DT) dense_d1_kernel(DenseCycle d) {
@@ -1097,8 +1103,10 @@ __global__ void __launch_bounds__(DT) dense_d2_kernel(DenseCycle d) {
   const int c = blockIdx.y;
   ColState* st = d.st + c;
   if (!st->active) return;
-  if (blockIdx.x == 0) {
-    if (d.k > 0 && !st->broke && st->m_eff == d.m && st->err == 0) restart_finish(d, c, A, sh);
+  // blocks 1..ns-1: shift solves; block 0 and blocks ns.. : slices of the restart products
+  if (blockIdx.x == 0 || (int)blockIdx.x >= d.ns) {
+    const int slice = blockIdx.x == 0 ? 0 : (int)blockIdx.x - d.ns + 1;
+    if (d.k > 0 && !st->broke && st->m_eff == d.m && st->err == 0) restart_finish(d, c, A, sh, slice, d.rslices);
   } else {
     shift_solve(d, c, blockIdx.x, A, sh);
   }
@@ -1609,7 +1617,9 @@ void dense_cycle(gdr_ctx* ctx, const DenseCycle& dc) {
     dense_d1_kernel<<<g1, DT, smem, ctx->stream>>>(d);
     GDR_LAUNCHED(ctx);
   }
-  dim3 g2((unsigned)d.ns, (unsigned)d.ncol);
+  // restart products over up to 8 CTAs per column, about 4 columns of P_k each
+  d.rslices = d.k > 0 ? std::max(1, std::min(8, d.k / 4)) : 1;
+  dim3 g2((unsigned)(d.ns + d.rslices - 1), (unsigned)d.ncol);
   {
     KProf kp(ctx, "dense_shifts_restart", 0.0);
     dense_d2_kernel<<<g2, DT, smem, ctx->stream>>>(d);

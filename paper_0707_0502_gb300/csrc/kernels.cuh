@@ -204,6 +204,7 @@ struct DenseCycle {
   int fom = 0;             // FOM-Sh / FOM-DR-Sh (Sec. 3): square Galerkin solves, regular Ritz restart
   c128* graw = nullptr;    // if set: harmonic Ritz stops after the eigenvectors, G ((m+1) x k per column,
   c128* gtheta = nullptr;  // last row 0) into graw and their values (selection order) into gtheta
+  int rslices = 1;         // CTAs per column that share the restart products (by columns of P_k)
 };
 
 // Projection over selected approximate eigenvectors of a kept pair (Sec. 4, Theorem 1,
