@@ -500,8 +500,10 @@ def dense_flops(name, m, k, ns, ncol):
         return ncol * qr
     if name == "dense_shifts_restart":
         return ncol * ((ns - 1) * qr + 8.0 * (m + 1) * m * k)
-    if name == "dense_projection":
-        return ncol * ns * 4.0 * (4.0 / 3.0) * k**3
+    if name == "dense_projection":  # the formed operators applied: (ns + 1) (k+1)^2 complex FMA
+        return ncol * 8.0 * (ns + 1) * (k + 1) ** 2
+    if name == "dense_projection_setup":  # per CTA: normal equations, 2 Gauss-Jordan, 3 products
+        return ncol * 8.0 * (k * k * (k + 1) + 3.0 * k**3 + 3.0 * k * (k + 1) ** 2)
     return 0.0
 
 
@@ -552,7 +554,6 @@ def kernel_roofline(g, ctx, op, p, params, stream, B, X, cid=CONFIG_ID, solve=No
                            if traffic is not None else "")}
     else:
         ns = len(p.sigma)
-        m = p.m if dom != "dense_projection" else p.k
         flops = dense_flops(dom, p.m, p.k, ns, 1)
         # one CTA per problem on one SM: 4 SMSPs x 32 lanes x 2 flops per 64 cycles
         # (one FP64 warp-instruction occupies its SMSP for 64 cycles on GB300)
