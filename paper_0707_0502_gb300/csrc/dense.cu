@@ -1193,7 +1193,7 @@ struct ProjArgs {
 // Gauss-Jordan elimination with partial pivoting on the k x w matrix W (column-major,
 // leading dimension k) whose first k columns hold a square system: on return columns
 // k..w-1 hold the system's inverse times the block they held.  Warp 0 finds the pivot
-// (largest |W[i, j]|, i >= j, the lower row on a tie); all threads swap and scale the
+// (largest |W[i, j]|, i >= j, the smaller row index on a tie); all threads swap and scale the
 // pivot row, then eliminate column j from the other rows in the columns after j.
 // False (uniform over the CTA) on a zero pivot.
 constexpr int GT = 256;  // threads of the Gauss-Jordan projection setup
