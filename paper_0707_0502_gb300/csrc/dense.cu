@@ -274,6 +274,99 @@ DEV void set_err(ColState* st, int code) {
   if (threadIdx.x == 0) atomicCAS(&st->err, 0, code);
 }
 
+// Back substitution R x = b in place (R: upper n x n of A, FP32), by one warp; false on a
+// zero pivot (that x_j := 0).
+DEV bool warp_backsolve32(const c64* A, int la, int n, c64* b) {
+  const int lane = threadIdx.x & 31;
+  bool ok = true;
+  for (int j = n - 1; j >= 0; --j) {
+    const c64 p = A[j + (long)j * la];
+    c64 xj = {0, 0};
+    if (p.x == 0.f && p.y == 0.f) ok = false;
+    else xj = cdiv(b[j], p);
+    __syncwarp();
+    if (lane == 0) b[j] = xj;
+    for (int i = lane; i < j; i += 32) b[i] -= A[i + (long)j * la] * xj;
+    __syncwarp();
+  }
+  return ok;
+}
+
+// min || c - Hhat y || for a Hessenberg recurrence (zero below the subdiagonal) built on a
+// complex64 basis, in FP32 with one step of refinement: warp 0 reduces [Hhat | c], rounded
+// to FP32, to triangular form by Givens rotations (kept) and back-substitutes; the FP64
+// residual r = c - Hhat y of the FP64 copy of y is rotated and solved the same way and the
+// correction added.  y then solves the least-squares problem to about (kappa eps_32)^2
+// relative (the residual norm to second order of that), below the basis' own rounding;
+// the caller forms s = c - Hhat y from this y in FP64, so the residual update stays
+// consistent with the solution update.  smem: the FP32 matrix and the rotations; r: rows
+// FP64 entries of scratch; y: me FP64 entries.  False on a zero pivot.
+DEV bool ls32_solve(const c128* H, int ldh, const c128* cv, c128 sig, int rows, int me, unsigned char* smem,
+                    c128* r, c128* y, Sh& sh) {
+  const int lane = threadIdx.x & 31;
+  const int la = odd_ld(rows);
+  c64* A = reinterpret_cast<c64*>(smem);                          // rows x (me + 1)
+  float* rot = reinterpret_cast<float*>(A + (long)la * (me + 1));  // 3 per column
+  c64* b = A + (long)me * la;                                      // right-hand column
+  load_shifted(A, la, H, ldh, rows, me, sig);
+  for (int i = threadIdx.x; i < rows; i += DT) b[i] = cvt<float>(cv[i]);
+  if (threadIdx.x == 0) sh.ibc[0] = 0;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    for (int j = 0; j < me && j + 1 < rows; ++j) {
+      float g[3];
+      givens(A[j + (long)j * la], A[j + 1 + (long)j * la], g);
+      __syncwarp();  // every lane has read the pair before column j is rotated
+      if (lane == 0) {
+        rot[3 * j] = g[0];
+        rot[3 * j + 1] = g[1];
+        rot[3 * j + 2] = g[2];
+      }
+      const float cs = g[0];
+      const c64 sn = {g[1], g[2]};
+      for (int cc = j + lane; cc <= me; cc += 32) {
+        const c64 a = A[j + (long)cc * la], bb = A[j + 1 + (long)cc * la];
+        A[j + (long)cc * la] = cs * a + sn * bb;
+        A[j + 1 + (long)cc * la] = cs * bb - conj(sn) * a;
+      }
+      __syncwarp();
+    }
+    if (!warp_backsolve32(A, la, me, b) && lane == 0) sh.ibc[0] = 1;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < me; i += DT) y[i] = up(b[i]);
+  __syncthreads();
+  for (int i = threadIdx.x; i < rows; i += DT) {
+    c128 v = cv[i];
+    for (int j = max(0, i - 1); j < me; ++j) {  // row i of a Hessenberg matrix starts at column i-1
+      c128 h = H[i + (long)j * ldh];
+      if (i == j) h -= sig;
+      v -= h * y[j];
+    }
+    r[i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    for (int i = lane; i < rows; i += 32) b[i] = cvt<float>(r[i]);
+    __syncwarp();
+    if (lane == 0) {
+      for (int j = 0; j < me && j + 1 < rows; ++j) {
+        const float cs = rot[3 * j];
+        const c64 sn = {rot[3 * j + 1], rot[3 * j + 2]};
+        const c64 a = b[j], bb = b[j + 1];
+        b[j] = cs * a + sn * bb;
+        b[j + 1] = cs * bb - conj(sn) * a;
+      }
+    }
+    __syncwarp();
+    if (!warp_backsolve32(A, la, me, b) && lane == 0) sh.ibc[0] = 1;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < me; i += DT) y[i] += up(b[i]);
+  __syncthreads();
+  return sh.ibc[0] == 0;
+}
+
 // ------------------------------------------------- reduced solves (D1/D2)
 
 // base least squares: d_1 into Cf column k+1 (+ s into Cf column k+1+ns if want_r)
@@ -288,17 +381,23 @@ DEV void base_ls(const DenseCycle& d, int c, c128* A, Sh& sh) {
   // square m x m Galerkin system
   const int rows = (broke || d.fom) ? me : me + 1;
   const int lda = odd_ld(rows);
-  load_shifted(A, lda, H, m + 1, rows, me, sig);
-  for (int i = threadIdx.x; i < rows; i += DT) A[i + (long)me * lda] = cv[i];
   c128* tau = A + (long)lda * (me + 1);
   c128* y = tau + (me + 1);
   c128* rinv = y + (me + 1);
-  if (threadIdx.x == 0) sh.ibc[0] = 0;
-  __syncthreads();
-  hess_qr(A, lda, rows, me, me + 1, tau, sh, d.kfull);
-  for (int i = threadIdx.x; i < me; i += DT) y[i] = A[i + (long)me * lda];
-  __syncthreads();
-  if (!fast_backsolve(A, lda, me, y, rinv, sh)) set_err(st, GDR_EBREAKDOWN);
+  if (d.ls32 && d.kfull <= 1 && !d.fom) {
+    // complex64 basis, Hessenberg recurrence: FP32 least squares + refinement (tau as scratch)
+    if (!ls32_solve(H, m + 1, cv, sig, rows, me, reinterpret_cast<unsigned char*>(A), tau, y, sh))
+      set_err(st, GDR_EBREAKDOWN);
+  } else {
+    load_shifted(A, lda, H, m + 1, rows, me, sig);
+    for (int i = threadIdx.x; i < rows; i += DT) A[i + (long)me * lda] = cv[i];
+    if (threadIdx.x == 0) sh.ibc[0] = 0;
+    __syncthreads();
+    hess_qr(A, lda, rows, me, me + 1, tau, sh, d.kfull);
+    for (int i = threadIdx.x; i < me; i += DT) y[i] = A[i + (long)me * lda];
+    __syncthreads();
+    if (!fast_backsolve(A, lda, me, y, rinv, sh)) set_err(st, GDR_EBREAKDOWN);
+  }
   // d_1 -> Cf, s = c - Hhat d_1 from the original Hbar
   c128* Cf = d.Cf + (long)c * d.ccs;
   const int xc = (k > 0 ? k + 1 : 0);

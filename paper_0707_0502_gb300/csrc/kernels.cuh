@@ -205,6 +205,7 @@ struct DenseCycle {
   c128* graw = nullptr;    // if set: harmonic Ritz stops after the eigenvectors, G ((m+1) x k per column,
   c128* gtheta = nullptr;  // last row 0) into graw and their values (selection order) into gtheta
   int rslices = 1;         // CTAs per column that share the restart products (by columns of P_k)
+  int ls32 = 0;            // complex64 basis: base least squares of a Hessenberg recurrence in FP32 + refinement
 };
 
 // Projection over selected approximate eigenvectors of a kept pair (Sec. 4, Theorem 1,

@@ -548,6 +548,7 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
   d.scratch_per_col = 0;
   d.st = b.st;
   d.want_r = true;
+  d.ls32 = std::is_same<R, float>::value;  // GMRES(m_p) cycles on a complex64 basis
 
   const bool sweep = job.sweep && sweep_fits<R>(ctx, A, b) &&
                     sweep_choice(A, std::is_same<R, double>::value, ncol, mp) != 0;
