@@ -83,4 +83,8 @@ def test_invalid_arguments_are_einval(ctx):
     with pytest.raises(g.GdrError) as e:
         _small_solve(ctx, p, prm)
     assert e.value.status == g.GDR_EINVAL
+    prm = g.gdr_params_default(m=p.m, k=p.k, tol=1e-8, prec=g.GDR_PREC_FP64, m_refine=g.GDR_MAX_M + 1)
+    with pytest.raises(g.GdrError) as e:
+        _small_solve(ctx, p, prm)
+    assert e.value.status == g.GDR_EINVAL
     assert g.gdr_barrier_selftest(ctx, 0, 0) == g.GDR_EINVAL
