@@ -77,6 +77,16 @@ typedef enum { GDR_LINK_C128 = 0, GDR_LINK_C64 = 1, GDR_LINK_BF16 = 2 } gdr_link
                                      or FOM-DR(m,k)-Sh (Sec. 3, Examples 2-3): square Galerkin solves for
                                      every shift (residuals parallel by construction) and a restart with
                                      regular Ritz vectors; later stages unchanged */
+#define GDR_FLAG_CGS2      2048u /* MIXED: Arnoldi steps of the complex64 stages (outside the persistent
+                                     sweep) by classical Gram-Schmidt twice, four passes over the basis
+                                     per step, instead of the default delayed reorthogonalisation (DCGS2:
+                                     the second pass of step j merged into the projection of step j+1,
+                                     two passes per step); the FP64 stages always use the former */
+#define GDR_FLAG_FP64_DENSE 4096u /* MIXED: every small dense step in FP64 -- the harmonic-Ritz eigensolve
+                                     (as GDR_FLAG_FP64_EIG) and the reduced least squares of the GMRES(m_p)
+                                     cycles of the Proj and refinement stages (default: FP32 Givens QR with
+                                     one FP64-residual refinement step, the FP64 form when that step's
+                                     correction exceeds 1e-4 of the solution) */
 #define GDR_FLAG_AUTOTUNE   128u  /* before the first cycle, run gdr_autotune for the matvec and Arnoldi
                                      form of each stage whose (precision, columns, m) the operator has
                                      no tuned shape for yet (the tuning time is part of the solve) */
@@ -106,6 +116,14 @@ typedef struct {
   int k_select;       /* GDR_FLAG_EIG_SELECT: approximate eigenvectors projected over (1..k; <= 0: k) */
   int m_refine;       /* cycle length of the refinement / cleanup solves (not in the paper); <= 0:
                          min(m, m_p + (m - m_p) / 2) for vectors of at most 2^17 elements, else m_p */
+  double refine_rank_tol; /* MIXED, shift-shared refinement (not in the paper): a complex64 refinement
+                         pass may refine the residuals of one right-hand side's shifts over a few
+                         orthonormal directions of their span (pivoted Cholesky of their Gram matrix,
+                         directions kept while the rest exceeds refine_rank_tol times the largest
+                         residual), each direction one multi-shift GMRES(m_refine)-Proj(k)-Sh column
+                         for all shifts, followed by the extra-right-hand-side correction; used when
+                         that needs at most 0.7 times the columns of per-pair refinement and the Proj
+                         stage's extra solutions exist (nrhs > 1).  0: automatic (3e-4); < 0: never */
 } gdr_params;
 
 typedef struct {
@@ -128,6 +146,10 @@ typedef struct {
   double related_resid; /* GDR_FLAG_RELATED_RHS: largest ||b_j - B d|| / ||b_j|| over j >= 2 (else 0) */
   double eig_resid_max; /* GDR_FLAG_EIG_SELECT: largest eigen-residual ||A z - theta z|| (||z|| = 1)
                            of the selected approximate eigenvectors (else 0) */
+  long shared_cols;     /* multi-shift columns of the shift-shared refinement passes (summed) */
+  long shared_pairs;    /* (shift, rhs) pairs those passes refined (summed); per-pair passes would
+                           have used one column each */
+  long mvps_shared;     /* matvecs of the shift-shared passes (part of mvps_refine) */
 } gdr_report;
 
 /* ---------------------------------------------------------------- context */
@@ -285,6 +307,22 @@ gdr_status gdr_profile_report(gdr_ctx *ctx, char *buf, long len);
  * FP64 column h (c128[j+2]: h_0..h_j, h_{j+1,j}) into `hcol`. */
 gdr_status gdr_arnoldi_step(gdr_ctx *ctx, const gdr_op *A, gdr_prec prec, void *V, int j, double *hcol);
 
+/* Arnoldi steps j0..m-1 of A V_m = V_{m+1} Hbar_m (eq. recurAr), continuing, when
+ * j0 > 0, from a kept pair A V_{j0} = V_{j0+1} Hbar_{j0} as after a GMRES-DR restart
+ * (eq. recur1), in the form the solves use: FP64 by classical Gram-Schmidt twice per
+ * step; MIXED in complex64 by Gram-Schmidt with delayed reorthogonalisation (the
+ * second pass of step j merged into the projection of step j+1, then a finalising
+ * pass for v_m), or twice per step with GDR_FLAG_CGS2 in `flags`.
+ * V: n x (m+1), `prec` vectors, leading dimension n; columns 0..j0 given (orthonormal),
+ * columns j0+1..m written.  Hbar: c128 (m+1) x m, column-major, device; columns
+ * 0..j0-1 given (rows 0..j0), columns j0..m-1 written with zeros below row j+1.
+ * m_eff (host, may be NULL): m, or j+1 after a lucky breakdown at step j
+ * (h_{j+1,j} <= 1e-12 ||A v_j||; the later columns of V are then zero and those of
+ * Hbar unspecified).  GDR_ENAN on a
+ * non-finite value.  Synchronises the context stream. */
+gdr_status gdr_arnoldi_cycle(gdr_ctx *ctx, const gdr_op *A, gdr_prec prec, void *V, int j0, int m, double *Hbar,
+                             unsigned flags, int *m_eff);
+
 /* GMRES-Sh reduced solve (Sec. 2.1, eqs. gsh1-gsh3; GMRES-DR-Sh steps 3-5), FP64:
  * Hbar: c128 (m+1) x m, c: c128[m+1], sigma: host c128[ns], beta: c128[ns] in.
  * Out: D c128 m x ns, s c128[m+1], beta_new c128[ns], norms double[ns]
@@ -304,7 +342,9 @@ gdr_status gdr_dense_gmres_sh(gdr_ctx *ctx, int m, int ns, const double *Hbar, c
  * cudaFree or an allocating library routine.  Limits: m <= GDR_NOALLOC_MAX_M,
  * ns <= GDR_NOALLOC_MAX_NS; larger sizes return GDR_EINVAL.  The first call on
  * a device looks up the array's device address, so make it before any stream
- * capture.  All calls share the one array, which keeps the last call's
+ * capture; with CUDA's lazy module loading (the default) that first call is also
+ * when the array's memory is committed, so a caller with a fixed memory budget
+ * should make one call while setting up.  All calls share the one array, which keeps the last call's
  * contents: calls that overlap on the GPU race and must be serialised by the
  * caller.  Synchronises the context stream before returning. */
 #define GDR_NOALLOC_MAX_M 96
@@ -312,6 +352,19 @@ gdr_status gdr_dense_gmres_sh(gdr_ctx *ctx, int m, int ns, const double *Hbar, c
 gdr_status gdr_dense_gmres_sh_noalloc(gdr_ctx *ctx, int m, int ns, const double *Hbar, const double *c,
                                       const double *sigma, const double *beta, double *D, double *s,
                                       double *beta_new, double *norms);
+
+/* Base least squares of a GMRES cycle (Sec. 2.1: the base system of eqs. gsh1-gsh2,
+ * GMRES-DR-Sh step 3): y = argmin || c - (Hbar - sigma1 Ibar) y || for an upper
+ * Hessenberg Hbar (c128 (m+1) x m, column-major, zero below the subdiagonal),
+ * c: c128[m+1], sigma1: host c128.  Out (device): y c128[m], s = c - (Hbar - sigma1 Ibar) y
+ * c128[m+1], formed in FP64.  FP64: Givens QR in FP64.  MIXED: the form of the complex64
+ * GMRES(m_p) cycles -- FP32 Givens QR, back substitution and one refinement step with
+ * the FP64 residual (y then accurate to about the correction's size, ||s|| within ~1e-9
+ * of the minimum); when the correction exceeds 1e-4 ||y|| or a pivot is zero, the FP64
+ * form instead.  GDR_EBREAKDOWN on a singular system.
+ * Synchronises the context stream. */
+gdr_status gdr_dense_ls(gdr_ctx *ctx, gdr_prec prec, int m, const double *sigma1, const double *Hbar,
+                        const double *c, double *y, double *s);
 
 /* GMRES-DR restart (Sec. 2.2): harmonic Ritz pairs of Hhat = Hbar - sigma1 Ibar,
  * k of smallest |theta| (ties: larger Im, then larger Re), P_{k+1} = [orth([G;0]), p],

@@ -26,9 +26,10 @@ GDR_OK, GDR_EINVAL, GDR_ENOMEM, GDR_ECUDA, GDR_ENOCONV, GDR_EBREAKDOWN, GDR_ENAN
 GDR_PREC_FP64, GDR_PREC_MIXED = 0, 1
 GDR_LINK_C128, GDR_LINK_C64, GDR_LINK_BF16 = 0, 1, 2
 GDR_MAX_M = 96
+GDR_NOALLOC_MAX_M, GDR_NOALLOC_MAX_NS = 96, 16
 (GDR_FLAG_HOST_PTRS, GDR_FLAG_NO_GRAPH, GDR_FLAG_SEQUENTIAL, GDR_FLAG_NO_PROJ, GDR_FLAG_NO_REFINE, GDR_FLAG_NO_SWEEP,
  GDR_FLAG_FP64_EIG, GDR_FLAG_AUTOTUNE, GDR_FLAG_RELATED_RHS, GDR_FLAG_EIG_SELECT,
- GDR_FLAG_FOM) = 1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024
+ GDR_FLAG_FOM, GDR_FLAG_CGS2, GDR_FLAG_FP64_DENSE) = 1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096
 
 
 class gdr_params(ctypes.Structure):
@@ -36,7 +37,7 @@ class gdr_params(ctypes.Structure):
                 ("tol", ctypes.c_double), ("extra_tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
                 ("refine_tol", ctypes.c_double), ("max_mvps", ctypes.c_long), ("max_cycles", ctypes.c_int), ("refine_max", ctypes.c_int),
                 ("prec", ctypes.c_int), ("flags", ctypes.c_uint), ("k_select", ctypes.c_int),
-                ("m_refine", ctypes.c_int)]
+                ("m_refine", ctypes.c_int), ("refine_rank_tol", ctypes.c_double)]
 
 
 class gdr_report(ctypes.Structure):
@@ -46,7 +47,8 @@ class gdr_report(ctypes.Structure):
                 ("max_relres", ctypes.c_double), ("t_total_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_long), ("t_rhs1_ms", ctypes.c_double),
                 ("t_proj_ms", ctypes.c_double), ("t_refine_ms", ctypes.c_double), ("host_syncs", ctypes.c_long),
-                ("related_resid", ctypes.c_double), ("eig_resid_max", ctypes.c_double)]
+                ("related_resid", ctypes.c_double), ("eig_resid_max", ctypes.c_double),
+                ("shared_cols", ctypes.c_long), ("shared_pairs", ctypes.c_long), ("mvps_shared", ctypes.c_long)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -110,10 +112,13 @@ _SIGS = {
     "gdr_defl_export": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_int)]),
     "gdr_defl_destroy": (None, [_P]),
     "gdr_arnoldi_step": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int, _P]),
+    "gdr_arnoldi_cycle": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_uint,
+                                         ctypes.POINTER(ctypes.c_int)]),
     "gdr_dense_gmres_sh": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, _P]),
     "gdr_dense_gmres_sh_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P,
                                                   _P]),
     "gdr_barrier_selftest": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+    "gdr_dense_ls": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P]),
     "gdr_dense_restart": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P]),
     "gdr_basis_update": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_long, ctypes.c_int, _P, _P, ctypes.c_int,
                                         ctypes.c_int, _P]),
@@ -347,6 +352,16 @@ def gdr_arnoldi_step(ctx, op, prec, V, j, hcol):
     _check(lib().gdr_arnoldi_step(ctx, op, int(prec), _ptr(V), int(j), _ptr(hcol)), ctx)
 
 
+def gdr_arnoldi_cycle(ctx, op, prec, V, j0, m, Hbar, flags=0):
+    """V: (m+1, n) device tensor (rows are basis vectors; rows 0..j0 given), Hbar:
+    (m, m+1) complex128 device tensor (column-major (m+1) x m; columns < j0 given).
+    Returns m_eff (m, or the length after a lucky breakdown)."""
+    me = ctypes.c_int(0)
+    _check(lib().gdr_arnoldi_cycle(ctx, op, int(prec), _ptr(V), int(j0), int(m), _ptr(Hbar), int(flags),
+                                   ctypes.byref(me)), ctx)
+    return me.value
+
+
 def gdr_dense_gmres_sh(ctx, m, sigma, Hbar, c, beta, D, s, beta_new, norms):
     """Hbar: (m, m+1) complex128 device (column-major (m+1) x m), c: (m+1,), beta: (ns,);
     out D: (ns, m), s: (m+1,), beta_new: (ns,), norms: (ns,) float64."""
@@ -361,6 +376,13 @@ def gdr_dense_gmres_sh_noalloc(ctx, m, sigma, Hbar, c, beta, D, s, beta_new, nor
     sg = _c128_host(sigma)
     _check(lib().gdr_dense_gmres_sh_noalloc(ctx, int(m), len(sg), _ptr(Hbar), _ptr(c), sg.ctypes.data, _ptr(beta),
                                             _ptr(D), _ptr(s), _ptr(beta_new), _ptr(norms)), ctx)
+
+
+def gdr_dense_ls(ctx, prec, m, sigma1, Hbar, c, y, s):
+    """Hbar: (m, m+1) complex128 device (column-major (m+1) x m, Hessenberg), c: (m+1,);
+    out y: (m,), s: (m+1,) complex128 device."""
+    sg = _c128_host([sigma1])
+    _check(lib().gdr_dense_ls(ctx, int(prec), int(m), sg.ctypes.data, _ptr(Hbar), _ptr(c), _ptr(y), _ptr(s)), ctx)
 
 
 def gdr_dense_restart(ctx, prec, m, k, sigma1, Hbar, s, theta, P, Hk, ck):

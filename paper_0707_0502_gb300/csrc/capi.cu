@@ -58,6 +58,7 @@ gdr_params resolve_inner_tol(const gdr_ctx* ctx, const gdr_op* A, long n, const 
   // a complex64 refinement pass reliably reduces its residual by 1e-4: one pass then
   // usually finishes a pair that the stage left at ~1e-4
   if (!(r.refine_tol > 0)) r.refine_tol = std::min(r.inner_tol, 1e-4);
+  if (r.refine_rank_tol == 0) r.refine_rank_tol = 3e-4;
   return r;
 }
 
@@ -678,6 +679,85 @@ gdr_status gdr_arnoldi_step(gdr_ctx* ctx, const gdr_op* A, gdr_prec prec, void* 
   });
 }
 
+gdr_status gdr_arnoldi_cycle(gdr_ctx* ctx, const gdr_op* A, gdr_prec prec, void* V, int j0, int m, double* Hbar,
+                             unsigned flags, int* m_eff) {
+  if (!ctx || !A || !V || !Hbar) return GDR_EINVAL;
+  return guarded(ctx, [&] {
+    GDR_REQUIRE(m >= 1 && m <= GDR_MAX_M && j0 >= 0 && j0 < m, "bad j0 / m");
+    const long n = A->n;
+    GDR_REQUIRE(prec == GDR_PREC_FP64 || n % 2 == 0, "complex64 step-level calls need an even n");
+    auto run = [&](auto tag) {
+      using R = decltype(tag);
+      Batch<R> b;
+      b.ncol = 1;
+      b.n = n;
+      b.m = m;
+      b.ns = 1;
+      b.ldv = pad_ld(n);
+      b.vcs = b.ldv * (m + 1);
+      b.V = ctx->get<cx<R>>("cyc.V", (size_t)b.vcs);
+      GDR_CUDA(cudaMemsetAsync(b.V, 0, sizeof(cx<R>) * b.vcs, ctx->stream));  // columns a breakdown leaves: 0
+      // the given columns, in the library's vector order
+      if (A->kind == OP_WILSON)
+        op_order<cx<R>>(ctx, A, j0 + 1, static_cast<const cx<R>*>(V), n, b.V, b.ldv, true);
+      else
+        GDR_CUDA(cudaMemcpy2DAsync(b.V, b.ldv * sizeof(cx<R>), V, n * sizeof(cx<R>), n * sizeof(cx<R>), j0 + 1,
+                                   cudaMemcpyDeviceToDevice, ctx->stream));
+      b.wcs = b.ldv;
+      b.W = ctx->get<cx<R>>("cyc.W", (size_t)b.ldv);
+      b.W2 = ctx->get<cx<R>>("cyc.W2", (size_t)b.ldv);
+      b.H = ctx->get<c128>("cyc.H", (size_t)(m + 1) * m);
+      GDR_CUDA(cudaMemsetAsync(b.H, 0, sizeof(c128) * (m + 1) * m, ctx->stream));
+      if (j0 > 0)
+        GDR_CUDA(cudaMemcpyAsync(b.H, Hbar, sizeof(c128) * (m + 1) * j0, cudaMemcpyDeviceToDevice, ctx->stream));
+      b.cvec = nullptr;
+      b.h1 = ctx->get<c128>("cyc.h1", (size_t)(m + 2));
+      b.h2 = ctx->get<c128>("cyc.h2", (size_t)(m + 2));
+      b.hd = ctx->get<c128>("cyc.hd", (size_t)(2 * m + 8));
+      b.dc = ctx->get<c128>("cyc.dc", (size_t)(2 * m + 8));
+      const long units = (n * (long)sizeof(cx<R>) + 15) / 16;
+      b.nblk = (int)std::max<long>(1, std::min<long>((units + 255) / 256, 3L * ctx->num_sms));
+      b.pstride = (long)(b.nblk + 64) * (2 * m + 8);
+      b.part = ctx->get<c128>("cyc.part", (size_t)b.pstride + 64);
+      b.cnt = ctx->get<unsigned>("cyc.cnt", 4);
+      b.gcnt = ctx->get<unsigned>("cyc.gcnt", 64);
+      GDR_CUDA(cudaMemsetAsync(b.gcnt, 0, 64 * sizeof(unsigned), ctx->stream));
+      GDR_CUDA(cudaMemsetAsync(b.cnt, 0, 4 * sizeof(unsigned), ctx->stream));
+      b.st = ctx->get<ColState>("cyc.st", 1);
+      b.sigma = nullptr;
+      ColState s = {};
+      s.run = 1;
+      s.active = 1;
+      s.m_eff = m;
+      GDR_CUDA(cudaMemcpyAsync(b.st, &s, sizeof(s), cudaMemcpyHostToDevice, ctx->stream));
+      if (std::is_same<R, float>::value && !(flags & GDR_FLAG_CGS2)) {
+        arnoldi_dcgs2<R>(ctx, A, b, j0, m);
+      } else {
+        cx<R>* wl = nullptr;
+        for (int j = j0; j < m; ++j) arnoldi_step<R>(ctx, A, b, j, j0, m - 1, wl);
+      }
+      if (A->kind == OP_WILSON)
+        op_order<cx<R>>(ctx, A, m - j0, b.V + (long)(j0 + 1) * b.ldv, b.ldv,
+                        static_cast<cx<R>*>(V) + (long)(j0 + 1) * n, n, false);
+      else
+        GDR_CUDA(cudaMemcpy2DAsync(static_cast<cx<R>*>(V) + (long)(j0 + 1) * n, n * sizeof(cx<R>),
+                                   b.V + (long)(j0 + 1) * b.ldv, b.ldv * sizeof(cx<R>), n * sizeof(cx<R>), m - j0,
+                                   cudaMemcpyDeviceToDevice, ctx->stream));
+      GDR_CUDA(cudaMemcpyAsync(Hbar + 2 * (long)(m + 1) * j0, b.H + (long)(m + 1) * j0,
+                               sizeof(c128) * (m + 1) * (m - j0), cudaMemcpyDeviceToDevice, ctx->stream));
+      ColState out;
+      GDR_CUDA(cudaMemcpyAsync(&out, b.st, sizeof(out), cudaMemcpyDeviceToHost, ctx->stream));
+      GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+      if (m_eff) *m_eff = out.broke ? out.m_eff : m;
+      if (out.nan) throw gdr_error(GDR_ENAN, "NaN/Inf in the Arnoldi recurrence");
+    };
+    if (prec == GDR_PREC_FP64)
+      run(double{});
+    else
+      run(float{});
+  });
+}
+
 gdr_status gdr_dense_gmres_sh(gdr_ctx* ctx, int m, int ns, const double* Hbar, const double* c, const double* sigma,
                               const double* beta, double* D, double* s, double* beta_new, double* norms) {
   if (!ctx) return GDR_EINVAL;
@@ -712,6 +792,47 @@ gdr_status gdr_dense_gmres_sh(gdr_ctx* ctx, int m, int ns, const double* Hbar, c
     dense_cycle(ctx, d);
     GDR_CUDA(cudaMemcpy2DAsync(D, m * sizeof(c128), d.Cf, (m + 1) * sizeof(c128), m * sizeof(c128), ns,
                                cudaMemcpyDeviceToDevice, ctx->stream));
+    ColState out;
+    GDR_CUDA(cudaMemcpyAsync(&out, d.st, sizeof(out), cudaMemcpyDeviceToHost, ctx->stream));
+    GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (out.err) throw gdr_error((gdr_status)out.err, "singular reduced system");
+  });
+}
+
+gdr_status gdr_dense_ls(gdr_ctx* ctx, gdr_prec prec, int m, const double* sigma1, const double* Hbar, const double* c,
+                        double* y, double* s) {
+  if (!ctx) return GDR_EINVAL;
+  return guarded(ctx, [&] {
+    GDR_REQUIRE(m >= 1 && m <= GDR_MAX_M, "bad sizes");
+    GDR_REQUIRE(prec == GDR_PREC_FP64 || prec == GDR_PREC_MIXED, "prec must be GDR_PREC_FP64 or GDR_PREC_MIXED");
+    GDR_REQUIRE(sigma1 && Hbar && c && y && s, "null argument");
+    DenseCycle d{};
+    d.ncol = 1; d.m = m; d.k = 0; d.ns = 1; d.kfull = 0;  // Hessenberg recurrence
+    d.ls32 = (prec == GDR_PREC_MIXED) ? 1 : 0;
+    c128* sg = ctx->get<c128>("lstep.sigma", 1);
+    GDR_CUDA(cudaMemcpyAsync(sg, sigma1, sizeof(c128), cudaMemcpyHostToDevice, ctx->stream));
+    d.H = reinterpret_cast<const c128*>(Hbar);
+    d.cvec = reinterpret_cast<const c128*>(c);
+    d.sigma = sg;
+    d.beta = ctx->get<c128>("lstep.beta", 1);
+    d.norms = ctx->get<double>("lstep.norms", 1);
+    d.sact = ctx->get<int>("lstep.sact", 1);
+    const c128 one = {1.0, 0.0};
+    const int on = 1;
+    GDR_CUDA(cudaMemcpyAsync(d.beta, &one, sizeof(one), cudaMemcpyHostToDevice, ctx->stream));
+    GDR_CUDA(cudaMemcpyAsync(d.sact, &on, sizeof(on), cudaMemcpyHostToDevice, ctx->stream));
+    d.ldc = m + 1;
+    d.ccs = (long)(m + 1) * 2;
+    d.Cf = ctx->get<c128>("lstep.Cf", (size_t)d.ccs);
+    d.s = reinterpret_cast<c128*>(s);
+    d.st = ctx->get<ColState>("lstep.st", 1);
+    ColState st = {};
+    st.active = 1;
+    st.m_eff = m;
+    GDR_CUDA(cudaMemcpyAsync(d.st, &st, sizeof(st), cudaMemcpyHostToDevice, ctx->stream));
+    GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+    dense_cycle(ctx, d);
+    GDR_CUDA(cudaMemcpyAsync(y, d.Cf, m * sizeof(c128), cudaMemcpyDeviceToDevice, ctx->stream));
     ColState out;
     GDR_CUDA(cudaMemcpyAsync(&out, d.st, sizeof(out), cudaMemcpyDeviceToHost, ctx->stream));
     GDR_CUDA(cudaStreamSynchronize(ctx->stream));

@@ -296,11 +296,15 @@ DEV bool warp_backsolve32(const c64* A, int la, int n, c64* b) {
 // complex64 basis, in FP32 with one step of refinement: warp 0 reduces [Hhat | c], rounded
 // to FP32, to triangular form by Givens rotations (kept) and back-substitutes; the FP64
 // residual r = c - Hhat y of the FP64 copy of y is rotated and solved the same way and the
-// correction added.  y then solves the least-squares problem to about (kappa eps_32)^2
-// relative (the residual norm to second order of that), below the basis' own rounding;
-// the caller forms s = c - Hhat y from this y in FP64, so the residual update stays
-// consistent with the solution update.  smem: the FP32 matrix and the rotations; r: rows
-// FP64 entries of scratch; y: me FP64 entries.  False on a zero pivot.
+// correction added.  The correction measures the FP32 solve's error; when the least-squares
+// residual is large the step removes only part of it, so y is accurate to about the
+// correction's size, while ||c - Hhat y|| stays within ~1e-9 (relative) of the minimum --
+// what a GMRES cycle needs, since the caller forms s = c - Hhat y from this y in FP64 and
+// the residual update stays consistent with the solution update.  When the correction
+// exceeds 1e-4 ||y|| (kappa(Hhat) beyond ~1e5) or a pivot is zero, the result is not
+// trusted and the function returns false, for the caller's FP64 solve.
+// smem: the FP32 matrix and the rotations; r: rows FP64 entries of scratch; y: me FP64
+// entries.
 DEV bool ls32_solve(const c128* H, int ldh, const c128* cv, c128 sig, int rows, int me, unsigned char* smem,
                     c128* r, c128* y, Sh& sh) {
   const int lane = threadIdx.x & 31;
@@ -360,6 +364,18 @@ DEV bool ls32_solve(const c128* H, int ldh, const c128* cv, c128 sig, int rows, 
     }
     __syncwarp();
     if (!warp_backsolve32(A, la, me, b) && lane == 0) sh.ibc[0] = 1;
+    // size of the refinement step: ||correction||^2 <= 1e-8 ||y||^2
+    double cn = 0, yn = 0;
+    for (int i = lane; i < me; i += 32) {
+      cn += (double)norm2(b[i]);
+      yn += norm2(y[i]);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      cn += __shfl_xor_sync(0xffffffffu, cn, off);
+      yn += __shfl_xor_sync(0xffffffffu, yn, off);
+    }
+    if (lane == 0 && !(cn <= 1e-8 * yn)) sh.ibc[0] = 2;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < me; i += DT) y[i] += up(b[i]);
@@ -384,11 +400,11 @@ DEV void base_ls(const DenseCycle& d, int c, c128* A, Sh& sh) {
   c128* tau = A + (long)lda * (me + 1);
   c128* y = tau + (me + 1);
   c128* rinv = y + (me + 1);
-  if (d.ls32 && d.kfull <= 1 && !d.fom) {
-    // complex64 basis, Hessenberg recurrence: FP32 least squares + refinement (tau as scratch)
-    if (!ls32_solve(H, m + 1, cv, sig, rows, me, reinterpret_cast<unsigned char*>(A), tau, y, sh))
-      set_err(st, GDR_EBREAKDOWN);
-  } else {
+  // complex64 basis, Hessenberg recurrence: FP32 least squares + refinement (tau as
+  // scratch), the FP64 form below when that is not trusted
+  const bool done32 = d.ls32 && d.kfull <= 1 && !d.fom &&
+                      ls32_solve(H, m + 1, cv, sig, rows, me, reinterpret_cast<unsigned char*>(A), tau, y, sh);
+  if (!done32) {
     load_shifted(A, lda, H, m + 1, rows, me, sig);
     for (int i = threadIdx.x; i < rows; i += DT) A[i + (long)me * lda] = cv[i];
     if (threadIdx.x == 0) sh.ibc[0] = 0;

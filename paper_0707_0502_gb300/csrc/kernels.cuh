@@ -36,6 +36,8 @@ struct Batch {
   c128* cvec = nullptr;  // m+1 per column
   c128* h1 = nullptr;    // (m+2) per column: GS dots (+ ||w||^2 in slot m+1)
   c128* h2 = nullptr;
+  c128* hd = nullptr;    // DCGS2 dot values per column (2m + 8), see arnoldi_dcgs2
+  c128* dc = nullptr;    // DCGS2 update coefficients per column (2m + 8)
   c128* part = nullptr;  // block partials, per column pstride
   long pstride = 0;
   unsigned* cnt = nullptr;  // last-block counters, per column (4 slots)
@@ -91,6 +93,13 @@ void scale_into(gdr_ctx* ctx, const Batch<R>& b, int j, const cx<R>* w, long wcs
 // while the basis fits in L2, else matvec, dot, update, dot, update (+ scale at jlast).
 template <typename R>
 void arnoldi_step(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b, int j, int jstart, int jlast, cx<R>*& wlast);
+// Arnoldi steps jstart..jend-1 of every column by classical Gram-Schmidt with delayed
+// reorthogonalisation (DCGS2: per step one matvec, one dot pass and one update pass
+// over the basis), then a finalising pass that writes v_jend; v_jstart must be final
+// (normalised and orthogonal to v_0..v_{jstart-1}).  Needs the batch's hd / dc buffers
+// and partials of (2m + 8) values per slot.
+template <typename R>
+void arnoldi_dcgs2(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b, int jstart, int jend);
 // persistent Arnoldi sweep (sweep.cu): steps jstart..jend-1 of every column in one
 // cooperative launch; v_jend is left unnormalised in W2 (scale_into writes it).
 // sweep_fits: short vectors, where the sweep replaces the per-phase launches.

@@ -82,15 +82,17 @@ DEV bool last_block(unsigned* cnt) {
 // writing a group's slots (`nblk_group` blocks write into it) sums them, one
 // thread per value, into gpart[g * hs + i]; the last group sums the group results.
 // FP64 adds are costly on this GPU, so no single block sums all S partials.
+// Returns true in the one block that wrote `out` (its threads see `out` after a
+// __syncthreads()).
 constexpr int RG = 16;
-DEV void reduce2(const c128* part, c128* gpart, int hs, int S, int nval, unsigned* gcnt, unsigned* tcnt, int group,
+DEV bool reduce2(const c128* part, c128* gpart, int hs, int S, int nval, unsigned* gcnt, unsigned* tcnt, int group,
                  unsigned nblk_group, c128* out) {
   __shared__ bool last_g, last_t;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) last_g = (atomicAdd(&gcnt[group], 1u) == nblk_group - 1);
   __syncthreads();
-  if (!last_g) return;
+  if (!last_g) return false;
   __threadfence();
   const int s0 = group * RG, s1 = min(S, s0 + RG);
   for (int i = threadIdx.x; i < nval; i += NT) {
@@ -106,7 +108,7 @@ DEV void reduce2(const c128* part, c128* gpart, int hs, int S, int nval, unsigne
     last_t = (atomicAdd(tcnt, 1u) == (unsigned)ng - 1);
   }
   __syncthreads();
-  if (!last_t) return;
+  if (!last_t) return false;
   __threadfence();
   for (int i = threadIdx.x; i < nval; i += NT) {
     c128 acc = {0, 0};
@@ -114,6 +116,7 @@ DEV void reduce2(const c128* part, c128* gpart, int hs, int S, int nval, unsigne
     out[i] = acc;
   }
   if (threadIdx.x == 0) *tcnt = 0;
+  return true;
 }
 
 // ------------------------------------------------------------ Gram-Schmidt
@@ -389,6 +392,305 @@ __global__ void __launch_bounds__(NT) gs_update_kernel(Batch<R> b, int nv, cx<R>
       st.inv_norm = 1.0 / wn;
     }
     b.cnt[4 * c] = 0;
+  }
+}
+
+// ------------------------------------------- delayed reorthogonalisation (DCGS2)
+//
+// Arnoldi with classical Gram-Schmidt whose second (re)orthogonalisation pass is
+// delayed by one step and merged into the next step's projection, so a step reads
+// the basis twice (one dot pass, one update pass) instead of four times.  At step j
+// the basis v_0..v_{j-1} is final and u (the provisional v_j) is orthogonalised once
+// and unnormalised, with A v_{j-1} = V_j Hbar[0:j, j-1] + u.  With w = A u, one pass
+// gives s = V_j^H u, z = V_j^H w, omega = u^H u, zeta = u^H w; then
+//   nu = sqrt(omega - |s|^2),  v_j = (u - V_j s) / nu,
+//   Hbar[0:j, j-1] += s,  Hbar[j, j-1] = nu                (the delayed pass for step j-1)
+//   t = (zeta - s^H z) / nu,  Hbar[0:j+1, j] = ([z ; t] - Hbar[0:j+1, 0:j] s) / nu
+//   u' = (w - V_j z - t v_j) / nu = (w - V_j (z - (t/nu) s) - (t/nu) u) / nu,
+// u' being the next step's provisional vector (A v_j = V_{j+1} Hbar[0:j+1, j] + u').
+// The first step of a cycle starts from a final v_j (s = 0, nu = 1); after the last
+// step a finalising pass (dot + update without w) makes v_m from u.  Lucky breakdown
+// of step j-1 (nu <= 1e-12 ||A v_{j-1}||) is detected at step j: m_eff = j.
+//
+// Dot pass values per column at hd + c * (2m + 8): [s_i, z_i] interleaved (i < j),
+// then omega, zeta, w^H w.  Coefficients of the update pass at dc + c * (2m + 8):
+// a = s (m+1 slots), b = z - (t/nu) s (m+1 slots), t/nu, 1/nu.
+
+constexpr int DC_FIRST = 1, DC_FINAL = 2;
+
+template <typename R>
+__global__ void __launch_bounds__(NT, 3) dcgs2_dot_kernel(Batch<R> b, int j, const cx<R>* __restrict__ Uv, long ucs,
+                                                       const cx<R>* __restrict__ W, long wcs, int S, int G,
+                                                       int mode) {
+  const int c = blockIdx.y;
+  if (!b.st[c].run) return;
+  constexpr int K = U<R>::K;
+  // two staged vectors: half the complex64 tile of gs_dot_kernel keeps 3 blocks per SM
+  constexpr int DU = sizeof(R) == 4 ? DotTile<R>::DU / 2 : DotTile<R>::DU;
+  constexpr int TU = DU * 32;
+  __shared__ cx<R> ut[TU * K];
+  __shared__ cx<R> wt[TU * K];
+  __shared__ c128 accs[2 * GDR_MAX_M + 8];
+  const bool hasw = mode != DC_FINAL;
+  const cx<R>* __restrict__ V = b.V + c * b.vcs;
+  const cx<R>* __restrict__ u = Uv + c * ucs;
+  const cx<R>* __restrict__ w = W + c * wcs;
+  const long n = b.nvec ? (long)b.nvec[c] : b.n, nu = nunits<R>(n);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nvec_tot = j + 1;  // j basis vectors and the self terms
+  const int slot = blockIdx.x % S, grp = blockIdx.x / S;
+  const int vpg = (nvec_tot + G - 1) / G;
+  const int i0 = grp * vpg, i1 = min(nvec_tot, i0 + vpg);
+  const int hs = 2 * b.m + 8;
+  const int v0 = 2 * i0, v1 = 2 * i1 + (i1 == nvec_tot ? 1 : 0);  // value range of this block
+  for (int i = v0 + threadIdx.x; i < v1; i += NT) accs[i] = {0, 0};
+  const long ntiles = (nu + TU - 1) / TU;
+  for (long t = slot; t < ntiles && i0 < i1; t += S) {
+    const long u0 = t * TU;
+    __syncthreads();  // readers of the previous tile are done
+    for (int q = threadIdx.x; q < TU; q += NT) {
+      cx<R> tu[K], tw[K];
+      if (u0 + q < nu) {
+        ldu<R>(u, u0 + q, n, tu);
+        if (hasw) ldu<R>(w, u0 + q, n, tw);
+      }
+#pragma unroll
+      for (int kk = 0; kk < K; ++kk) {
+        if (u0 + q >= nu) tu[kk] = {0, 0};
+        if (u0 + q >= nu || !hasw) tw[kk] = {0, 0};
+        ut[q * K + kk] = tu[kk];
+        wt[q * K + kk] = tw[kk];
+      }
+    }
+    __syncthreads();
+    for (int i = i0 + warp; i < i1; i += NT / 32) {
+      cx<R> au = {0, 0}, aw = {0, 0}, ww = {0, 0};
+      if (i < j) {
+        const cx<R>* vi = V + (long)i * b.ldv;
+        cx<R> vv[DU][K];
+#pragma unroll
+        for (int tt = 0; tt < DU; ++tt) {
+          const long uu = u0 + lane + 32 * tt;
+          if (uu < nu) {
+            ldu<R>(vi, uu, n, vv[tt]);
+          } else {
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) vv[tt][kk] = {0, 0};
+          }
+        }
+#pragma unroll
+        for (int tt = 0; tt < DU; ++tt)
+#pragma unroll
+          for (int kk = 0; kk < K; ++kk) {
+            au += cmulc(vv[tt][kk], ut[(lane + 32 * tt) * K + kk]);
+            aw += cmulc(vv[tt][kk], wt[(lane + 32 * tt) * K + kk]);
+          }
+      } else {  // omega = u^H u (au.x), zeta = u^H w (aw), w^H w (ww.x)
+#pragma unroll
+        for (int tt = 0; tt < DU; ++tt)
+#pragma unroll
+          for (int kk = 0; kk < K; ++kk) {
+            const cx<R> a = ut[(lane + 32 * tt) * K + kk], bw = wt[(lane + 32 * tt) * K + kk];
+            au.x += norm2(a);
+            aw += cmulc(a, bw);
+            ww.x += norm2(bw);
+          }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        au.x += __shfl_xor_sync(FULL, au.x, off);
+        au.y += __shfl_xor_sync(FULL, au.y, off);
+        aw.x += __shfl_xor_sync(FULL, aw.x, off);
+        aw.y += __shfl_xor_sync(FULL, aw.y, off);
+        ww.x += __shfl_xor_sync(FULL, ww.x, off);
+      }
+      if (lane == 0) {
+        accs[2 * i] += up(au);
+        accs[2 * i + 1] += up(aw);
+        if (i == j) accs[2 * i + 2] += up(ww);
+      }
+    }
+  }
+  __syncthreads();
+  c128* part = b.part + c * b.pstride;
+  for (int i = v0 + threadIdx.x; i < v1; i += NT) part[(long)slot * hs + i] = accs[i];
+  const int rg = slot / RG;
+  const unsigned nbg = (unsigned)(min(S, (rg + 1) * RG) - rg * RG) * (unsigned)G;
+  c128* hv = b.hd + (long)c * hs;
+  if (!reduce2(part, part + (long)b.nblk * hs, hs, S, 2 * j + 3, b.gcnt + 64 * c, b.cnt + 4 * c + 1, rg, nbg, hv))
+    return;
+  __syncthreads();
+
+  // ---- coefficients (the block that holds the sums; FP64 except the small H s correction)
+  __shared__ c128 ssh[GDR_MAX_M + 2];
+  __shared__ double red_d[NT / 32];
+  __shared__ c128 red_c[NT / 32];
+  __shared__ double nu_s;
+  __shared__ int brk_s;
+  const int m = b.m;
+  const bool first = mode == DC_FIRST;
+  c128 szp = {0, 0};
+  double ssp = 0;
+  for (int i = threadIdx.x; i < j; i += NT) {
+    const c128 si = first ? c128{0, 0} : hv[2 * i];
+    ssh[i] = si;
+    ssp += norm2(si);
+    szp += cmulc(si, hv[2 * i + 1]);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    ssp += __shfl_xor_sync(FULL, ssp, off);
+    szp.x += __shfl_xor_sync(FULL, szp.x, off);
+    szp.y += __shfl_xor_sync(FULL, szp.y, off);
+  }
+  if (lane == 0) {
+    red_d[warp] = ssp;
+    red_c[warp] = szp;
+  }
+  __syncthreads();
+  ColState& st = b.st[c];
+  c128* H = b.H + (long)c * (m + 1) * m;
+  c128* dc = b.dc + (long)c * hs;
+  if (threadIdx.x == 0) {
+    double ss = 0;
+    c128 sz = {0, 0};
+    for (int q = 0; q < NT / 32; ++q) {
+      ss += red_d[q];
+      sz += red_c[q];
+    }
+    const double omega = hv[2 * j].x;
+    double nuv = first ? 1.0 : sqrt(fmax(omega - ss, 0.0));
+    int brk = 0;
+    if (!first) {
+      if (!isfinite(nuv) || !isfinite(omega)) {
+        st.nan = 1;
+        brk = 1;
+      } else if (nuv <= 1e-12 * st.wnorm0) {
+        brk = 1;
+      }
+      H[(long)(j - 1) * (m + 1) + j] = {nuv, 0.0};
+      if (brk) {
+        st.broke = 1;
+        st.run = 0;
+        st.m_eff = j;
+      }
+    }
+    if (!brk) {
+      st.inv_norm = 1.0 / nuv;
+      st.j = j;
+      if (mode != DC_FINAL) {
+        const c128 zeta = hv[2 * j + 1];
+        const c128 t = (1.0 / nuv) * (zeta - sz);
+        dc[2 * (m + 1)] = (1.0 / nuv) * t;  // t / nu
+        ssh[GDR_MAX_M + 1] = t;
+        const double ww = hv[2 * j + 2].x;
+        st.wnorm0 = sqrt(ww) / nuv;
+        if (!isfinite(ww)) {
+          st.nan = 1;
+          st.broke = 1;
+          st.run = 0;
+          st.m_eff = j + 1;
+          brk = 1;
+        }
+      }
+      dc[2 * (m + 1) + 1] = {1.0 / nuv, 0.0};
+    }
+    nu_s = nuv;
+    brk_s = brk;
+  }
+  __syncthreads();
+  if (brk_s) return;
+  const double nuv = nu_s;
+  // the delayed pass completes column j-1
+  if (!first)
+    for (int i = threadIdx.x; i < j; i += NT) H[(long)(j - 1) * (m + 1) + i] += ssh[i];
+  for (int i = threadIdx.x; i < j; i += NT) dc[i] = ssh[i];
+  if (mode == DC_FINAL) return;
+  __syncthreads();
+  const c128 t = ssh[GDR_MAX_M + 1];
+  const c128 tn = (1.0 / nuv) * t;
+  for (int i = threadIdx.x; i < j; i += NT) dc[(m + 1) + i] = hv[2 * i + 1] - tn * ssh[i];
+  // column j: ([z ; t] - Hbar[0:j+1, 0:j] s) / nu; s is O(rounding), so H s in FP32
+  for (int i = threadIdx.x; i <= j; i += NT) {
+    c64 hsum = {0.f, 0.f};
+    if (!first)
+      for (int l = 0; l < j; ++l) hsum += to64(H[(long)l * (m + 1) + i]) * to64(ssh[l]);
+    const c128 zi = (i < j) ? hv[2 * i + 1] : t;
+    H[(long)j * (m + 1) + i] = (1.0 / nuv) * (zi - to128(hsum));
+  }
+}
+
+// DCGS2 update pass of step j (every unit of every running column):
+//   v_j = (u - V_j a) / nu      into V[:, j]   (not on the first step: v_j is final)
+//   u'  = (w - V_j b - (t/nu) u) / nu  into Unew (may alias u; not on the finalising pass)
+template <typename R>
+__global__ void __launch_bounds__(NT) dcgs2_update_kernel(Batch<R> b, int j, const cx<R>* Uv, long ucs,
+                                                          const cx<R>* __restrict__ W, cx<R>* Unew, int mode) {
+  const int c = blockIdx.y;
+  if (!b.st[c].run) return;
+  constexpr int K = U<R>::K;
+  const int m = b.m, hs = 2 * m + 8;
+  __shared__ cx<R> sa[GDR_MAX_M + 1], sb[GDR_MAX_M + 1];
+  __shared__ cx<R> tnu_s;
+  __shared__ R inu_s;
+  const c128* dc = b.dc + (long)c * hs;
+  const bool first = mode == DC_FIRST, fin = mode == DC_FINAL;
+  for (int i = threadIdx.x; i < j; i += NT) {
+    sa[i] = cvt<R>(dc[i]);
+    sb[i] = cvt<R>(dc[(m + 1) + i]);
+  }
+  if (threadIdx.x == 0) {
+    tnu_s = fin ? cx<R>{0, 0} : cvt<R>(dc[2 * (m + 1)]);
+    inu_s = (R)dc[2 * (m + 1) + 1].x;
+  }
+  __syncthreads();
+  const cx<R> tnu = tnu_s;
+  const R inu = inu_s;
+  const cx<R>* __restrict__ V = b.V + c * b.vcs;
+  const cx<R>* u = Uv + c * ucs;
+  const cx<R>* __restrict__ w = W + c * b.wcs;
+  cx<R>* un = Unew + c * b.wcs;
+  cx<R>* vj = b.V + c * b.vcs + (long)j * b.ldv;
+  const long n = b.nvec ? (long)b.nvec[c] : b.n, nu = nunits<R>(n);
+  const long gt = blockIdx.x * (long)NT + threadIdx.x, gs = (long)gridDim.x * NT;
+  for (long q = gt; q < nu; q += gs) {
+    cx<R> uu[K], acc_a[K], acc_b[K];
+    ldu<R>(u, q, n, uu);
+    if (!fin) {
+      ldu<R>(w, q, n, acc_b);
+    } else {
+#pragma unroll
+      for (int kk = 0; kk < K; ++kk) acc_b[kk] = {0, 0};
+    }
+#pragma unroll
+    for (int kk = 0; kk < K; ++kk) acc_a[kk] = uu[kk];
+    for (int g0 = 0; g0 < j; g0 += JB) {
+      cx<R> vv[JB][K];
+#pragma unroll
+      for (int qq = 0; qq < JB; ++qq)
+        if (g0 + qq < j) ldu<R>(V + (long)(g0 + qq) * b.ldv, q, n, vv[qq]);
+#pragma unroll
+      for (int qq = 0; qq < JB; ++qq) {
+        if (g0 + qq < j) {
+          const cx<R> ai = sa[g0 + qq], bi = sb[g0 + qq];
+#pragma unroll
+          for (int kk = 0; kk < K; ++kk) {
+            if (!first) acc_a[kk] -= vv[qq][kk] * ai;
+            if (!fin) acc_b[kk] -= vv[qq][kk] * bi;
+          }
+        }
+      }
+    }
+    if (!first) {
+#pragma unroll
+      for (int kk = 0; kk < K; ++kk) acc_a[kk] = inu * acc_a[kk];
+      stu<R>(vj, q, n, acc_a);
+    }
+    if (!fin) {
+#pragma unroll
+      for (int kk = 0; kk < K; ++kk) acc_b[kk] = inu * (acc_b[kk] - tnu * uu[kk]);
+      stu<R>(un, q, n, acc_b);
+    }
   }
 }
 
@@ -688,6 +990,40 @@ void arnoldi_step(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b, int j, int j
 }
 
 template <typename R>
+void arnoldi_dcgs2(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b, int jstart, int jend) {
+  GDR_REQUIRE(b.hd && b.dc, "arnoldi_dcgs2: batch without DCGS2 buffers");
+  const int is = (int)(sizeof(ColState) / sizeof(int));
+  const double sv = sizeof(cx<R>);
+  for (int j = jstart; j <= jend; ++j) {
+    const int mode = (j == jend) ? DC_FINAL : (j == jstart ? DC_FIRST : 0);
+    // u: the final v_j on the first step, else the provisional vector in W2
+    const cx<R>* Uv = (mode == DC_FIRST) ? b.V + (long)j * b.ldv : b.W2;
+    const long ucs = (mode == DC_FIRST) ? b.vcs : b.wcs;
+    if (mode != DC_FINAL)
+      op_apply_skip(ctx, A, b.ncol, nullptr, Uv, ucs, b.W, b.wcs, nullptr, 0, &b.st[0].run, is, b.cpp);
+    int S, G;
+    dot_grid(ctx, b, j + 1, S, G);
+    const double act = run_share(ctx, b);
+    {
+      KProf kp(ctx, sizeof(R) == 4 ? "dcgs2_dot_c64" : "dcgs2_dot_c128",
+               ((double)j + (mode == DC_FINAL ? 1.0 : 2.0)) * col_len(b) * sv * act);
+      dcgs2_dot_kernel<R><<<dim3((unsigned)(S * G), (unsigned)b.ncol), NT, 0, ctx->stream>>>(b, j, Uv, ucs, b.W,
+                                                                                           b.wcs, S, G, mode);
+      GDR_LAUNCHED(ctx);
+    }
+    {
+      const double reads = (double)j + (mode == DC_FINAL ? 1.0 : 2.0);
+      const double writes = (mode == 0) ? 2.0 : 1.0;
+      KProf kp(ctx, sizeof(R) == 4 ? "dcgs2_update_c64" : "dcgs2_update_c128",
+               (reads + writes) * col_len(b) * sv * run_share(ctx, b));
+      dcgs2_update_kernel<R><<<dim3((unsigned)b.nblk, (unsigned)b.ncol), NT, 0, ctx->stream>>>(b, j, Uv, ucs, b.W,
+                                                                                             b.W2, mode);
+      GDR_LAUNCHED(ctx);
+    }
+  }
+}
+
+template <typename R>
 void start_cycle(gdr_ctx* ctx, const Batch<R>& b, const cx<R>* r, long rcs) {
   double* rn2 = ctx->get<double>("start_rn2", b.ncol);
   norms2<cx<R>>(ctx, b.n, b.ncol, r, rcs, rn2, b.part, b.nblk, b.cnt, b.nvec);
@@ -773,6 +1109,8 @@ template void scale_into<float>(gdr_ctx*, const Batch<float>&, int, const c64*, 
 template void scale_into<double>(gdr_ctx*, const Batch<double>&, int, const c128*, long);
 template void arnoldi_step<float>(gdr_ctx*, const gdr_op*, const Batch<float>&, int, int, int, c64*&);
 template void arnoldi_step<double>(gdr_ctx*, const gdr_op*, const Batch<double>&, int, int, int, c128*&);
+template void arnoldi_dcgs2<float>(gdr_ctx*, const gdr_op*, const Batch<float>&, int, int);
+template void arnoldi_dcgs2<double>(gdr_ctx*, const gdr_op*, const Batch<double>&, int, int);
 template void start_cycle<float>(gdr_ctx*, const Batch<float>&, const c64*, long);
 template void start_cycle<double>(gdr_ctx*, const Batch<double>&, const c128*, long);
 template void norms2<c64>(gdr_ctx*, long, int, const c64*, long, double*, c128*, int, unsigned*, const int*);

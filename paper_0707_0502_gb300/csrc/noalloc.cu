@@ -10,7 +10,10 @@
 // input and output buffers.
 //
 // The array exists on every device that loads the library, for the lifetime
-// of the process.  Its device address is looked up once per device with
+// of the process.  It belongs to the library's device code, so under CUDA's lazy
+// module loading (the default) its memory is committed when that code is first
+// loaded, at the first call on a device: a caller working to a fixed memory
+// budget should make one call while setting up.  Its device address is looked up once per device with
 // cudaGetSymbolAddress (host code cannot use the symbol itself: on the host it
 // names a stand-in, not device memory).  That lookup happens on the first call
 // made on a device, so make the first call before any stream capture.  Every

@@ -243,8 +243,11 @@ Batch<R> make_batch(gdr_ctx* ctx, const std::string& tag, long n, int ncol, int 
   b.cvec = ctx->get<c128>(tag + ".c", (size_t)(m + 1) * ncol);
   b.h1 = ctx->get<c128>(tag + ".h1", (size_t)(m + 2) * ncol);
   b.h2 = ctx->get<c128>(tag + ".h2", (size_t)(m + 2) * ncol);
+  b.hd = ctx->get<c128>(tag + ".hd", (size_t)(2 * m + 8) * ncol);
+  b.dc = ctx->get<c128>(tag + ".dc", (size_t)(2 * m + 8) * ncol);
   b.nblk = nblk_for<R>(ctx, n);
-  b.pstride = (long)(b.nblk + 64) * std::max(m + 2, hmin);  // block partials, then slot-group partials
+  // block partials, then slot-group partials (DCGS2 dot pass: 2m + 8 values per slot)
+  b.pstride = (long)(b.nblk + 64) * std::max(2 * m + 8, hmin);
   b.part = ctx->get<c128>(tag + ".part", (size_t)b.pstride * ncol + 64);
   b.cnt = ctx->get<unsigned>(tag + ".cnt", (size_t)4 * ncol);
   b.gcnt = ctx->get<unsigned>(tag + ".gcnt", (size_t)64 * ncol);
@@ -295,6 +298,85 @@ void reorth_column(gdr_ctx* ctx, const Batch<R>& b, int j, double* nrm2) {
   dim3 g(grid1(ctx, b.n), (unsigned)b.ncol);
   normalize_kernel<R><<<g, 256, 0, ctx->stream>>>(b.V, b.ldv, b.vcs, j, b.n, nrm2, b.st, b.nvec);
   GDR_LAUNCHED(ctx);
+}
+
+// ---- shift-shared refinement helpers (not in the paper)
+
+// Pivoted Cholesky of a Hermitian positive semidefinite Gram matrix G (nc x nc,
+// column-major): G ~= L L^H with L (nc x p, column-major), column t of L belonging to
+// pivot piv[t] (L[piv[s], t] = 0 for t > s).  Pivots are taken greedily (largest
+// remaining diagonal) until the trace of the remaining Schur complement is <= thr2
+// or p == pmax.  Returns p.
+int pivoted_cholesky(const std::vector<c128>& G, int nc, double thr2, int pmax, std::vector<c128>& L,
+                     std::vector<int>& piv) {
+  std::vector<double> d(nc);
+  std::vector<char> used(nc, 0);
+  for (int i = 0; i < nc; ++i) d[i] = G[i + (long)i * nc].x;
+  L.assign((size_t)nc * std::max(pmax, 1), c128{0, 0});
+  piv.clear();
+  int p = 0;
+  while (p < pmax) {
+    double tr = 0, best = 0;
+    int pv = -1;
+    for (int i = 0; i < nc; ++i)
+      if (!used[i]) {
+        tr += std::max(d[i], 0.0);
+        if (d[i] > best) {
+          best = d[i];
+          pv = i;
+        }
+      }
+    if (pv < 0 || tr <= thr2) break;
+    const double lpp = std::sqrt(best);
+    for (int i = 0; i < nc; ++i) {
+      if (used[i]) continue;
+      c128 v = G[i + (long)pv * nc];
+      for (int t = 0; t < p; ++t) v -= L[i + (long)t * nc] * conj(L[pv + (long)t * nc]);
+      L[i + (long)p * nc] = (1.0 / lpp) * v;
+    }
+    L[pv + (long)p * nc] = {lpp, 0.0};
+    for (int i = 0; i < nc; ++i)
+      if (!used[i] && i != pv) d[i] -= norm2(L[i + (long)p * nc]);
+    used[pv] = 1;
+    piv.push_back(pv);
+    ++p;
+  }
+  return p;
+}
+
+// Y = R W with orthonormal columns for the pivoted Cholesky factor L of R^H R:
+// Y = R_piv L_piv^{-H}, so W[piv[s], t] = (L_piv^{-H})[s, t] (upper triangular,
+// column-major nc x p), zero in the other rows.
+std::vector<c128> orth_weights(const std::vector<c128>& L, const std::vector<int>& piv, int nc) {
+  const int p = (int)piv.size();
+  // M = L_piv^{-1} (lower triangular, p x p) by forward substitution, then W = M^H
+  std::vector<c128> M((size_t)p * p, c128{0, 0});
+  for (int t = 0; t < p; ++t) {  // column t of L_piv^{-1}: solve L_piv x = e_t
+    for (int s = 0; s < p; ++s) {
+      c128 v = {s == t ? 1.0 : 0.0, 0.0};
+      for (int u = 0; u < s; ++u) v -= L[piv[s] + (long)u * nc] * M[u + (long)t * p];
+      const c128 dg = L[piv[s] + (long)s * nc];
+      const double dn = norm2(dg);
+      M[s + (long)t * p] = (1.0 / dn) * (conj(dg) * v);
+    }
+  }
+  std::vector<c128> W((size_t)nc * p, c128{0, 0});
+  for (int s = 0; s < p; ++s)
+    for (int t = 0; t < p; ++t) W[piv[s] + (long)t * nc] = conj(M[t + (long)s * p]);
+  return W;
+}
+
+// X[:, i] += sum_t C[t, i] Z[:, t*ns + i] for the shifts i of one right-hand side whose
+// flag act[i] is set (C: p x ns column-major, device; Z: FP64 columns at stride ldz)
+__global__ void shared_apply_kernel(long n, int ns, int p, const c128* __restrict__ C, const int* __restrict__ act,
+                                    const c128* __restrict__ Z, long ldz, c128* X, long ldx) {
+  const int i = blockIdx.y;
+  if (!act[i]) return;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    c128 acc = {0, 0};
+    for (int t = 0; t < p; ++t) acc += C[t + (long)i * p] * Z[((long)t * ns + i) * ldz + e];
+    X[(long)i * ldx + e] += acc;
+  }
 }
 
 std::vector<ColState> read_states(gdr_ctx* ctx, const ColState* st, int ncol) {
@@ -367,6 +449,8 @@ DrResult dr_sh(gdr_ctx* ctx, const gdr_op* A, const DrJob<R>& job, bool use_grap
       if (sweep) {
         arnoldi_sweep<R>(ctx, A, b, jstart, m);
         scale_into<R>(ctx, b, m, b.W2, b.wcs);
+      } else if (std::is_same<R, float>::value && job.dcgs2) {
+        arnoldi_dcgs2<R>(ctx, A, b, jstart, m);
       } else {
         cx<R>* wl = nullptr;
         for (int j = jstart; j < m; ++j) arnoldi_step<R>(ctx, A, b, j, jstart, m - 1, wl);
@@ -449,13 +533,17 @@ void tune_arnoldi(gdr_ctx* ctx, const gdr_op* A, int ncol, int m, double& t_swee
                                                               sh.gamma, sh.norms);
   GDR_LAUNCHED(ctx);
   start_cycle<R>(ctx, b, r, b.ldv);
-  // one pass j = 0..m-1 in either form, from the same v_0 each time
+  // one pass j = 0..m-1 in either form, from the same v_0 each time (the launch form as
+  // the solves run it by default: delayed reorthogonalisation on a complex64 basis)
+  constexpr bool dcgs2 = true;
   auto pass = [&](bool sw) {
     set_run_kernel<<<(ncol + 31) / 32, 32, 0, ctx->stream>>>(b.st, ncol);
     GDR_LAUNCHED(ctx);
     if (sw) {
       arnoldi_sweep<R>(ctx, A, b, 0, m);
       scale_into<R>(ctx, b, m, b.W2, b.wcs);
+    } else if (std::is_same<R, float>::value && dcgs2) {
+      arnoldi_dcgs2<R>(ctx, A, b, 0, m);
     } else {
       cx<R>* wl = nullptr;
       for (int j = 0; j < m; ++j) arnoldi_step<R>(ctx, A, b, j, 0, m - 1, wl);
@@ -548,7 +636,7 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
   d.scratch_per_col = 0;
   d.st = b.st;
   d.want_r = true;
-  d.ls32 = std::is_same<R, float>::value;  // GMRES(m_p) cycles on a complex64 basis
+  d.ls32 = std::is_same<R, float>::value && job.ls32;  // GMRES(m_p) cycles on a complex64 basis
 
   const bool sweep = job.sweep && sweep_fits<R>(ctx, A, b) &&
                     sweep_choice(A, std::is_same<R, double>::value, ncol, mp) != 0;
@@ -575,6 +663,8 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
     if (sweep) {
       arnoldi_sweep<R>(ctx, A, b, 0, mp);
       scale_into<R>(ctx, b, mp, b.W2, b.wcs);
+    } else if (std::is_same<R, float>::value && job.dcgs2) {
+      arnoldi_dcgs2<R>(ctx, A, b, 0, mp);
     } else {
       cx<R>* wl = nullptr;
       for (int j = 0; j < mp; ++j) arnoldi_step<R>(ctx, A, b, j, 0, mp - 1, wl);
@@ -710,7 +800,8 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
   dj.max_mvps = p.max_mvps;
   dj.max_cycles = p.max_cycles;
   dj.sweep = !(p.flags & GDR_FLAG_NO_SWEEP);
-  dj.eig32 = !(p.flags & GDR_FLAG_FP64_EIG);
+  dj.dcgs2 = !(p.flags & GDR_FLAG_CGS2);
+  dj.eig32 = !(p.flags & (GDR_FLAG_FP64_EIG | GDR_FLAG_FP64_DENSE));
   dj.fom = (p.flags & GDR_FLAG_FOM) != 0;
   DrResult dr = dr_sh<R>(ctx, A, dj, use_graph);
   rep.t_rhs1_ms = ms_since(tp);
@@ -778,6 +869,10 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
   const int np = ns * nrhs;
   c128* Rres = ctx->get<c128>("pl.Rres", (size_t)ld * np);
   std::vector<double> relres(np, std::numeric_limits<double>::infinity());
+  // the extra right-hand side's FP64 solutions s_i ((A - sigma_i) s_i ~ v_{k+1}) and
+  // v_{k+1}, once the Proj stage has formed them: the shift-shared refinement's correction
+  const c128* S_extra = nullptr;
+  const c128* v_extra = nullptr;
 
   // ---- FP64 true residuals, refinement (MIXED) and cleanup of the (shift, rhs) pairs of
   //      right-hand sides [r0, r1); relres of those pairs updated
@@ -794,6 +889,187 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
       for (int q = 0; q < nq; ++q) relres[qg + q] = rr[q];
     };
     residuals();
+    // Shift-shared pass (not in the paper; complex64 only): per right-hand side j, the
+    // active residuals R_j = [r_i^j] are written as Y_j C_j + E_j with Y_j orthonormal
+    // (pivoted Cholesky of R_j^H R_j, ||E_j||_F <= refine_rank_tol ||R_j||_2 roughly);
+    // each column of Y_j is solved for all shifts at once by GMRES(m_r)-Proj(k)-Sh
+    // (one Krylov space per column, as for the later right-hand sides of Sec. 4), then
+    // x_i^j += sum_t C_j[t, i] z_{t,i}, and the v_{k+1} components of the new true
+    // residuals are removed with the extra right-hand side's solutions (eq. keyder4b:
+    // x_i += (v_{k+1}^H r_i) s_i).  With bf16 links the stage's residuals are close to
+    // low rank across the shifts (their differences come from the link rounding acting
+    // on solutions that vary smoothly with the shift), so this needs far fewer columns
+    // than one per pair.  Returns false (nothing done) when it would not.
+    auto shared_pass = [&](const std::vector<int>& mask) -> bool {
+      if (!mixed || !(p.refine_rank_tol > 0) || kd <= 0 || !project || !S_extra || ns < 2) return false;
+      if (!std::is_same<R, float>::value) return false;
+      const int nr = r1 - r0;
+      // Gram matrices of the active residuals of each right-hand side (FP64 dots)
+      c128* gram = ctx->get<c128>("sh.gram", (size_t)nr * ns * ns);
+      const int gnb = (int)std::min<long>((n + 255) / 256, 2L * ctx->num_sms);
+      c128* gpart = ctx->get<c128>("sh.part", (size_t)gnb * ns + 64);
+      unsigned* gcnt = ctx->get<unsigned>("sh.cnt", (size_t)4 * ns);
+      GDR_CUDA(cudaMemsetAsync(gcnt, 0, sizeof(unsigned) * 4 * ns, ctx->stream));
+      for (int j = 0; j < nr; ++j)
+        for (int a = 0; a < ns; ++a) {
+          if (!mask[j * ns + a]) continue;
+          const c128* ra = Rq + (long)(j * ns + a) * ld;
+          // r_a^H r_b for b >= a (columns of R_j from a on)
+          dots128(ctx, n, ns - a, ra, 0, Rq + (long)(j * ns + a) * ld, ld, gram + ((long)j * ns + a) * ns + a,
+                  gpart, gnb, gcnt);
+        }
+      std::vector<c128> Gh((size_t)nr * ns * ns);
+      GDR_CUDA(cudaMemcpyAsync(Gh.data(), gram, sizeof(c128) * Gh.size(), cudaMemcpyDeviceToHost, ctx->stream));
+      stream_sync(ctx);
+      struct Rhs {
+        int j, nc, p;
+        std::vector<int> act;  // shifts of this rhs in the pass (indices into 0..ns-1)
+        std::vector<c128> W, C;
+        std::vector<double> tol;
+      };
+      std::vector<Rhs> rs;
+      int cols = 0, pairs = 0;
+      for (int j = 0; j < nr; ++j) {
+        Rhs e;
+        e.j = j;
+        for (int i = 0; i < ns; ++i)
+          if (mask[j * ns + i]) e.act.push_back(i);
+        e.nc = (int)e.act.size();
+        if (e.nc == 0) continue;
+        // Gram of the active columns, G[x, y] = r_{act x}^H r_{act y}, from the stored
+        // gram[(j*ns + a)*ns + b] = r_a^H r_b (b >= a)
+        std::vector<c128> G((size_t)e.nc * e.nc);
+        double gmax = 0;
+        for (int x = 0; x < e.nc; ++x)
+          for (int y = 0; y < e.nc; ++y) {
+            const int a = std::min(e.act[x], e.act[y]), b = std::max(e.act[x], e.act[y]);
+            c128 v = Gh[((size_t)j * ns + a) * ns + b];
+            if (e.act[x] > e.act[y]) v = conj(v);
+            G[x + (size_t)y * e.nc] = v;
+            gmax = std::max(gmax, G[x + (size_t)x * e.nc].x);
+          }
+        std::vector<c128> L;
+        std::vector<int> piv;
+        const double thr = p.refine_rank_tol * std::sqrt(gmax);
+        e.p = pivoted_cholesky(G, e.nc, thr * thr, e.nc, L, piv);
+        if (e.p == 0) continue;
+        e.W = orth_weights(L, piv, e.nc);
+        e.C.assign((size_t)e.p * ns, c128{0, 0});
+        std::vector<double> cmax(e.p, 0.0);
+        for (int t = 0; t < e.p; ++t)
+          for (int x = 0; x < e.nc; ++x) {
+            e.C[t + (size_t)e.act[x] * e.p] = conj(L[x + (size_t)t * e.nc]);
+            cmax[t] = std::max(cmax[t], std::sqrt(norm2(L[x + (size_t)t * e.nc])));
+          }
+        // column t is refined until its error, weighted by its largest coefficient, is
+        // below the target 0.3 tol ||b_j||, but not beyond refine_tol
+        e.tol.resize(e.p);
+        for (int t = 0; t < e.p; ++t)
+          e.tol[t] = std::min(0.5, std::max(0.3 * p.tol * bnq[j] / std::max(cmax[t], 1e-300), p.refine_tol));
+        cols += e.p;
+        pairs += e.nc;
+        rs.push_back(std::move(e));
+      }
+      if (cols == 0 || cols > 0.7 * pairs) return false;
+      rep.shared_cols += cols;
+      rep.shared_pairs += pairs;
+      // memory: per column a complex64 Krylov basis of m_r + 1 vectors (+ work), its FP64
+      // right-hand side and the FP64 solutions of all shifts
+      size_t freeb = 0, totb = 0;
+      GDR_CUDA(cudaMemGetInfo(&freeb, &totb));
+      const size_t per_col = (size_t)ld * (sizeof(cx<R>) * (mr + 6) + sizeof(c128) * (ns + 1)) + 65536;
+      const int chunk = (int)std::max<size_t>(1, (freeb / 2) / per_col);
+      size_t e0 = 0;
+      while (e0 < rs.size()) {  // groups of right-hand sides whose columns fit
+        size_t e1 = e0;
+        int cn = 0;
+        while (e1 < rs.size() && (cn == 0 || cn + rs[e1].p <= chunk)) cn += rs[e1++].p;
+        c128* Y128 = ctx->get<c128>("sh.Y128", (size_t)ld * cn);
+        cx<R>* Y = ctx->get<cx<R>>("sh.Y", (size_t)ld * cn);
+        c128* Z = ctx->get<c128>("sh.Z", (size_t)ld * ns * cn);
+        c128* Wd = ctx->get<c128>("sh.W", (size_t)ns * ns * (e1 - e0));
+        c128* Cd = ctx->get<c128>("sh.C", (size_t)ns * ns * (e1 - e0));
+        int* actd = ctx->get<int>("sh.act", (size_t)ns * (e1 - e0));
+        GDR_CUDA(cudaMemsetAsync(Y128, 0, sizeof(c128) * ld * cn, ctx->stream));
+        GDR_CUDA(cudaMemsetAsync(Z, 0, sizeof(c128) * ld * ns * cn, ctx->stream));
+        ProjJob<R> job;
+        job.ncol = cn;
+        job.ns = ns;
+        job.m_p = mr;
+        job.k = kd;
+        job.project = true;
+        job.Vd = Vd;
+        job.ldvd = ld;
+        job.Hk = Hkd;
+        job.rhs = Y;
+        job.ldrhs = ld;
+        job.sigma.resize((size_t)cn * ns);
+        job.tol.clear();
+        job.X = Z;
+        job.ldx = ld;
+        job.xcs = (long)ns * ld;
+        job.max_mvps = p.max_mvps;
+        job.sweep = !(p.flags & GDR_FLAG_NO_SWEEP);
+        job.dcgs2 = !(p.flags & GDR_FLAG_CGS2);
+        job.ls32 = !(p.flags & GDR_FLAG_FP64_DENSE);
+        int c0 = 0;
+        for (size_t e = e0; e < e1; ++e) {
+          const Rhs& r = rs[e];
+          const long slot = (long)(e - e0);
+          // W padded to ns x ns (rows = all shifts of the rhs, inactive rows zero), C as p x ns
+          std::vector<c128> Wf((size_t)ns * r.p, c128{0, 0});
+          for (int x = 0; x < r.nc; ++x)
+            for (int t = 0; t < r.p; ++t) Wf[r.act[x] + (size_t)t * ns] = r.W[x + (size_t)t * r.nc];
+          std::vector<int> af(ns, 0);
+          for (int i : r.act) af[i] = 1;
+          GDR_CUDA(cudaMemcpyAsync(Wd + slot * ns * ns, Wf.data(), sizeof(c128) * Wf.size(), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+          GDR_CUDA(cudaMemcpyAsync(Cd + slot * ns * ns, r.C.data(), sizeof(c128) * r.C.size(),
+                                   cudaMemcpyHostToDevice, ctx->stream));
+          GDR_CUDA(cudaMemcpyAsync(actd + slot * ns, af.data(), sizeof(int) * ns, cudaMemcpyHostToDevice,
+                                   ctx->stream));
+          // Y_j = R_j W (FP64), then its complex64 copy as the right-hand sides
+          combine<double>(ctx, n, 1, const_cast<c128*>(Rq + (long)r.j * ns * ld), ld, 0, ns, Wd + slot * ns * ns,
+                          ns, 0, 0, r.p, 0, Y128 + (long)c0 * ld, ld, 0, nullptr, 0, nullptr);
+          for (int t = 0; t < r.p; ++t) {
+            for (int i = 0; i < ns; ++i) job.sigma[(size_t)(c0 + t) * ns + i] = sigma[i];
+            job.tol.push_back(r.tol[t]);
+          }
+          c0 += r.p;
+        }
+        to_inner<R>(ctx, n, cn, Y128, ld, Y, ld);
+        ProjResult pr = proj_batch<R>(ctx, A, job, use_graph);
+        for (int c = 0; c < cn; ++c) {
+          rep.mvps_refine += pr.mvps[c];
+          rep.mvps_shared += pr.mvps[c];
+        }
+        if (pr.status == GDR_ENAN || pr.status == GDR_ECUDA) worst(pr.status);
+        // x_i^j += sum_t C_j[t, i] z_{t,i}
+        c0 = 0;
+        for (size_t e = e0; e < e1; ++e) {
+          const Rhs& r = rs[e];
+          const long slot = (long)(e - e0);
+          dim3 ga(grid1(ctx, n), (unsigned)ns);
+          shared_apply_kernel<<<ga, 256, 0, ctx->stream>>>(n, ns, r.p, Cd + slot * ns * ns, actd + slot * ns,
+                                                          Z + (long)c0 * ns * ld, ld, Xq + (long)r.j * ns * ldx, ldx);
+          GDR_LAUNCHED(ctx);
+          c0 += r.p;
+        }
+        e0 = e1;
+      }
+      // remove the v_{k+1} components of the new true residuals (shifts i >= 1)
+      residuals();
+      c128* gam = ctx->get<c128>("sh.gam", (size_t)nq);
+      const int dnb = (int)std::min<long>((n + 255) / 256, 2L * ctx->num_sms);
+      c128* dpart = ctx->get<c128>("sh.dpart", (size_t)dnb * nq + 64);
+      unsigned* dcnt = ctx->get<unsigned>("sh.dcnt", (size_t)4 * nq);
+      GDR_CUDA(cudaMemsetAsync(dcnt, 0, sizeof(unsigned) * 4 * nq, ctx->stream));
+      dots128(ctx, n, nq, v_extra, 0, Rq, ld, gam, dpart, dnb, dcnt);
+      dim3 gc(grid1(ctx, n), (unsigned)nq);
+      correct_kernel<<<gc, 256, 0, ctx->stream>>>(n, ns, gam, S_extra, ld, Xq, ldx);
+      GDR_LAUNCHED(ctx);
+      return true;
+    };
     const int max_pass = (p.flags & GDR_FLAG_NO_REFINE) ? -1 : std::max(0, p.refine_max);
     for (int pass = 0; pass <= max_pass; ++pass) {
       std::vector<int> mask(nq, 0);
@@ -807,6 +1083,10 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
       const bool cleanup = (pass == max_pass) || !mixed;
       rep.refine_passes++;
       if (cleanup) rep.pairs_cleaned += nact;
+      if (!cleanup && shared_pass(mask)) {
+        residuals();
+        continue;
+      }
       // chunk the pairs by memory
       size_t freeb = 0, totb = 0;
       GDR_CUDA(cudaMemGetInfo(&freeb, &totb));
@@ -858,6 +1138,8 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
           job.xcs = ldx;
           job.max_mvps = p.max_mvps;
           job.sweep = !(p.flags & GDR_FLAG_NO_SWEEP);
+          job.dcgs2 = !(p.flags & GDR_FLAG_CGS2);
+          job.ls32 = !(p.flags & GDR_FLAG_FP64_DENSE);
           ProjResult pr = proj_batch<RR>(ctx, A, job, use_graph);
           for (int c = 0; c < cn; ++c) rep.mvps_refine += pr.mvps[c];
           if (pr.status == GDR_ENAN || pr.status == GDR_ECUDA) worst(pr.status);
@@ -910,6 +1192,8 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
       job.xcs = (long)ns * ld;
       job.max_mvps = p.max_mvps;
       job.sweep = !(p.flags & GDR_FLAG_NO_SWEEP);
+      job.dcgs2 = !(p.flags & GDR_FLAG_CGS2);
+      job.ls32 = !(p.flags & GDR_FLAG_FP64_DENSE);
       if (eigsel) job.eigsel = &es;
       ProjResult pr = proj_batch<R>(ctx, A, job, use_graph && !seq);
       for (int c = 0; c < cn; ++c) {
@@ -956,6 +1240,8 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
         scale_extra();
         std::vector<double> bn2(bnorm.begin() + 1, bnorm.end());
         correct_slots(1, nrhs - 1, B + ldb, ldb, bn2);
+        S_extra = XP;  // slot 0: s_i = s~_i / (1 - gamma_i)
+        v_extra = v128;
       }
       // results of RHS 2.. into X
       for (int j = 1; j < nrhs; ++j)
@@ -1096,7 +1382,8 @@ gdr_status solve_batch_pipeline(gdr_ctx* ctx, const gdr_op* A, int ns, const std
   dj.max_mvps = p.max_mvps;
   dj.max_cycles = p.max_cycles;
   dj.sweep = !(p.flags & GDR_FLAG_NO_SWEEP);
-  dj.eig32 = !(p.flags & GDR_FLAG_FP64_EIG);
+  dj.dcgs2 = !(p.flags & GDR_FLAG_CGS2);
+  dj.eig32 = !(p.flags & (GDR_FLAG_FP64_EIG | GDR_FLAG_FP64_DENSE));
   dj.fom = (p.flags & GDR_FLAG_FOM) != 0;
   DrResult dr = dr_sh<R>(ctx, A, dj, use_graph);
   for (long v : dr.col_mvps) rep.mvps_rhs1 += v;
@@ -1167,6 +1454,8 @@ gdr_status solve_batch_pipeline(gdr_ctx* ctx, const gdr_op* A, int ns, const std
       job.xcs = ld;
       job.max_mvps = p.max_mvps;
       job.sweep = !(p.flags & GDR_FLAG_NO_SWEEP);
+      job.dcgs2 = !(p.flags & GDR_FLAG_CGS2);
+      job.ls32 = !(p.flags & GDR_FLAG_FP64_DENSE);
       ProjResult pr = proj_batch<RR>(ctx, A, job, use_graph);
       for (long v : pr.mvps) rep.mvps_refine += v;
       if (pr.status == GDR_ENAN) status = GDR_ENAN;

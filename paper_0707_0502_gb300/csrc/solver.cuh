@@ -21,6 +21,7 @@ struct DrJob {
   bool sweep = true;           // persistent Arnoldi sweep where it fits (sweep_fits)
   bool eig32 = true;           // complex64 basis: harmonic-Ritz eigensolve in FP32
   bool fom = false;            // FOM-Sh / FOM-DR-Sh instead of GMRES-Sh / GMRES-DR-Sh (Sec. 3)
+  bool dcgs2 = true;           // complex64 launches: delayed reorthogonalisation (else CGS2)
 };
 
 struct DrResult {
@@ -62,6 +63,8 @@ struct ProjJob {
   long max_mvps = 100000;
   bool sweep = true;           // persistent Arnoldi sweep where it fits (sweep_fits)
   const EigSel* eigsel = nullptr;  // project over selected approximate eigenvectors instead (Theorem 1)
+  bool dcgs2 = true;           // complex64 launches: delayed reorthogonalisation (else CGS2)
+  bool ls32 = true;            // complex64 basis: FP32 least squares + FP64-residual refinement step
 };
 
 struct ProjResult {

@@ -1,0 +1,103 @@
+"""Mixed-precision solves with gauge links stored in bfloat16 against the oracle
+(runs on a GB300; -m gpu).
+
+bf16 links (8-bit significand) make the complex64 stages' operator differ from
+A by ~1e-3 relative, so everything past the stages is the FP64 refinement's
+work; the result must still be the oracle's solution:
+
+* the config-2 operator (Wilson 8^4, eps 0.3, six kappa shifts, GMRES-DR(40,20))
+  with bf16 links: every shift against the oracle's GMRES-DR-Sh solution
+  converged to 1e-12 (<= 1e-6 relative) and its FP64 true residual with the
+  oracle's operator (<= 1e-8);
+* three Z2 right-hand sides on the same lattice: the Proj stage, the extra
+  right-hand side and the shift-shared refinement passes (residuals of one
+  right-hand side's shifts refined over a few directions of their span, each a
+  multi-shift column, then the extra-right-hand-side correction).  Checked with
+  the default rank tolerance and with a loose one that forces passes over one or
+  two directions only (the remaining pairs then go through later passes): every
+  pair against the oracle (<= 1e-6) and by its FP64 true residual (<= 1e-8)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import WilsonOperator, gmres_dr_sh
+from tests.gpu_util import dev, host
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no GPU", allow_module_level=True)
+
+import paper_0707_0502_gb300 as g  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__
+    __graft_entry__.build()
+    c = g.gdr_create(0)
+    yield c
+    g.gdr_destroy(c)
+
+
+@pytest.fixture(scope="module")
+def cfg2_oracle():
+    """The config-2 operator, and the oracle's converged solutions of three right-hand
+    sides (the config's Gaussian one and two Z2 ones)."""
+    p = W.config(2)
+    A = WilsonOperator(p.op[1], p.op[3], diag_a=p.op[2])
+    B = np.concatenate([p.B[:, :1], W.z2_noise(W.rng(2, 7), p.n, 2)], axis=1)
+    ref = [gmres_dr_sh(A.matvec, B[:, j], p.sigma, p.m, p.k, 1e-12)["x"] for j in range(B.shape[1])]
+    return p, A, B, ref
+
+
+def check_against_oracle(A, p, B, X, ref):
+    for j in range(B.shape[1]):
+        b = B[:, j]
+        for i, s in enumerate(p.sigma):
+            x = X[j, i]
+            assert np.linalg.norm(b - (A.matvec(x) - s * x)) <= 1e-8 * np.linalg.norm(b), (j, i)
+            xr = ref[j][:, i]
+            assert np.linalg.norm(x - xr) <= 1e-6 * np.linalg.norm(xr), (j, i, np.linalg.norm(x - xr) / np.linalg.norm(xr))
+
+
+def test_bf16_links_config2(ctx, cfg2_oracle):
+    p, A, B, ref = cfg2_oracle
+    op = g.make_operator(ctx, p, store=g.GDR_LINK_BF16)
+    prm = g.gdr_params_default(m=p.m, k=p.k, m_proj=p.m_proj, tol=p.tol, extra_tol=p.extra_tol,
+                               prec=g.GDR_PREC_MIXED, flags=g.GDR_FLAG_AUTOTUNE)
+    X = torch.zeros((1, len(p.sigma), p.n), dtype=torch.complex128, device="cuda")
+    st, rep, _ = g.gdr_solve_multishift(ctx, op, p.sigma, dev(np.ascontiguousarray(B[:, :1].T)), X, prm)
+    assert st == g.GDR_OK and rep["max_relres"] <= 1e-8, rep
+    check_against_oracle(A, p, B[:, :1], host(X), ref[:1])
+    g.gdr_op_destroy(op)
+
+
+@pytest.mark.parametrize("rank_tol", [0.0, 0.1], ids=["default", "loose"])
+def test_bf16_links_shared_refinement(ctx, cfg2_oracle, rank_tol):
+    p, A, B, ref = cfg2_oracle
+    op = g.make_operator(ctx, p, store=g.GDR_LINK_BF16)
+    prm = g.gdr_params_default(m=p.m, k=p.k, m_proj=p.m_proj, tol=p.tol, extra_tol=p.extra_tol,
+                               prec=g.GDR_PREC_MIXED, flags=g.GDR_FLAG_AUTOTUNE, refine_rank_tol=rank_tol)
+    nrhs = B.shape[1]
+    X = torch.zeros((nrhs, len(p.sigma), p.n), dtype=torch.complex128, device="cuda")
+    st, rep, _ = g.gdr_solve_multishift(ctx, op, p.sigma, dev(np.ascontiguousarray(B.T)), X, prm)
+    assert st == g.GDR_OK and rep["max_relres"] <= 1e-8, rep
+    if rank_tol > 0:  # the loose tolerance always takes the shift-shared passes
+        assert rep["shared_cols"] > 0 and rep["shared_cols"] < rep["shared_pairs"], rep
+    check_against_oracle(A, p, B, host(X), ref)
+    g.gdr_op_destroy(op)
+
+
+def test_shared_refinement_off_is_per_pair(ctx, cfg2_oracle):
+    """refine_rank_tol < 0 switches the shift-shared passes off."""
+    p, A, B, ref = cfg2_oracle
+    op = g.make_operator(ctx, p, store=g.GDR_LINK_BF16)
+    prm = g.gdr_params_default(m=p.m, k=p.k, m_proj=p.m_proj, tol=p.tol, extra_tol=p.extra_tol,
+                               prec=g.GDR_PREC_MIXED, flags=g.GDR_FLAG_AUTOTUNE, refine_rank_tol=-1.0)
+    X = torch.zeros((B.shape[1], len(p.sigma), p.n), dtype=torch.complex128, device="cuda")
+    st, rep, _ = g.gdr_solve_multishift(ctx, op, p.sigma, dev(np.ascontiguousarray(B.T)), X, prm)
+    assert st == g.GDR_OK and rep["max_relres"] <= 1e-8 and rep["shared_cols"] == 0, rep
+    check_against_oracle(A, p, B, host(X), ref)
+    g.gdr_op_destroy(op)

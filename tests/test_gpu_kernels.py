@@ -223,3 +223,48 @@ def test_basis_update(ctx):
     Vr = V32.astype(complex)
     assert rel(host(Vt).T[:, :nout], Vr @ C[:, :nout]) < 1e-6
     assert rel(host(Xt).T, X0[:n2] + Vr @ C[:, nout:]) < 1e-6
+
+
+# ------------------------------------------------------------ base least squares (a4)
+
+def hessenberg_with_condition(m, kappa, seed):
+    """An (m+1) x m upper Hessenberg matrix whose singular values spread from 1 to about
+    1/kappa: a unitarily similar Hessenberg form of U diag(s) W^H, last column dropped."""
+    rng = np.random.default_rng(seed)
+
+    def unitary(k):
+        q, _ = np.linalg.qr(rng.standard_normal((k, k)) + 1j * rng.standard_normal((k, k)))
+        return q
+    s = np.logspace(0, -np.log10(kappa), m + 1)
+    M = unitary(m + 1) @ np.diag(s) @ unitary(m + 1).conj().T
+    import scipy.linalg as sla
+    return sla.hessenberg(M)[:, :m]
+
+
+@pytest.mark.parametrize("kappa", [1e1, 1e3, 1e6])
+@pytest.mark.parametrize("prec", [g.GDR_PREC_FP64, g.GDR_PREC_MIXED], ids=["fp64", "mixed"])
+def test_dense_ls(ctx, kappa, prec):
+    """The base least squares of a GMRES cycle against numpy's least-squares solution.  The
+    complex64-basis form (FP32 QR + one FP64-residual refinement step, random c: a large
+    least-squares residual) leaves y accurate to about its correction's size -- ~3e-6 at
+    kappa 1e3, ~5e-4 at kappa 1e6 (numpy emulation of the same arithmetic) -- and the
+    residual norm within ~1e-9 of the minimum.  At kappa 1e6 the correction exceeds
+    1e-4 ||y||, so the FP64 form must take over: the 1e-7 bar there holds only through
+    that fallback.  s = c - Hhat y is formed from y in FP64, so its error is bounded by
+    ||Hhat|| ||dy||."""
+    m = 30
+    Hh = hessenberg_with_condition(m, kappa, 11)
+    sigma1 = 0.25 - 0.5j
+    H = Hh + sigma1 * np.eye(m + 1, m)  # Hbar with Hbar - sigma1 Ibar = Hh
+    rng = np.random.default_rng(12)
+    c = rng.standard_normal(m + 1) + 1j * rng.standard_normal(m + 1)
+    y_ref = np.linalg.lstsq(Hh, c, rcond=None)[0]
+    s_ref = c - Hh @ y_ref
+    y = torch.zeros(m, dtype=torch.complex128, device="cuda")
+    s = torch.zeros(m + 1, dtype=torch.complex128, device="cuda")
+    g.gdr_dense_ls(ctx, prec, m, sigma1, dev(np.ascontiguousarray(H.T)), dev(c), y, s)
+    tol = 1e-8 if prec == g.GDR_PREC_FP64 else (1e-7 if kappa > 1e5 else 3e-5)
+    assert rel(host(y), y_ref) <= tol, rel(host(y), y_ref)
+    assert np.linalg.norm(host(s)) <= (1 + 1e-8) * np.linalg.norm(s_ref)
+    bound = tol * np.linalg.norm(Hh, 2) * np.linalg.norm(y_ref) + 1e-12 * np.linalg.norm(c)
+    assert np.linalg.norm(host(s) - s_ref) <= bound, (np.linalg.norm(host(s) - s_ref), bound)

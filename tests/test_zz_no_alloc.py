@@ -1,16 +1,20 @@
-"""The allocation-free GMRES-Sh reduced solve gives the same results as the
-allocating entry point (-m gpu).
+"""The allocation-free GMRES-Sh reduced solve against the oracle's reduced
+solve and against the allocating entry point (-m gpu).
 
 gdr_dense_gmres_sh_noalloc serves callers that cannot let the library
 allocate device memory; it keeps its workspace in one fixed device array.
-Two calls in a row with different inputs check that nothing left over from
-the previous call leaks into the next one.  This file sorts last so that a
-run stopping at the first failure has already run every other test."""
+Its outputs (D, s, beta_new, norms) are compared with the oracle's
+gmres_sh_dense_step on the same recorded Hbar and c, to 1e-10 (FP64), and
+with gdr_dense_gmres_sh.  Two calls in a row with different inputs check that
+nothing left over from the previous call leaks into the next one; one call at
+the documented limits (m = 96, ns = 16) and one past them (GDR_EINVAL).  This
+file sorts last so that a run stopping at the first failure has already run
+every other test."""
 import numpy as np
 import pytest
 
 import workloads as W
-from oracle import CSROperator, gmres_dr_sh
+from oracle import CSROperator, arnoldi_cgs2_step, gmres_dr_sh, gmres_sh_dense_step
 
 pytestmark = pytest.mark.gpu
 
@@ -52,17 +56,38 @@ def test_noalloc_matches_allocating_entry_point():
         p, hist = _inputs()
         calls = [(hist[1], p.sigma, np.array([1.0, 0.8 - 0.3j, 1.7j, -0.4])),
                  (hist[0], p.sigma[:3], np.array([1.0, -2.0 + 0.5j, 0.3j]))]
-        for h, sig, beta in calls:            # two calls in a row, different sizes and inputs
+        # a recurrence at the documented limits: 96 Arnoldi steps on the bidiagonal
+        # matrix, 16 shifts
+        A = CSROperator(*p.op[1:])
+        m96 = g.GDR_NOALLOC_MAX_M
+        V = np.zeros((p.n, m96 + 1), dtype=np.complex128)
+        H96 = np.zeros((m96 + 1, m96), dtype=np.complex128)
+        V[:, 0] = p.B[:, 0] / np.linalg.norm(p.B[:, 0])
+        for j in range(m96):
+            arnoldi_cgs2_step(A.matvec, V, H96, j)
+        c96 = np.zeros(m96 + 1, dtype=np.complex128)
+        c96[0] = np.linalg.norm(p.B[:, 0])
+        sig16 = np.concatenate([p.sigma, -np.linspace(0.1, 30.0, 12) + 0.05j])
+        beta16 = np.exp(0.3j * np.arange(16)) * np.linspace(1.0, 0.2, 16)
+        calls.append(({"Hbar": H96, "c": c96}, sig16, beta16))
+        for h, sig, beta in calls:            # calls in a row, different sizes and inputs
             Hbar, c = h["Hbar"], h["c"]
             m = Hbar.shape[1]
-            ref = _run(g.gdr_dense_gmres_sh, ctx, m, sig, Hbar, c, beta)
             out = _run(g.gdr_dense_gmres_sh_noalloc, ctx, m, sig, Hbar, c, beta)
+            # the oracle's reduced solve on the same Hbar, c; s = c - Hhat d_1 is small
+            # near convergence, so it is compared on the scale of c
+            D, s, bn, nr = gmres_sh_dense_step(Hbar, c, np.asarray(sig), beta, np.ones(len(sig), bool))
+            assert rel(out[0], D.T) < 1e-10, rel(out[0], D.T)
+            assert np.linalg.norm(out[1] - s) < 1e-10 * np.linalg.norm(c)
+            assert rel(out[2], bn) < 1e-10 and rel(out[3], nr) < 1e-10
+            # and the allocating entry point
+            ref = _run(g.gdr_dense_gmres_sh, ctx, m, sig, Hbar, c, beta)
             for a, b in zip(out, ref):
                 assert rel(a, b) < 1e-10
         with pytest.raises(g.GdrError) as e:
             h = hist[0]
-            _run(g.gdr_dense_gmres_sh_noalloc, ctx, h["Hbar"].shape[1], np.zeros(17), h["Hbar"], h["c"],
-                 np.ones(17, complex))
+            _run(g.gdr_dense_gmres_sh_noalloc, ctx, h["Hbar"].shape[1], np.zeros(g.GDR_NOALLOC_MAX_NS + 1),
+                 h["Hbar"], h["c"], np.ones(g.GDR_NOALLOC_MAX_NS + 1, complex))
         assert e.value.status == g.GDR_EINVAL and "GDR_NOALLOC_MAX_NS" in str(e.value)
     finally:
         g.gdr_destroy(ctx)
