@@ -115,15 +115,19 @@ typedef struct {
   unsigned flags;
   int k_select;       /* GDR_FLAG_EIG_SELECT: approximate eigenvectors projected over (1..k; <= 0: k) */
   int m_refine;       /* cycle length of the refinement / cleanup solves (not in the paper); <= 0:
-                         min(m, m_p + (m - m_p) / 2) for vectors of at most 2^17 elements, else m_p */
-  double refine_rank_tol; /* MIXED, shift-shared refinement (not in the paper): a complex64 refinement
-                         pass may refine the residuals of one right-hand side's shifts over a few
-                         orthonormal directions of their span (pivoted Cholesky of their Gram matrix,
-                         directions kept while the rest exceeds refine_rank_tol times the largest
-                         residual), each direction one multi-shift GMRES(m_refine)-Proj(k)-Sh column
-                         for all shifts, followed by the extra-right-hand-side correction; used when
-                         that needs at most 0.7 times the columns of per-pair refinement and the Proj
-                         stage's extra solutions exist (nrhs > 1).  0: automatic (3e-4); < 0: never */
+                         min(m, m_p + (m - m_p) / 2) for vectors of at most 2^17 elements, else
+                         min(m_p, 12) */
+  double refine_rank_tol; /* MIXED, shift-shared refinement (not in the paper; off when <= 0, the
+                         default): a complex64 refinement pass may refine the residuals of one
+                         right-hand side's shifts over a few orthonormal directions of their span
+                         (pivoted Cholesky of their Gram matrix, directions kept while the rest
+                         exceeds refine_rank_tol times the largest residual), each direction one
+                         multi-shift GMRES(m_refine)-Proj(k)-Sh column for all shifts, followed by the
+                         extra-right-hand-side correction; used when that needs at most 0.7 times the
+                         columns of per-pair refinement and the Proj stage's extra solutions exist
+                         (nrhs > 1).  Off by default: on the bf16-link 24^3x32 workload it took more
+                         matvecs than per-pair refinement (its non-base shifts converge slowly in
+                         short restarted cycles) */
 } gdr_params;
 
 typedef struct {

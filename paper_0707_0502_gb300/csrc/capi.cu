@@ -58,7 +58,6 @@ gdr_params resolve_inner_tol(const gdr_ctx* ctx, const gdr_op* A, long n, const 
   // a complex64 refinement pass reliably reduces its residual by 1e-4: one pass then
   // usually finishes a pair that the stage left at ~1e-4
   if (!(r.refine_tol > 0)) r.refine_tol = std::min(r.inner_tol, 1e-4);
-  if (r.refine_rank_tol == 0) r.refine_rank_tol = 3e-4;
   return r;
 }
 

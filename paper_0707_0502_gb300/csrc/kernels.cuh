@@ -75,6 +75,9 @@ template <typename R> inline double basis_len(const Batch<R>& b) {
 template <typename R>
 void gs_dot(gdr_ctx* ctx, const Batch<R>& b, int nv, const cx<R>* w, long wcs, c128* h_out, bool wnorm,
             const cx<R>* wprev = nullptr);
+// workspace of gs_dot for ncol columns sharing one basis of nv <= 48 vectors (vcs = 0), to be
+// reserved before a CUDA graph capture that contains such a gs_dot
+void gs_dot_shared_reserve(gdr_ctx* ctx, long n, int ncol, int nv);
 // wout_c = w_c - V_c[:, 0:nv] h_c and h_out[c][0..nv-1] = V_c[:, 0:nv]^H wout_c in one pass
 template <typename R>
 void gs_update_dot(gdr_ctx* ctx, const Batch<R>& b, int nv, const cx<R>* w, cx<R>* wout, long wcs, const c128* h,

@@ -419,18 +419,20 @@ __global__ void __launch_bounds__(NT) gs_update_kernel(Batch<R> b, int nv, cx<R>
 constexpr int DC_FIRST = 1, DC_FINAL = 2;
 
 template <typename R>
-__global__ void __launch_bounds__(NT, 3) dcgs2_dot_kernel(Batch<R> b, int j, const cx<R>* __restrict__ Uv, long ucs,
+__global__ void __launch_bounds__(NT, 2) dcgs2_dot_kernel(Batch<R> b, int j, const cx<R>* __restrict__ Uv, long ucs,
                                                        const cx<R>* __restrict__ W, long wcs, int S, int G,
                                                        int mode) {
   const int c = blockIdx.y;
   if (!b.st[c].run) return;
   constexpr int K = U<R>::K;
-  // two staged vectors: half the complex64 tile of gs_dot_kernel keeps 3 blocks per SM
-  constexpr int DU = sizeof(R) == 4 ? DotTile<R>::DU / 2 : DotTile<R>::DU;
-  constexpr int TU = DU * 32;
-  __shared__ cx<R> ut[TU * K];
-  __shared__ cx<R> wt[TU * K];
-  __shared__ c128 accs[2 * GDR_MAX_M + 8];
+  constexpr int DU = 8;        // units per lane of a warp's slab
+  constexpr int SU = 32 * DU;  // units per slab
+  constexpr int NW = NT / 32;
+  // Each warp keeps its slab of u and w in registers and streams every basis vector of
+  // its group through it (DU loads in flight per lane and vector), reduces the two dots
+  // over the warp and adds them to its own FP32 sums in shared memory; no block
+  // barrier until the end, so warps never wait for each other.
+  __shared__ cx<R> accw[NW][2 * GDR_MAX_M + 8];
   const bool hasw = mode != DC_FINAL;
   const cx<R>* __restrict__ V = b.V + c * b.vcs;
   const cx<R>* __restrict__ u = Uv + c * ucs;
@@ -443,57 +445,58 @@ __global__ void __launch_bounds__(NT, 3) dcgs2_dot_kernel(Batch<R> b, int j, con
   const int i0 = grp * vpg, i1 = min(nvec_tot, i0 + vpg);
   const int hs = 2 * b.m + 8;
   const int v0 = 2 * i0, v1 = 2 * i1 + (i1 == nvec_tot ? 1 : 0);  // value range of this block
-  for (int i = v0 + threadIdx.x; i < v1; i += NT) accs[i] = {0, 0};
-  const long ntiles = (nu + TU - 1) / TU;
-  for (long t = slot; t < ntiles && i0 < i1; t += S) {
-    const long u0 = t * TU;
-    __syncthreads();  // readers of the previous tile are done
-    for (int q = threadIdx.x; q < TU; q += NT) {
-      cx<R> tu[K], tw[K];
-      if (u0 + q < nu) {
-        ldu<R>(u, u0 + q, n, tu);
-        if (hasw) ldu<R>(w, u0 + q, n, tw);
-      }
+  for (int v = v0 + lane; v < v1; v += 32) accw[warp][v] = {0, 0};
+  __syncwarp();
+  const long nslabs = (nu + SU - 1) / SU;
+  for (long sl = (long)slot * NW + warp; sl < nslabs && i0 < i1; sl += (long)S * NW) {
+    const long ub = sl * SU;
+    cx<R> uu[DU][K], ww[DU][K];
 #pragma unroll
-      for (int kk = 0; kk < K; ++kk) {
-        if (u0 + q >= nu) tu[kk] = {0, 0};
-        if (u0 + q >= nu || !hasw) tw[kk] = {0, 0};
-        ut[q * K + kk] = tu[kk];
-        wt[q * K + kk] = tw[kk];
+    for (int t = 0; t < DU; ++t) {
+      const long q = ub + lane + 32 * t;
+      if (q < nu) {
+        ldu<R>(u, q, n, uu[t]);
+        if (hasw) {
+          ldu<R>(w, q, n, ww[t]);
+        } else {
+#pragma unroll
+          for (int kk = 0; kk < K; ++kk) ww[t][kk] = {0, 0};
+        }
+      } else {
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) uu[t][kk] = ww[t][kk] = {0, 0};
       }
     }
-    __syncthreads();
-    for (int i = i0 + warp; i < i1; i += NT / 32) {
-      cx<R> au = {0, 0}, aw = {0, 0}, ww = {0, 0};
+    for (int i = i0; i < i1; ++i) {
+      cx<R> au = {0, 0}, aw = {0, 0}, wn = {0, 0};
       if (i < j) {
         const cx<R>* vi = V + (long)i * b.ldv;
         cx<R> vv[DU][K];
 #pragma unroll
-        for (int tt = 0; tt < DU; ++tt) {
-          const long uu = u0 + lane + 32 * tt;
-          if (uu < nu) {
-            ldu<R>(vi, uu, n, vv[tt]);
+        for (int t = 0; t < DU; ++t) {
+          const long q = ub + lane + 32 * t;
+          if (q < nu) {
+            ldu<R>(vi, q, n, vv[t]);
           } else {
 #pragma unroll
-            for (int kk = 0; kk < K; ++kk) vv[tt][kk] = {0, 0};
+            for (int kk = 0; kk < K; ++kk) vv[t][kk] = {0, 0};
           }
         }
 #pragma unroll
-        for (int tt = 0; tt < DU; ++tt)
+        for (int t = 0; t < DU; ++t)
 #pragma unroll
           for (int kk = 0; kk < K; ++kk) {
-            au += cmulc(vv[tt][kk], ut[(lane + 32 * tt) * K + kk]);
-            aw += cmulc(vv[tt][kk], wt[(lane + 32 * tt) * K + kk]);
+            au += cmulc(vv[t][kk], uu[t][kk]);
+            aw += cmulc(vv[t][kk], ww[t][kk]);
           }
-      } else {  // omega = u^H u (au.x), zeta = u^H w (aw), w^H w (ww.x)
+      } else {  // omega = u^H u (au.x), zeta = u^H w (aw), w^H w (wn.x)
 #pragma unroll
-        for (int tt = 0; tt < DU; ++tt)
+        for (int t = 0; t < DU; ++t)
 #pragma unroll
           for (int kk = 0; kk < K; ++kk) {
-            const cx<R> a = ut[(lane + 32 * tt) * K + kk], bw = wt[(lane + 32 * tt) * K + kk];
-            au.x += norm2(a);
-            aw += cmulc(a, bw);
-            ww.x += norm2(bw);
+            au.x += norm2(uu[t][kk]);
+            aw += cmulc(uu[t][kk], ww[t][kk]);
+            wn.x += norm2(ww[t][kk]);
           }
       }
 #pragma unroll
@@ -502,18 +505,26 @@ __global__ void __launch_bounds__(NT, 3) dcgs2_dot_kernel(Batch<R> b, int j, con
         au.y += __shfl_xor_sync(FULL, au.y, off);
         aw.x += __shfl_xor_sync(FULL, aw.x, off);
         aw.y += __shfl_xor_sync(FULL, aw.y, off);
-        ww.x += __shfl_xor_sync(FULL, ww.x, off);
       }
-      if (lane == 0) {
-        accs[2 * i] += up(au);
-        accs[2 * i + 1] += up(aw);
-        if (i == j) accs[2 * i + 2] += up(ww);
+      if (i == j) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) wn.x += __shfl_xor_sync(FULL, wn.x, off);
+      }
+      if (lane == (i & 31)) {  // each lane owns the sums of every 32nd vector
+        accw[warp][2 * i] += au;
+        accw[warp][2 * i + 1] += aw;
+        if (i == j) accw[warp][2 * i + 2] += wn;
       }
     }
   }
   __syncthreads();
   c128* part = b.part + c * b.pstride;
-  for (int i = v0 + threadIdx.x; i < v1; i += NT) part[(long)slot * hs + i] = accs[i];
+  for (int v = v0 + threadIdx.x; v < v1; v += NT) {  // the block's sums, warps in a fixed order, FP64
+    c128 sacc = {0, 0};
+#pragma unroll
+    for (int q = 0; q < NW; ++q) sacc += up(accw[q][v]);
+    part[(long)slot * hs + v] = sacc;
+  }
   const int rg = slot / RG;
   const unsigned nbg = (unsigned)(min(S, (rg + 1) * RG) - rg * RG) * (unsigned)G;
   c128* hv = b.hd + (long)c * hs;
@@ -849,6 +860,164 @@ __global__ void __launch_bounds__(CT) combine_kernel(long n, cx<R>* V, long ldv,
   }
 }
 
+// Basis combination for many columns sharing one basis (vcs = 0, no in-place outputs),
+// as in the projection over the kept V_{k+1} of the Proj and refinement stages: a
+// persistent block stages every column's coefficients once (complex64 or FP64 as the
+// vectors, nv x ntot per column) and, for each of its row tiles, the tile of V once,
+// then forms every column's outputs from it -- the basis is read from HBM once instead
+// of once per column.
+template <typename R>
+__global__ void __launch_bounds__(CT) combine_shared_kernel(long n, const cx<R>* __restrict__ V, long ldv, int nv,
+                                                            const c128* __restrict__ C, int ldc, long ccs, int nx,
+                                                            int rmode, c128* X, long ldx, long xcs, cx<R>* Rv,
+                                                            long rcs, const ColState* st, int ncol) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ntot = nx + (rmode ? 1 : 0);
+  cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);  // CR x nv (row-fast)
+  cx<R>* cf = tile + (long)CR * nv;                   // ncol x (nv x ntot)
+  const long per = (long)nv * ntot;
+  for (long t = threadIdx.x; t < per * ncol; t += CT) {
+    const int c = (int)(t / per);
+    const int q = (int)(t % per), i = q % nv, o = q / nv;
+    cf[t] = cvt<R>(C[c * ccs + (long)o * ldc + i]);
+  }
+  const long ntiles = (n + CR - 1) / CR;
+  const int rr = threadIdx.x % CR;
+  for (long tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
+    const long r0 = tl * CR;
+    const int rows = (int)min((long)CR, n - r0);
+    __syncthreads();  // the previous tile's readers are done (and the coefficients staged)
+    for (int t = threadIdx.x; t < CR * nv; t += CT) {
+      const int r = t % CR, i = t / CR;
+      tile[t] = (r < rows) ? V[(long)i * ldv + r0 + r] : cx<R>{0, 0};
+    }
+    __syncthreads();
+    if (rr >= rows) continue;
+    const long row = r0 + rr;
+    // the (column, output) pairs, four independent accumulations per thread at a time;
+    // the CT / CR = 4 thread groups of a row take interleaved pairs
+    const long P = (long)ncol * ntot;
+    for (long p0 = threadIdx.x / CR; p0 < P; p0 += 4 * (CT / CR)) {
+      cx<R> acc[4];
+      const cx<R>* co[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const long pq = min(p0 + (long)q * (CT / CR), P - 1);
+        co[q] = cf + (pq / ntot) * per + (pq % ntot) * nv;
+        acc[q] = {0, 0};
+      }
+      for (int i = 0; i < nv; ++i) {
+        const cx<R> t = tile[(long)i * CR + rr];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] += t * co[q][i];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const long pq = p0 + (long)q * (CT / CR);
+        if (pq >= P) break;
+        const int c = (int)(pq / ntot), o = (int)(pq % ntot);
+        if (st && !st[c].active) continue;
+        if (o < nx) {
+          c128* xp = X + c * xcs + (long)o * ldx + row;
+          *xp = *xp + up(acc[q]);
+        } else {
+          cx<R>* rp = Rv + c * rcs + row;
+          if (rmode == 1) *rp = acc[q];
+          else *rp = *rp + acc[q];
+        }
+      }
+    }
+  }
+}
+
+// h_c = V^H r_c (nv <= NVM basis vectors) for ncol columns sharing one basis V, as in
+// the projection c = V_{k+1}^H r of the Proj and refinement stages.  Block (g, slot)
+// stages row tiles of V (32 EPL rows x nv, complex64 or FP64 as the vectors) in shared
+// memory; its warp w takes column c = 8 g + w, each lane holding its rows of r_c and
+// partial sums for every basis vector in registers, flushed to FP64 in shared memory
+// every FL tiles.  The column groups of one tile slot are consecutive blocks, so they
+// read the same tiles of V close together (L2 reuse): V comes from HBM about once.
+// part[(slot * ncol + c) * nv + i] receives each block's FP64 sums; gs_dot_shared_sum
+// adds them over the slots in a fixed order.
+constexpr int DS_W = 8, DS_EPL = 4, DS_TR = 32 * DS_EPL, DS_FL = 16;
+
+template <typename R, int NVM>
+__global__ void __launch_bounds__(DS_W * 32) gs_dot_shared_kernel(long n, const cx<R>* __restrict__ V, long ldv,
+                                                                   int nv, const cx<R>* __restrict__ Rv, long rcs,
+                                                                   int ncol, const ColState* st, c128* part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<R>* vt = reinterpret_cast<cx<R>*>(smem_raw);                       // nv x DS_TR
+  c128* accd = reinterpret_cast<c128*>(vt + (long)NVM * DS_TR);          // DS_W x NVM
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = blockIdx.x, slot = blockIdx.y;
+  const int c = grp * DS_W + warp;
+  const bool live = c < ncol && (!st || st[c].run);
+  for (int i = lane; i < NVM; i += 32) accd[warp * NVM + i] = {0, 0};
+  cx<R> acc[NVM];
+#pragma unroll
+  for (int i = 0; i < NVM; ++i) acc[i] = {0, 0};
+  const cx<R>* r = Rv + (long)(live ? c : 0) * rcs;
+  const long ntiles = (n + DS_TR - 1) / DS_TR;
+  int cnt = 0;
+  auto flush = [&]() {
+#pragma unroll
+    for (int i = 0; i < NVM; ++i) {
+      if (i >= nv) break;
+      cx<R> a = acc[i];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        a.x += __shfl_xor_sync(FULL, a.x, off);
+        a.y += __shfl_xor_sync(FULL, a.y, off);
+      }
+      if (lane == (i & 31)) accd[warp * NVM + i] += up(a);
+      acc[i] = {0, 0};
+    }
+  };
+  for (long tl = slot; tl < ntiles; tl += gridDim.y) {
+    const long r0 = tl * DS_TR;
+    const int rows = (int)min((long)DS_TR, n - r0);
+    __syncthreads();  // the previous tile's readers are done
+    for (int t = threadIdx.x; t < nv * DS_TR; t += DS_W * 32) {
+      const int i = t / DS_TR, e = t % DS_TR;
+      vt[t] = (e < rows) ? V[(long)i * ldv + r0 + e] : cx<R>{0, 0};
+    }
+    __syncthreads();
+    if (!live) continue;
+    cx<R> rv[DS_EPL];
+#pragma unroll
+    for (int q = 0; q < DS_EPL; ++q) {
+      const int e = lane + 32 * q;
+      rv[q] = (e < rows) ? r[r0 + e] : cx<R>{0, 0};
+    }
+#pragma unroll
+    for (int i = 0; i < NVM; ++i) {
+      if (i >= nv) break;
+#pragma unroll
+      for (int q = 0; q < DS_EPL; ++q) acc[i] += cmulc(vt[i * DS_TR + lane + 32 * q], rv[q]);
+    }
+    if (++cnt == DS_FL) {
+      flush();
+      cnt = 0;
+    }
+  }
+  if (!live) return;
+  flush();
+  __syncwarp();
+  for (int i = lane; i < nv; i += 32) part[((long)slot * ncol + c) * nv + i] = accd[warp * NVM + i];
+}
+
+// hout[c * hs + i] = sum over the S slots of part[(slot * ncol + c) * nv + i] (fixed order)
+__global__ void gs_dot_shared_sum_kernel(int S, int ncol, int nv, const c128* __restrict__ part, c128* hout, int hs,
+                                         const ColState* st) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ncol * nv) return;
+  const int c = t / nv, i = t % nv;
+  if (st && !st[c].run) return;
+  c128 acc = {0, 0};
+  for (int q = 0; q < S; ++q) acc += part[((long)q * ncol + c) * nv + i];
+  hout[(long)c * hs + i] = acc;
+}
+
 // -------------------------------------------------------- small vector ops
 
 __global__ void cvt_128_64_kernel(long n, const c128* in, long ics, c64* out, long ocs) {
@@ -921,9 +1090,48 @@ static void dot_grid(gdr_ctx* ctx, const Batch<R>& b, int nvec, int& S, int& G) 
   G = std::max(G, 1);
 }
 
+// tile slots of the shared-basis dot: about two blocks per SM in all
+static int dot_shared_slots(gdr_ctx* ctx, long n, int ncol) {
+  const int groups = (ncol + DS_W - 1) / DS_W;
+  const long ntiles = (n + DS_TR - 1) / DS_TR;
+  return (int)std::max<long>(1, std::min<long>(ntiles, std::max(1, 2 * ctx->num_sms / groups)));
+}
+
+template <typename R>
+static bool dot_shared_applies(const Batch<R>& b, int nv, bool wnorm, const cx<R>* wprev) {
+  return b.vcs == 0 && b.ncol > 1 && b.nvec == nullptr && nv <= 48 && !wnorm && !wprev;
+}
+
+void gs_dot_shared_reserve(gdr_ctx* ctx, long n, int ncol, int nv) {
+  ctx->get<c128>("dsh.part", (size_t)dot_shared_slots(ctx, n, ncol) * ncol * nv + 64);
+}
+
+template <typename R, int NVM>
+static void gs_dot_shared_launch(gdr_ctx* ctx, const Batch<R>& b, int nv, const cx<R>* w, long wcs, c128* h_out) {
+  const int S = dot_shared_slots(ctx, b.n, b.ncol);
+  c128* part = ctx->get<c128>("dsh.part", (size_t)S * b.ncol * nv + 64);
+  const size_t smem = sizeof(cx<R>) * NVM * DS_TR + sizeof(c128) * DS_W * NVM;
+  dim3 grid((unsigned)((b.ncol + DS_W - 1) / DS_W), (unsigned)S);
+  {
+    KProf kp(ctx, sizeof(R) == 4 ? "gs_dot_shared_c64" : "gs_dot_shared_c128",
+             ((double)nv * b.n + col_len(b)) * sizeof(cx<R>) * run_share(ctx, b));
+    gs_dot_shared_kernel<R, NVM><<<grid, DS_W * 32, smem, ctx->stream>>>(b.n, b.V, b.ldv, nv, w, wcs, b.ncol, b.st,
+                                                                          part);
+    GDR_LAUNCHED(ctx);
+  }
+  const int tot = b.ncol * nv;
+  gs_dot_shared_sum_kernel<<<(tot + 255) / 256, 256, 0, ctx->stream>>>(S, b.ncol, nv, part, h_out, b.m + 2, b.st);
+  GDR_LAUNCHED(ctx);
+}
+
 template <typename R>
 void gs_dot(gdr_ctx* ctx, const Batch<R>& b, int nv, const cx<R>* w, long wcs, c128* h_out, bool wnorm,
             const cx<R>* wprev) {
+  if (dot_shared_applies(b, nv, wnorm, wprev)) {  // one basis for many columns: read it once
+    if (nv <= 24) gs_dot_shared_launch<R, 24>(ctx, b, nv, w, wcs, h_out);
+    else gs_dot_shared_launch<R, 48>(ctx, b, nv, w, wcs, h_out);
+    return;
+  }
   int S, G;
   dot_grid(ctx, b, nv + (wnorm ? 1 : 0), S, G);
   dim3 grid((unsigned)(S * G), (unsigned)b.ncol);
@@ -989,6 +1197,20 @@ void arnoldi_step(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b, int j, int j
   if (j == jlast) scale_into<R>(ctx, b, j + 1, wlast, b.wcs);
 }
 
+// tile slots S x vector groups G of the DCGS2 dot pass: a block takes NT/32 slabs of 256
+// units per round; about two blocks per SM per column, vectors split over G blocks when
+// slabs are scarce (short vectors); S <= nblk bounds the partials
+template <typename R>
+static void dcgs2_grid(gdr_ctx* ctx, const Batch<R>& b, int nvec, int& S, int& G) {
+  const long slabs = (nunits<R>(b.n) + 255) / 256;
+  const long tiles = (slabs + NT / 32 - 1) / (NT / 32);
+  const long target = 2L * ctx->num_sms;
+  S = (int)std::max<long>(1, std::min<long>(tiles, std::min<long>(target, b.nblk)));
+  G = 1;
+  if (S < target) G = (int)std::min<long>((target + S - 1) / S, (nvec + NT / 32 - 1) / (NT / 32));
+  G = std::max(G, 1);
+}
+
 template <typename R>
 void arnoldi_dcgs2(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b, int jstart, int jend) {
   GDR_REQUIRE(b.hd && b.dc, "arnoldi_dcgs2: batch without DCGS2 buffers");
@@ -1002,7 +1224,7 @@ void arnoldi_dcgs2(gdr_ctx* ctx, const gdr_op* A, const Batch<R>& b, int jstart,
     if (mode != DC_FINAL)
       op_apply_skip(ctx, A, b.ncol, nullptr, Uv, ucs, b.W, b.wcs, nullptr, 0, &b.st[0].run, is, b.cpp);
     int S, G;
-    dot_grid(ctx, b, j + 1, S, G);
+    dcgs2_grid(ctx, b, j + 1, S, G);
     const double act = run_share(ctx, b);
     {
       KProf kp(ctx, sizeof(R) == 4 ? "dcgs2_dot_c64" : "dcgs2_dot_c128",
@@ -1062,6 +1284,20 @@ void combine(gdr_ctx* ctx, long n, int ncol, cx<R>* V, long ldv, long vcs, int n
   const double cl = lenh > 0 ? lenh : (double)n * ncol;
   const double vl = vlenh > 0 ? vlenh : (vcs == 0 ? (double)n : (vpp > 1 ? (double)n * ((ncol + vpp - 1) / vpp) : cl));
   const double act = st ? run_share(ctx, ncol, &st[0].run, (int)(sizeof(ColState) / sizeof(int)), nvec) : 1.0;
+  // one basis shared by several columns: stream it once for all of them when their
+  // coefficients fit in shared memory beside a row tile
+  const size_t smem_sh = sizeof(cx<R>) * ((size_t)CR * nv + (size_t)nv * ntot * ncol);
+  if (vcs == 0 && nout == 0 && ncol > 1 && nvec == nullptr && smem_sh <= ctx->combine_smem_limit) {
+    KProf kp(ctx, sizeof(R) == 4 ? "combine_shared_c64" : "combine_shared_c128",
+             act * ((double)n * nv * sizeof(cx<R>) +
+                    cl * (2.0 * nx * sizeof(c128) + (rmode == 2 ? 2.0 : (rmode == 1 ? 1.0 : 0.0)) * sizeof(cx<R>))));
+    const long ntiles = (n + CR - 1) / CR;
+    const unsigned g = (unsigned)std::max<long>(1, std::min<long>(ntiles, 2L * ctx->num_sms));
+    combine_shared_kernel<R><<<g, CT, smem_sh, ctx->stream>>>(n, V, ldv, nv, C, ldc, ccs, nx, rmode, X, ldx, xcs, Rv,
+                                                              rcs, st, ncol);
+    GDR_LAUNCHED(ctx);
+    return;
+  }
   KProf kp(ctx, sizeof(R) == 4 ? "combine_c64" : "combine_c128",
            act * (vl * nv * sizeof(cx<R>) + cl * (nout * sizeof(cx<R>) + 2.0 * nx * sizeof(c128) +
                                                  (rmode == 2 ? 2.0 : (rmode == 1 ? 1.0 : 0.0)) * sizeof(cx<R>))));
@@ -1073,6 +1309,12 @@ void combine(gdr_ctx* ctx, long n, int ncol, cx<R>* V, long ldv, long vcs, int n
 void krylov_init(gdr_ctx* ctx) {
   ctx->combine_smem_limit =
       std::min(set_max_dyn_smem(ctx, combine_kernel<float>), set_max_dyn_smem(ctx, combine_kernel<double>));
+  ctx->combine_smem_limit = std::min(ctx->combine_smem_limit, set_max_dyn_smem(ctx, combine_shared_kernel<float>));
+  ctx->combine_smem_limit = std::min(ctx->combine_smem_limit, set_max_dyn_smem(ctx, combine_shared_kernel<double>));
+  set_max_dyn_smem(ctx, gs_dot_shared_kernel<float, 24>);
+  set_max_dyn_smem(ctx, gs_dot_shared_kernel<float, 48>);
+  set_max_dyn_smem(ctx, gs_dot_shared_kernel<double, 24>);
+  set_max_dyn_smem(ctx, gs_dot_shared_kernel<double, 48>);
 }
 
 void cvt_128_to_64(gdr_ctx* ctx, long n, int cols, const c128* in, long ics, c64* out, long ocs) {

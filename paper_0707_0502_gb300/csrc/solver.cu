@@ -160,6 +160,15 @@ __global__ void related_guess_kernel(long n, int ns, int j, const c128* __restri
   }
 }
 
+// D_c += Cp_c[:, 0:ns] ((k+1) x ns per column, leading dimension k+1) for the active columns:
+// the projection's solution coefficients summed over the cycles of a Proj batch, so that
+// x_i += V_k d_i is applied once at the end instead of every cycle
+__global__ void dacc_kernel(int k1, int ns, const c128* __restrict__ Cp, long ccs, c128* D, const ColState* st) {
+  const int c = blockIdx.y;
+  if (!st[c].active) return;
+  for (int t = threadIdx.x; t < k1 * ns; t += blockDim.x) D[(long)c * k1 * ns + t] += Cp[c * ccs + t];
+}
+
 // X[:, q] += Y[:, q], q < cols
 __global__ void add_cols_kernel(long n, const c128* __restrict__ Y, long ldy, c128* X, long ldx) {
   const int q = blockIdx.y;
@@ -617,6 +626,13 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
   bd.m = k;
   c128* cproj = ctx->get<c128>("pj.cproj", (size_t)(k + 2) * ncol);
   c128* Cp = ctx->get<c128>("pj.Cp", (size_t)(k + 1) * (ns + 1) * ncol);
+  if (k > 0 && job.project && job.vdcs == 0) gs_dot_shared_reserve(ctx, n, ncol, k + 1);
+  // the projection's solution coefficients, summed over the cycles (applied to X at the end)
+  c128* Dacc = nullptr;
+  if (k > 0 && job.project) {
+    Dacc = ctx->get<c128>("pj.Dacc", (size_t)(k + 1) * ns * ncol);
+    GDR_CUDA(cudaMemsetAsync(Dacc, 0, sizeof(c128) * (k + 1) * ns * ncol, ctx->stream));
+  }
   c128* pops = nullptr;  // the projection's solution operators, formed once for all cycles
   if (k > 0 && job.project && !job.eigsel) {
     pops = ctx->get<c128>("pj.ops", (size_t)(k + 1) * (k + 1) * (ns + 1) * ncol);
@@ -654,9 +670,12 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
       gs_dot<R>(ctx, bd, k + 1, r, ldr, cproj, false);
       dense_projection(ctx, ncol, k, ns, job.Hk, cproj, b.sigma, sh.beta, sh.sact, sh.gamma, Cp, (long)(k + 1) * (ns + 1),
                        pops, b.st, job.hkcs, job.dpp, job.eigsel);
-      // x_i += V_k d_i, r -= V_{k+1} (Hbar_k - sigma_1 Ibar) d_1
-      combine<R>(ctx, n, ncol, bd.V, bd.ldv, job.vdcs, k + 1, Cp, k + 1, (long)(k + 1) * (ns + 1), 0, ns, 2, job.X,
-                 job.ldx, job.xcs, r, ldr, b.st, b.nvec, job.dpp, col_len(b), basis_len(bd));
+      // r -= V_{k+1} (Hbar_k - sigma_1 Ibar) d_1 now; x_i += V_k d_i summed over the cycles
+      const long pcs = (long)(k + 1) * (ns + 1);
+      dacc_kernel<<<dim3(1, (unsigned)ncol), 128, 0, ctx->stream>>>(k + 1, ns, Cp, pcs, Dacc, b.st);
+      GDR_LAUNCHED(ctx);
+      combine<R>(ctx, n, ncol, bd.V, bd.ldv, job.vdcs, k + 1, Cp + (long)ns * (k + 1), k + 1, pcs, 0, 0, 2,
+                 nullptr, 0, 0, r, ldr, b.st, b.nvec, job.dpp, col_len(b), basis_len(bd));
     }
     // step 5: one GMRES(m_p)-Sh cycle on r
     start_cycle<R>(ctx, b, r, ldr);
@@ -696,6 +715,9 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
       break;
     }
   }
+  if (Dacc)  // x_i += V_k (sum of the cycles' d_i), every column (zero where it never ran)
+    combine<R>(ctx, n, ncol, bd.V, bd.ldv, job.vdcs, k + 1, Dacc, k + 1, (long)(k + 1) * ns, 0, ns, 0, job.X,
+               job.ldx, job.xcs, nullptr, 0, nullptr, b.nvec, job.dpp, col_len(b), basis_len(bd));
   res.gamma.resize((size_t)ncol * ns);
   GDR_CUDA(cudaMemcpyAsync(res.gamma.data(), sh.gamma, sizeof(c128) * ncol * ns, cudaMemcpyDeviceToHost, ctx->stream));
   stream_sync(ctx);
@@ -745,9 +767,12 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
   const int m = p.m, k = p.k, mp = p.m_proj > 0 ? p.m_proj : p.m - p.k;
   // refinement cycles: on short vectors (latency-bound steps) longer than the Proj stage's,
   // fewer restarts of the per-pair solves (measured: 8^4 14.0 -> 13.4 ms, the CSR batch
-  // 611 -> 592 ms); on long vectors the Gram-Schmidt bytes grow with the cycle (16^4:
-  // 480 -> 582 ms), so the Proj stage's length
-  const int mr = p.m_refine > 0 ? p.m_refine : (A->n <= (1L << 17) ? std::min(m, mp + (m - mp) / 2) : mp);
+  // 611 -> 592 ms); on long vectors the Gram-Schmidt bytes of a step grow with its index
+  // while the deflated projection keeps restarts cheap, so short cycles (measured on
+  // GB300: 24^3x32 refinement 7.0 s at 40, 4.4 s at 20, 3.9 s at 12; 16^4 189 ms at 30,
+  // 133 ms at 12)
+  const int mr = p.m_refine > 0 ? p.m_refine
+                                : (A->n <= (1L << 17) ? std::min(m, mp + (m - mp) / 2) : std::min(mp, 12));
   const long ld = pad_ld(n);
   gdr_status status = GDR_OK;
   auto worst = [&](gdr_status s) {
@@ -1327,9 +1352,12 @@ gdr_status solve_batch_pipeline(gdr_ctx* ctx, const gdr_op* A, int ns, const std
   const int m = p.m, k = p.k, mp = p.m_proj > 0 ? p.m_proj : p.m - p.k;
   // refinement cycles: on short vectors (latency-bound steps) longer than the Proj stage's,
   // fewer restarts of the per-pair solves (measured: 8^4 14.0 -> 13.4 ms, the CSR batch
-  // 611 -> 592 ms); on long vectors the Gram-Schmidt bytes grow with the cycle (16^4:
-  // 480 -> 582 ms), so the Proj stage's length
-  const int mr = p.m_refine > 0 ? p.m_refine : (A->n <= (1L << 17) ? std::min(m, mp + (m - mp) / 2) : mp);
+  // 611 -> 592 ms); on long vectors the Gram-Schmidt bytes of a step grow with its index
+  // while the deflated projection keeps restarts cheap, so short cycles (measured on
+  // GB300: 24^3x32 refinement 7.0 s at 40, 4.4 s at 20, 3.9 s at 12; 16^4 189 ms at 30,
+  // 133 ms at 12)
+  const int mr = p.m_refine > 0 ? p.m_refine
+                                : (A->n <= (1L << 17) ? std::min(m, mp + (m - mp) / 2) : std::min(mp, 12));
   const int npair = np * ns;
   GDR_CUDA(cudaMemsetAsync(X, 0, sizeof(c128) * ld * npair, ctx->stream));
   // per-pair lengths (pair q = problem q / ns, shift q % ns)
