@@ -43,7 +43,7 @@ UNIT = "solutions/s"
 # columns), as counted by the library's FP64 path, which repeats the oracle's
 # algorithm cycle for cycle.  Used only to scale the oracle's timed Arnoldi steps
 # (bounded samples) to a whole solve.
-FP64_SOLVE_MVPS = {3: 2400, 4: 4520}
+FP64_SOLVE_MVPS = {3: 2580, 4: 4360}
 
 # DRAM traffic of the dominant kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum over the algorithmic bytes of the same launch), valid for the
