@@ -87,6 +87,9 @@ typedef enum { GDR_LINK_C128 = 0, GDR_LINK_C64 = 1, GDR_LINK_BF16 = 2 } gdr_link
                                      cycles of the Proj and refinement stages (default: FP32 Givens QR with
                                      one FP64-residual refinement step, the FP64 form when that step's
                                      correction exceeds 1e-4 of the solution) */
+#define GDR_FLAG_NO_TENSOR_CORES 8192u /* MIXED: the projection dot of the Proj and refinement batches over
+                                     the shared kept basis on the CUDA cores (FP32) instead of the tensor
+                                     cores (TF32, tcgen05) */
 #define GDR_FLAG_AUTOTUNE   128u  /* before the first cycle, run gdr_autotune for the matvec and Arnoldi
                                      form of each stage whose (precision, columns, m) the operator has
                                      no tuned shape for yet (the tuning time is part of the solve) */
@@ -390,6 +393,19 @@ gdr_status gdr_dense_restart(gdr_ctx *ctx, gdr_prec prec, int m, int k, const do
  * X[:, i] += V C[:, nout + i] for i < nx (X c128 n x nx). */
 gdr_status gdr_basis_update(gdr_ctx *ctx, gdr_prec prec, long n, int nv, void *V, const double *C, int nout,
                             int nx, double *X);
+
+/* Projection dot (Sec. 2.3, GMRES-Proj-Sh step 4: c = V_{k+1}^H r for every
+ * column): C[c*nv + i] = v_i^H r_c for the nv vectors of one basis V and ncol
+ * columns R.  V: n x nv (`prec`: complex64 for GDR_PREC_MIXED, complex128 for
+ * GDR_PREC_FP64), column-major with stride n; R: n x ncol of the same type,
+ * column stride ldr >= n; C: c128 nv x ncol (all device).  nv <= GDR_MAX_M + 1.
+ * The complex64 form with ncol >= 16 runs on the tensor cores (TF32 inputs,
+ * FP32 accumulation: each dot to about 1e-3 of ||v_i|| ||r_c||) when R and V
+ * start on 16-byte boundaries, n and ldr are even and nv <= 128, unless flags has
+ * GDR_FLAG_NO_TENSOR_CORES; otherwise the CUDA cores form it (FP32 products,
+ * FP64 sums).  GDR_ETIMEOUT if a tensor-core wait gave up (C unspecified). */
+gdr_status gdr_basis_dot(gdr_ctx *ctx, gdr_prec prec, long n, int nv, const void *V, int ncol, const void *R,
+                         long ldr, double *C, unsigned flags);
 
 #ifdef __cplusplus
 }

@@ -29,7 +29,8 @@ GDR_MAX_M = 96
 GDR_NOALLOC_MAX_M, GDR_NOALLOC_MAX_NS = 96, 16
 (GDR_FLAG_HOST_PTRS, GDR_FLAG_NO_GRAPH, GDR_FLAG_SEQUENTIAL, GDR_FLAG_NO_PROJ, GDR_FLAG_NO_REFINE, GDR_FLAG_NO_SWEEP,
  GDR_FLAG_FP64_EIG, GDR_FLAG_AUTOTUNE, GDR_FLAG_RELATED_RHS, GDR_FLAG_EIG_SELECT,
- GDR_FLAG_FOM, GDR_FLAG_CGS2, GDR_FLAG_FP64_DENSE) = 1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096
+ GDR_FLAG_FOM, GDR_FLAG_CGS2, GDR_FLAG_FP64_DENSE, GDR_FLAG_NO_TENSOR_CORES) = (
+    1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 8192)
 
 
 class gdr_params(ctypes.Structure):
@@ -122,6 +123,8 @@ _SIGS = {
     "gdr_dense_restart": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P]),
     "gdr_basis_update": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_long, ctypes.c_int, _P, _P, ctypes.c_int,
                                         ctypes.c_int, _P]),
+    "gdr_basis_dot": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_long, ctypes.c_int, _P, ctypes.c_int, _P,
+                                     ctypes.c_long, _P, ctypes.c_uint]),
 }
 
 _lib = None
@@ -400,6 +403,11 @@ def gdr_barrier_selftest(ctx, rounds, phantom):
 def gdr_basis_update(ctx, prec, n, nv, V, C, nout, nx, X):
     _check(lib().gdr_basis_update(ctx, int(prec), int(n), int(nv), _ptr(V), _ptr(C), int(nout), int(nx), _ptr(X)),
            ctx)
+
+
+def gdr_basis_dot(ctx, prec, n, nv, V, ncol, R, ldr, C, flags=0):
+    _check(lib().gdr_basis_dot(ctx, int(prec), int(n), int(nv), _ptr(V), int(ncol), _ptr(R), int(ldr), _ptr(C),
+                               int(flags)), ctx)
 
 
 # ------------------------------------------------------------- convenience

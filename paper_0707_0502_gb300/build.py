@@ -21,7 +21,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libgdr.so")
-SOURCES = ["ops.cu", "krylov.cu", "sweep.cu", "dense.cu", "solver.cu", "capi.cu", "noalloc.cu", "tune.cu"]
+SOURCES = ["ops.cu", "krylov.cu", "sweep.cu", "dense.cu", "solver.cu", "capi.cu", "noalloc.cu", "tune.cu",
+           "tc_proj.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC] + ARCH

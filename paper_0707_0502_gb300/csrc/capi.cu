@@ -29,7 +29,21 @@ gdr_status guarded(gdr_ctx* ctx, F&& f) {
   }
 }
 
-void check_params(const gdr_params& p) {
+// a tensor-core wait that gave up during the call (the kernel then returned without
+// its result): report it as GDR_ETIMEOUT and clear the flag for the next call
+void tc_check(gdr_ctx* ctx) {
+  if (!ctx->tc_err) return;
+  int e = 0;
+  GDR_CUDA(cudaMemcpy(&e, ctx->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) {
+    GDR_CUDA(cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), ctx->stream));
+    GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+    throw gdr_error(GDR_ETIMEOUT, "tensor-core projection: a wait gave up");
+  }
+}
+
+void check_params(gdr_ctx* ctx, const gdr_params& p) {
+  ctx->tc_proj = !(p.flags & GDR_FLAG_NO_TENSOR_CORES);
   GDR_REQUIRE(p.m >= 2 && p.m <= GDR_MAX_M, "m must be in [2, GDR_MAX_M]");
   GDR_REQUIRE(p.k >= 0 && p.k < p.m, "k must satisfy 0 <= k < m");
   GDR_REQUIRE(p.m_proj >= 0 && p.m_proj <= GDR_MAX_M, "m_proj must be in [0, GDR_MAX_M]");
@@ -128,6 +142,7 @@ gdr_status gdr_create(gdr_ctx** out, int device, void* cuda_stream) {
     dense_init(ctx);
     krylov_init(ctx);
     sweep_init(ctx);
+    tc_proj_init(ctx);
   });
   if (st != GDR_OK) {
     delete ctx;
@@ -382,7 +397,7 @@ gdr_status gdr_solve_multishift(gdr_ctx* ctx, const gdr_op* A, int ns, const dou
     GDR_REQUIRE(params && sigma && B && X, "null argument");
     GDR_REQUIRE(ns >= 1 && nrhs >= 1, "ns and nrhs must be >= 1");
     const gdr_params& p = *params;
-    check_params(p);
+    check_params(ctx, p);
     GDR_CUDA(cudaSetDevice(ctx->device));
     const auto t0 = std::chrono::steady_clock::now();
     const long launches0 = ctx->launches;
@@ -408,6 +423,7 @@ gdr_status gdr_solve_multishift(gdr_ctx* ctx, const gdr_op* A, int ns, const dou
       result = solve_pipeline<double>(ctx, A, sig, nrhs, Bi, ld, Xi, ld, pr, defl_out, rep);
     stage_out(ctx, A, ns * nrhs, Xi, ld, X, kout);
     GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+    tc_check(ctx);
     rep.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     rep.kernel_launches = ctx->launches - launches0;
   });
@@ -424,7 +440,7 @@ gdr_status gdr_solve_batch(gdr_ctx* ctx, const gdr_op* A, int ns, const double* 
     GDR_REQUIRE(A->kind == OP_CSR_BATCH, "gdr_solve_batch needs an operator from gdr_op_csr_batch");
     GDR_REQUIRE(params && sigma && B && X && ns >= 1, "bad gdr_solve_batch arguments");
     const gdr_params& p = *params;
-    check_params(p);
+    check_params(ctx, p);
     GDR_CUDA(cudaSetDevice(ctx->device));
     const auto t0 = std::chrono::steady_clock::now();
     const long launches0 = ctx->launches;
@@ -463,6 +479,7 @@ gdr_status gdr_solve_batch(gdr_ctx* ctx, const gdr_op* A, int ns, const double* 
       off += nq;
     }
     GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+    tc_check(ctx);
     rep.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     rep.kernel_launches = ctx->launches - launches0;
   });
@@ -481,7 +498,7 @@ gdr_status gdr_solve_proj(gdr_ctx* ctx, const gdr_op* A, const gdr_defl* defl, i
     GDR_REQUIRE(defl->n == A->n, "deflation space size differs from the operator");
     GDR_REQUIRE(defl->wilson_V == (A->kind == OP_WILSON ? A->V : 0), "deflation space from another operator kind");
     const gdr_params& p = *params;
-    check_params(p);
+    check_params(ctx, p);
     GDR_CUDA(cudaSetDevice(ctx->device));
     const auto t0 = std::chrono::steady_clock::now();
     const long launches0 = ctx->launches;
@@ -543,6 +560,7 @@ gdr_status gdr_solve_proj(gdr_ctx* ctx, const gdr_op* A, const gdr_defl* defl, i
       run(double{});
     stage_out(ctx, A, ns * nrhs, Xi, ld, X, kout);
     GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+    tc_check(ctx);
     rep.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     rep.kernel_launches = ctx->launches - launches0;
   });
@@ -899,6 +917,53 @@ gdr_status gdr_basis_update(gdr_ctx* ctx, gdr_prec prec, long n, int nv, void* V
     else
       combine<float>(ctx, n, 1, static_cast<c64*>(V), n, 0, nv, reinterpret_cast<const c128*>(C), nv, 0, nout, nx, 0,
                      reinterpret_cast<c128*>(X), n, 0, nullptr, 0, nullptr);
+  });
+}
+
+gdr_status gdr_basis_dot(gdr_ctx* ctx, gdr_prec prec, long n, int nv, const void* V, int ncol, const void* R, long ldr,
+                         double* C, unsigned flags) {
+  if (!ctx) return GDR_EINVAL;
+  return guarded(ctx, [&] {
+    GDR_REQUIRE(n > 0 && nv >= 1 && nv <= GDR_MAX_M + 1 && ncol >= 1 && ldr >= n, "bad sizes");
+    GDR_REQUIRE(V && R && C, "null argument");
+    GDR_CUDA(cudaSetDevice(ctx->device));
+    ctx->tc_proj = !(flags & GDR_FLAG_NO_TENSOR_CORES);
+    auto run = [&](auto zero) {
+      using R_ = decltype(zero);
+      Batch<R_> b;
+      b.ncol = ncol;
+      b.n = n;
+      b.m = nv;
+      b.V = static_cast<cx<R_>*>(const_cast<void*>(V));
+      b.ldv = n;
+      b.vcs = 0;
+      const long units = (n * (long)sizeof(cx<R_>) + 15) / 16;
+      b.nblk = (int)std::max<long>(1, std::min<long>((units + 255) / 256, 3L * ctx->num_sms));
+      b.pstride = (long)(b.nblk + 64) * (nv + 3);
+      b.part = ctx->get<c128>("bdot.part", (size_t)b.pstride * ncol + 64);
+      b.cnt = ctx->get<unsigned>("bdot.cnt", (size_t)4 * ncol);
+      b.gcnt = ctx->get<unsigned>("bdot.gcnt", (size_t)64 * ncol);
+      GDR_CUDA(cudaMemsetAsync(b.cnt, 0, 4 * sizeof(unsigned) * ncol, ctx->stream));
+      GDR_CUDA(cudaMemsetAsync(b.gcnt, 0, 64 * sizeof(unsigned) * ncol, ctx->stream));
+      b.st = ctx->get<ColState>("bdot.st", (size_t)ncol);
+      ColState s0 = {};
+      s0.run = 1;
+      s0.active = 1;
+      s0.m_eff = nv;
+      std::vector<ColState> sv(ncol, s0);
+      GDR_CUDA(cudaMemcpyAsync(b.st, sv.data(), sizeof(ColState) * ncol, cudaMemcpyHostToDevice, ctx->stream));
+      c128* h = ctx->get<c128>("bdot.h", (size_t)(nv + 2) * ncol);
+      gs_dot_shared_reserve(ctx, n, ncol, nv);
+      gs_dot<R_>(ctx, b, nv, static_cast<const cx<R_>*>(R), ldr, h, false, nullptr);
+      GDR_CUDA(cudaMemcpy2DAsync(C, sizeof(c128) * nv, h, sizeof(c128) * (nv + 2), sizeof(c128) * nv, ncol,
+                                 cudaMemcpyDeviceToDevice, ctx->stream));
+      GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+      tc_check(ctx);
+    };
+    if (prec == GDR_PREC_FP64)
+      run(double{});
+    else
+      run(float{});
   });
 }
 

@@ -142,6 +142,16 @@ void combine(gdr_ctx* ctx, long n, int ncol, cx<R>* V, long ldv, long vcs, int n
 
 void krylov_init(gdr_ctx* ctx);
 
+// tc_proj.cu: the projection dot C = V^H R over a basis shared by many complex64 columns on
+// the tensor cores (TF32 inputs, FP32 accumulation): partials per (K range, column, vector)
+// into part; nsplit receives the number of K ranges; prof_bytes is the algorithmic byte count
+// the profiler records for the launch.  False (nothing launched) when it does not apply
+// (nv > 128, no tensor-map encoder, V or R not on 16-byte boundaries or an odd stride).
+void tc_proj_init(gdr_ctx* ctx);
+int tc_proj_splits(gdr_ctx* ctx, long n, int ncol);
+bool tc_proj_dot(gdr_ctx* ctx, long n, const c64* V, long ldv, int nv, const c64* R, long ldr, int ncol, c128* part,
+                 int* err, int& nsplit, double prof_bytes);
+
 // conversions / small vector ops (FP64 <-> complex64)
 void cvt_128_to_64(gdr_ctx* ctx, long n, int cols, const c128* in, long ics, c64* out, long ocs);
 void cvt_64_to_128(gdr_ctx* ctx, long n, int cols, const c64* in, long ics, c128* out, long ocs);

@@ -1103,8 +1103,17 @@ static bool dot_shared_applies(const Batch<R>& b, int nv, bool wnorm, const cx<R
 }
 
 void gs_dot_shared_reserve(gdr_ctx* ctx, long n, int ncol, int nv) {
-  ctx->get<c128>("dsh.part", (size_t)dot_shared_slots(ctx, n, ncol) * ncol * nv + 64);
+  const int S = std::max(dot_shared_slots(ctx, n, ncol), tc_proj_splits(ctx, n, ncol));
+  ctx->get<c128>("dsh.part", (size_t)S * ncol * nv + 64);
+  if (!ctx->tc_err) {
+    ctx->tc_err = ctx->get<int>("tc.err", 4);
+    GDR_CUDA(cudaMemsetAsync(ctx->tc_err, 0, sizeof(int) * 4, ctx->stream));
+  }
 }
+
+// the tensor-core form for complex64 columns: from this many columns on (fewer leave the
+// CUDA-core kernel memory-bound anyway)
+constexpr int TC_MIN_COLS = 16;
 
 template <typename R, int NVM>
 static void gs_dot_shared_launch(gdr_ctx* ctx, const Batch<R>& b, int nv, const cx<R>* w, long wcs, c128* h_out) {
@@ -1127,6 +1136,21 @@ static void gs_dot_shared_launch(gdr_ctx* ctx, const Batch<R>& b, int nv, const 
 template <typename R>
 void gs_dot(gdr_ctx* ctx, const Batch<R>& b, int nv, const cx<R>* w, long wcs, c128* h_out, bool wnorm,
             const cx<R>* wprev) {
+  if (std::is_same<R, float>::value && b.vcs == 0 && b.ncol >= TC_MIN_COLS && b.nvec == nullptr && !wnorm &&
+      !wprev && ctx->tc_ok && ctx->tc_proj && ctx->tc_err) {  // tensor cores
+    const int S0 = tc_proj_splits(ctx, b.n, b.ncol);
+    c128* part = ctx->get<c128>("dsh.part", (size_t)S0 * b.ncol * nv + 64);
+    int S = 0;
+    const double bytes = ctx->profile ? ((double)nv * b.n + col_len(b)) * sizeof(cx<R>) * run_share(ctx, b) : 0.0;
+    if (tc_proj_dot(ctx, b.n, reinterpret_cast<const c64*>(b.V), b.ldv, nv, reinterpret_cast<const c64*>(w), wcs,
+                    b.ncol, part, ctx->tc_err, S, bytes)) {
+      const int tot = b.ncol * nv;
+      gs_dot_shared_sum_kernel<<<(tot + 255) / 256, 256, 0, ctx->stream>>>(S, b.ncol, nv, part, h_out, b.m + 2,
+                                                                           b.st);
+      GDR_LAUNCHED(ctx);
+      return;
+    }
+  }
   if (dot_shared_applies(b, nv, wnorm, wprev)) {  // one basis for many columns: read it once
     if (nv <= 24) gs_dot_shared_launch<R, 24>(ctx, b, nv, w, wcs, h_out);
     else gs_dot_shared_launch<R, 48>(ctx, b, nv, w, wcs, h_out);

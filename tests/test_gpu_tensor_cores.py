@@ -1,0 +1,112 @@
+"""The projection dot C = V^H R on the tensor cores (runs on a GB300; -m gpu).
+
+gdr_basis_dot forms c = V_{k+1}^H r of GMRES-Proj-Sh step 4 (Sec. 2.3) for many
+columns at once.  For complex64 inputs with 16 or more columns it runs on the
+tensor cores: TF32 inputs (10 fraction bits) and FP32 accumulation.  Each dot
+is then bounded, element by element, by
+
+    |C - C_exact| <= (2^-9 + 2n 2^-24) * sum_k |v_k| |r_k|
+
+(two input roundings of at most 2^-10 relative each, and a worst-case FP32
+accumulation over the 2n real products; the sum is over the real interleaved
+components, the same for the real and the imaginary part).  The CUDA-core
+form (FP32 products, FP64 sums) is held to 2^-22 of the same sum.  C_exact is
+numpy's FP64 product of the same complex64 inputs.
+
+Cases span ragged K stages (2n not a multiple of 32), one and two column tiles
+(ncol up to 200: 128 columns per tile), basis sizes from 1 to 97 (the MMA has
+128 rows, zero-filled above nv), a padded column stride, and the fallbacks (odd n, fewer than 16
+columns, the flag) that must give the CUDA-core result.  The kernel that ran is
+read from the library's profiler."""
+import numpy as np
+import pytest
+
+from tests.gpu_util import dev
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no GPU", allow_module_level=True)
+
+import paper_0707_0502_gb300 as g  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__
+    __graft_entry__.build()
+    c = g.gdr_create(0)
+    yield c
+    g.gdr_destroy(c)
+
+
+def c64(rng, *shape):
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
+
+
+def run_dot(ctx, n, nv, ncol, ldr, seed, flags=0):
+    rng = np.random.default_rng(seed)
+    V = c64(rng, nv, n)             # row i = basis vector v_i (column-major n x nv)
+    V /= np.linalg.norm(V, axis=1, keepdims=True)
+    Rm = c64(rng, ncol, ldr)        # row c = column r_c, stride ldr
+    Rm[:, :n] *= np.exp(rng.uniform(-3, 3, size=(ncol, 1))).astype(np.float32)  # column scales over ~6 decades
+    Cd = torch.zeros((ncol, nv), dtype=torch.complex128, device="cuda")
+    g.gdr_profile(ctx, True)
+    g.gdr_basis_dot(ctx, g.GDR_PREC_MIXED, n, nv, dev(V), ncol, dev(Rm), ldr, Cd, flags)
+    prof = g.gdr_profile_report(ctx)
+    g.gdr_profile(ctx, False)
+    R = Rm[:, :n]
+    exact = np.conj(V.astype(np.complex128)) @ R.astype(np.complex128).T        # nv x ncol
+    Vf = np.abs(V.view(np.float32)).astype(np.float64)                            # nv x 2n
+    Rf = np.abs(R.view(np.float32)).astype(np.float64)                            # ncol x 2n
+    S = Vf @ Rf.T
+    return Cd.cpu().numpy().T, exact, S, prof
+
+
+def tc_ran(prof):
+    return prof.get("tc_proj_dot_c64", {}).get("launches", 0) > 0
+
+
+@pytest.mark.parametrize("n,nv,ncol,ldr", [
+    (3000, 21, 16, 3000),      # 2n = 6000: a ragged last K stage
+    (5000, 21, 40, 5006),      # padded column stride
+    (2048, 64, 130, 2048),     # two column tiles (65 + 65)
+    (4000, 97, 120, 4000),     # the largest basis (m + 1 = 97 of the MMA's 128 rows)
+    (1000, 1, 200, 1000),      # one basis vector, two tiles of 100
+    (262144, 21, 120, 262144), # a long vector split over many CTAs
+])
+def test_tensor_core_dot(ctx, n, nv, ncol, ldr):
+    C, exact, S, prof = run_dot(ctx, n, nv, ncol, ldr, seed=n + nv + ncol)
+    assert tc_ran(prof), prof
+    bound = (2.0 ** -9 + 2 * n * 2.0 ** -24) * S
+    assert np.all(np.abs(C.real - exact.real) <= bound)
+    assert np.all(np.abs(C.imag - exact.imag) <= bound)
+    # and the rounding is TF32's, not lost terms: typical errors far below the bound
+    assert np.median(np.abs(C - exact) / S) < 2.0 ** -10
+
+
+@pytest.mark.parametrize("n,nv,ncol,ldr,flags", [
+    (3001, 21, 40, 3001, 0),                            # odd n: rows not on 16-byte boundaries
+    (3000, 21, 15, 3000, 0),                            # too few columns
+    (3000, 21, 40, 3000, 8192),                         # GDR_FLAG_NO_TENSOR_CORES
+])
+def test_cuda_core_fallback(ctx, n, nv, ncol, ldr, flags):
+    assert flags in (0, g.GDR_FLAG_NO_TENSOR_CORES)
+    C, exact, S, prof = run_dot(ctx, n, nv, ncol, ldr, seed=7 * n + nv, flags=flags)
+    assert not tc_ran(prof), prof
+    bound = 2.0 ** -22 * S
+    assert np.all(np.abs(C.real - exact.real) <= bound)
+    assert np.all(np.abs(C.imag - exact.imag) <= bound)
+
+
+def test_fp64_dot(ctx):
+    rng = np.random.default_rng(3)
+    n, nv, ncol = 4000, 30, 24
+    V = rng.standard_normal((nv, n)) + 1j * rng.standard_normal((nv, n))
+    R = rng.standard_normal((ncol, n)) + 1j * rng.standard_normal((ncol, n))
+    Cd = torch.zeros((ncol, nv), dtype=torch.complex128, device="cuda")
+    g.gdr_basis_dot(ctx, g.GDR_PREC_FP64, n, nv, dev(V), ncol, dev(R), n, Cd)
+    exact = np.conj(V) @ R.T
+    S = np.abs(V) @ np.abs(R).T
+    assert np.all(np.abs(Cd.cpu().numpy().T - exact) <= 1e-13 * S)
