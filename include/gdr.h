@@ -119,7 +119,7 @@ typedef struct {
   int k_select;       /* GDR_FLAG_EIG_SELECT: approximate eigenvectors projected over (1..k; <= 0: k) */
   int m_refine;       /* cycle length of the refinement / cleanup solves (not in the paper); <= 0:
                          min(m, m_p + (m - m_p) / 2) for vectors of at most 2^17 elements, else
-                         min(m_p, 12) */
+                         min(m_p, 8) */
   double refine_rank_tol; /* MIXED, shift-shared refinement (not in the paper; off when <= 0, the
                          default): a complex64 refinement pass may refine the residuals of one
                          right-hand side's shifts over a few orthonormal directions of their span
@@ -399,13 +399,29 @@ gdr_status gdr_basis_update(gdr_ctx *ctx, gdr_prec prec, long n, int nv, void *V
  * columns R.  V: n x nv (`prec`: complex64 for GDR_PREC_MIXED, complex128 for
  * GDR_PREC_FP64), column-major with stride n; R: n x ncol of the same type,
  * column stride ldr >= n; C: c128 nv x ncol (all device).  nv <= GDR_MAX_M + 1.
- * The complex64 form with ncol >= 16 runs on the tensor cores (TF32 inputs,
+ * The complex64 form with ncol >= 8 runs on the tensor cores (TF32 inputs,
  * FP32 accumulation: each dot to about 1e-3 of ||v_i|| ||r_c||) when R and V
  * start on 16-byte boundaries, n and ldr are even and nv <= 128, unless flags has
  * GDR_FLAG_NO_TENSOR_CORES; otherwise the CUDA cores form it (FP32 products,
  * FP64 sums).  GDR_ETIMEOUT if a tensor-core wait gave up (C unspecified). */
 gdr_status gdr_basis_dot(gdr_ctx *ctx, gdr_prec prec, long n, int nv, const void *V, int ncol, const void *R,
                          long ldr, double *C, unsigned flags);
+
+/* Residual update of the projection (Sec. 2.3, GMRES-Proj-Sh step 4:
+ * r_c <- r_c - V_{k+1} (Hbar_k - sigma_1 Ibar) d_c for every column c, with
+ * T[:, c] = -(Hbar_k - sigma_1 Ibar) d_c formed by the caller):
+ * R[:, c] += V T[:, c] for the nv vectors of one basis V and ncol columns.
+ * V: n x nv (`prec`: complex64 for GDR_PREC_MIXED, complex128 for
+ * GDR_PREC_FP64), column-major with stride n; T: c128 nv x ncol, column c at
+ * T + c*nv; R: n x ncol of V's type, column stride ldr >= n (all device).
+ * nv <= GDR_MAX_M + 1.  The complex64 form with ncol >= 8 and nv <= 48 runs
+ * on the tensor cores with V and T split into two TF32 parts each (three
+ * products, FP32 accumulation: the accuracy of FP32 arithmetic), unless flags
+ * has GDR_FLAG_NO_TENSOR_CORES; otherwise the CUDA cores form it in FP32
+ * (complex64) or FP64.  GDR_ETIMEOUT if a tensor-core wait gave up (R then
+ * unspecified). */
+gdr_status gdr_basis_residual_update(gdr_ctx *ctx, gdr_prec prec, long n, int nv, const void *V, int ncol,
+                                     const double *T, void *R, long ldr, unsigned flags);
 
 #ifdef __cplusplus
 }

@@ -125,6 +125,8 @@ _SIGS = {
                                         ctypes.c_int, _P]),
     "gdr_basis_dot": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_long, ctypes.c_int, _P, ctypes.c_int, _P,
                                      ctypes.c_long, _P, ctypes.c_uint]),
+    "gdr_basis_residual_update": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_long, ctypes.c_int, _P, ctypes.c_int, _P,
+                                                 _P, ctypes.c_long, ctypes.c_uint]),
 }
 
 _lib = None
@@ -408,6 +410,11 @@ def gdr_basis_update(ctx, prec, n, nv, V, C, nout, nx, X):
 def gdr_basis_dot(ctx, prec, n, nv, V, ncol, R, ldr, C, flags=0):
     _check(lib().gdr_basis_dot(ctx, int(prec), int(n), int(nv), _ptr(V), int(ncol), _ptr(R), int(ldr), _ptr(C),
                                int(flags)), ctx)
+
+
+def gdr_basis_residual_update(ctx, prec, n, nv, V, ncol, T, R, ldr, flags=0):
+    _check(lib().gdr_basis_residual_update(ctx, int(prec), int(n), int(nv), _ptr(V), int(ncol), _ptr(T), _ptr(R),
+                                           int(ldr), int(flags)), ctx)
 
 
 # ------------------------------------------------------------- convenience

@@ -967,4 +967,31 @@ gdr_status gdr_basis_dot(gdr_ctx* ctx, gdr_prec prec, long n, int nv, const void
   });
 }
 
+gdr_status gdr_basis_residual_update(gdr_ctx* ctx, gdr_prec prec, long n, int nv, const void* V, int ncol,
+                                     const double* T, void* R, long ldr, unsigned flags) {
+  if (!ctx) return GDR_EINVAL;
+  return guarded(ctx, [&] {
+    GDR_REQUIRE(n > 0 && nv >= 1 && nv <= GDR_MAX_M + 1 && ncol >= 1 && ldr >= n, "bad sizes");
+    GDR_REQUIRE(V && T && R, "null argument");
+    GDR_CUDA(cudaSetDevice(ctx->device));
+    ctx->tc_proj = !(flags & GDR_FLAG_NO_TENSOR_CORES);
+    ColState* st = ctx->get<ColState>("bres.st", (size_t)ncol);
+    ColState s0 = {};
+    s0.run = 1;
+    s0.active = 1;
+    std::vector<ColState> sv(ncol, s0);
+    GDR_CUDA(cudaMemcpyAsync(st, sv.data(), sizeof(ColState) * ncol, cudaMemcpyHostToDevice, ctx->stream));
+    gs_dot_shared_reserve(ctx, n, ncol, nv);
+    const c128* Tc = reinterpret_cast<const c128*>(T);
+    if (prec == GDR_PREC_FP64)
+      combine<double>(ctx, n, ncol, static_cast<c128*>(const_cast<void*>(V)), n, 0, nv, Tc, nv, nv, 0, 0, 2, nullptr,
+                      0, 0, static_cast<c128*>(R), ldr, st);
+    else
+      combine<float>(ctx, n, ncol, static_cast<c64*>(const_cast<void*>(V)), n, 0, nv, Tc, nv, nv, 0, 0, 2, nullptr, 0,
+                     0, static_cast<c64*>(R), ldr, st);
+    GDR_CUDA(cudaStreamSynchronize(ctx->stream));
+    tc_check(ctx);
+  });
+}
+
 }  // extern "C"

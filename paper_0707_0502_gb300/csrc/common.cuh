@@ -93,6 +93,7 @@ struct gdr_ctx {
   size_t dense_smem_limit = 0;    // dynamic shared memory available to the dense kernels
   size_t combine_smem_limit = 0;  // ... and to the basis-combination kernel
   bool tc_ok = false;              // tensor-core projection dot usable (tensor-map encoder, shared memory)
+  bool tc_update_ok = false;     // the residual-update kernel fits this device
   bool tc_proj = true;             // use it in this solve (GDR_FLAG_NO_TENSOR_CORES clears it)
   int* tc_err = nullptr;           // set by the tensor-core kernel when a wait timed out
   int sweep_blocks[3] = {0, 0, 0};  // co-resident blocks per SM of the sweep kernel (c64, bf16 links, c128)

@@ -129,7 +129,8 @@ void dots128(gdr_ctx* ctx, long n, int cols, const c128* u, long ucs, const c128
 
 // Basis combination (restart + multi-shift update, Proj updates):
 //   V_c[:, 0:nout] <- V_c[:, 0:nv] C_c[:, 0:nout]            (in place)
-//   X_c[:, i]      += V_c[:, 0:nv] C_c[:, nout+i], i < nx    (X is FP64)
+//   X_c[:, i]      += V_c[:, 0:nv] C_c[:, nout+i], i < nx    (X is FP64; with Xf, Xf_c[:, i]
+//                     is updated instead, in the vectors' precision, same strides; nout = 0)
 //   rmode 1: Rv_c = V_c C_c[:, nout+nx];  rmode 2: Rv_c += V_c C_c[:, nout+nx]
 // C_c is c128 nv x (nout+nx+(rmode?1:0)), column-major with leading dim ldc, column stride ccs.
 // vcs = 0 shares one basis between all columns.
@@ -138,7 +139,7 @@ template <typename R>
 // profiler's byte count (0: n per column; one basis when vcs = 0)
 void combine(gdr_ctx* ctx, long n, int ncol, cx<R>* V, long ldv, long vcs, int nv, const c128* C, int ldc, long ccs,
              int nout, int nx, int rmode, c128* X, long ldx, long xcs, cx<R>* Rv, long rcs, const ColState* st,
-             const int* nvec = nullptr, int vpp = 1, double lenh = 0, double vlenh = 0);
+             const int* nvec = nullptr, int vpp = 1, double lenh = 0, double vlenh = 0, cx<R>* Xf = nullptr);
 
 void krylov_init(gdr_ctx* ctx);
 
@@ -151,6 +152,12 @@ void tc_proj_init(gdr_ctx* ctx);
 int tc_proj_splits(gdr_ctx* ctx, long n, int ncol);
 bool tc_proj_dot(gdr_ctx* ctx, long n, const c64* V, long ldv, int nv, const c64* R, long ldr, int ncol, c128* part,
                  int* err, int& nsplit, double prof_bytes);
+// R += V T (rmode 2) or R = V T (rmode 1) for ncol complex64 columns over one basis V
+// (nv <= 48 vectors), T's column c at C + c * ccs, on the tensor cores with split TF32
+// (FP32-level accuracy); columns whose state is not active are left alone.  False
+// (nothing launched) when it does not apply.
+bool tc_proj_update(gdr_ctx* ctx, long n, const c64* V, long ldv, int nv, const c128* C, long ccs, int rmode, c64* R,
+                    long ldr, int ncol, const ColState* st, int* err, double prof_bytes);
 
 // conversions / small vector ops (FP64 <-> complex64)
 void cvt_128_to_64(gdr_ctx* ctx, long n, int cols, const c128* in, long ics, c64* out, long ocs);

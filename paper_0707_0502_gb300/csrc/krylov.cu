@@ -735,16 +735,30 @@ __global__ void __launch_bounds__(NT) norms2_kernel(long n, const T* __restrict_
   const int c = blockIdx.y;
   if (nvec) n = nvec[c];
   const T* xc = x + c * xcs;
-  cx<R> a[1] = {{0, 0}};
-  // FP64 per-thread accumulation for accuracy of ||b||
+  // FP64 per-thread accumulation.  Complex64 vectors carry 2^-24 relative precision, so
+  // their squares are summed in FP32 over groups of four elements (relative error
+  // <= 8 * 2^-24 per group) and only the group sums in FP64: the FP64 pipe, slow on this
+  // part, would otherwise bound the kernel.  FP64 vectors are summed in FP64 throughout.
   double s = 0;
-  for (long i = blockIdx.x * (long)NT + threadIdx.x; i < n; i += (long)gridDim.x * NT) {
+  long i = blockIdx.x * (long)NT + threadIdx.x;
+  const long stride = (long)gridDim.x * NT;
+  if (sizeof(R) == 4) {
+    for (; i + 3 * stride < n; i += 4 * stride) {
+      T v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = xc[i + q * stride];
+      float f = 0.f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) f = fmaf((float)v[q].x, (float)v[q].x, fmaf((float)v[q].y, (float)v[q].y, f));
+      s += (double)f;
+    }
+  }
+  for (; i < n; i += stride) {
     const T v = xc[i];
     s += (double)v.x * v.x + (double)v.y * v.y;
   }
   c128 d[1] = {{s, 0}};
   block_reduce<double, 1>(d, part + (long)c * gridDim.x + blockIdx.x, 1);
-  (void)a;
   if (!last_block(cnt + 4 * c)) return;
   if (threadIdx.x < 32) {
     const c128 t = warp_sum_partials(part + (long)c * gridDim.x, 1, threadIdx.x);
@@ -818,7 +832,7 @@ template <typename R>
 __global__ void __launch_bounds__(CT) combine_kernel(long n, cx<R>* V, long ldv, long vcs, int nv,
                                                      const c128* __restrict__ C, int ldc, long ccs, int nout, int nx,
                                                      int rmode, c128* X, long ldx, long xcs, cx<R>* Rv, long rcs,
-                                                     const ColState* st, const int* nvec, int vpp) {
+                                                     const ColState* st, const int* nvec, int vpp, cx<R>* Xf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int c = blockIdx.y;
   if (st && !st[c].active) return;
@@ -850,12 +864,72 @@ __global__ void __launch_bounds__(CT) combine_kernel(long n, cx<R>* V, long ldv,
     if (o < nout) {
       Vc[(long)o * ldv + row] = acc;
     } else if (o < nout + nx) {
-      c128* xp = X + c * xcs + (long)(o - nout) * ldx + row;
-      *xp = *xp + up(acc);
+      if (Xf) {
+        cx<R>* fp = Xf + c * xcs + (long)(o - nout) * ldx + row;
+        *fp = *fp + acc;
+      } else {
+        c128* xp = X + c * xcs + (long)(o - nout) * ldx + row;
+        *xp = *xp + up(acc);
+      }
     } else {
       cx<R>* rp = Rv + c * rcs + row;
       if (rmode == 1) *rp = acc;
       else *rp = *rp + acc;
+    }
+  }
+}
+
+// Basis combination without in-place outputs (the solution update x_i += V_m d_i of a
+// cycle and the residual r = V_{m+1} s, per column with its own basis): rows are
+// independent, so each thread takes rows in a grid-stride loop and reads its row of V
+// directly (coalesced across the warp); the block stages the column's coefficients once.
+// Same summation order as combine_kernel.
+constexpr int CW_MAXO = 12, CW_MAXCF = 1280;
+template <typename R, int NO>  // NO >= ntot outputs, so no unrolled work is predicated off for nothing
+__global__ void __launch_bounds__(256) combine_rows_kernel(long n, const cx<R>* __restrict__ V, long ldv, long vcs,
+                                                           int nv, const c128* __restrict__ C, int ldc, long ccs,
+                                                           int nx, int rmode, c128* X, long ldx, long xcs, cx<R>* Rv,
+                                                           long rcs, const ColState* st, const int* nvec, int vpp,
+                                                           cx<R>* Xf) {
+  __shared__ cx<R> cf[CW_MAXCF];  // ntot x nv
+  const int c = blockIdx.y;
+  if (st && !st[c].active) return;
+  if (nvec) n = nvec[c];
+  const int ntot = nx + (rmode ? 1 : 0);
+  const c128* Cc = C + c * ccs;
+  for (int t = threadIdx.x; t < nv * ntot; t += 256) {
+    const int i = t % nv, o = t / nv;
+    cf[t] = cvt<R>(Cc[(long)o * ldc + i]);
+  }
+  __syncthreads();
+  const cx<R>* Vc = V + (c / vpp) * vcs;
+  for (long row = blockIdx.x * 256L + threadIdx.x; row < n; row += (long)gridDim.x * 256) {
+    cx<R> acc[NO];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) acc[o] = {0, 0};
+#pragma unroll 4
+    for (int i = 0; i < nv; ++i) {
+      const cx<R> v = Vc[(long)i * ldv + row];
+#pragma unroll
+      for (int o = 0; o < NO; ++o)
+        if (o < ntot) acc[o] += v * cf[o * nv + i];
+    }
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      if (o >= ntot) break;
+      if (o < nx) {
+        if (Xf) {  // correction accumulated in the vectors' precision
+          cx<R>* fp = Xf + c * xcs + (long)o * ldx + row;
+          *fp = *fp + acc[o];
+        } else {
+          c128* xp = X + c * xcs + (long)o * ldx + row;
+          *xp = *xp + up(acc[o]);
+        }
+      } else {
+        cx<R>* rp = Rv + c * rcs + row;
+        if (rmode == 1) *rp = acc[o];
+        else *rp = *rp + acc[o];
+      }
     }
   }
 }
@@ -1111,9 +1185,9 @@ void gs_dot_shared_reserve(gdr_ctx* ctx, long n, int ncol, int nv) {
   }
 }
 
-// the tensor-core form for complex64 columns: from this many columns on (fewer leave the
-// CUDA-core kernel memory-bound anyway)
-constexpr int TC_MIN_COLS = 16;
+// the tensor-core forms for complex64 columns: from this many columns on (with fewer the
+// CUDA-core kernels are memory-bound anyway)
+constexpr int TC_MIN_COLS = 8;
 
 template <typename R, int NVM>
 static void gs_dot_shared_launch(gdr_ctx* ctx, const Batch<R>& b, int nv, const cx<R>* w, long wcs, c128* h_out) {
@@ -1284,7 +1358,7 @@ template <typename T>
 void norms2(gdr_ctx* ctx, long n, int cols, const T* x, long xcs, double* out, c128* part, int nblk, unsigned* cnt,
             const int* nvec) {
   dim3 grid((unsigned)nblk, (unsigned)cols);
-  KProf kp(ctx, "norms", (double)n * sizeof(T) * cols);
+  KProf kp(ctx, sizeof(T) == 8 ? "norms_c64" : "norms_c128", (double)n * sizeof(T) * cols);
   norms2_kernel<T><<<grid, NT, 0, ctx->stream>>>(n, x, xcs, out, part, cnt, nvec);
   GDR_LAUNCHED(ctx);
 }
@@ -1298,7 +1372,7 @@ void dots128(gdr_ctx* ctx, long n, int cols, const c128* u, long ucs, const c128
 template <typename R>
 void combine(gdr_ctx* ctx, long n, int ncol, cx<R>* V, long ldv, long vcs, int nv, const c128* C, int ldc, long ccs,
              int nout, int nx, int rmode, c128* X, long ldx, long xcs, cx<R>* Rv, long rcs, const ColState* st,
-             const int* nvec, int vpp, double lenh, double vlenh) {
+             const int* nvec, int vpp, double lenh, double vlenh, cx<R>* Xf) {
   const int ntot = nout + nx + (rmode ? 1 : 0);
   if (ntot == 0 || ncol == 0) return;
   const size_t smem = sizeof(cx<R>) * ((size_t)CR * nv + (size_t)nv * ntot);
@@ -1311,7 +1385,14 @@ void combine(gdr_ctx* ctx, long n, int ncol, cx<R>* V, long ldv, long vcs, int n
   // one basis shared by several columns: stream it once for all of them when their
   // coefficients fit in shared memory beside a row tile
   const size_t smem_sh = sizeof(cx<R>) * ((size_t)CR * nv + (size_t)nv * ntot * ncol);
-  if (vcs == 0 && nout == 0 && ncol > 1 && nvec == nullptr && smem_sh <= ctx->combine_smem_limit) {
+  if (!Xf && std::is_same<R, float>::value && vcs == 0 && nout == 0 && nx == 0 && (rmode == 1 || rmode == 2) &&
+      ncol >= TC_MIN_COLS && nvec == nullptr && vpp == 1 && ctx->tc_ok && ctx->tc_proj && ctx->tc_err) {
+    const double bytes = ctx->profile ? act * ((double)n * nv + cl * (rmode == 2 ? 2.0 : 1.0)) * sizeof(cx<R>) : 0.0;
+    if (tc_proj_update(ctx, n, reinterpret_cast<const c64*>(V), ldv, nv, C, ccs, rmode, reinterpret_cast<c64*>(Rv),
+                       rcs, ncol, st, ctx->tc_err, bytes))
+      return;
+  }
+  if (!Xf && vcs == 0 && nout == 0 && ncol > 1 && nvec == nullptr && smem_sh <= ctx->combine_smem_limit) {
     KProf kp(ctx, sizeof(R) == 4 ? "combine_shared_c64" : "combine_shared_c128",
              act * ((double)n * nv * sizeof(cx<R>) +
                     cl * (2.0 * nx * sizeof(c128) + (rmode == 2 ? 2.0 : (rmode == 1 ? 1.0 : 0.0)) * sizeof(cx<R>))));
@@ -1322,11 +1403,35 @@ void combine(gdr_ctx* ctx, long n, int ncol, cx<R>* V, long ldv, long vcs, int n
     GDR_LAUNCHED(ctx);
     return;
   }
-  KProf kp(ctx, sizeof(R) == 4 ? "combine_c64" : "combine_c128",
+  // profiler names by use: basis restart (in-place outputs), solution update, residual only
+  const char* pname = nout > 0 ? (sizeof(R) == 4 ? "combine_restart_c64" : "combine_restart_c128")
+                      : nx > 0 ? (sizeof(R) == 4 ? "combine_update_c64" : "combine_update_c128")
+                               : (sizeof(R) == 4 ? "combine_resid_c64" : "combine_resid_c128");
+  if (nout == 0 && ntot <= CW_MAXO && (long)nv * ntot <= CW_MAXCF) {
+    KProf kp(ctx, pname,
+             act * (vl * nv * sizeof(cx<R>) + cl * (2.0 * nx * (Xf ? sizeof(cx<R>) : sizeof(c128)) +
+                                                   (rmode == 2 ? 2.0 : (rmode == 1 ? 1.0 : 0.0)) * sizeof(cx<R>))));
+    // enough blocks per column to fill the GPU on its own: late in a batch few columns
+    // are still active, and the blocks of the others return at once
+    const long rblk = (n + 255) / 256;
+    dim3 g((unsigned)std::max<long>(1, std::min(rblk, 8L * ctx->num_sms)), (unsigned)ncol);
+#define GDR_ROWS(NO)                                                                                           \
+  combine_rows_kernel<R, NO><<<g, 256, 0, ctx->stream>>>(n, V, ldv, vcs, nv, C, ldc, ccs, nx, rmode, X, ldx, xcs, Rv, \
+                                                         rcs, st, nvec, vpp, Xf)
+    if (ntot <= 1) GDR_ROWS(1);
+    else if (ntot <= 2) GDR_ROWS(2);
+    else if (ntot <= 4) GDR_ROWS(4);
+    else if (ntot <= 8) GDR_ROWS(8);
+    else GDR_ROWS(CW_MAXO);
+#undef GDR_ROWS
+    GDR_LAUNCHED(ctx);
+    return;
+  }
+  KProf kp(ctx, pname,
            act * (vl * nv * sizeof(cx<R>) + cl * (nout * sizeof(cx<R>) + 2.0 * nx * sizeof(c128) +
                                                  (rmode == 2 ? 2.0 : (rmode == 1 ? 1.0 : 0.0)) * sizeof(cx<R>))));
   combine_kernel<R><<<grid, CT, smem, ctx->stream>>>(n, V, ldv, vcs, nv, C, ldc, ccs, nout, nx, rmode, X, ldx, xcs,
-                                                     Rv, rcs, st, nvec, vpp);
+                                                     Rv, rcs, st, nvec, vpp, Xf);
   GDR_LAUNCHED(ctx);
 }
 
@@ -1382,6 +1487,6 @@ template void start_cycle<double>(gdr_ctx*, const Batch<double>&, const c128*, l
 template void norms2<c64>(gdr_ctx*, long, int, const c64*, long, double*, c128*, int, unsigned*, const int*);
 template void norms2<c128>(gdr_ctx*, long, int, const c128*, long, double*, c128*, int, unsigned*, const int*);
 template void combine<float>(gdr_ctx*, long, int, c64*, long, long, int, const c128*, int, long, int, int, int, c128*,
-                             long, long, c64*, long, const ColState*, const int*, int, double, double);
+                             long, long, c64*, long, const ColState*, const int*, int, double, double, c64*);
 template void combine<double>(gdr_ctx*, long, int, c128*, long, long, int, const c128*, int, long, int, int, int,
-                              c128*, long, long, c128*, long, const ColState*, const int*, int, double, double);
+                              c128*, long, long, c128*, long, const ColState*, const int*, int, double, double, c128*);

@@ -88,6 +88,27 @@ __global__ void correct_kernel(long n, int ns, const c128* gam, const c128* S, l
     X[(long)p * ldx + r] += g * S[(long)i * lds + r];
 }
 
+// Residuals after the correction, without a matvec: with s_i = s~_i / (1 - gs_i) and
+// r^s_i = v - (A - sigma_i) s~_i, (A - sigma_i) s_i = (v - r^s_i) / (1 - gs_i), so
+// x_i += g_i s_i turns r_i into r_i - g_i / (1 - gs_i) (v - r^s_i) (i >= 1; i = 0 is not
+// corrected).  Pairs p = j*ns + i of the right-hand sides j of the batch; Rs = the extra
+// system's residuals r^s_i, gs = its gamma_i; Rin / Rout at stride ld per pair.
+__global__ void corrected_resid_kernel(long n, int ns, const c128* gam, const c128* gs, const c128* v, const c128* Rs,
+                                       const c128* Rin, c128* Rout, long ld) {
+  const int p = blockIdx.y, i = p % ns;
+  c128 f = {0, 0};
+  if (i > 0) {
+    const c128 om = {1.0 - gs[i].x, -gs[i].y};
+    const double d = om.x * om.x + om.y * om.y;
+    f = gam[p] * c128{om.x / d, -om.y / d};
+  }
+  const c128* ri = Rin + (long)p * ld;
+  c128* ro = Rout + (long)p * ld;
+  const c128* rs = Rs + (long)i * ld;
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < n; r += (long)gridDim.x * blockDim.x)
+    ro[r] = i > 0 ? ri[r] - f * (v[r] - rs[r]) : ri[r];
+}
+
 // Related right-hand sides (Sec. 5, eqs. relrhs1-relrhs2).  M is the j x (j+1)
 // augmented system [B^H B | B^H b_j] (row-major, FP64, overwritten); d solves it by
 // Gaussian elimination with partial pivoting, one warp (lanes stride the rows).  A
@@ -163,6 +184,17 @@ __global__ void related_guess_kernel(long n, int ns, int j, const c128* __restri
 // D_c += Cp_c[:, 0:ns] ((k+1) x ns per column, leading dimension k+1) for the active columns:
 // the projection's solution coefficients summed over the cycles of a Proj batch, so that
 // x_i += V_k d_i is applied once at the end instead of every cycle
+// X[c][i] += E[c][i] (FP64 += complex64): the summed corrections of a Proj batch
+template <typename R>
+__global__ void add_correction_kernel(long n, int ns, const cx<R>* __restrict__ E, long ldx, long xcs, c128* X,
+                                      const int* nvec) {
+  const int c = blockIdx.y / ns, i = blockIdx.y % ns;
+  const long nc = nvec ? nvec[c] : n;
+  const cx<R>* e = E + c * xcs + (long)i * ldx;
+  c128* x = X + c * xcs + (long)i * ldx;
+  for (long r = blockIdx.x * 256L + threadIdx.x; r < nc; r += (long)gridDim.x * 256) x[r] = x[r] + up(e[r]);
+}
+
 __global__ void dacc_kernel(int k1, int ns, const c128* __restrict__ Cp, long ccs, c128* D, const ColState* st) {
   const int c = blockIdx.y;
   if (!st[c].active) return;
@@ -627,6 +659,15 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
   c128* cproj = ctx->get<c128>("pj.cproj", (size_t)(k + 2) * ncol);
   c128* Cp = ctx->get<c128>("pj.Cp", (size_t)(k + 1) * (ns + 1) * ncol);
   if (k > 0 && job.project && job.vdcs == 0) gs_dot_shared_reserve(ctx, n, ncol, k + 1);
+  // complex64 vectors: the cycles' solution updates V_m y_i are summed in complex64 (the
+  // precision the correction is computed in) and added to the FP64 solutions once, at
+  // the end, instead of FP64 arithmetic per element and cycle
+  cx<R>* Ef = nullptr;
+  if (std::is_same<R, float>::value) {
+    const size_t ne = (size_t)ncol * job.xcs;
+    Ef = ctx->get<cx<R>>("pj.E", ne);
+    GDR_CUDA(cudaMemsetAsync(Ef, 0, sizeof(cx<R>) * ne, ctx->stream));
+  }
   // the projection's solution coefficients, summed over the cycles (applied to X at the end)
   c128* Dacc = nullptr;
   if (k > 0 && job.project) {
@@ -690,7 +731,7 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
     }
     dense_cycle(ctx, d);
     combine<R>(ctx, n, ncol, b.V, b.ldv, b.vcs, mp + 1, d.Cf, ldc, d.ccs, 0, ns, 1, job.X, job.ldx, job.xcs, r, ldr,
-               b.st, b.nvec, 1, col_len(b));
+               b.st, b.nvec, 1, col_len(b), 0, Ef);
     cycle_finish(ctx, d, b.H, b.cvec);
   };
   for (;;) {
@@ -718,6 +759,11 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
   if (Dacc)  // x_i += V_k (sum of the cycles' d_i), every column (zero where it never ran)
     combine<R>(ctx, n, ncol, bd.V, bd.ldv, job.vdcs, k + 1, Dacc, k + 1, (long)(k + 1) * ns, 0, ns, 0, job.X,
                job.ldx, job.xcs, nullptr, 0, nullptr, b.nvec, job.dpp, col_len(b), basis_len(bd));
+  if (Ef) {  // x_i += e_i, the cycles' corrections, once in FP64
+    dim3 ge(grid1(ctx, n), (unsigned)(ncol * ns));
+    add_correction_kernel<R><<<ge, 256, 0, ctx->stream>>>(n, ns, Ef, job.ldx, job.xcs, job.X, b.nvec);
+    GDR_LAUNCHED(ctx);
+  }
   res.gamma.resize((size_t)ncol * ns);
   GDR_CUDA(cudaMemcpyAsync(res.gamma.data(), sh.gamma, sizeof(c128) * ncol * ns, cudaMemcpyDeviceToHost, ctx->stream));
   stream_sync(ctx);
@@ -726,14 +772,29 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
 
 // --------------------------------------------------------- FP64 residuals
 
-// R[:, j*ns + i] = B[:, j] - (A - sigma_i I) X[:, j*ns + i]; relres[p] = ||R_p|| / ||b_j||
+// R[:, j*ns + i] = B[:, j] - (A - sigma_i I) X[:, j*ns + i]; relres[p] = ||R_p|| / ||b_j||.
+// With `only`, the pairs p with only[p] == 0 keep the residual R already holds (their X
+// has not changed since it was formed) and only the others are recomputed.
 void true_residuals(gdr_ctx* ctx, const gdr_op* A, int ns, const c128* sigma_dev, int nrhs, const c128* B, long ldb,
                     const c128* X, long ldx, c128* R, long ldr, std::vector<double>& relres,
-                    const std::vector<double>& bnorm) {
+                    const std::vector<double>& bnorm, const std::vector<int>* only) {
   const long n = A->n;
-  for (int j = 0; j < nrhs; ++j)
-    op_apply<double>(ctx, A, ns, sigma_dev, X + (long)j * ns * ldx, ldx, R + (long)j * ns * ldr, ldr, B + j * ldb, 0);
   const int np = ns * nrhs;
+  int* run = nullptr;
+  if (only) {
+    GDR_REQUIRE((int)only->size() == np, "true_residuals: mask size");
+    run = ctx->get<int>("res.run", (size_t)np);
+    GDR_CUDA(cudaMemcpyAsync(run, only->data(), sizeof(int) * np, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  for (int j = 0; j < nrhs; ++j) {
+    if (only) {
+      bool any = false;
+      for (int i = 0; i < ns; ++i) any = any || (*only)[(long)j * ns + i];
+      if (!any) continue;
+    }
+    op_apply_skip(ctx, A, ns, sigma_dev, X + (long)j * ns * ldx, ldx, R + (long)j * ns * ldr, ldr, B + j * ldb, 0,
+                  run ? run + (long)j * ns : nullptr, 1);
+  }
   const int nblk = (int)std::min<long>((n + 255) / 256, 2L * ctx->num_sms);
   c128* part = ctx->get<c128>("res.part", (size_t)nblk * np + 64);
   unsigned* cnt = ctx->get<unsigned>("res.cnt", (size_t)4 * np);
@@ -769,10 +830,10 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
   // fewer restarts of the per-pair solves (measured: 8^4 14.0 -> 13.4 ms, the CSR batch
   // 611 -> 592 ms); on long vectors the Gram-Schmidt bytes of a step grow with its index
   // while the deflated projection keeps restarts cheap, so short cycles (measured on
-  // GB300: 24^3x32 refinement 7.0 s at 40, 4.4 s at 20, 3.9 s at 12; 16^4 189 ms at 30,
-  // 133 ms at 12)
+  // GB300: 24^3x32 refinement 7.0 s at 40, 4.4 s at 20, 3.9 s at 12, 2.2 s at 8 and 6
+  // with the current kernels; 16^4 189 ms at 30, 133 ms at 12, 88 ms at 8)
   const int mr = p.m_refine > 0 ? p.m_refine
-                                : (A->n <= (1L << 17) ? std::min(m, mp + (m - mp) / 2) : std::min(mp, 12));
+                                : (A->n <= (1L << 17) ? std::min(m, mp + (m - mp) / 2) : std::min(mp, 8));
   const long ld = pad_ld(n);
   gdr_status status = GDR_OK;
   auto worst = [&](gdr_status s) {
@@ -901,6 +962,7 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
 
   // ---- FP64 true residuals, refinement (MIXED) and cleanup of the (shift, rhs) pairs of
   //      right-hand sides [r0, r1); relres of those pairs updated
+  std::vector<int> resid_ready;  // per pair: its FP64 residual is already in Rres
   auto refine_rhs = [&](int r0, int r1) {
     const int qg = r0 * ns, nq = (r1 - r0) * ns;
     const c128* Bq = B + (long)r0 * ldb;
@@ -908,12 +970,25 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
     c128* Rq = Rres + (long)qg * ld;
     std::vector<double> bnq(bnorm.begin() + r0, bnorm.begin() + r1);
     std::vector<double> rr;
-    auto residuals = [&]() {
-      true_residuals(ctx, A, ns, sig_dev, r1 - r0, Bq, ldb, Xq, ldx, Rq, ld, rr, bnq);
-      rep.resid_cols += nq;
+    // the first evaluation skips the pairs whose residuals the correction phase left in Rres
+    const bool pre = !resid_ready.empty() && r0 == 0 && r1 == nrhs;
+    auto residuals = [&](const std::vector<int>* only = nullptr) {
+      true_residuals(ctx, A, ns, sig_dev, r1 - r0, Bq, ldb, Xq, ldx, Rq, ld, rr, bnq, only);
+      if (only) {
+        for (int v : *only) rep.resid_cols += v ? 1 : 0;
+      } else {
+        rep.resid_cols += nq;
+      }
       for (int q = 0; q < nq; ++q) relres[qg + q] = rr[q];
     };
-    residuals();
+    if (pre) {
+      std::vector<int> todo(nq);
+      for (int q = 0; q < nq; ++q) todo[q] = resid_ready[q] ? 0 : 1;
+      resid_ready.clear();
+      residuals(&todo);
+    } else {
+      residuals();
+    }
     // Shift-shared pass (not in the paper; complex64 only): per right-hand side j, the
     // active residuals R_j = [r_i^j] are written as Y_j C_j + E_j with Y_j orthonormal
     // (pivoted Cholesky of R_j^H R_j, ||E_j||_F <= refine_rank_tol ||R_j||_2 roughly);
@@ -1116,7 +1191,7 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
       size_t freeb = 0, totb = 0;
       GDR_CUDA(cudaMemGetInfo(&freeb, &totb));
       const size_t elem = cleanup ? sizeof(c128) : sizeof(cx<R>);
-      const size_t per_col = elem * (size_t)ld * (mr + 4) + 4096;
+      const size_t per_col = elem * (size_t)ld * (mr + 5) + 4096;  // basis, work vectors, correction
       int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)nq, (freeb / 2) / per_col));
       for (int q0 = 0; q0 < nq; q0 += chunk) {
         const int cn = std::min(chunk, nq - q0);
@@ -1174,7 +1249,7 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
         else
           run_refine(R{});
       }
-      residuals();
+      residuals(&mask);  // only the pairs this pass refined have a new X
     }
   };
 
@@ -1267,6 +1342,14 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
         correct_slots(1, nrhs - 1, B + ldb, ldb, bn2);
         S_extra = XP;  // slot 0: s_i = s~_i / (1 - gamma_i)
         v_extra = v128;
+        if (nrhs > 1) {  // the corrected residuals of RHS 2.. (pairs ns..), for the refinement
+          dim3 gr(grid1(ctx, n), (unsigned)(ns * (nrhs - 1)));
+          corrected_resid_kernel<<<gr, 256, 0, ctx->stream>>>(n, ns, gam + ns, gam, v128, RP, RP + (long)ns * ld,
+                                                              Rres + (long)ns * ld, ld);
+          GDR_LAUNCHED(ctx);
+          resid_ready.assign((size_t)nrhs * ns, 1);
+          for (int i = 0; i < ns; ++i) resid_ready[i] = 0;
+        }
       }
       // results of RHS 2.. into X
       for (int j = 1; j < nrhs; ++j)
@@ -1354,10 +1437,10 @@ gdr_status solve_batch_pipeline(gdr_ctx* ctx, const gdr_op* A, int ns, const std
   // fewer restarts of the per-pair solves (measured: 8^4 14.0 -> 13.4 ms, the CSR batch
   // 611 -> 592 ms); on long vectors the Gram-Schmidt bytes of a step grow with its index
   // while the deflated projection keeps restarts cheap, so short cycles (measured on
-  // GB300: 24^3x32 refinement 7.0 s at 40, 4.4 s at 20, 3.9 s at 12; 16^4 189 ms at 30,
-  // 133 ms at 12)
+  // GB300: 24^3x32 refinement 7.0 s at 40, 4.4 s at 20, 3.9 s at 12, 2.2 s at 8 and 6
+  // with the current kernels; 16^4 189 ms at 30, 133 ms at 12, 88 ms at 8)
   const int mr = p.m_refine > 0 ? p.m_refine
-                                : (A->n <= (1L << 17) ? std::min(m, mp + (m - mp) / 2) : std::min(mp, 12));
+                                : (A->n <= (1L << 17) ? std::min(m, mp + (m - mp) / 2) : std::min(mp, 8));
   const int npair = np * ns;
   GDR_CUDA(cudaMemsetAsync(X, 0, sizeof(c128) * ld * npair, ctx->stream));
   // per-pair lengths (pair q = problem q / ns, shift q % ns)

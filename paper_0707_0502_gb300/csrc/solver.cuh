@@ -94,7 +94,7 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
 
 void true_residuals(gdr_ctx* ctx, const gdr_op* A, int ns, const c128* sigma_dev, int nrhs, const c128* B, long ldb,
                     const c128* X, long ldx, c128* R, long ldr, std::vector<double>& relres,
-                    const std::vector<double>& bnorm);
+                    const std::vector<double>& bnorm, const std::vector<int>* only = nullptr);
 
 template <typename R>
 gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>& sigma, int nrhs, const c128* B,

@@ -20,6 +20,18 @@
 // residuals with the same coefficients, so an error in c only makes one projection
 // slightly less than optimal; residuals and solutions stay consistent.
 //
+// The residual update R += V T over the same basis (the projection's r -= V_{k+1}(Hbar_k -
+// sigma_1 Ibar) d_1 of every column, T = -(Hbar_k - sigma_1 Ibar) d_1) is the transposed
+// problem: with the real form of V (row 2i: [Re v_j, -Im v_j], row 2i+1: [Im v_j, Re v_j]
+// over j) and the coefficients interleaved, R's real rows += A B^T with K = 2 nv.  A tile
+// of 64 complex rows is one 128-row MMA; four warps load V (plain coalesced loads) and
+// write A in the 128-byte-swizzled K-major layout, the coefficients sit in shared memory
+// for the whole launch, and eight warps add the accumulators to R (plain loads and
+// stores, one 128-byte line per warp and column).  The residual must stay consistent
+// with the solution update (applied in FP64 on the CUDA cores), so the product is split:
+// A = A_hi + A_lo and B = B_hi + B_lo with TF32 parts, D = A_hi B_hi + A_lo B_hi + A_hi B_lo,
+// which leaves an error of ~2^-21 relative per product, the level of FP32.
+//
 // Every wait on an mbarrier gives up after about a second, marks the call failed
 // (err, checked by the host) and the CTA winds down, freeing its tensor memory.
 #include <cuda.h>
@@ -276,6 +288,226 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_proj_dot_kernel(const __grid
   }
 }
 
+// ---------------------------------------------------------------- residual update
+
+constexpr int TU_ROWS = 64;         // complex rows per tile: 128 real MMA rows
+constexpr int TU_THREADS = 512;     // warp 1 MMA, warp 2 tensor memory, warps 4-7 A tiles, warps 8-15 epilogue
+constexpr int TU_MAXNV = 48;        // K = 2 nv <= 96: three 32-float swizzle atoms
+constexpr unsigned TU_ATOM_A = 128u * 128u;  // one K atom of A: 128 rows x 128 bytes
+
+struct TuArgs {
+  long n, ntiles;
+  int nv, ncol, nt, ka, kp;  // basis vectors, columns, columns per tile (<= 128, multiple of 32), K atoms, K padded to 8
+  int rmode;                 // 1: R = V T, 2: R += V T
+  const c64* V;
+  long ldv;
+  const c128* C;             // coefficients of column c at C + c * ccs (nv values)
+  long ccs;
+  float* R;                  // R as floats, column c at R + 2 * c * ldr
+  long ldr;
+  const ColState* st;
+  int* err;
+};
+
+DEV uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+// x = hi + lo, both TF32
+DEV void split_tf32(float x, float& hi, float& lo) {
+  hi = __uint_as_float(tf32_rna(x));
+  lo = __uint_as_float(tf32_rna(x - hi));
+}
+// byte offset of element (row, k) in a K-major, 128-byte-swizzled operand of `rows` rows
+DEV unsigned swz_off(int row, int k, int rows) {
+  const int a = k >> 5, kin = k & 31;
+  return (unsigned)a * (unsigned)rows * 128u + (unsigned)row * 128u + ((unsigned)((kin >> 2) ^ (row & 7)) << 4) +
+         (unsigned)(kin & 3) * 4u;
+}
+
+__global__ void __launch_bounds__(TU_THREADS, 1) tc_proj_update_kernel(TuArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  unsigned char* Ahi = base;
+  unsigned char* Alo = Ahi + (size_t)a.ka * TU_ATOM_A;
+  unsigned char* Bhi = Alo + (size_t)a.ka * TU_ATOM_A;
+  unsigned char* Blo = Bhi + (size_t)a.ka * a.nt * 128;
+  __shared__ __align__(8) uint64_t aready, afree, dfull[2], dempty[2], fin;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_s;
+  __shared__ int act[128];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int col0 = blockIdx.y * a.nt;
+  const long my_tiles = blockIdx.x < a.ntiles ? (a.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+
+  if (threadIdx.x == 0) {
+    mbar_init(&aready, 128);
+    mbar_init(&afree, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&dfull[b], 1);
+      mbar_init(&dempty[b], 256);
+    }
+    mbar_init(&fin, 1);
+    abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_addr(&tmem_base)),
+                 "r"(256)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // A's padding (k >= 2 nv) stays zero; B = the coefficients split into TF32 parts, K-major
+  {
+    uint4* z = reinterpret_cast<uint4*>(Ahi);
+    const unsigned nz = 2u * a.ka * TU_ATOM_A / 16u;
+    for (unsigned q = threadIdx.x; q < nz; q += TU_THREADS) z[q] = make_uint4(0, 0, 0, 0);
+    const int kw = a.ka * 32;
+    for (int t = threadIdx.x; t < a.nt * kw; t += TU_THREADS) {
+      const int c = t / kw, k = t % kw, j = k >> 1;
+      float hi = 0.f, lo = 0.f;
+      if (col0 + c < a.ncol && j < a.nv) {
+        const c128 v = a.C[(long)(col0 + c) * a.ccs + j];
+        const double x = (k & 1) ? v.y : v.x;
+        hi = __uint_as_float(tf32_rna((float)x));
+        lo = __uint_as_float(tf32_rna((float)(x - (double)hi)));
+      }
+      const unsigned off = swz_off(c, k, a.nt);
+      *reinterpret_cast<float*>(Bhi + off) = hi;
+      *reinterpret_cast<float*>(Blo + off) = lo;
+    }
+    for (int c = threadIdx.x; c < a.nt; c += TU_THREADS)
+      act[c] = (col0 + c < a.ncol) && (!a.st || a.st[col0 + c].active);
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tm = tmem_base;
+  volatile int* abort = &abort_s;
+
+  if (warp == 1) {  // ---- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc(a.nt);
+      const uint64_t dah = sm_desc(Ahi), dal = sm_desc(Alo), dbh = sm_desc(Bhi), dbl = sm_desc(Blo);
+      const uint32_t astep = TU_ATOM_A >> 4, bstep = (uint32_t)(a.nt * 128) >> 4;  // one K atom, in 16-byte units
+      for (long it = 0; it < my_tiles; ++it) {
+        const int b = (int)(it & 1);
+        if (!mbar_wait(&aready, (unsigned)(it & 1), abort)) break;
+        if (it >= 2 && !mbar_wait(&dempty[b], (unsigned)(((it >> 1) & 1) ^ 1), abort)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tm + (uint32_t)(b * 128);
+        for (int pass = 0; pass < 3; ++pass) {  // hi*hi, lo*hi, hi*lo
+          const uint64_t da = pass == 1 ? dal : dah, db = pass == 2 ? dbl : dbh;
+          for (int kk = 0; kk < a.kp / 8; ++kk) {
+            const uint32_t ka = (uint32_t)(kk >> 2), kin = (uint32_t)(kk & 3) * 2;
+            mma_tf32(d, da + ka * astep + kin, db + ka * bstep + kin, idesc, (pass > 0 || kk > 0) ? 1u : 0u);
+          }
+        }
+        mma_commit(&dfull[b]);
+        mma_commit(&afree);
+      }
+      mma_commit(&fin);  // arrives once every MMA issued above has completed
+      int own = 0;
+      if (!mbar_wait(&fin, 0, &own)) *abort = 1;
+    }
+  } else if (warp >= 4 && warp < 8) {  // ---- A tiles from V
+    // lane = (row, basis vector) as 8 x 4: a load instruction reads 4 runs of 64 bytes of V,
+    // and a store writes 8 rows x 32 bytes of A, which the swizzle spreads over all banks
+    const int w4 = warp - 4, il = lane >> 2, jl = lane & 3;
+    float2 v[2][TU_MAXNV / 4];
+    auto load = [&](long it) {
+      const long rb = (blockIdx.x + it * (long)gridDim.x) * TU_ROWS + w4 * 16 + il;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const long row = rb + 8 * h;
+#pragma unroll
+        for (int q = 0; q < TU_MAXNV / 4; ++q) {
+          const int j = jl + 4 * q;
+          v[h][q] = make_float2(0.f, 0.f);
+          if (j < a.nv && row < a.n) {
+            const c64 x = a.V[(long)j * a.ldv + row];
+            v[h][q] = make_float2(x.x, x.y);
+          }
+        }
+      }
+    };
+    if (my_tiles > 0) load(0);
+    for (long it = 0; it < my_tiles; ++it) {
+      if (it >= 1 && !mbar_wait(&afree, (unsigned)((it - 1) & 1), abort)) break;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = w4 * 16 + il + 8 * h;  // complex row of the tile: real rows 2i, 2i + 1
+#pragma unroll
+        for (int q = 0; q < TU_MAXNV / 4; ++q) {
+          const int j = jl + 4 * q;
+          if (j < a.nv) {
+            float rh, rl, ih, il2;
+            split_tf32(v[h][q].x, rh, rl);
+            split_tf32(v[h][q].y, ih, il2);
+            const unsigned o0 = swz_off(2 * i, 2 * j, 128), o1 = swz_off(2 * i + 1, 2 * j, 128);
+            *reinterpret_cast<float2*>(Ahi + o0) = make_float2(rh, -ih);
+            *reinterpret_cast<float2*>(Ahi + o1) = make_float2(ih, rh);
+            *reinterpret_cast<float2*>(Alo + o0) = make_float2(rl, -il2);
+            *reinterpret_cast<float2*>(Alo + o1) = make_float2(il2, rl);
+          }
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&aready);
+      if (it + 1 < my_tiles) load(it + 1);
+    }
+  } else if (warp >= 8) {  // ---- R += D
+    const int q4 = warp & 3, half = (warp - 8) >> 2;
+    const int m = q4 * 32 + lane;  // real row of the tile = tensor-memory lane
+    const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
+    const int nch = a.nt / 32;
+    for (long it = 0; it < my_tiles; ++it) {
+      const int b = (int)(it & 1);
+      const long r0 = (blockIdx.x + it * (long)gridDim.x) * TU_ROWS;
+      const long g = 2 * r0 + m;  // float index within a column
+      const bool rowok = g < 2 * a.n;
+      int own = 0;
+      const bool got = mbar_wait(&dfull[b], (unsigned)((it >> 1) & 1), &own);
+      if (!got) *abort = 1;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (__any_sync(0xffffffffu, !got || *abort)) break;  // warp-uniform: tcgen05.ld is .sync.aligned
+      for (int cc = half; cc < nch; cc += 2) {
+        float old[32];
+        if (a.rmode == 2) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int c = cc * 32 + j;
+            old[j] = (rowok && act[c]) ? a.R[2 * (long)(col0 + c) * a.ldr + g] : 0.f;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) old[j] = 0.f;
+        }
+        float d[32];
+        tmem_ld32(tm + lane_base + (uint32_t)(b * 128 + cc * 32), d);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int c = cc * 32 + j;
+          if (rowok && act[c]) a.R[2 * (long)(col0 + c) * a.ldr + g] = old[j] + d[j];
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&dempty[b]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (*abort && threadIdx.x == 0) atomicExch(a.err, 1);
+  if (warp == 2) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(256) : "memory");
+  }
+}
+
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -345,6 +577,40 @@ bool tc_proj_dot(gdr_ctx* ctx, long n, const c64* V, long ldv, int nv, const c64
   return true;
 }
 
+size_t tc_update_smem(int ka, int nt) { return 1024 + 2 * (size_t)ka * TU_ATOM_A + 2 * (size_t)ka * nt * 128; }
+
+bool tc_proj_update(gdr_ctx* ctx, long n, const c64* V, long ldv, int nv, const c128* C, long ccs, int rmode, c64* R,
+                    long ldr, int ncol, const ColState* st, int* err, double prof_bytes) {
+  if (nv < 1 || nv > TU_MAXNV || ncol < 1 || (rmode != 1 && rmode != 2) || !ctx->tc_ok || !ctx->tc_update_ok)
+    return false;
+  const int ctiles = (ncol + 127) / 128;
+  const int per = (ncol + ctiles - 1) / ctiles;
+  TuArgs a;
+  a.n = n;
+  a.ntiles = (n + TU_ROWS - 1) / TU_ROWS;
+  a.nv = nv;
+  a.ncol = ncol;
+  a.nt = (per + 31) / 32 * 32;
+  a.kp = (2 * nv + 7) / 8 * 8;
+  a.ka = (a.kp + 31) / 32;
+  a.rmode = rmode;
+  a.V = V;
+  a.ldv = ldv;
+  a.C = C;
+  a.ccs = ccs;
+  a.R = reinterpret_cast<float*>(R);
+  a.ldr = ldr;
+  a.st = st;
+  a.err = err;
+  const size_t smem = tc_update_smem(a.ka, a.nt);
+  const long want = std::max(1, ctx->num_sms / ctiles);
+  dim3 grid((unsigned)std::min<long>(want, a.ntiles), (unsigned)ctiles);
+  KProf kp(ctx, "tc_proj_update_c64", prof_bytes);
+  tc_proj_update_kernel<<<grid, TU_THREADS, smem, ctx->stream>>>(a);
+  GDR_LAUNCHED(ctx);
+  return true;
+}
+
 void tc_proj_init(gdr_ctx* ctx) {
   ctx->tc_ok = false;
   if (!encoder()) return;
@@ -355,4 +621,12 @@ void tc_proj_init(gdr_ctx* ctx) {
   if (cudaFuncSetAttribute(tc_proj_dot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need) != cudaSuccess)
     return;
   ctx->tc_ok = true;
+  ctx->tc_update_ok = false;
+  if (cudaFuncGetAttributes(&at, tc_proj_update_kernel) != cudaSuccess) return;
+  const size_t need_u = tc_update_smem(3, 128);
+  if (need_u + at.sharedSizeBytes > ctx->max_smem_optin) return;
+  if (cudaFuncSetAttribute(tc_proj_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need_u) !=
+      cudaSuccess)
+    return;
+  ctx->tc_update_ok = true;
 }

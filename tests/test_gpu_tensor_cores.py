@@ -1,7 +1,7 @@
 """The projection dot C = V^H R on the tensor cores (runs on a GB300; -m gpu).
 
 gdr_basis_dot forms c = V_{k+1}^H r of GMRES-Proj-Sh step 4 (Sec. 2.3) for many
-columns at once.  For complex64 inputs with 16 or more columns it runs on the
+columns at once.  For complex64 inputs with 8 or more columns it runs on the
 tensor cores: TF32 inputs (10 fraction bits) and FP32 accumulation.  Each dot
 is then bounded, element by element, by
 
@@ -15,8 +15,9 @@ numpy's FP64 product of the same complex64 inputs.
 
 Cases span ragged K stages (2n not a multiple of 32), one and two column tiles
 (ncol up to 200: 128 columns per tile), basis sizes from 1 to 97 (the MMA has
-128 rows, zero-filled above nv), a padded column stride, and the fallbacks (odd n, fewer than 16
-columns, the flag) that must give the CUDA-core result.  The kernel that ran is
+128 rows, zero-filled above nv), a padded column stride, and the fallbacks (odd
+n, fewer than 8 columns, the flag) that must give the CUDA-core result.  The
+residual update (second half of the file) is checked the same way.  The kernel that ran is
 read from the library's profiler."""
 import numpy as np
 import pytest
@@ -69,7 +70,7 @@ def tc_ran(prof):
 
 
 @pytest.mark.parametrize("n,nv,ncol,ldr", [
-    (3000, 21, 16, 3000),      # 2n = 6000: a ragged last K stage
+    (3000, 21, 8, 3000),       # 2n = 6000: a ragged last K stage; fewest columns
     (5000, 21, 40, 5006),      # padded column stride
     (2048, 64, 130, 2048),     # two column tiles (65 + 65)
     (4000, 97, 120, 4000),     # the largest basis (m + 1 = 97 of the MMA's 128 rows)
@@ -88,7 +89,7 @@ def test_tensor_core_dot(ctx, n, nv, ncol, ldr):
 
 @pytest.mark.parametrize("n,nv,ncol,ldr,flags", [
     (3001, 21, 40, 3001, 0),                            # odd n: rows not on 16-byte boundaries
-    (3000, 21, 15, 3000, 0),                            # too few columns
+    (3000, 21, 7, 3000, 0),                             # too few columns
     (3000, 21, 40, 3000, 8192),                         # GDR_FLAG_NO_TENSOR_CORES
 ])
 def test_cuda_core_fallback(ctx, n, nv, ncol, ldr, flags):
@@ -110,3 +111,81 @@ def test_fp64_dot(ctx):
     exact = np.conj(V) @ R.T
     S = np.abs(V) @ np.abs(R).T
     assert np.all(np.abs(Cd.cpu().numpy().T - exact) <= 1e-13 * S)
+
+
+# ------------------------------------------------------------------ residual update
+#
+# gdr_basis_residual_update: R[:, c] += V T[:, c] (the projection's residual update).
+# On the tensor cores V and T are split into two TF32 parts each and three products
+# are accumulated in FP32, so the result carries FP32-level errors, element by element
+#
+#     |R_out - R_exact| <= 2^-16 * S + 2^-22 * (|R_in| + |R_exact|),
+#
+# S = sum_k |A_mk| |B_kc| over the real form (K = 2 nv terms; 2^-16 covers the worst-case
+# FP32 accumulation of up to 96 terms and the dropped lo*lo product), the second term
+# the final FP32 addition.  A single TF32 product would leave errors near 2^-11 S: the
+# median is held far below that.  The CUDA-core form is held to the same bound.
+
+def run_update(ctx, n, nv, ncol, ldr, seed, flags=0):
+    rng = np.random.default_rng(seed)
+    V = c64(rng, nv, n)
+    V /= np.linalg.norm(V, axis=1, keepdims=True)
+    T = rng.standard_normal((ncol, nv)) + 1j * rng.standard_normal((ncol, nv))
+    T *= np.exp(rng.uniform(-4, 2, size=(ncol, 1)))           # column scales over ~6 decades
+    Rm = c64(rng, ncol, ldr)
+    R0 = Rm.copy()
+    Rd = dev(Rm)
+    g.gdr_profile(ctx, True)
+    g.gdr_basis_residual_update(ctx, g.GDR_PREC_MIXED, n, nv, dev(V), ncol, dev(T), Rd, ldr, flags)
+    prof = g.gdr_profile_report(ctx)
+    g.gdr_profile(ctx, False)
+    out = Rd.cpu().numpy()
+    Vd = V.astype(np.complex128)
+    exact = R0[:, :n].astype(np.complex128) + T @ Vd            # row c: r_c + V T[:, c]
+    # S over the real form: |Re v||Re t| + |Im v||Im t| (real row), |Im v||Re t| + |Re v||Im t| (imag row)
+    Sre = np.abs(T.real) @ np.abs(Vd.real) + np.abs(T.imag) @ np.abs(Vd.imag)
+    Sim = np.abs(T.real) @ np.abs(Vd.imag) + np.abs(T.imag) @ np.abs(Vd.real)
+    return out, R0, exact, Sre, Sim, prof
+
+
+def check_update(out, R0, exact, Sre, Sim, n):
+    got = out[:, :n].astype(np.complex128)
+    r0 = R0[:, :n].astype(np.complex128)
+    bre = 2.0 ** -16 * Sre + 2.0 ** -22 * (np.abs(r0.real) + np.abs(exact.real))
+    bim = 2.0 ** -16 * Sim + 2.0 ** -22 * (np.abs(r0.imag) + np.abs(exact.imag))
+    assert np.all(np.abs(got.real - exact.real) <= bre)
+    assert np.all(np.abs(got.imag - exact.imag) <= bim)
+    assert np.array_equal(out[:, n:], R0[:, n:])                 # padding of the column stride untouched
+
+
+def tcu_ran(prof):
+    return prof.get("tc_proj_update_c64", {}).get("launches", 0) > 0
+
+
+@pytest.mark.parametrize("n,nv,ncol,ldr", [
+    (3000, 21, 8, 3000),        # ragged last row tile (3000 = 46 x 64 + 56); fewest columns
+    (5000, 41, 120, 5006),      # the 24^3x32 Proj shape (k = 40), padded stride
+    (4096, 48, 130, 4096),      # largest basis of this form, two column tiles of 96
+    (1000, 1, 40, 1000),        # one basis vector
+    (262144, 31, 96, 262144),   # a long vector: many row tiles per CTA
+])
+def test_tensor_core_residual_update(ctx, n, nv, ncol, ldr):
+    out, R0, exact, Sre, Sim, prof = run_update(ctx, n, nv, ncol, ldr, seed=n + 3 * nv + ncol)
+    assert tcu_ran(prof), prof
+    check_update(out, R0, exact, Sre, Sim, n)
+    # split TF32: errors at the FP32 level, far below a single TF32 product's ~2^-11 S
+    got = out[:, :n].astype(np.complex128)
+    rel = np.abs(got.real - exact.real) / (Sre + np.abs(exact.real))
+    assert np.median(rel) < 2.0 ** -20
+
+
+@pytest.mark.parametrize("n,nv,ncol,flags", [
+    (3000, 21, 7, 0),                         # too few columns
+    (3000, 49, 40, 0),                        # more basis vectors than this form takes
+    (3000, 21, 40, 8192),                     # GDR_FLAG_NO_TENSOR_CORES
+])
+def test_residual_update_cuda_cores(ctx, n, nv, ncol, flags):
+    assert flags in (0, g.GDR_FLAG_NO_TENSOR_CORES)
+    out, R0, exact, Sre, Sim, prof = run_update(ctx, n, nv, ncol, n, seed=11 * n + nv, flags=flags)
+    assert not tcu_ran(prof), prof
+    check_update(out, R0, exact, Sre, Sim, n)
