@@ -211,8 +211,10 @@ gdr_status gdr_op_apply(gdr_ctx *ctx, const gdr_op *A, gdr_prec prec, int ncol, 
  * operators and are lost with gdr_op_destroy. */
 typedef struct {
   int form;       /* Wilson: 0 one thread per site, 1 direction-split (a warp per direction,
-                     32 sites per block).  CSR: threads per row, 1, 2, 4 or 8 */
-  int threads;    /* threads per block: 64, 128 or 256 (direction-split: 128) */
+                     32 sites per block), 2 one thread per site and column pair with packed
+                     FP32x2 arithmetic (complex64 only; an odd last column is paired with itself).
+                     CSR: threads per row, 1, 2, 4 or 8 */
+  int threads;    /* threads per block: 64, 128 or 256 (direction-split: 128; pairs: 64 or 128) */
   int col_inner;  /* 1: consecutive blocks take one site/row tile for consecutive columns
                      (links / rows read from HBM once for all columns); 0: column-major grid */
 } gdr_shape;

@@ -356,7 +356,8 @@ gdr_status gdr_op_set_shape(gdr_op* A, gdr_prec prec, int ncol, const gdr_shape*
   MvShape s{shape->form, shape->threads, shape->col_inner ? 1 : 0};
   if (A->kind == OP_WILSON) {
     if (s.form == 1 && s.threads != 128) return GDR_EINVAL;
-    if (s.form != 0 && s.form != 1) return GDR_EINVAL;
+    if (s.form < 0 || s.form > 2) return GDR_EINVAL;
+    if (s.form >= 2 && (fk == 1 || s.threads == 256)) return GDR_EINVAL;  // pairs: complex64, 64 or 128 threads
     if (s.threads != 64 && s.threads != 128 && s.threads != 256) return GDR_EINVAL;
   } else {
     if (s.form != 1 && s.form != 2 && s.form != 4 && s.form != 8) return GDR_EINVAL;

@@ -64,13 +64,15 @@ double time_adaptive(gdr_ctx* ctx, F&& launch, double budget_ms) {
   return time_calls(ctx, launch, reps);
 }
 
-std::vector<MvShape> candidates(const gdr_op* A, int ncol) {
+std::vector<MvShape> candidates(const gdr_op* A, int ncol, bool f64) {
   std::vector<MvShape> out;
   const int orders = ncol > 1 ? 2 : 1;
   for (int ci = 0; ci < orders; ++ci) {
     if (A->kind == OP_WILSON) {
       for (int t : {64, 128, 256}) out.push_back(MvShape{0, t, ci});
       out.push_back(MvShape{1, 128, ci});
+      if (!f64 && ncol > 1)  // column pairs with packed FP32x2 arithmetic
+        for (int t : {64, 128}) out.push_back(MvShape{2, t, ci});
     } else {
       for (int tpr : {1, 2, 4, 8})
         for (int t : {128, 256}) out.push_back(MvShape{tpr, t, ci});
@@ -106,7 +108,7 @@ static void tune_matvec(gdr_ctx* ctx, gdr_op* A, int ncol, gdr_tune_result& out)
   MvShape best = def;
   double tbest = 1e30, tdef = -1;
   int count = 0;
-  for (const MvShape& s : candidates(A, ncol)) {
+  for (const MvShape& s : candidates(A, ncol, F64)) {
     A->mv_tuned[key] = s;
     const double t = time_adaptive(ctx, run, 20.0);
     ++count;

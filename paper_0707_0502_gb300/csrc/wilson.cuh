@@ -171,4 +171,143 @@ DEV void hop_mu(const LT* __restrict__ links, const cx<R>* x, long V, long site,
   hop<MU, false, R, LT>(links, V, bwd, pb, acc);
 }
 
+// ---- two columns per thread, packed FP32x2 arithmetic (sm_100 and later)
+// A pair value holds one real component of two columns: column 2p in the low lane,
+// 2p + 1 in the high lane.  One packed FMA does the work of two scalar ones, and the
+// link (the same for both columns) is loaded and converted once for both.
+typedef unsigned long long f2;
+DEV f2 f2_pack(float lo, float hi) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+DEV void f2_unpack(f2 v, float& lo, float& hi) { asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v)); }
+DEV f2 f2_add(f2 a, f2 b) {
+  f2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+DEV f2 f2_sub(f2 a, f2 b) {
+  f2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+DEV f2 f2_mul(f2 a, f2 b) {
+  f2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+DEV f2 f2_fma(f2 a, f2 b, f2 c) {
+  f2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+struct cx2 {
+  f2 re, im;
+};
+struct Spinor2 {
+  cx2 s[12];
+};
+
+// u + ph z with ph = 1, i, -1, -i for PH = 0..3
+template <int PH>
+DEV cx2 addph(cx2 u, cx2 z) {
+  if (PH == 0) return {f2_add(u.re, z.re), f2_add(u.im, z.im)};
+  if (PH == 1) return {f2_sub(u.re, z.im), f2_add(u.im, z.re)};
+  if (PH == 2) return {f2_sub(u.re, z.re), f2_sub(u.im, z.im)};
+  return {f2_add(u.re, z.im), f2_sub(u.im, z.re)};
+}
+
+// the spinors of site `site` in columns x0 and x1 (pair-major order)
+DEV void load_spinor2(const c64* x0, const c64* x1, long V, long site, Spinor2& p) {
+  const float4* q0 = reinterpret_cast<const float4*>(x0) + site;
+  const float4* q1 = reinterpret_cast<const float4*>(x1) + site;
+  float4 a[6], b[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    a[i] = __ldg(q0 + i * V);
+    b[i] = __ldg(q1 + i * V);
+  }
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    p.s[2 * i] = {f2_pack(a[i].x, b[i].x), f2_pack(a[i].y, b[i].y)};
+    p.s[2 * i + 1] = {f2_pack(a[i].z, b[i].z), f2_pack(a[i].w, b[i].w)};
+  }
+}
+
+// The phases of one hop, read off b_mul / bh_mul: with backward-hop signs, the half
+// spinor is h_0 = u_0 + ph z_0, h_1 = u_1 + ph' z_1 (z from the lower components d_0,
+// d_1) and the lower components gain ph g (from g_0 or g_1); the forward hop negates
+// every term (PH + 2).
+template <int MU> struct HopTab;
+template <> struct HopTab<0> { static constexpr int h0z = 1, h0p = 3, h1z = 0, h1p = 3, r6g = 1, r6p = 1, r9g = 0, r9p = 1; };
+template <> struct HopTab<1> { static constexpr int h0z = 1, h0p = 2, h1z = 0, h1p = 0, r6g = 1, r6p = 0, r9g = 0, r9p = 2; };
+template <> struct HopTab<2> { static constexpr int h0z = 0, h0p = 3, h1z = 1, h1p = 1, r6g = 0, r6p = 1, r9g = 1, r9p = 3; };
+template <> struct HopTab<3> { static constexpr int h0z = 0, h0p = 0, h1z = 1, h1p = 0, r6g = 0, r6p = 0, r9g = 1, r9p = 0; };
+
+// one hop for two columns (see hop): FWD (1 - gamma) U(x) psi(x+mu), else (1 + gamma) U(x-mu)^H psi(x-mu);
+// ldu(e) gives link element e = a*3 + b of the hop's link
+template <int MU, bool FWD, typename LoadU>
+DEV void hop2_core(const Spinor2& p, LoadU ldu, Spinor2& acc) {
+  using T = HopTab<MU>;
+  constexpr int S = FWD ? 2 : 0;
+  cx2 h[2][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const cx2 d[2] = {p.s[6 + a], p.s[9 + a]};
+    h[0][a] = addph<(T::h0p + S) & 3>(p.s[a], d[T::h0z]);
+    h[1][a] = addph<(T::h1p + S) & 3>(p.s[3 + a], d[T::h1z]);
+  }
+  cx2 g[2][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) g[0][a] = g[1][a] = {0ull, 0ull};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const c64 u = ldu(a * 3 + b);
+      const f2 ur = f2_pack(u.x, u.x), ui = f2_pack(u.y, u.y), nui = f2_pack(-u.y, -u.y);
+#pragma unroll
+      for (int sp = 0; sp < 2; ++sp) {
+        if (FWD) {  // g_a += U_ab h_b
+          cx2& t = g[sp][a];
+          const cx2 hb = h[sp][b];
+          t.re = f2_fma(nui, hb.im, f2_fma(ur, hb.re, t.re));
+          t.im = f2_fma(ui, hb.re, f2_fma(ur, hb.im, t.im));
+        } else {    // g_b += conj(U_ab) h_a
+          cx2& t = g[sp][b];
+          const cx2 ha = h[sp][a];
+          t.re = f2_fma(ui, ha.im, f2_fma(ur, ha.re, t.re));
+          t.im = f2_fma(nui, ha.re, f2_fma(ur, ha.im, t.im));
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    acc.s[a] = addph<0>(acc.s[a], g[0][a]);
+    acc.s[3 + a] = addph<0>(acc.s[3 + a], g[1][a]);
+    acc.s[6 + a] = addph<(T::r6p + S) & 3>(acc.s[6 + a], g[T::r6g][a]);
+    acc.s[9 + a] = addph<(T::r9p + S) & 3>(acc.s[9 + a], g[T::r9g][a]);
+  }
+}
+
+template <int MU, bool FWD, typename LT>
+DEV void hop2(const LT* __restrict__ links, long V, long lsite, const Spinor2& p, Spinor2& acc) {
+  const LT* L = links + (long)MU * 9 * V + lsite;
+  hop2_core<MU, FWD>(p, [&](int e) { return LinkLd<float, LT>::ld(L, (long)e * V); }, acc);
+}
+
+template <int MU, typename LT>
+DEV void hop_mu2(const LT* __restrict__ links, const c64* x0, const c64* x1, long V, long site, int coord, int L,
+                 long stride, Spinor2& acc) {
+  const long fwd = (coord == L - 1) ? site - (long)(L - 1) * stride : site + stride;
+  const long bwd = (coord == 0) ? site + (long)(L - 1) * stride : site - stride;
+  Spinor2 p;
+  load_spinor2(x0, x1, V, fwd, p);
+  hop2<MU, true, LT>(links, V, site, p, acc);
+  load_spinor2(x0, x1, V, bwd, p);
+  hop2<MU, false, LT>(links, V, bwd, p, acc);
+}
+
 }  // namespace

@@ -5,8 +5,11 @@ gdr_op_set_shape and compared with the oracle's operator, so that whichever
 shape a tuned solve runs with is covered by parity: the shapes only move the
 same arithmetic around (the FP64 results agree with the oracle to rounding,
 whatever the order of a CSR row's or the four directions' partial sums).
-Then gdr_autotune on a lattice where the persistent sweep applies, and a full
-solve with GDR_FLAG_AUTOTUNE checked by the oracle's operator."""
+The column-pair form (packed FP32x2 arithmetic, complex64 only) is checked
+the same way, against the oracle and, with bf16 links, against the one-column
+form on the same operator.  Then gdr_autotune on a lattice where the persistent
+sweep applies, a full solve with GDR_FLAG_AUTOTUNE checked by the oracle's
+operator, and one with the pair form forced for every column count."""
 import numpy as np
 import pytest
 
@@ -37,6 +40,7 @@ def rel(a, b):
 
 
 WILSON_SHAPES = [(0, t, ci) for t in (64, 128, 256) for ci in (0, 1)] + [(1, 128, 0), (1, 128, 1)]
+PAIR_SHAPES = [(2, t, ci) for t in (64, 128) for ci in (0, 1)]
 CSR_SHAPES = [(tpr, t, ci) for tpr in (1, 2, 4, 8) for t in (128, 256) for ci in (0, 1)]
 
 
@@ -64,6 +68,62 @@ def test_wilson_every_shape(ctx, dims, ncol):
         assert rel(host(Y), ref) < 1e-14, (form, threads, ci)
         assert rel(host(Y32), ref) < 1e-6, (form, threads, ci)
     g.gdr_op_destroy(op)
+
+
+# ncol 1: a column paired with itself; 5: an odd last pair; 6: pairs only
+@pytest.mark.parametrize("dims", [(3, 4, 2, 6), (8, 8, 4, 4)])
+@pytest.mark.parametrize("ncol", [1, 5, 6])
+def test_wilson_pair_shapes(ctx, dims, ncol):
+    links = W.su3_links(dims, 0.4, W.rng(43, 0))
+    op_o = WilsonOperator(dims, links, diag_a=0.5)
+    rng = np.random.default_rng(7)
+    X = rng.standard_normal((ncol, op_o.n)) + 1j * rng.standard_normal((ncol, op_o.n))
+    sig = -1.0 / np.linspace(0.12, 0.13, ncol) + 0.01j * np.arange(1, ncol + 1)
+    ref = np.stack([op_o.matvec(X[c]) - sig[c] * X[c] for c in range(ncol)])
+    X64 = dev(X, torch.complex64)
+    for store in (g.GDR_LINK_C64, g.GDR_LINK_BF16):
+        op = g.gdr_op_wilson(ctx, dims, dev(links), 0.5, store)
+        g.gdr_op_set_shape(op, g.GDR_PREC_MIXED, ncol, 0, 128, 0)
+        Y1 = torch.zeros((ncol, op_o.n), dtype=torch.complex64, device="cuda")
+        g.gdr_op_apply(ctx, op, g.GDR_PREC_MIXED, sig, X64, Y1)      # one column per thread
+        for form, threads, ci in PAIR_SHAPES:
+            g.gdr_op_set_shape(op, g.GDR_PREC_MIXED, ncol, form, threads, ci)
+            assert g.gdr_op_get_shape(op, g.GDR_PREC_MIXED, ncol) == {"form": form, "threads": threads,
+                                                                      "col_inner": ci}
+            Y = torch.full((ncol, op_o.n), 7.0 + 7.0j, dtype=torch.complex64, device="cuda")  # all entries written
+            g.gdr_op_apply(ctx, op, g.GDR_PREC_MIXED, sig, X64, Y)
+            torch.cuda.synchronize()
+            if store == g.GDR_LINK_C64:
+                assert rel(host(Y), ref) < 1e-6, (form, threads, ci)
+            assert rel(host(Y), host(Y1)) < 1e-6, (store, form, threads, ci)
+        g.gdr_op_destroy(op)
+
+
+def test_solve_with_pair_forms(ctx):
+    """Every complex64 matvec of a mixed solve in a pair form (forced for each column
+    count the solve uses: the nearest set count within 2x applies), including the
+    stages that scale or subtract from a right-hand side."""
+    p = W.wilson_problem(2, dims=(8, 8, 8, 8), eps=0.3, nshift=4, nrhs=3, m=24, k=10, m_proj=14,
+                         kappa_c=0.1325)
+    dims, diag_a, links = p.op[1], p.op[2], p.op[3]
+    op_o = WilsonOperator(dims, links, diag_a=diag_a)
+    for form in (2,):
+        op = g.gdr_op_wilson(ctx, dims, dev(links), diag_a, g.GDR_LINK_BF16)
+        for nc in (1, 2, 4, 8, 16, 32, 64, 128):
+            g.gdr_op_set_shape(op, g.GDR_PREC_MIXED, nc, form, 128, nc % 2)
+        params = g.gdr_params_default(m=p.m, k=p.k, m_proj=p.m_proj, tol=1e-8, prec=g.GDR_PREC_MIXED,
+                                      flags=g.GDR_FLAG_NO_SWEEP)
+        nrhs = p.B.shape[1]
+        X = torch.zeros((nrhs, len(p.sigma), p.n), dtype=torch.complex128, device="cuda")
+        st, rep, _ = g.gdr_solve_multishift(ctx, op, p.sigma, dev(np.ascontiguousarray(p.B.T)), X, params)
+        assert st == g.GDR_OK, rep
+        Xh = host(X)
+        for j in range(nrhs):
+            b = p.B[:, j]
+            for i, s in enumerate(p.sigma):
+                x = Xh[j, i]
+                assert np.linalg.norm(b - (op_o.matvec(x) - s * x)) / np.linalg.norm(b) <= 1.05e-8, (form, j, i)
+        g.gdr_op_destroy(op)
 
 
 @pytest.mark.parametrize("ncol", [1, 3])
@@ -114,9 +174,12 @@ def test_csr_batch_every_shape(ctx):
 def test_set_shape_rejects_bad_shapes(ctx):
     links = W.su3_links((2, 2, 2, 2), 0.3, W.rng(42, 0))
     op = g.gdr_op_wilson(ctx, (2, 2, 2, 2), dev(links), 0.0, g.GDR_LINK_C64)
-    for form, threads in ((1, 256), (2, 128), (0, 96)):
+    for form, threads in ((1, 256), (2, 128), (0, 96), (3, 128)):
         with pytest.raises(g.GdrError):
             g.gdr_op_set_shape(op, g.GDR_PREC_FP64, 1, form, threads, 0)
+    for form, threads in ((2, 256), (3, 64)):   # pairs: complex64, 64 or 128 threads
+        with pytest.raises(g.GdrError):
+            g.gdr_op_set_shape(op, g.GDR_PREC_MIXED, 2, form, threads, 0)
     g.gdr_op_set_shape(op, g.GDR_PREC_FP64, 4, 0, 256, 1)
     assert g.gdr_op_get_shape(op, g.GDR_PREC_FP64, 8)["threads"] == 256   # nearest count within 2x
     assert g.gdr_op_get_shape(op, g.GDR_PREC_FP64, 9)["form"] == 1        # beyond: default (tiny lattice)
