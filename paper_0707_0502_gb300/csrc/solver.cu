@@ -756,9 +756,17 @@ ProjResult proj_batch(gdr_ctx* ctx, const gdr_op* A, const ProjJob<R>& job, bool
       break;
     }
   }
-  if (Dacc)  // x_i += V_k (sum of the cycles' d_i), every column (zero where it never ran)
-    combine<R>(ctx, n, ncol, bd.V, bd.ldv, job.vdcs, k + 1, Dacc, k + 1, (long)(k + 1) * ns, 0, ns, 0, job.X,
-               job.ldx, job.xcs, nullptr, 0, nullptr, b.nvec, job.dpp, col_len(b), basis_len(bd));
+  if (Dacc) {  // x_i += V_k (sum of the cycles' d_i), every column (zero where it never ran)
+    if (Ef && job.vdcs == 0 && job.xcs == (long)ns * job.ldx && b.nvec == nullptr && job.dpp == 1) {
+      // into the complex64 corrections, as ncol * ns columns e_p += V_k Dacc_p (the
+      // shared-basis update, on the tensor cores where it applies), added to X below
+      combine<R>(ctx, n, ncol * ns, bd.V, bd.ldv, 0, k + 1, Dacc, k + 1, k + 1, 0, 0, 2, nullptr, 0, 0, Ef, job.ldx,
+                 nullptr, nullptr, 1, col_len(b) * ns, basis_len(bd));
+    } else {
+      combine<R>(ctx, n, ncol, bd.V, bd.ldv, job.vdcs, k + 1, Dacc, k + 1, (long)(k + 1) * ns, 0, ns, 0, job.X,
+                 job.ldx, job.xcs, nullptr, 0, nullptr, b.nvec, job.dpp, col_len(b), basis_len(bd));
+    }
+  }
   if (Ef) {  // x_i += e_i, the cycles' corrections, once in FP64
     dim3 ge(grid1(ctx, n), (unsigned)(ncol * ns));
     add_correction_kernel<R><<<ge, 256, 0, ctx->stream>>>(n, ns, Ef, job.ldx, job.xcs, job.X, b.nvec);

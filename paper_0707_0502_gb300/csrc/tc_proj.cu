@@ -337,10 +337,33 @@ __global__ void __launch_bounds__(TU_THREADS, 1) tc_proj_update_kernel(TuArgs a)
   __shared__ __align__(8) uint64_t aready, afree, dfull[2], dempty[2], fin;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_s;
-  __shared__ int act[128];
+  __shared__ int cmap[128];  // the active columns of this column tile, compacted
+  __shared__ int wcnt[4], nact_s;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int col0 = blockIdx.y * a.nt;
   const long my_tiles = blockIdx.x < a.ntiles ? (a.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+
+  // active columns: the MMA width and the epilogue follow their number, and a tile
+  // whose columns have all converged has nothing to do
+  bool f = false;
+  unsigned bal = 0;
+  if (warp < 4) {
+    const int c = threadIdx.x;
+    f = c < a.nt && col0 + c < a.ncol && (!a.st || a.st[col0 + c].active);
+    bal = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) wcnt[warp] = __popc(bal);
+  }
+  __syncthreads();
+  if (warp < 4) {
+    int off = 0;
+    for (int w = 0; w < warp; ++w) off += wcnt[w];
+    if (f) cmap[off + __popc(bal & ((1u << lane) - 1u))] = threadIdx.x;
+    if (threadIdx.x == 0) nact_s = wcnt[0] + wcnt[1] + wcnt[2] + wcnt[3];
+  }
+  __syncthreads();
+  const int nact = nact_s;
+  if (nact == 0 || my_tiles == 0) return;  // uniform over the CTA, before any barrier or tensor memory
+  const int ne = (nact + 31) / 32 * 32;   // MMA N: compacted columns, zero rows above nact
 
   if (threadIdx.x == 0) {
     mbar_init(&aready, 128);
@@ -359,27 +382,26 @@ __global__ void __launch_bounds__(TU_THREADS, 1) tc_proj_update_kernel(TuArgs a)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  // A's padding (k >= 2 nv) stays zero; B = the coefficients split into TF32 parts, K-major
+  // A's padding (k >= 2 nv) stays zero; B = the active columns' coefficients split into
+  // TF32 parts, K-major, row k = column cmap[k]
   {
     uint4* z = reinterpret_cast<uint4*>(Ahi);
     const unsigned nz = 2u * a.ka * TU_ATOM_A / 16u;
     for (unsigned q = threadIdx.x; q < nz; q += TU_THREADS) z[q] = make_uint4(0, 0, 0, 0);
     const int kw = a.ka * 32;
-    for (int t = threadIdx.x; t < a.nt * kw; t += TU_THREADS) {
-      const int c = t / kw, k = t % kw, j = k >> 1;
+    for (int t = threadIdx.x; t < ne * kw; t += TU_THREADS) {
+      const int r = t / kw, k = t % kw, j = k >> 1;
       float hi = 0.f, lo = 0.f;
-      if (col0 + c < a.ncol && j < a.nv) {
-        const c128 v = a.C[(long)(col0 + c) * a.ccs + j];
+      if (r < nact && j < a.nv) {
+        const c128 v = a.C[(long)(col0 + cmap[r]) * a.ccs + j];
         const double x = (k & 1) ? v.y : v.x;
         hi = __uint_as_float(tf32_rna((float)x));
         lo = __uint_as_float(tf32_rna((float)(x - (double)hi)));
       }
-      const unsigned off = swz_off(c, k, a.nt);
+      const unsigned off = swz_off(r, k, ne);
       *reinterpret_cast<float*>(Bhi + off) = hi;
       *reinterpret_cast<float*>(Blo + off) = lo;
     }
-    for (int c = threadIdx.x; c < a.nt; c += TU_THREADS)
-      act[c] = (col0 + c < a.ncol) && (!a.st || a.st[col0 + c].active);
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -390,9 +412,9 @@ __global__ void __launch_bounds__(TU_THREADS, 1) tc_proj_update_kernel(TuArgs a)
 
   if (warp == 1) {  // ---- MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = instr_desc(a.nt);
+      const uint32_t idesc = instr_desc(ne);
       const uint64_t dah = sm_desc(Ahi), dal = sm_desc(Alo), dbh = sm_desc(Bhi), dbl = sm_desc(Blo);
-      const uint32_t astep = TU_ATOM_A >> 4, bstep = (uint32_t)(a.nt * 128) >> 4;  // one K atom, in 16-byte units
+      const uint32_t astep = TU_ATOM_A >> 4, bstep = (uint32_t)(ne * 128) >> 4;  // one K atom, in 16-byte units
       for (long it = 0; it < my_tiles; ++it) {
         const int b = (int)(it & 1);
         if (!mbar_wait(&aready, (unsigned)(it & 1), abort)) break;
@@ -463,36 +485,40 @@ __global__ void __launch_bounds__(TU_THREADS, 1) tc_proj_update_kernel(TuArgs a)
     const int q4 = warp & 3, half = (warp - 8) >> 2;
     const int m = q4 * 32 + lane;  // real row of the tile = tensor-memory lane
     const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
-    const int nch = a.nt / 32;
+    const int nch = ne / 32;      // this warp takes chunks half and half + 2 (nch <= 4)
     for (long it = 0; it < my_tiles; ++it) {
       const int b = (int)(it & 1);
       const long r0 = (blockIdx.x + it * (long)gridDim.x) * TU_ROWS;
       const long g = 2 * r0 + m;  // float index within a column
       const bool rowok = g < 2 * a.n;
+      // R's current values for both chunks, requested before the accumulators are ready
+      float old[2][32];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int cc = half + 2 * u;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int k = cc * 32 + j;
+          old[u][j] = (a.rmode == 2 && cc < nch && rowok && k < nact)
+                          ? a.R[2 * (long)(col0 + cmap[k]) * a.ldr + g] : 0.f;
+        }
+      }
       int own = 0;
       const bool got = mbar_wait(&dfull[b], (unsigned)((it >> 1) & 1), &own);
       if (!got) *abort = 1;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       __syncwarp();
       if (__any_sync(0xffffffffu, !got || *abort)) break;  // warp-uniform: tcgen05.ld is .sync.aligned
-      for (int cc = half; cc < nch; cc += 2) {
-        float old[32];
-        if (a.rmode == 2) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int c = cc * 32 + j;
-            old[j] = (rowok && act[c]) ? a.R[2 * (long)(col0 + c) * a.ldr + g] : 0.f;
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) old[j] = 0.f;
-        }
+      for (int u = 0; u < 2; ++u) {
+        const int cc = half + 2 * u;
+        if (cc >= nch) break;
         float d[32];
         tmem_ld32(tm + lane_base + (uint32_t)(b * 128 + cc * 32), d);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          const int c = cc * 32 + j;
-          if (rowok && act[c]) a.R[2 * (long)(col0 + c) * a.ldr + g] = old[j] + d[j];
+          const int k = cc * 32 + j;
+          if (rowok && k < nact) a.R[2 * (long)(col0 + cmap[k]) * a.ldr + g] = old[u][j] + d[j];
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
