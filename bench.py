@@ -75,7 +75,12 @@ def parse():
                          "(profiling runs pin the form the plain run chose: serialised launches under ncu "
                          "would bias the tuner)")
     ap.add_argument("--matvec-only", action="store_true",
-                    help="with --kernels-only: the matvecs alone (no Arnoldi basis on the device)")
+                    help="with --kernels-only: the matvecs alone (same as --part matvec)")
+    ap.add_argument("--part", choices=["all", "arnoldi", "matvec", "projection"], default="all",
+                    help="with --kernels-only: only the Arnoldi steps, the matvecs, or the shared-basis projection "
+                         "(tensor-core dot and residual update)")
+    ap.add_argument("--shape", default=None, metavar="FORM,THREADS,COLINNER",
+                    help="with --kernels-only: the multi-column matvec's launch shape (default: the library's)")
     return ap.parse_args()
 
 
@@ -356,8 +361,10 @@ def main():
         import paper_0707_0502_gb300 as g
         stream = torch.cuda.Stream()
         ctx = g.gdr_create(0, stream)
+        part = "matvec" if args.matvec_only else args.part
+        shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else None
         out = kernels_at_scale(g, ctx, stream, only=args.kernels_only, link_store=args.links, tune=False,
-                               step=not args.matvec_only)
+                               parts=("arnoldi", "matvec", "projection") if part == "all" else (part,), shape=shape)
         print(json.dumps({"kernels_at_scale": out}), flush=True)
         g.gdr_destroy(ctx)
         return
@@ -741,15 +748,20 @@ def kernel_roofline(g, ctx, p, solve):
     return roof, table
 
 
-def kernels_at_scale(g, ctx, stream, only=None, link_store=None, tune=True, step=True):
+def kernels_at_scale(g, ctx, stream, only=None, link_store=None, tune=True, parts=("arnoldi", "matvec", "projection"),
+                     shape=None):
     """The HBM-bound kernels on the two large lattices of the workload family
     (Wilson 16^4, complex64 links; 24^3x32, bf16 links), each profiled alone: the
     last steps of an m-step complex64 Arnoldi cycle (steps m-3..m-1 and the
     finalising pass, m = 60 / 80, the form the solves run), the single-column
     matvec and the multi-column matvec of the Proj / refinement stages (8 / 12
     columns) in the launch shape the autotuner chose (its time and the default
-    shape's reported beside).  Inputs far larger than L2.  Per kernel:
-    microseconds per launch, GB/s and fraction of measured HBM peak."""
+    shape's reported beside), and the projection over a kept basis shared by the
+    120 columns of a refinement batch (k + 1 = 41 vectors: the dot c = V^H r and
+    the residual update r += V t, on the tensor cores).  Inputs far larger than
+    L2.  Per kernel: microseconds per launch, GB/s and fraction of measured HBM
+    peak."""
+    step = "arnoldi" in parts
     import torch
     hbm = peaks().get("hbm_gbs", 6800.0)
     out = {}
@@ -801,9 +813,27 @@ def kernels_at_scale(g, ctx, stream, only=None, link_store=None, tune=True, step
             res[f"arnoldi_steps_j{m - 3}_to_{m - 1}"] = profiled(
                 lambda: g.gdr_arnoldi_cycle(ctx, op, g.GDR_PREC_MIXED, V, m - 3, m, Hb), reps=3)
         X1, Y1 = X[:1], Y[:1]
-        res["matvec_1col"] = profiled(lambda: g.gdr_op_apply(ctx, op, g.GDR_PREC_MIXED, np.zeros(1), X1, Y1))
-        res[f"matvec_{ncol}col"] = profiled(
-            lambda: g.gdr_op_apply(ctx, op, g.GDR_PREC_MIXED, np.zeros(ncol), X, Y))
+        if "matvec" in parts:
+            if shape is not None:
+                g.gdr_op_set_shape(op, g.GDR_PREC_MIXED, ncol, *shape)
+            res["matvec_1col"] = profiled(lambda: g.gdr_op_apply(ctx, op, g.GDR_PREC_MIXED, np.zeros(1), X1, Y1))
+            res[f"matvec_{ncol}col"] = profiled(
+                lambda: g.gdr_op_apply(ctx, op, g.GDR_PREC_MIXED, np.zeros(ncol), X, Y))
+        if "projection" in parts:  # the refinement batch's shared-basis projection
+            nvp, ncp = 41, 120
+            with torch.cuda.stream(stream):
+                gen2 = torch.Generator(device="cuda").manual_seed(cid + 100)
+                Vp = torch.randn((nvp, n), dtype=torch.complex64, device="cuda", generator=gen2)
+                Rp = torch.randn((ncp, n), dtype=torch.complex64, device="cuda", generator=gen2)
+                Tp = 1e-3 * torch.randn((ncp, nvp), dtype=torch.complex128, device="cuda", generator=gen2)
+                Cp = torch.zeros((ncp, nvp), dtype=torch.complex128, device="cuda")
+            stream.synchronize()
+
+            def proj():
+                g.gdr_basis_dot(ctx, g.GDR_PREC_MIXED, n, nvp, Vp, ncp, Rp, n, Cp)
+                g.gdr_basis_residual_update(ctx, g.GDR_PREC_MIXED, n, nvp, Vp, ncp, Tp, Rp, n)
+            res[f"projection_{nvp}x{ncp}col"] = profiled(proj)
+            del Vp, Rp, Tp, Cp
         entry = {"n": n, "links": "bf16" if store == g.GDR_LINK_BF16 else "c64", "kernels": res,
                  "matvec_autotune": tuned}
         if tuned:  # the tuner's back-to-back timing of the chosen shape (no per-launch events)
