@@ -106,7 +106,7 @@ typedef struct {
   double extra_tol;   /* relative tolerance for the extra right-hand side v_{k+1} */
   double inner_tol;   /* MIXED: relative residual of the complex64 GMRES-DR / Proj stages before FP64
                          refinement; <= 0 chooses it: 1e-3 when the complex64 basis fits in half of
-                         the L2 cache (cycles limited by the FP64 dense steps), else 1e-5 with bf16
+                         the L2 cache (cycles limited by the FP64 dense steps), else 1e-4 with bf16
                          Wilson links, 1e-6 for a CSR batch, 3e-7 otherwise */
   double refine_tol;  /* MIXED: floor of the relative reduction asked of one complex64 refinement pass
                          (its target is max(0.3 tol ||b|| / ||r||, refine_tol)); <= 0 chooses

@@ -65,7 +65,10 @@ gdr_params resolve_inner_tol(const gdr_ctx* ctx, const gdr_op* A, long n, const 
   if (!(r.inner_tol > 0)) {
     const double basis = (double)(p.m + 1) * (double)n * sizeof(c64);
     if (basis <= 0.5 * (double)ctx->l2_bytes) r.inner_tol = 1e-3;
-    else if (A->kind == OP_WILSON && A->store == GDR_LINK_BF16) r.inner_tol = 1e-5;
+    // bf16 links: the links' rounding holds the stages' true residuals near 1e-3 whatever
+    // the inner tolerance; measured at 24^3x32: 1e-4 2.71 s, 1e-5 2.94 s, 3e-4 and 1e-3 a
+    // third refinement pass (2.78 / 2.86 s)
+    else if (A->kind == OP_WILSON && A->store == GDR_LINK_BF16) r.inner_tol = 1e-4;
     else if (A->kind == OP_CSR_BATCH) r.inner_tol = 1e-6;
     else r.inner_tol = 3e-7;
   }

@@ -133,17 +133,27 @@ DEV void hop(const LT* __restrict__ links, long V, long lsite, const Spinor<R>& 
 #pragma unroll
   for (int a = 0; a < 3; ++a) { g[0][a] = {0, 0}; g[1][a] = {0, 0}; }
   const LT* L = links + (long)MU * 9 * V + lsite;
+  // each complex multiply-add as four FMAs into the accumulator (a product followed by
+  // an add would take six floating-point operations: the FP64 residual matvec is bound
+  // by them, the complex64 one by instruction issue)
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      cx<R> u = LinkLd<R, LT>::ld(L, (long)(a * 3 + b) * V);
-      if (FWD) {  // g_a += U_ab h_b
-        g[0][a] += u * h[0][b];
-        g[1][a] += u * h[1][b];
-      } else {    // g_b += conj(U_ab) h_a
-        g[0][b] += cmulc(u, h[0][a]);
-        g[1][b] += cmulc(u, h[1][a]);
+      const cx<R> u = LinkLd<R, LT>::ld(L, (long)(a * 3 + b) * V);
+#pragma unroll
+      for (int sp = 0; sp < 2; ++sp) {
+        if (FWD) {  // g_a += U_ab h_b
+          cx<R>& t = g[sp][a];
+          const cx<R> hb = h[sp][b];
+          t.x = fma(-u.y, hb.y, fma(u.x, hb.x, t.x));
+          t.y = fma(u.y, hb.x, fma(u.x, hb.y, t.y));
+        } else {    // g_b += conj(U_ab) h_a
+          cx<R>& t = g[sp][b];
+          const cx<R> ha = h[sp][a];
+          t.x = fma(u.y, ha.y, fma(u.x, ha.x, t.x));
+          t.y = fma(-u.y, ha.x, fma(u.x, ha.y, t.y));
+        }
       }
     }
   }
