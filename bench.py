@@ -49,7 +49,8 @@ FP64_SOLVE_MVPS = {3: 2580, 4: 4360}
 # dram__bytes_write.sum over the algorithmic bytes of the same launch), valid for the
 # kernel source it was measured on (sha256 prefix of the file); reported as null once
 # that file changes.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"dcgs2_update_c64": {"ratio": 0.995, "sha16": "f3b874a769f6dc87",
+                                    "profile": "dcgs2_update_wilson16x16x16x16"}}
 
 
 def parse():
@@ -109,6 +110,16 @@ def peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         return {}
+
+
+# the profiling recipe's stated fallback when no measured peaks are on the box
+FALLBACK_HBM_GBS = 6800.0
+
+
+def hbm_peak():
+    """(HBM GB/s denominator, "measured" | "fallback")."""
+    v = peaks().get("hbm_gbs")
+    return (float(v), "measured") if v else (FALLBACK_HBM_GBS, "fallback")
 
 
 def workload(cid):
@@ -709,7 +720,7 @@ def kernel_roofline(g, ctx, p, solve):
     every kernel's launches, time and algorithmic bytes; the roofline of the one
     with the largest total time."""
     pk = peaks()
-    hbm = pk.get("hbm_gbs", 6800.0)
+    hbm, hbm_src = hbm_peak()
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
     g.gdr_profile(ctx, True)
     solve()
@@ -731,7 +742,7 @@ def kernel_roofline(g, ctx, p, solve):
         traffic, tnote = traffic_for(dom, bpl)
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic, "bytes_per_launch": bpl,
-                "note": "peak = MEASURED_PEAKS.json hbm_gbs (of measured); traffic: " + tnote}
+                "note": f"peak = HBM copy bandwidth (of {hbm_src}); traffic: " + tnote}
     else:
         ns = len(p.sigma)
         flops = dense_flops(dom, p.m, p.k, ns, 1)
@@ -759,11 +770,11 @@ def kernels_at_scale(g, ctx, stream, only=None, link_store=None, tune=True, part
     shape's reported beside), and the projection over a kept basis shared by the
     120 columns of a refinement batch (k + 1 = 41 vectors: the dot c = V^H r and
     the residual update r += V t, on the tensor cores).  Inputs far larger than
-    L2.  Per kernel: microseconds per launch, GB/s and fraction of measured HBM
+    L2.  Per kernel: microseconds per launch, GB/s and fraction of the HBM
     peak."""
     step = "arnoldi" in parts
     import torch
-    hbm = peaks().get("hbm_gbs", 6800.0)
+    hbm, hbm_src = hbm_peak()
     out = {}
     for cid, dims, eps, store, m, ncol in [(3, (16, 16, 16, 16), 0.4, g.GDR_LINK_C64, 60, 8),
                                            (4, (24, 24, 24, 32), 0.5, g.GDR_LINK_BF16, 80, 12)]:
@@ -805,7 +816,7 @@ def kernels_at_scale(g, ctx, stream, only=None, link_store=None, tune=True, part
                 us = v["ms"] / v["launches"] * 1e3
                 gbs = v["bytes"] / (v["ms"] / 1e3) / 1e9
                 tab[name] = {"launches": v["launches"], "us_per_launch": round(us, 1), "GBs": round(gbs, 1),
-                             "frac_of_measured_hbm": round(gbs / hbm, 3)}
+                             "frac_of_hbm": round(gbs / hbm, 3), "hbm_peak": hbm_src}
             return tab
 
         res = {}
@@ -844,7 +855,7 @@ def kernels_at_scale(g, ctx, stream, only=None, link_store=None, tune=True, part
                 gbs = byt / (t["mv_ms"] * 1e-3) / 1e9
                 entry["matvec_back_to_back"][c + "col"] = {"us_per_launch": round(t["mv_ms"] * 1e3, 1),
                                                            "GBs": round(gbs, 1),
-                                                           "frac_of_measured_hbm": round(gbs / hbm, 3)}
+                                                           "frac_of_hbm": round(gbs / hbm, 3)}
         out["x".join(map(str, dims))] = entry
         g.gdr_op_destroy(op)
         del X, Y, X1, Y1
