@@ -736,6 +736,7 @@ gdr_status gdr_arnoldi_cycle(gdr_ctx* ctx, const gdr_op* A, gdr_prec prec, void*
       b.h2 = ctx->get<c128>("cyc.h2", (size_t)(m + 2));
       b.hd = ctx->get<c128>("cyc.hd", (size_t)(2 * m + 8));
       b.dc = ctx->get<c128>("cyc.dc", (size_t)(2 * m + 8));
+      b.Hf = ctx->get<c64>("cyc.Hf", (size_t)(m + 1) * m);
       const long units = (n * (long)sizeof(cx<R>) + 15) / 16;
       b.nblk = (int)std::max<long>(1, std::min<long>((units + 255) / 256, 3L * ctx->num_sms));
       b.pstride = (long)(b.nblk + 64) * (2 * m + 8);

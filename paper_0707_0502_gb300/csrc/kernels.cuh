@@ -38,6 +38,7 @@ struct Batch {
   c128* h2 = nullptr;
   c128* hd = nullptr;    // DCGS2 dot values per column (2m + 8), see arnoldi_dcgs2
   c128* dc = nullptr;    // DCGS2 update coefficients per column (2m + 8)
+  c64* Hf = nullptr;     // DCGS2: FP32 copy of H (same layout), for the small H s correction
   c128* part = nullptr;  // block partials, per column pstride
   long pstride = 0;
   unsigned* cnt = nullptr;  // last-block counters, per column (4 slots)

@@ -612,22 +612,45 @@ __global__ void __launch_bounds__(NT, 2) dcgs2_dot_kernel(Batch<R> b, int j, con
   __syncthreads();
   if (brk_s) return;
   const double nuv = nu_s;
+  // H's FP32 copy (for the H s term below): rebuilt from H on the first step of a cycle
+  // (the restart may have rewritten the kept columns), then kept with the two columns
+  // each step changes
+  c64* Hf = b.Hf ? b.Hf + (long)c * (m + 1) * m : nullptr;
+  if (first && Hf)
+    for (int q = threadIdx.x; q < j * (m + 1); q += NT) Hf[q] = to64(H[q]);
   // the delayed pass completes column j-1
   if (!first)
-    for (int i = threadIdx.x; i < j; i += NT) H[(long)(j - 1) * (m + 1) + i] += ssh[i];
+    for (int i = threadIdx.x; i <= j; i += NT) {
+      c128& hij = H[(long)(j - 1) * (m + 1) + i];
+      if (i < j) hij += ssh[i];
+      if (Hf) Hf[(long)(j - 1) * (m + 1) + i] = to64(hij);
+    }
   for (int i = threadIdx.x; i < j; i += NT) dc[i] = ssh[i];
   if (mode == DC_FINAL) return;
+  __shared__ c64 s32[GDR_MAX_M + 1];
+  for (int i = threadIdx.x; i < j; i += NT) s32[i] = to64(ssh[i]);
   __syncthreads();
   const c128 t = ssh[GDR_MAX_M + 1];
   const c128 tn = (1.0 / nuv) * t;
   for (int i = threadIdx.x; i < j; i += NT) dc[(m + 1) + i] = hv[2 * i + 1] - tn * ssh[i];
-  // column j: ([z ; t] - Hbar[0:j+1, 0:j] s) / nu; s is O(rounding), so H s in FP32
+  // column j: ([z ; t] - Hbar[0:j+1, 0:j] s) / nu; s is O(rounding), so H s in FP32 (from the
+  // FP32 copy: no conversions on the FP64 pipe, loads issued eight ahead)
+  if (Hf)  // the copy's rows below the subdiagonal are zero, as H's are
+    for (int i = j + 1 + threadIdx.x; i <= m; i += NT) Hf[(long)j * (m + 1) + i] = {0.f, 0.f};
   for (int i = threadIdx.x; i <= j; i += NT) {
     c64 hsum = {0.f, 0.f};
-    if (!first)
-      for (int l = 0; l < j; ++l) hsum += to64(H[(long)l * (m + 1) + i]) * to64(ssh[l]);
+    if (!first) {
+      if (Hf) {
+#pragma unroll 8
+        for (int l = 0; l < j; ++l) hsum += Hf[(long)l * (m + 1) + i] * s32[l];
+      } else {
+        for (int l = 0; l < j; ++l) hsum += to64(H[(long)l * (m + 1) + i]) * s32[l];
+      }
+    }
     const c128 zi = (i < j) ? hv[2 * i + 1] : t;
-    H[(long)j * (m + 1) + i] = (1.0 / nuv) * (zi - to128(hsum));
+    const c128 hnew = (1.0 / nuv) * (zi - to128(hsum));
+    H[(long)j * (m + 1) + i] = hnew;
+    if (Hf) Hf[(long)j * (m + 1) + i] = to64(hnew);
   }
 }
 

@@ -286,6 +286,7 @@ Batch<R> make_batch(gdr_ctx* ctx, const std::string& tag, long n, int ncol, int 
   b.h2 = ctx->get<c128>(tag + ".h2", (size_t)(m + 2) * ncol);
   b.hd = ctx->get<c128>(tag + ".hd", (size_t)(2 * m + 8) * ncol);
   b.dc = ctx->get<c128>(tag + ".dc", (size_t)(2 * m + 8) * ncol);
+  b.Hf = ctx->get<c64>(tag + ".Hf", (size_t)(m + 1) * m * ncol);
   b.nblk = nblk_for<R>(ctx, n);
   // block partials, then slot-group partials (DCGS2 dot pass: 2m + 8 values per slot)
   b.pstride = (long)(b.nblk + 64) * std::max(2 * m + 8, hmin);
