@@ -49,7 +49,7 @@ FP64_SOLVE_MVPS = {3: 2580, 4: 4360}
 # dram__bytes_write.sum over the algorithmic bytes of the same launch), valid for the
 # kernel source it was measured on (sha256 prefix of the file); reported as null once
 # that file changes.
-NCU_TRAFFIC = {"dcgs2_update_c64": {"ratio": 0.995, "sha16": "f3b874a769f6dc87",
+NCU_TRAFFIC = {"dcgs2_update_c64": {"ratio": 0.996, "sha16": "915cf905142f8a03",
                                     "profile": "dcgs2_update_wilson16x16x16x16"}}
 
 
