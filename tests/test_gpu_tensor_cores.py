@@ -189,3 +189,41 @@ def test_residual_update_cuda_cores(ctx, n, nv, ncol, flags):
     out, R0, exact, Sre, Sim, prof = run_update(ctx, n, nv, ncol, n, seed=11 * n + nv, flags=flags)
     assert not tcu_ran(prof), prof
     check_update(out, R0, exact, Sre, Sim, n)
+
+
+# ------------------------------------------------------------------ whole solves
+
+def test_solve_with_and_without_tensor_cores(ctx):
+    """A mixed solve whose refinement batch (3 right-hand sides x 4 shifts = 12 pair
+    columns over the kept basis) takes the tensor-core projection, against the same
+    solve with GDR_FLAG_NO_TENSOR_CORES: both reach the FP64 true residual 1e-8 with the
+    oracle's operator, their solutions agree to 1e-6, and the tensor-core kernels ran in
+    the first only."""
+    import workloads as W
+    from oracle import WilsonOperator
+    p = W.wilson_problem(2, dims=(8, 8, 8, 8), eps=0.3, nshift=4, nrhs=3, m=24, k=10, m_proj=14,
+                         kappa_c=0.1325)
+    dims, diag_a, links = p.op[1], p.op[2], p.op[3]
+    op_o = WilsonOperator(dims, links, diag_a=diag_a)
+    op = g.gdr_op_wilson(ctx, dims, dev(links), diag_a, g.GDR_LINK_C64)
+    out = {}
+    for flags in (0, g.GDR_FLAG_NO_TENSOR_CORES):
+        prm = g.gdr_params_default(m=p.m, k=p.k, m_proj=p.m_proj, tol=1e-8, prec=g.GDR_PREC_MIXED, flags=flags)
+        X = torch.zeros((p.B.shape[1], len(p.sigma), p.n), dtype=torch.complex128, device="cuda")
+        g.gdr_profile(ctx, True)
+        st, rep, _ = g.gdr_solve_multishift(ctx, op, p.sigma, dev(np.ascontiguousarray(p.B.T)), X, prm)
+        prof = g.gdr_profile_report(ctx)
+        g.gdr_profile(ctx, False)
+        assert st == g.GDR_OK, rep
+        ran = tc_ran(prof) or tcu_ran(prof)
+        assert ran == (flags == 0), (flags, sorted(prof))
+        Xh = X.cpu().numpy()
+        for j in range(p.B.shape[1]):
+            b = p.B[:, j]
+            for i, s in enumerate(p.sigma):
+                x = Xh[j, i]
+                assert np.linalg.norm(b - (op_o.matvec(x) - s * x)) <= 1.05e-8 * np.linalg.norm(b), (flags, j, i)
+        out[flags] = Xh
+    a, b = out[0], out[g.GDR_FLAG_NO_TENSOR_CORES]
+    assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(b)
+    g.gdr_op_destroy(op)
