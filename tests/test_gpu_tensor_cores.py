@@ -76,6 +76,7 @@ def tc_ran(prof):
     (4000, 97, 120, 4000),     # the largest basis (m + 1 = 97 of the MMA's 128 rows)
     (1000, 1, 200, 1000),      # one basis vector, two tiles of 100
     (262144, 21, 120, 262144), # a long vector split over many CTAs
+    (2000, 64, 300, 2002),     # three column tiles (112 wide), padded stride
 ])
 def test_tensor_core_dot(ctx, n, nv, ncol, ldr):
     C, exact, S, prof = run_dot(ctx, n, nv, ncol, ldr, seed=n + nv + ncol)
@@ -168,6 +169,7 @@ def tcu_ran(prof):
     (4096, 48, 130, 4096),      # largest basis of this form, two column tiles of 96
     (1000, 1, 40, 1000),        # one basis vector
     (262144, 31, 96, 262144),   # a long vector: many row tiles per CTA
+    (2000, 41, 300, 2002),      # three column tiles (128 wide), padded stride
 ])
 def test_tensor_core_residual_update(ctx, n, nv, ncol, ldr):
     out, R0, exact, Sre, Sim, prof = run_update(ctx, n, nv, ncol, ldr, seed=n + 3 * nv + ncol)
@@ -189,6 +191,19 @@ def test_residual_update_cuda_cores(ctx, n, nv, ncol, flags):
     out, R0, exact, Sre, Sim, prof = run_update(ctx, n, nv, ncol, n, seed=11 * n + nv, flags=flags)
     assert not tcu_ran(prof), prof
     check_update(out, R0, exact, Sre, Sim, n)
+
+
+def test_fp64_residual_update(ctx):
+    rng = np.random.default_rng(5)
+    n, nv, ncol = 3000, 30, 20
+    V = rng.standard_normal((nv, n)) + 1j * rng.standard_normal((nv, n))
+    T = rng.standard_normal((ncol, nv)) + 1j * rng.standard_normal((ncol, nv))
+    R0 = rng.standard_normal((ncol, n)) + 1j * rng.standard_normal((ncol, n))
+    Rd = dev(R0)
+    g.gdr_basis_residual_update(ctx, g.GDR_PREC_FP64, n, nv, dev(V), ncol, dev(T), Rd, n)
+    exact = R0 + T @ V
+    S = np.abs(T) @ np.abs(V) + np.abs(R0)
+    assert np.all(np.abs(Rd.cpu().numpy() - exact) <= 1e-13 * S)
 
 
 # ------------------------------------------------------------------ whole solves
