@@ -830,6 +830,15 @@ def kernels_at_scale(g, ctx, stream, only=None, link_store=None, tune=True, part
             res["matvec_1col"] = profiled(lambda: g.gdr_op_apply(ctx, op, g.GDR_PREC_MIXED, np.zeros(1), X1, Y1))
             res[f"matvec_{ncol}col"] = profiled(
                 lambda: g.gdr_op_apply(ctx, op, g.GDR_PREC_MIXED, np.zeros(ncol), X, Y))
+            # the FP64 true-residual matvec: one right-hand side's shifts as complex128 columns
+            nf = min(10, ncol)
+            with torch.cuda.stream(stream):
+                X64 = X[:nf].to(torch.complex128)
+                Y64 = torch.empty_like(X64)
+            stream.synchronize()
+            res[f"matvec_fp64_{nf}col"] = profiled(
+                lambda: g.gdr_op_apply(ctx, op, g.GDR_PREC_FP64, np.zeros(nf), X64, Y64), reps=3)
+            del X64, Y64
         if "projection" in parts:  # the refinement batch's shared-basis projection
             nvp, ncp = 41, 120
             with torch.cuda.stream(stream):
