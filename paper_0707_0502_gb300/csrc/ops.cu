@@ -158,15 +158,35 @@ __global__ void __launch_bounds__(NT, wilson_min_blocks<R>(NT)) wilson_kernel(co
   cx<R>* y = Y + c * ldy;
   const R sc = xs ? (R)xs[(long)c * xs_stride] : R(1);
   const cx<R>* b = B ? B + (c / cpp) * ldb : nullptr;
+  // (a - sigma) x - H x or b + H x - (a - sigma) x as FMA chains (two FMAs and at most one
+  // add per real component; the unscaled forms skip the multiplication by s_c = 1)
+  auto out = [&](cx<R> xv, cx<R> av, cx<R> bv, bool hasb) -> cx<R> {
+    if (hasb) {
+      const R ur = bv.x + av.x, ui = bv.y + av.y;
+      return {fma(dg.y, xv.y, fma(-dg.x, xv.x, ur)), fma(-dg.y, xv.x, fma(-dg.x, xv.y, ui))};
+    }
+    return {fma(-dg.y, xv.y, fma(dg.x, xv.x, -av.x)), fma(dg.y, xv.x, fma(dg.x, xv.y, -av.y))};
+  };
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    cx<R> v0 = sc * (dg * p.s[2 * i] - acc.s[2 * i]);
-    cx<R> v1 = sc * (dg * p.s[2 * i + 1] - acc.s[2 * i + 1]);
-    if (b) {
+    cx<R> v0, v1;
+    if (xs) {
+      v0 = sc * (dg * p.s[2 * i] - acc.s[2 * i]);
+      v1 = sc * (dg * p.s[2 * i + 1] - acc.s[2 * i + 1]);
+      if (b) {
+        cx<R> b0, b1;
+        load_pair<R>(b, V, site, i, b0, b1);
+        v0 = b0 - v0;
+        v1 = b1 - v1;
+      }
+    } else if (b) {
       cx<R> b0, b1;
       load_pair<R>(b, V, site, i, b0, b1);
-      v0 = b0 - v0;
-      v1 = b1 - v1;
+      v0 = out(p.s[2 * i], acc.s[2 * i], b0, true);
+      v1 = out(p.s[2 * i + 1], acc.s[2 * i + 1], b1, true);
+    } else {
+      v0 = out(p.s[2 * i], acc.s[2 * i], {0, 0}, false);
+      v1 = out(p.s[2 * i + 1], acc.s[2 * i + 1], {0, 0}, false);
     }
     store_pair<R>(y, V, site, i, v0, v1);
   }
