@@ -110,7 +110,8 @@ typedef struct {
                          Wilson links, 1e-6 for a CSR batch, 3e-7 otherwise */
   double refine_tol;  /* MIXED: floor of the relative reduction asked of one complex64 refinement pass
                          (its target is max(0.3 tol ||b|| / ||r||, refine_tol)); <= 0 chooses
-                         min(inner_tol, 1e-4) */
+                         2e-4 with bf16 Wilson links when the basis does not fit in half of L2,
+                         else min(inner_tol, 1e-4) */
   long max_mvps;      /* cap on Arnoldi matvecs per solve stage (per column) */
   int max_cycles;     /* 0: unlimited; else stop RHS 1 after this many cycles */
   int refine_max;     /* MIXED: refinement passes before the FP64 cleanup */
@@ -119,7 +120,7 @@ typedef struct {
   int k_select;       /* GDR_FLAG_EIG_SELECT: approximate eigenvectors projected over (1..k; <= 0: k) */
   int m_refine;       /* cycle length of the refinement / cleanup solves (not in the paper); <= 0:
                          min(m, m_p + (m - m_p) / 2) for vectors of at most 2^17 elements, else
-                         min(m_p, 8) */
+                         min(m_p, 6) with bf16 Wilson links, min(m_p, 8) otherwise */
   double refine_rank_tol; /* MIXED, shift-shared refinement (not in the paper; off when <= 0, the
                          default): a complex64 refinement pass may refine the residuals of one
                          right-hand side's shifts over a few orthonormal directions of their span

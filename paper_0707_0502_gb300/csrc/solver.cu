@@ -840,9 +840,11 @@ gdr_status solve_pipeline(gdr_ctx* ctx, const gdr_op* A, const std::vector<c128>
   // 611 -> 592 ms); on long vectors the Gram-Schmidt bytes of a step grow with its index
   // while the deflated projection keeps restarts cheap, so short cycles (measured on
   // GB300: 24^3x32 refinement 7.0 s at 40, 4.4 s at 20, 3.9 s at 12, 2.2 s at 8 and 6
-  // with the current kernels; 16^4 189 ms at 30, 133 ms at 12, 88 ms at 8)
+  // with the current kernels; 16^4 189 ms at 30, 133 ms at 12, 88 ms at 8; with bf16 links,
+  // whose passes ask less of the inner solve, 6: 24^3x32 2.53 s against 2.58 s at 8)
   const int mr = p.m_refine > 0 ? p.m_refine
-                                : (A->n <= (1L << 17) ? std::min(m, mp + (m - mp) / 2) : std::min(mp, 8));
+                                : (A->n <= (1L << 17) ? std::min(m, mp + (m - mp) / 2)
+                                                      : std::min(mp, (A->kind == OP_WILSON && A->store == GDR_LINK_BF16) ? 6 : 8));
   const long ld = pad_ld(n);
   gdr_status status = GDR_OK;
   auto worst = [&](gdr_status s) {
@@ -1447,9 +1449,11 @@ gdr_status solve_batch_pipeline(gdr_ctx* ctx, const gdr_op* A, int ns, const std
   // 611 -> 592 ms); on long vectors the Gram-Schmidt bytes of a step grow with its index
   // while the deflated projection keeps restarts cheap, so short cycles (measured on
   // GB300: 24^3x32 refinement 7.0 s at 40, 4.4 s at 20, 3.9 s at 12, 2.2 s at 8 and 6
-  // with the current kernels; 16^4 189 ms at 30, 133 ms at 12, 88 ms at 8)
+  // with the current kernels; 16^4 189 ms at 30, 133 ms at 12, 88 ms at 8; with bf16 links,
+  // whose passes ask less of the inner solve, 6: 24^3x32 2.53 s against 2.58 s at 8)
   const int mr = p.m_refine > 0 ? p.m_refine
-                                : (A->n <= (1L << 17) ? std::min(m, mp + (m - mp) / 2) : std::min(mp, 8));
+                                : (A->n <= (1L << 17) ? std::min(m, mp + (m - mp) / 2)
+                                                      : std::min(mp, (A->kind == OP_WILSON && A->store == GDR_LINK_BF16) ? 6 : 8));
   const int npair = np * ns;
   GDR_CUDA(cudaMemsetAsync(X, 0, sizeof(c128) * ld * npair, ctx->stream));
   // per-pair lengths (pair q = problem q / ns, shift q % ns)
