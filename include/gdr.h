@@ -217,7 +217,11 @@ typedef struct {
                      CSR: threads per row, 1, 2, 4 or 8 */
   int threads;    /* threads per block: 64, 128 or 256 (direction-split: 128; pairs: 64 or 128) */
   int col_inner;  /* 1: consecutive blocks take one site/row tile for consecutive columns
-                     (links / rows read from HBM once for all columns); 0: column-major grid */
+                     (links / rows read from HBM once for all columns); g >= 2 (at most
+                     65535): that order within groups of g columns (column pairs in form 2),
+                     the groups one after another (links read once per group, the group's
+                     vectors still in L2 when a neighbour plane reuses them); 0: column-major
+                     grid.  GDR_EINVAL for a negative value */
 } gdr_shape;
 
 typedef struct {

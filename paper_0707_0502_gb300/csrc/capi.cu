@@ -360,7 +360,8 @@ gdr_status gdr_op_set_shape(gdr_op* A, gdr_prec prec, int ncol, const gdr_shape*
     return GDR_OK;
   }
   if (ncol < 1) return GDR_EINVAL;
-  MvShape s{shape->form, shape->threads, shape->col_inner ? 1 : 0};
+  if (shape->col_inner < 0 || shape->col_inner > 65535) return GDR_EINVAL;
+  MvShape s{shape->form, shape->threads, shape->col_inner};
   if (A->kind == OP_WILSON) {
     if (s.form == 1 && s.threads != 128) return GDR_EINVAL;
     if (s.form < 0 || s.form > 2) return GDR_EINVAL;

@@ -180,7 +180,8 @@ enum OpKind { OP_CSR = 0, OP_WILSON = 1, OP_CSR_BATCH = 2 };
 struct MvShape {
   int form = 0;       // Wilson: 0 one thread per site, 1 direction-split; CSR: threads per row (1, 2, 4, 8)
   int threads = 128;  // threads per block
-  int col_inner = 0;  // 1: consecutive blocks take one site / row tile for consecutive columns
+  int col_inner = 0;  // 1: consecutive blocks take one site / row tile for consecutive columns;
+                      // g >= 2: the same within groups of g columns (pairs for the pair form)
 };
 
 struct gdr_op {

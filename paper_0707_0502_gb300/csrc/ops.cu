@@ -26,11 +26,19 @@ namespace {
 
 // Block -> (tile, column).  col_inner: consecutive blocks take one tile for
 // consecutive columns, so the tile's links or matrix rows are fetched from HBM
-// once and served from L2 to the other columns' blocks running beside it.
+// once and served from L2 to the other columns' blocks running beside it.  With
+// col_inner = g >= 2 that order holds within groups of g columns and the groups
+// follow one another (the last may be narrower): the links are fetched once per
+// group, and a neighbour read a few planes of sites later still finds the
+// group's vectors in L2, which all columns at once would have pushed out.
 DEV void tile_col(int ncol, int col_inner, long& tile, int& c) {
   if (col_inner) {
-    tile = blockIdx.x / ncol;
-    c = (int)(blockIdx.x % ncol);
+    const unsigned G = (col_inner == 1 || col_inner > ncol) ? (unsigned)ncol : (unsigned)col_inner;
+    const unsigned span = gridDim.x / (unsigned)ncol * G;  // blocks of one full group
+    const unsigned grp = blockIdx.x / span, r = blockIdx.x - grp * span;
+    const unsigned gw = min(G, (unsigned)ncol - grp * G);  // this group's width
+    tile = r / gw;
+    c = (int)(grp * G + r % gw);
   } else {
     tile = blockIdx.x;
     c = blockIdx.y;

@@ -71,8 +71,16 @@ std::vector<MvShape> candidates(const gdr_op* A, int ncol, bool f64) {
     if (A->kind == OP_WILSON) {
       for (int t : {64, 128, 256}) out.push_back(MvShape{0, t, ci});
       out.push_back(MvShape{1, 128, ci});
-      if (!f64 && ncol > 1)  // column pairs with packed FP32x2 arithmetic
+      if (!f64 && ncol > 1) {  // column pairs with packed FP32x2 arithmetic
         for (int t : {64, 128}) out.push_back(MvShape{2, t, ci});
+        // many columns: pairs in groups (the order of all pairs at once keeps too
+        // many vectors between a site and its t-neighbour for L2)
+        const int npair = (ncol + 1) / 2;
+        if (ci == 1)
+          for (int grp : {2, 4})
+            if (npair > grp)
+              for (int t : {64, 128}) out.push_back(MvShape{2, t, grp});
+      }
     } else {
       for (int tpr : {1, 2, 4, 8})
         for (int t : {128, 256}) out.push_back(MvShape{tpr, t, ci});

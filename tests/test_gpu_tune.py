@@ -39,9 +39,11 @@ def rel(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
 
 
-WILSON_SHAPES = [(0, t, ci) for t in (64, 128, 256) for ci in (0, 1)] + [(1, 128, 0), (1, 128, 1)]
-PAIR_SHAPES = [(2, t, ci) for t in (64, 128) for ci in (0, 1)]
-CSR_SHAPES = [(tpr, t, ci) for tpr in (1, 2, 4, 8) for t in (128, 256) for ci in (0, 1)]
+# col_inner 2 / 3: column groups (ragged last group for 5 columns or 3 pairs)
+WILSON_SHAPES = [(0, t, ci) for t in (64, 128, 256) for ci in (0, 1)] + [(1, 128, 0), (1, 128, 1),
+                                                                         (0, 128, 2), (0, 64, 3), (1, 128, 2)]
+PAIR_SHAPES = [(2, t, ci) for t in (64, 128) for ci in (0, 1, 2)]
+CSR_SHAPES = [(tpr, t, ci) for tpr in (1, 2, 4, 8) for t in (128, 256) for ci in (0, 1)] + [(2, 128, 2)]
 
 
 # 3x4x2x6: 144 sites, ragged last tile for every block size; 8x8x4x4 several tiles
@@ -186,6 +188,8 @@ def test_set_shape_rejects_bad_shapes(ctx):
     g.gdr_op_set_shape(op, g.GDR_PREC_FP64, 0)                            # forget all
     assert g.gdr_op_get_shape(op, g.GDR_PREC_FP64, 1)["col_inner"] == 0   # defaults: one column
     assert g.gdr_op_get_shape(op, g.GDR_PREC_FP64, 4)["col_inner"] == 1   # several: column-inner order
+    with pytest.raises(g.GdrError):
+        g.gdr_op_set_shape(op, g.GDR_PREC_FP64, 4, 0, 128, -1)             # no negative column order
     with pytest.raises(g.GdrError):
         g.gdr_autotune(ctx, op, g.GDR_PREC_FP64, 0)
     g.gdr_op_destroy(op)
